@@ -1,0 +1,34 @@
+"""Oracle for the outer-region R-matrix hot path (R -> K -> Omega).
+
+TEST INFRASTRUCTURE ONLY. This package is a plain, slow CPU restatement of
+what the GPU path computes, written from the paper (Section "Overview",
+Eqs. radial, match, wnk, rmatrix; Section "Glossary of terms" for T and
+Omega; Section "namelist stgf MQDT variables" for closed-channel
+elimination). Only tests/, __graft_entry__.smoke() and bench.py's CPU
+baseline leg may import it. It shares no code with the CUDA library and does
+not import the product package.
+
+Floating point is IEEE double throughout, except the special functions of
+oracle/coulomb_ref.c, which are evaluated in binary128 and rounded to double.
+Linear algebra uses numpy/LAPACK (LU with partial pivoting) as a library
+primitive.
+
+Parity status per function (what pins it, in tests/test_oracle_pins.py):
+  coulomb functions     mpmath coulombf/coulombg, Wronskian, eta = 0 closed forms
+  closed log-derivative mpmath whitw, hydrogenic integer-nu closed forms
+  regular_analytic      Gamow-factor relation to F at positive energy
+  r_matrix              brute-force mpmath sum, exact symmetry, single-pole limit
+  k_direct              one-channel hand formula, square well vs closed-form
+                        tan(delta), 1 open + 1 closed closed form, symmetry,
+                        unitarity of S
+  k_mqdt                identity with k_direct (exact elimination identity)
+  t_matrix / omega      optical theorem, symmetric Omega, real-form |T|^2
+  cross-threshold K, Omega beyond these checks: parity unpinned (the paper
+                        prints no K or Omega values for any system).
+"""
+from .rmatrix import (  # noqa: F401
+    RM_OK, RM_ETHRESHOLD, RM_ENEAR_POLE, RM_ESINGULAR, RM_ECF_NOCONV,
+    MODE_DIRECT, MODE_MQDT,
+    channel_functions, r_matrix, match_direct, mqdt_set, match_mqdt,
+    t_matrix, omega_add, solve_energy, solve_energies, tri_index,
+)
