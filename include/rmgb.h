@@ -1,0 +1,193 @@
+/*
+ * rmgb — GB300-native outer-region R-matrix hot path: R -> K -> Omega.
+ *
+ * For every (partial wave, incident energy) pair the library
+ *   (a) forms the channel R-matrix (Section "Overview", Eq. rmatrix)
+ *         R_ij(E) = (1/2a) sum_k w_ik w_jk / (E_k - E),
+ *   (b) evaluates the asymptotic channel functions at r = a: energy-normalised
+ *       Coulomb functions s = F/sqrt(k), c = G/sqrt(k) for open channels and
+ *       the decaying Whittaker function for closed channels (Section
+ *       "Overview", Eq. radial with U = 0; Section "Glossary of terms", open
+ *       and closed channels),
+ *   (c) solves the matching condition (Eq. match)
+ *         psi(a) = R (a psi'(a) - b psi(a))
+ *       for the open-channel K-matrix, eliminating closed channels by their
+ *       decaying boundary condition or, in MQDT mode, through the unphysical
+ *       K-matrix (Section "namelist stgf MQDT variables", iqdt),
+ *   (d) forms T = 2iK(1 - iK)^{-1} and accumulates g |T|^2 into collision
+ *       strengths Omega_IJ(E) (Section "Glossary of terms").
+ *
+ * Units: energies in Rydberg, radii in Bohr. Channels keep their input order;
+ * K rows and columns are the open channels in ascending channel index.
+ *
+ * Conventions for every call:
+ *  - Return value 0 on success, a negative RM_E* code on error; no call aborts,
+ *    traps or exits. rm_last_error(ctx) gives a one-line reason.
+ *  - Host pointers are read during the call and not retained. Pointers marked
+ *    "device" must be device memory of the context's GPU (e.g. torch tensors).
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - Work is enqueued on the context's stream; only rm_collision_strengths,
+ *    rm_sync and the calls documented as synchronous wait for it.
+ */
+#ifndef RMGB_H
+#define RMGB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+/* Call return codes (negative). */
+#define RM_SUCCESS        0
+#define RM_EINVAL        -1   /* bad argument (size, pointer, non-finite value) */
+#define RM_ENOMEM        -2   /* device or host allocation failed; no partial state */
+#define RM_ECUDA         -3   /* a CUDA runtime call failed */
+#define RM_EGRID         -4   /* energy grid differs from the one Omega accumulates on */
+#define RM_ENOTLOADED    -5   /* partial wave has no poles or no channels */
+#define RM_EUNSUPPORTED  -6   /* option not supported for this size or mode */
+#define RM_ETIMEOUT      -7   /* a bounded device wait gave up */
+
+/* Per-energy status codes (written to status_out, non-negative). An energy
+ * whose status is not RM_OK contributes nothing to Omega. */
+#define RM_OK             0
+#define RM_ETHRESHOLD     1   /* |E - e_i| < eps_thr for some channel i */
+#define RM_ENEAR_POLE     2   /* |E - E_k| < 1e-12 max(1,|E|) for some pole k */
+#define RM_ESINGULAR      3   /* matching system (or MQDT elimination) singular */
+#define RM_ECF_NOCONV     4   /* a Coulomb continued fraction did not converge */
+
+/* Precision of the R-matrix formation (step (a)). Channel functions, the
+ * matching solve, T and Omega are always FP64. */
+#define RM_FP64           0   /* FP64 formation */
+#define RM_FP32           1   /* FP32 products and accumulation, near-pole terms in FP64 */
+#define RM_BF16X3         2   /* tensor cores: bf16 hi/lo split, 3 products, FP32
+                                 accumulate; near-pole terms in FP64 */
+
+/* Matching modes. */
+#define RM_DIRECT         0   /* closed channels by their decaying boundary condition */
+#define RM_MQDT           1   /* closed channels through the unphysical K-matrix */
+
+typedef struct rm_ctx rm_ctx;
+
+typedef struct rm_opts {
+    int precision;          /* RM_FP64 (default), RM_FP32, RM_BF16X3 */
+    double delta_pole;      /* mixed precision: poles with |E_k - E| < delta_pole
+                               are summed in FP64 (default 1e-3 Ry) */
+    double eps_thr;         /* |E - e_i| below this is RM_ETHRESHOLD (default 1e-10 Ry) */
+    double fnumin;          /* MQDT: closed channels with nu < fnumin are not
+                               quantum-defect eliminated (default 0) */
+    double nu_margin;       /* MQDT: ... nor those with nu < l + nu_margin (default 0.1) */
+    int device;             /* CUDA device ordinal (default 0) */
+    void *stream;           /* cudaStream_t to enqueue on (cudaStreamLegacy for
+                               the legacy default stream); NULL = a non-blocking
+                               stream the context creates and owns */
+    size_t mem_budget;      /* bytes of per-call device workspace (0 = 1 GiB) */
+} rm_opts;
+
+/* Fills *opts with the defaults above. */
+void rm_default_opts(rm_opts *opts);
+
+/* Creates a context on opts->device (opts may be NULL for defaults).
+ * Errors: RM_EINVAL (out NULL, bad option), RM_ECUDA. */
+int rm_create(rm_ctx **out, const rm_opts *opts);
+
+/* Frees every device buffer the context owns. NULL is a no-op. */
+void rm_destroy(rm_ctx *ctx);
+
+/* Loads the inner-region data of partial wave `pw` (0 <= pw < 4096):
+ * n_poles pole energies E_k (host, [n_poles]) and surface amplitudes w_ik
+ * (Eq. wnk) as W (host, row-major [n_ch][n_poles], W[i*n_poles + k] = w_ik),
+ * boundary radius a > 0 and log-derivative b (Eq. match, usually 0).
+ * The data are copied to the device (the caller keeps its buffers); poles are
+ * stored sorted, which does not change R. Replacing a loaded pw frees its old
+ * buffers. Synchronous. Errors: RM_EINVAL (n <= 0, a <= 0, non-finite input),
+ * RM_ENOMEM, RM_ECUDA. */
+int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const double *E_k,
+                  const double *W, double a, double b);
+
+/* Sets the channels of partial wave `pw`: thresholds e_thr (host, [n_ch], Ry),
+ * orbital angular momenta l (host, [n_ch], 0 <= l <= 64), ion charge z >= 0,
+ * target level of each channel level (host, [n_ch], 0 <= level < n_levels;
+ * channels of one level must share its threshold), and the statistical weight
+ * g of the partial wave (e.g. (2J+1)/2). n_ch must equal the loaded n_ch.
+ * Closed channels with z = 0 are supported; open channels need z >= 0.
+ * Synchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
+int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, double z,
+                    const int *level, int n_levels, double g_weight);
+
+/* Solves n_E energies E (host or device, [n_E], Ry) of partial wave `pw` in
+ * `mode` (RM_DIRECT or RM_MQDT) and adds g |T|^2 into the context's Omega
+ * accumulator. The first call after creation or a reset registers the grid;
+ * later calls must pass the same n_E, the same energies and the same n_levels
+ * (RM_EGRID otherwise). Optional outputs (NULL to skip), all device:
+ *   K_out      [n_E][n_ch*n_ch]: K_ab at K_out[e*n_ch*n_ch + a*n_ch + b],
+ *              a, b < n_open[e] (open channels in ascending order)
+ *   n_open_out [n_E]
+ *   status_out [n_E] per-energy RM_OK / RM_E* (non-negative) codes
+ * Asynchronous on the context stream. Errors: RM_EINVAL, RM_ENOTLOADED,
+ * RM_EGRID, RM_EUNSUPPORTED, RM_ENOMEM, RM_ECUDA. */
+int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
+                      double *K_out, int *n_open_out, int *status_out);
+
+/* Copies the accumulated collision strengths to omega_out (host,
+ * [n_E][n_levels*(n_levels+1)/2], upper triangle row-wise: (I, J), I <= J,
+ * at I*n_levels - I*(I-1)/2 + (J - I)); entries of levels closed at E are 0.
+ * Synchronises the stream. reset != 0 zeroes the accumulator and forgets the
+ * grid. omega_out may be NULL (reset only). Errors: RM_EINVAL (no grid yet),
+ * RM_ECUDA. */
+int rm_collision_strengths(rm_ctx *ctx, double *omega_out, int reset);
+
+/* Zeroes the Omega accumulator, keeping the registered grid. Asynchronous.
+ * Errors: RM_EINVAL (no grid yet), RM_ECUDA. */
+int rm_reset_omega(rm_ctx *ctx);
+
+/* Number of energies and of Omega entries per energy of the registered grid
+ * (both 0 before the first solve). */
+int rm_grid_shape(rm_ctx *ctx, int *n_E, int *n_tri);
+
+/* Inspection of step (b), for tests: channel functions of `pw` at n_E
+ * energies E (device). Writes out (device, [n_E][n_ch][4] doubles): open
+ * channel {s, s', c, c'}; closed channel {theta, theta', 0, 0} scaled so that
+ * theta^2 + (a theta')^2 = 1; and status (device, [n_E], may be NULL).
+ * Asynchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ECUDA. */
+int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *E, double *out,
+                         int *status);
+
+/* Inspection of step (a), for tests: R-matrices of `pw` at n_E energies E
+ * (device), with the context's formation precision, written to R_out
+ * (device, [n_E][n_ch][n_ch], full symmetric matrix). Asynchronous.
+ * Errors: RM_EINVAL, RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
+int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *R_out);
+
+/* Per-phase device timing (tracing). With enable != 0 the context records a
+ * CUDA event pair on its stream around every kernel of every phase;
+ * rm_profile_get synchronises and returns, for phase p, the number of
+ * launches and their summed device time in milliseconds since the last
+ * enable. Phases: */
+#define RM_PH_NEARPOLE    0   /* near-pole check */
+#define RM_PH_CHANFN      1   /* step (b) channel functions */
+#define RM_PH_FORM        2   /* step (a) R formation (all precisions) */
+#define RM_PH_FIXUP       3   /* step (a) near-pole FP64 terms (mixed precision) */
+#define RM_PH_SOLVE       4   /* steps (c)+(d) matching, T, Omega */
+#define RM_PH_COUNT       5
+int rm_profile_enable(rm_ctx *ctx, int enable);
+int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms);
+
+/* Waits for all work enqueued on the context's stream. */
+int rm_sync(rm_ctx *ctx);
+
+/* Number of kernels this context has launched since creation. */
+long long rm_launch_count(rm_ctx *ctx);
+
+/* Static description of a code (never NULL). */
+const char *rm_strerror(int code);
+
+/* One-line description of the last error on ctx (never NULL). */
+const char *rm_last_error(rm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMGB_H */

@@ -1,0 +1,309 @@
+// Step (b): asymptotic channel functions at r = a, one thread per (energy, channel).
+//
+// The outer-region equation (Section "Overview", Eq. radial, U = 0, Rydberg units)
+//   u'' + (eps + 2z/r - l(l+1)/r^2) u = 0,   eps = E - e_i,
+// is the Coulomb wave equation in rho = k r, eta = -z/k for an open channel
+// (eps = k^2 > 0) and Whittaker's equation in x = 2 kappa r, nu = z/kappa for a
+// closed channel (eps = -kappa^2 < 0).
+//
+// Open channel (Steed's method, FP64):
+//   1. CF1 for f_l = F_l'/F_l at the channel's own l by modified Lentz. The
+//      Lentz ratios D_n = B_{n-1}/B_n are ratios of a solution of the l-recurrence
+//      that vanishes at l; for large n it is a positive multiple of F_l G_{l+n},
+//      and G > 0 deep in the barrier, so prod sign(D_n) = sign(F_l).
+//   2. F is carried down to l = 0 by the l-recurrences (stable: F is minimal
+//      upwards), giving F_0'/F_0 up to one common scale.
+//   3. CF2 for H+'/H+ = p + iq at l = 0, where r = a is never inside a barrier
+//      for an attractive potential. Forward Lentz only finds the depth n at
+//      which the fraction settles; the value is then taken bottom-up from
+//      depth 2n + 20, which avoids the rounding that forward Lentz accumulates
+//      on the slowly converging fractions near threshold (|eta| >> 1, rho << 1).
+//   4. The Wronskian q (F^2 + G^2) = 1 fixes |F_0|; G_0 = (F_0' - p F_0)/q.
+//   5. G is carried up to l by the l-recurrences (stable: G is dominant upwards).
+//   Energy normalisation: s = F/sqrt(k), s' = sqrt(k) F', c = G/sqrt(k), c' = sqrt(k) G'.
+//
+// Closed channel: the log-derivative L = theta'/theta of the decaying solution
+// theta ~ W_{nu,l+1/2}(2 kappa r) from CF2 continued to imaginary k
+// (k = i kappa, eta = i nu, rho = i kappa a), which is real:
+//   L = -kappa + (nu + Phi)/a,  Phi = a_1/(b_1 - a_2/(b_2 - ...)),
+//   a_n = (L0 + n - nu)(n - 1 - L0 - nu),  b_n = 2(kappa a - nu + n),
+// evaluated at a low l = L0 and carried to l with the Coulomb ladder operator
+//   y_{L+1} = c/(T - y_L) - T,  T = (L+1)/a - z/(L+1),  c = eps + z^2/(L+1)^2.
+// The fraction at the channel's own l loses up to ~13 digits (more near
+// threshold) when r = a lies inside the inner centrifugal barrier; the ladder
+// is stable upwards there. L0 = 0 unless nu <= l + 1/2, where the operator
+// would pass near its null case nu = L+1; then L0 = ceil(nu - 1/2).
+// Output pair (theta, theta') scaled to theta^2 + (a theta')^2 = 1.
+#include <math.h>
+
+#include "rm_internal.cuh"
+
+namespace rmgb {
+namespace {
+
+constexpr int CF_MAXIT = 1 << 20;
+constexpr double TINY = 1e-300;
+constexpr double CF_TOL = 4e-16;
+
+struct Cf1 {
+    double f;
+    int sgn;
+    int ok;
+};
+
+// f_l = S_{l+1} + K(a_n / b_n), a_n = -(1 + eta^2/(l+n)^2), b_n = S_{l+n} + S_{l+n+1},
+// S_L = L/rho + eta/L.
+__device__ Cf1 cf1_lentz(int l, double eta, double rho)
+{
+    const double irho = 1.0 / rho;
+    double L1 = l + 1.0;
+    double S = L1 * irho + eta / L1;
+    double f = (S == 0.0) ? TINY : S;
+    double C = f, D = 0.0;
+    int sgn = 1;
+    for (int n = 1; n < CF_MAXIT; ++n) {
+        double Ln = l + n;
+        double Ln1 = Ln + 1.0;
+        double Snext = Ln1 * irho + eta / Ln1;
+        double er = eta / Ln;
+        double an = -(1.0 + er * er);
+        double bn = S + Snext;
+        D = bn + an * D;
+        if (D == 0.0) D = TINY;
+        C = bn + an / C;
+        if (C == 0.0) C = TINY;
+        D = 1.0 / D;
+        if (D < 0.0) sgn = -sgn;
+        double delta = C * D;
+        f *= delta;
+        if (fabs(delta - 1.0) < CF_TOL) return {f, sgn, 1};
+        S = Snext;
+    }
+    return {f, sgn, 0};
+}
+
+// p + iq = H+'/H+ at l = 0: i(1 - eta/rho) + (i/rho) K(a_m / b_m),
+// a_m = (m + i eta)(m - 1 + i eta), b_m = 2(rho - eta) + 2 i m.
+__device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
+{
+    const double br = 2.0 * (rho - eta);
+    // forward Lentz, only to find the depth
+    double fr = TINY, fi = 0.0, Cr = fr, Ci = 0.0, Dr = 0.0, Di = 0.0;
+    int n = 1;
+    for (; n < CF_MAXIT; ++n) {
+        double m = n;
+        double ar = m * (m - 1.0) - eta * eta;
+        double ai = eta * (2.0 * m - 1.0);
+        double bi = 2.0 * m;
+        // D = b + a D
+        double tr = br + (ar * Dr - ai * Di);
+        double ti = bi + (ar * Di + ai * Dr);
+        if (tr == 0.0 && ti == 0.0) tr = TINY;
+        // C = b + a / C
+        double cm = 1.0 / (Cr * Cr + Ci * Ci);
+        double ur = br + (ar * Cr + ai * Ci) * cm;
+        double ui = bi + (ai * Cr - ar * Ci) * cm;
+        if (ur == 0.0 && ui == 0.0) ur = TINY;
+        Cr = ur;
+        Ci = ui;
+        double dm = 1.0 / (tr * tr + ti * ti);
+        Dr = tr * dm;
+        Di = -ti * dm;
+        double er = Cr * Dr - Ci * Di;
+        double ei = Cr * Di + Ci * Dr;
+        double nfr = fr * er - fi * ei;
+        fi = fr * ei + fi * er;
+        fr = nfr;
+        if (fabs(er - 1.0) + fabs(ei) < CF_TOL) break;
+    }
+    if (n >= CF_MAXIT) return 0;
+    // bottom-up evaluation from depth 2n + 20
+    const int N = 2 * n + 20;
+    double vr = 0.0, vi = 0.0;
+    for (int m_ = N; m_ >= 1; --m_) {
+        double m = m_;
+        double ar = m * (m - 1.0) - eta * eta;
+        double ai = eta * (2.0 * m - 1.0);
+        double dr = br + vr;
+        double di = 2.0 * m + vi;
+        double dm = 1.0 / (dr * dr + di * di);
+        vr = (ar * dr + ai * di) * dm;
+        vi = (ai * dr - ar * di) * dm;
+    }
+    *p = -vi / rho;
+    *q = (1.0 - eta / rho) + vr / rho;
+    return 1;
+}
+
+// Closed-channel log-derivative (r-units) at l = L0 from CF2 at imaginary k.
+__device__ int cf2_closed(int L0, double nu, double kap, double a, double *y)
+{
+    const double base = kap * a - nu;
+    auto an = [&](int m) { return (L0 + m - nu) * (m - 1.0 - L0 - nu); };
+    // forward Lentz on K(A_n / b_n), A_1 = a_1, A_n = -a_n, b_n = 2(base + n)
+    double f = TINY, C = f, D = 0.0;
+    int n = 1;
+    for (; n < CF_MAXIT; ++n) {
+        double A = (n == 1) ? an(1) : -an(n);
+        double B = 2.0 * (base + n);
+        D = B + A * D;
+        if (D == 0.0) D = TINY;
+        C = B + A / C;
+        if (C == 0.0) C = TINY;
+        D = 1.0 / D;
+        double delta = C * D;
+        f *= delta;
+        if (fabs(delta - 1.0) < CF_TOL) break;
+    }
+    if (n >= CF_MAXIT) return 0;
+    const int N = 2 * n + 20;
+    double v = 0.0;
+    for (int m = N; m >= 2; --m) v = -an(m) / (2.0 * (base + m) + v);
+    double phi = an(1) / (2.0 * (base + 1.0) + v);
+    *y = -kap + (nu + phi) / a;
+    return 1;
+}
+
+__global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
+                              ChanFn *__restrict__ out, int *__restrict__ status)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = pw.n;
+    if (idx >= (long long)nE * n) return;
+    const int e = (int)(idx / n);
+    const int i = (int)(idx - (long long)e * n);
+    const double eps = E[e] - pw.e_thr[i];
+    const int l = pw.l[i];
+    const double a = pw.a, z = pw.z;
+    ChanFn r = {0.0, 0.0, 0.0, 0.0};
+    int bad = RM_OK;
+    if (fabs(eps) < o.eps_thr) {
+        bad = RM_ETHRESHOLD;
+    } else if (eps > 0.0) {
+        const double k = sqrt(eps);
+        const double eta = -z / k;
+        const double rho = k * a;
+        Cf1 c1 = cf1_lentz(l, eta, rho);
+        double p, q;
+        int ok2 = cf2_open_l0(eta, rho, &p, &q);
+        if (!c1.ok || !ok2) {
+            bad = RM_ECF_NOCONV;
+        } else {
+            // F_l, F_l' up to a common scale, carried down to l = 0
+            const double Fl = (double)c1.sgn, Fpl = c1.f * Fl;
+            double F = Fl, Fp = Fpl;
+            for (int L = l; L >= 1; --L) {
+                const double SL = L / rho + eta / L;
+                const double RL = sqrt(1.0 + (eta / L) * (eta / L));
+                const double Fm = (SL * F + Fp) / RL;
+                Fp = SL * Fm - RL * F;
+                F = Fm;
+            }
+            const double f0 = Fp / F;
+            double F0 = sqrt(q / ((f0 - p) * (f0 - p) + q * q));
+            if (F < 0.0) F0 = -F0;
+            const double scale = F0 / F;
+            double G = scale * (Fp - p * F) / q;
+            double Gp = p * G - q * F0;
+            for (int L = 0; L < l; ++L) {
+                const double L1 = L + 1.0;
+                const double S1 = L1 / rho + eta / L1;
+                const double R1 = sqrt(1.0 + (eta / L1) * (eta / L1));
+                const double Gn = (S1 * G - Gp) / R1;
+                Gp = R1 * G - S1 * Gn;
+                G = Gn;
+            }
+            const double sk = sqrt(k);
+            r.s = scale * Fl / sk;
+            r.sp = scale * Fpl * sk;
+            r.gh = G / sk;
+            r.ghp = Gp * sk;
+        }
+    } else {
+        const double kap = sqrt(-eps);
+        const double nu = z / kap;
+        int L0 = 0;
+        if (nu <= l + 0.5) {
+            L0 = (int)ceil(nu - 0.5);
+            L0 = L0 < 0 ? 0 : (L0 > l ? l : L0);
+        }
+        double y;
+        if (!cf2_closed(L0, nu, kap, a, &y)) {
+            bad = RM_ECF_NOCONV;
+        } else {
+            for (int L = L0; L < l; ++L) {
+                const double L1 = L + 1.0;
+                const double T = L1 / a - z / L1;
+                const double c = eps + (z / L1) * (z / L1);
+                y = c / (T - y) - T;
+            }
+            const double nrm = 1.0 / sqrt(1.0 + (a * y) * (a * y));
+            r.gh = nrm;
+            r.ghp = y * nrm;
+        }
+    }
+    out[idx] = r;
+    if (bad != RM_OK) atomicCAS(status + e, RM_OK, bad);
+}
+
+__global__ void nearpole_kernel(PwDev pw, const double *__restrict__ E, int nE,
+                                int *__restrict__ status)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    const double x = E[e];
+    const double tol = 1e-12 * fmax(1.0, fabs(x));
+    int lo = 0, hi = pw.N;  // first index with Ek >= x
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (pw.Ek[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    bool near = (lo < pw.N && fabs(pw.Ek[lo] - x) < tol) ||
+                (lo > 0 && fabs(pw.Ek[lo - 1] - x) < tol);
+    if (near) atomicCAS(status + e, RM_OK, RM_ENEAR_POLE);
+}
+
+__global__ void export_kernel(PwDev pw, const double *__restrict__ E, int nE,
+                              const ChanFn *__restrict__ cf, double *__restrict__ out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nE * pw.n) return;
+    const ChanFn c = cf[i];
+    const bool open = E[i / pw.n] - pw.e_thr[i % pw.n] > 0.0;
+    out[4 * i + 0] = open ? c.s : c.gh;
+    out[4 * i + 1] = open ? c.sp : c.ghp;
+    out[4 * i + 2] = open ? c.gh : 0.0;
+    out[4 * i + 3] = open ? c.ghp : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
+                          ChanFn *cf, MqdtFn *mq, int *status, cudaStream_t s)
+{
+    (void)mq;
+    if (mqdt) return cudaErrorNotSupported;
+    const long long total = (long long)nE * pw.n;
+    if (total == 0) return cudaSuccess;
+    const int bs = 128;
+    chanfn_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(pw, E, nE, o, cf, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nearpole(const PwDev &pw, const double *E, int nE, int *status, cudaStream_t s)
+{
+    if (nE == 0) return cudaSuccess;
+    nearpole_kernel<<<(nE + 255) / 256, 256, 0, s>>>(pw, E, nE, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chanfn_export(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
+                                 double *out, cudaStream_t s)
+{
+    const int count = nE * pw.n;
+    if (count == 0) return cudaSuccess;
+    export_kernel<<<(count + 255) / 256, 256, 0, s>>>(pw, E, nE, cf, out);
+    return cudaGetLastError();
+}
+
+}  // namespace rmgb

@@ -1,0 +1,125 @@
+// Step (a), FP64: R_ij(E) = (1/2a) sum_k w_ik w_jk / (E_k - E)  (Section "Overview",
+// Eq. rmatrix), one symmetric n x n matrix per energy, written in full.
+//
+// This is the plain-FP64 baseline the mixed-precision path is measured
+// against. Only the upper triangle is computed (tiles with tile_j >= tile_i)
+// and mirrored, so every R is exactly symmetric. d_k = 1/(E_k - E) is formed
+// once per (tile, k) in shared memory and folded into the j-operand.
+#include "rm_internal.cuh"
+
+namespace rmgb {
+namespace {
+
+// n < 32: one thread per (energy, i <= j), plain loop over poles.
+__global__ void form_r_naive(PwDev pw, const double *__restrict__ E, int nE,
+                             double *__restrict__ R)
+{
+    const int n = pw.n;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nE * n * n) return;
+    const int e = (int)(idx / ((long long)n * n));
+    const int ij = (int)(idx - (long long)e * n * n);
+    const int i = ij / n, j = ij - (ij / n) * n;
+    if (i > j) return;
+    const double x = E[e];
+    const double *wi = pw.W + (size_t)i * pw.N;
+    const double *wj = pw.W + (size_t)j * pw.N;
+    double acc = 0.0;
+    for (int k = 0; k < pw.N; ++k) acc = fma(wi[k], wj[k] / (pw.Ek[k] - x), acc);
+    acc *= 0.5 / pw.a;
+    double *Re = R + (size_t)e * n * n;
+    Re[i * n + j] = acc;
+    Re[j * n + i] = acc;
+}
+
+constexpr int TB = 64;   // output tile
+constexpr int TK = 16;   // pole chunk
+constexpr int TT = 4;    // outputs per thread per dimension
+
+// n >= 32: CTA per (energy, 64x64 upper tile); 256 threads x 4x4 outputs.
+__global__ void __launch_bounds__(256) form_r_tiled(PwDev pw, const double *__restrict__ E,
+                                                    double *__restrict__ R)
+{
+    const int ti = blockIdx.y, tj = blockIdx.x;
+    if (tj < ti) return;
+    const int e = blockIdx.z;
+    const int n = pw.n, N = pw.N;
+    const int i0 = ti * TB, j0 = tj * TB;
+    __shared__ double Wi[TK][TB + 1];
+    __shared__ double Wj[TK][TB + 1];
+    __shared__ double dk[TK];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const double x = E[e];
+    double acc[TT][TT];
+#pragma unroll
+    for (int a = 0; a < TT; ++a)
+#pragma unroll
+        for (int b = 0; b < TT; ++b) acc[a][b] = 0.0;
+
+    for (int k0 = 0; k0 < N; k0 += TK) {
+        if (tid < TK) {
+            const int k = k0 + tid;
+            dk[tid] = (k < N) ? 1.0 / (pw.Ek[k] - x) : 0.0;
+        }
+        __syncthreads();
+        // 64 rows x 16 poles per operand: 4 elements per thread, k fastest
+#pragma unroll
+        for (int t = 0; t < (TB * TK) / 256; ++t) {
+            const int q = tid + t * 256;
+            const int r = q / TK, c = q - (q / TK) * TK;
+            const int k = k0 + c;
+            const int gi = i0 + r, gj = j0 + r;
+            Wi[c][r] = (gi < n && k < N) ? pw.W[(size_t)gi * N + k] : 0.0;
+            Wj[c][r] = (gj < n && k < N) ? pw.W[(size_t)gj * N + k] * dk[c] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < TK; ++c) {
+            double av[TT], bv[TT];
+#pragma unroll
+            for (int a = 0; a < TT; ++a) av[a] = Wi[c][ty * TT + a];
+#pragma unroll
+            for (int b = 0; b < TT; ++b) bv[b] = Wj[c][tx * TT + b];
+#pragma unroll
+            for (int a = 0; a < TT; ++a)
+#pragma unroll
+                for (int b = 0; b < TT; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+    const double h = 0.5 / pw.a;
+    double *Re = R + (size_t)e * n * n;
+#pragma unroll
+    for (int a = 0; a < TT; ++a) {
+        const int i = i0 + ty * TT + a;
+#pragma unroll
+        for (int b = 0; b < TT; ++b) {
+            const int j = j0 + tx * TT + b;
+            if (i < n && j < n && i <= j) {
+                const double v = acc[a][b] * h;
+                Re[(size_t)i * n + j] = v;
+                Re[(size_t)j * n + i] = v;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_form_r_fp64(const PwDev &pw, const double *E, int nE, double *R,
+                               cudaStream_t s)
+{
+    if (nE == 0) return cudaSuccess;
+    if (pw.n < 32) {
+        const long long total = (long long)nE * pw.n * pw.n;
+        form_r_naive<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pw, E, nE, R);
+    } else {
+        const int t = (pw.n + TB - 1) / TB;
+        dim3 grid(t, t, nE);
+        form_r_tiled<<<grid, 256, 0, s>>>(pw, E, R);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rmgb

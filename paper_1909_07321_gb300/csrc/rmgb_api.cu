@@ -1,0 +1,589 @@
+// C ABI of the R -> K -> Omega hot path (declared in include/rmgb.h).
+//
+// The context owns every device buffer: per partial wave the sorted poles,
+// the surface amplitudes and the channel tables; per call a workspace sized
+// by opts.mem_budget; and the Omega accumulator of the registered grid.
+// A call to rm_solve_energies enqueues, per block of energies,
+//   near-pole check -> channel functions -> R formation -> matching + T + Omega
+// on the context stream, with no host synchronisation.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <vector>
+
+#include "rm_internal.cuh"
+
+using namespace rmgb;
+
+namespace {
+
+constexpr int MAX_PW = 4096;
+constexpr int MAX_L = 64;
+constexpr int MAX_BLOCK_E = 32768;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow-only; contents are not preserved
+    cudaError_t reserve(size_t b)
+    {
+        if (b <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return e;
+        }
+        bytes = b;
+        return cudaSuccess;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct PwHost {
+    bool loaded = false, channels = false;
+    int n = 0, N = 0, n_levels = 0;
+    double a = 0, b = 0, z = 0, g = 0;
+    DevBuf Ek, W, e_thr, l, level, lev_start, lev_chan, lev_thr;
+    std::vector<double> h_e_thr;
+    void release()
+    {
+        for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr}) d->release();
+        loaded = channels = false;
+    }
+    PwDev dev() const
+    {
+        PwDev d;
+        d.n = n;
+        d.N = N;
+        d.a = a;
+        d.b = b;
+        d.z = z;
+        d.g = g;
+        d.n_levels = n_levels;
+        d.Ek = Ek.as<double>();
+        d.W = W.as<double>();
+        d.e_thr = e_thr.as<double>();
+        d.l = l.as<int>();
+        d.level = level.as<int>();
+        d.lev_start = lev_start.as<int>();
+        d.lev_chan = lev_chan.as<int>();
+        d.lev_thr = lev_thr.as<double>();
+        return d;
+    }
+};
+
+}  // namespace
+
+struct rm_ctx {
+    rm_opts opts;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<PwHost> pw;
+    // grid and Omega accumulator
+    int grid_nE = 0, grid_nlev = 0, grid_ntri = 0;
+    std::vector<double> grid_host;
+    DevBuf omega;
+    // workspace
+    DevBuf wsE, wsCf, wsR, wsStatus, wsMq;
+    long long launches = 0;
+    // per-phase event pairs (tracing)
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[RM_PH_COUNT];
+    size_t ev_used[RM_PH_COUNT] = {0, 0, 0, 0, 0};
+    char err[512] = "no error";
+};
+
+namespace {
+
+int fail(rm_ctx *c, int code, const char *fmt, ...)
+{
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->err, sizeof(c->err), fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? RM_ENOMEM : RM_ECUDA,   \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,      \
+                        __LINE__);                                                      \
+    } while (0)
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool finite_all(const double *x, size_t n)
+{
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+int check_pw(rm_ctx *ctx, int pw, bool need_channels)
+{
+    if (!ctx) return RM_EINVAL;
+    if (pw < 0 || pw >= MAX_PW) return fail(ctx, RM_EINVAL, "pw %d out of range [0, %d)", pw, MAX_PW);
+    if ((int)ctx->pw.size() <= pw || !ctx->pw[pw].loaded)
+        return fail(ctx, RM_ENOTLOADED, "partial wave %d has no poles loaded", pw);
+    if (need_channels && !ctx->pw[pw].channels)
+        return fail(ctx, RM_ENOTLOADED, "partial wave %d has no channels set", pw);
+    return RM_SUCCESS;
+}
+
+template <class T> cudaError_t upload(DevBuf &d, const T *h, size_t count, cudaStream_t s)
+{
+    cudaError_t e = d.reserve(count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(d.p, h, count * sizeof(T), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+// Records the start event of a traced launch of `phase` (no-op if tracing is off).
+cudaError_t prof_begin(rm_ctx *ctx, int phase)
+{
+    if (!ctx->prof) return cudaSuccess;
+    auto &v = ctx->ev[phase];
+    size_t &u = ctx->ev_used[phase];
+    if (u == v.size()) {
+        cudaEvent_t a, b;
+        cudaError_t e = cudaEventCreate(&a);
+        if (e != cudaSuccess) return e;
+        e = cudaEventCreate(&b);
+        if (e != cudaSuccess) return e;
+        v.push_back({a, b});
+    }
+    return cudaEventRecord(v[u].first, ctx->stream);
+}
+
+cudaError_t prof_end(rm_ctx *ctx, int phase)
+{
+    if (!ctx->prof) return cudaSuccess;
+    auto &v = ctx->ev[phase];
+    size_t &u = ctx->ev_used[phase];
+    cudaError_t e = cudaEventRecord(v[u].second, ctx->stream);
+    ++u;
+    return e;
+}
+
+Opts make_opts(const rm_opts &o)
+{
+    Opts r;
+    r.eps_thr = o.eps_thr;
+    r.delta_pole = o.delta_pole;
+    r.fnumin = o.fnumin;
+    r.nu_margin = o.nu_margin;
+    return r;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+
+extern "C" void rm_default_opts(rm_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = RM_FP64;
+    o->delta_pole = 1e-3;
+    o->eps_thr = 1e-10;
+    o->fnumin = 0.0;
+    o->nu_margin = 0.1;
+    o->device = 0;
+    o->stream = nullptr;
+    o->mem_budget = 0;
+}
+
+extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
+{
+    if (!out) return RM_EINVAL;
+    *out = nullptr;
+    rm_opts o;
+    if (opts) o = *opts; else rm_default_opts(&o);
+    if (o.mem_budget == 0) o.mem_budget = (size_t)1 << 30;
+    if (!(o.eps_thr >= 0) || !(o.delta_pole >= 0) || !std::isfinite(o.fnumin) ||
+        !std::isfinite(o.nu_margin) ||
+        (o.precision != RM_FP64 && o.precision != RM_FP32 && o.precision != RM_BF16X3))
+        return RM_EINVAL;
+    if (cudaSetDevice(o.device) != cudaSuccess) {
+        cudaGetLastError();
+        return RM_ECUDA;
+    }
+    rm_ctx *ctx = new (std::nothrow) rm_ctx();
+    if (!ctx) return RM_ENOMEM;
+    ctx->opts = o;
+    if (o.stream) {
+        ctx->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return RM_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    *out = ctx;
+    return RM_SUCCESS;
+}
+
+extern "C" void rm_destroy(rm_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->opts.device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &p : ctx->pw) p.release();
+    for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq})
+        d->release();
+    for (int p = 0; p < RM_PH_COUNT; ++p)
+        for (auto &pr : ctx->ev[p]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const double *E_k,
+                             const double *W, double a, double b)
+{
+    if (!ctx) return RM_EINVAL;
+    if (pw < 0 || pw >= MAX_PW) return fail(ctx, RM_EINVAL, "pw %d out of range", pw);
+    if (n_ch <= 0 || n_poles <= 0 || !E_k || !W)
+        return fail(ctx, RM_EINVAL, "n_ch=%d n_poles=%d must be > 0 with non-NULL arrays", n_ch,
+                    n_poles);
+    if (!(a > 0) || !std::isfinite(a) || !std::isfinite(b))
+        return fail(ctx, RM_EINVAL, "a=%g must be > 0 and b=%g finite", a, b);
+    if (!finite_all(E_k, n_poles) || !finite_all(W, (size_t)n_ch * n_poles))
+        return fail(ctx, RM_EINVAL, "non-finite pole energy or amplitude");
+    CK(cudaSetDevice(ctx->opts.device));
+    if ((int)ctx->pw.size() <= pw) ctx->pw.resize(pw + 1);
+    PwHost &P = ctx->pw[pw];
+    const bool same_n = P.loaded && P.n == n_ch;
+    // sort poles (R does not depend on their order); permute W's columns alike
+    std::vector<int> ord(n_poles);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return E_k[x] < E_k[y]; });
+    std::vector<double> Es(n_poles), Ws((size_t)n_ch * n_poles);
+    for (int k = 0; k < n_poles; ++k) Es[k] = E_k[ord[k]];
+    for (int i = 0; i < n_ch; ++i)
+        for (int k = 0; k < n_poles; ++k) Ws[(size_t)i * n_poles + k] = W[(size_t)i * n_poles + ord[k]];
+    P.Ek.release();
+    P.W.release();
+    CK(upload(P.Ek, Es.data(), Es.size(), ctx->stream));
+    CK(upload(P.W, Ws.data(), Ws.size(), ctx->stream));
+    P.n = n_ch;
+    P.N = n_poles;
+    P.a = a;
+    P.b = b;
+    P.loaded = true;
+    if (!same_n) P.channels = false;
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, double z,
+                               const int *level, int n_levels, double g_weight)
+{
+    int rc = check_pw(ctx, pw, false);
+    if (rc) return rc;
+    PwHost &P = ctx->pw[pw];
+    const int n = P.n;
+    if (!e_thr || !l || !level) return fail(ctx, RM_EINVAL, "NULL channel array");
+    if (!(z >= 0) || !std::isfinite(z) || !std::isfinite(g_weight) || n_levels <= 0)
+        return fail(ctx, RM_EINVAL, "z=%g must be >= 0, g finite, n_levels=%d > 0", z, n_levels);
+    if (!finite_all(e_thr, n)) return fail(ctx, RM_EINVAL, "non-finite threshold");
+    std::vector<double> lev_thr(n_levels, std::numeric_limits<double>::infinity());
+    std::vector<int> cnt(n_levels, 0);
+    for (int i = 0; i < n; ++i) {
+        if (l[i] < 0 || l[i] > MAX_L) return fail(ctx, RM_EINVAL, "l[%d]=%d out of [0,%d]", i, l[i], MAX_L);
+        if (level[i] < 0 || level[i] >= n_levels)
+            return fail(ctx, RM_EINVAL, "level[%d]=%d out of [0,%d)", i, level[i], n_levels);
+        double &t = lev_thr[level[i]];
+        if (cnt[level[i]] && t != e_thr[i])
+            return fail(ctx, RM_EINVAL, "channels of level %d have different thresholds", level[i]);
+        t = e_thr[i];
+        cnt[level[i]]++;
+    }
+    std::vector<int> start(n_levels + 1, 0), chan(n), fill(n_levels, 0);
+    for (int I = 0; I < n_levels; ++I) start[I + 1] = start[I] + cnt[I];
+    for (int i = 0; i < n; ++i) chan[start[level[i]] + fill[level[i]]++] = i;
+    CK(cudaSetDevice(ctx->opts.device));
+    CK(upload(P.e_thr, e_thr, n, ctx->stream));
+    CK(upload(P.l, l, n, ctx->stream));
+    CK(upload(P.level, level, n, ctx->stream));
+    CK(upload(P.lev_start, start.data(), start.size(), ctx->stream));
+    CK(upload(P.lev_chan, chan.data(), chan.size(), ctx->stream));
+    CK(upload(P.lev_thr, lev_thr.data(), lev_thr.size(), ctx->stream));
+    P.h_e_thr.assign(e_thr, e_thr + n);
+    P.z = z;
+    P.g = g_weight;
+    P.n_levels = n_levels;
+    P.channels = true;
+    return RM_SUCCESS;
+}
+
+namespace {
+
+// Energies as a device pointer on the context stream (copies host input).
+int device_energies(rm_ctx *ctx, int n_E, const double *E, const double **dE)
+{
+    if (is_device_ptr(E)) {
+        *dE = E;
+        return RM_SUCCESS;
+    }
+    if (!finite_all(E, n_E)) return fail(ctx, RM_EINVAL, "non-finite energy");
+    CK(ctx->wsE.reserve((size_t)n_E * sizeof(double)));
+    CK(cudaMemcpyAsync(ctx->wsE.p, E, (size_t)n_E * sizeof(double), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    *dE = ctx->wsE.as<double>();
+    return RM_SUCCESS;
+}
+
+int block_energies(rm_ctx *ctx, const PwHost &P)
+{
+    const size_t per = (size_t)P.n * P.n * sizeof(double) + (size_t)P.n * sizeof(ChanFn) + 64;
+    size_t B = ctx->opts.mem_budget / per;
+    if (B < 1) B = 1;
+    if (B > MAX_BLOCK_E) B = MAX_BLOCK_E;
+    return (int)B;
+}
+
+int form_r_block(rm_ctx *ctx, const PwHost &P, const double *E, int nE, double *R)
+{
+    const PwDev d = P.dev();
+    if (ctx->opts.precision != RM_FP64)
+        return fail(ctx, RM_EUNSUPPORTED, "formation precision %d not built yet", ctx->opts.precision);
+    CK(prof_begin(ctx, RM_PH_FORM));
+    CK(launch_form_r_fp64(d, E, nE, R, ctx->stream));
+    CK(prof_end(ctx, RM_PH_FORM));
+    ctx->launches++;
+    return RM_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
+                                 double *K_out, int *n_open_out, int *status_out)
+{
+    int rc = check_pw(ctx, pw, true);
+    if (rc) return rc;
+    if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
+    if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
+    if (mode == RM_MQDT) return fail(ctx, RM_EUNSUPPORTED, "MQDT mode not built yet");
+    const PwHost &P = ctx->pw[pw];
+    if (P.n > solve_small_max_n())
+        return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the solver limit %d", P.n,
+                    solve_small_max_n());
+    CK(cudaSetDevice(ctx->opts.device));
+    const bool dev_in = is_device_ptr(E);
+    // grid registration / check
+    const int ntri = P.n_levels * (P.n_levels + 1) / 2;
+    if (ctx->grid_nE == 0) {
+        CK(ctx->omega.reserve((size_t)n_E * ntri * sizeof(double)));
+        CK(cudaMemsetAsync(ctx->omega.p, 0, (size_t)n_E * ntri * sizeof(double), ctx->stream));
+        ctx->grid_nE = n_E;
+        ctx->grid_nlev = P.n_levels;
+        ctx->grid_ntri = ntri;
+        ctx->grid_host.clear();
+        if (!dev_in) ctx->grid_host.assign(E, E + n_E);
+    } else {
+        if (n_E != ctx->grid_nE || P.n_levels != ctx->grid_nlev)
+            return fail(ctx, RM_EGRID, "grid (%d energies, %d levels) differs from registered (%d, %d)",
+                        n_E, P.n_levels, ctx->grid_nE, ctx->grid_nlev);
+        if (!dev_in && !ctx->grid_host.empty() &&
+            memcmp(E, ctx->grid_host.data(), (size_t)n_E * sizeof(double)) != 0)
+            return fail(ctx, RM_EGRID, "energies differ from the registered grid");
+    }
+    const double *dE;
+    rc = device_energies(ctx, n_E, E, &dE);
+    if (rc) return rc;
+    const int B = std::min(n_E, block_energies(ctx, P));
+    CK(ctx->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
+    CK(ctx->wsR.reserve((size_t)B * P.n * P.n * sizeof(double)));
+    int *dstatus = status_out;
+    if (!dstatus) {
+        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        dstatus = ctx->wsStatus.as<int>();
+    }
+    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ctx->stream));
+    const PwDev d = P.dev();
+    const Opts o = make_opts(ctx->opts);
+    for (int e0 = 0; e0 < n_E; e0 += B) {
+        const int nb = std::min(B, n_E - e0);
+        const double *Eb = dE + e0;
+        int *sb = dstatus + e0;
+        CK(prof_begin(ctx, RM_PH_NEARPOLE));
+        CK(launch_nearpole(d, Eb, nb, sb, ctx->stream));
+        CK(prof_end(ctx, RM_PH_NEARPOLE));
+        CK(prof_begin(ctx, RM_PH_CHANFN));
+        CK(launch_chanfn(d, Eb, nb, o, 0, ctx->wsCf.as<ChanFn>(), nullptr, sb, ctx->stream));
+        CK(prof_end(ctx, RM_PH_CHANFN));
+        ctx->launches += 2;
+        rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
+        if (rc) return rc;
+        CK(prof_begin(ctx, RM_PH_SOLVE));
+        CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), nullptr, ctx->wsR.as<double>(), 0,
+                              sb, K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr,
+                              n_open_out ? n_open_out + e0 : nullptr,
+                              ctx->omega.as<double>() + (size_t)e0 * ntri, ntri, ctx->stream));
+        CK(prof_end(ctx, RM_PH_SOLVE));
+        ctx->launches++;
+    }
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_collision_strengths(rm_ctx *ctx, double *omega_out, int reset)
+{
+    if (!ctx) return RM_EINVAL;
+    CK(cudaSetDevice(ctx->opts.device));
+    if (ctx->grid_nE == 0) {
+        if (reset) return RM_SUCCESS;
+        return fail(ctx, RM_EINVAL, "no energy grid registered yet");
+    }
+    const size_t bytes = (size_t)ctx->grid_nE * ctx->grid_ntri * sizeof(double);
+    if (omega_out)
+        CK(cudaMemcpyAsync(omega_out, ctx->omega.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (reset) {
+        ctx->grid_nE = ctx->grid_nlev = ctx->grid_ntri = 0;
+        ctx->grid_host.clear();
+    }
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_reset_omega(rm_ctx *ctx)
+{
+    if (!ctx) return RM_EINVAL;
+    if (ctx->grid_nE == 0) return fail(ctx, RM_EINVAL, "no energy grid registered yet");
+    CK(cudaSetDevice(ctx->opts.device));
+    CK(cudaMemsetAsync(ctx->omega.p, 0, (size_t)ctx->grid_nE * ctx->grid_ntri * sizeof(double),
+                       ctx->stream));
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_profile_enable(rm_ctx *ctx, int enable)
+{
+    if (!ctx) return RM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->prof = enable != 0;
+    for (int p = 0; p < RM_PH_COUNT; ++p) ctx->ev_used[p] = 0;
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms)
+{
+    if (!ctx || phase < 0 || phase >= RM_PH_COUNT) return RM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    double tot = 0.0;
+    for (size_t i = 0; i < ctx->ev_used[phase]; ++i) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, ctx->ev[phase][i].first, ctx->ev[phase][i].second));
+        tot += t;
+    }
+    if (launches) *launches = (int)ctx->ev_used[phase];
+    if (ms) *ms = tot;
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_grid_shape(rm_ctx *ctx, int *n_E, int *n_tri)
+{
+    if (!ctx) return RM_EINVAL;
+    if (n_E) *n_E = ctx->grid_nE;
+    if (n_tri) *n_tri = ctx->grid_ntri;
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *E, double *out,
+                                    int *status)
+{
+    int rc = check_pw(ctx, pw, true);
+    if (rc) return rc;
+    if (n_E <= 0 || !E || !out) return fail(ctx, RM_EINVAL, "bad arguments");
+    if (!is_device_ptr(E) || !is_device_ptr(out) || (status && !is_device_ptr(status)))
+        return fail(ctx, RM_EINVAL, "E, out and status must be device pointers");
+    CK(cudaSetDevice(ctx->opts.device));
+    const PwHost &P = ctx->pw[pw];
+    CK(ctx->wsCf.reserve((size_t)n_E * P.n * sizeof(ChanFn)));
+    int *st = status;
+    if (!st) {
+        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        st = ctx->wsStatus.as<int>();
+    }
+    CK(cudaMemsetAsync(st, 0, (size_t)n_E * sizeof(int), ctx->stream));
+    const PwDev d = P.dev();
+    CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ctx->wsCf.as<ChanFn>(), nullptr, st,
+                     ctx->stream));
+    CK(launch_chanfn_export(d, E, n_E, ctx->wsCf.as<ChanFn>(), out, ctx->stream));
+    ctx->launches += 2;
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *R_out)
+{
+    int rc = check_pw(ctx, pw, false);
+    if (rc) return rc;
+    if (n_E <= 0 || !E || !R_out) return fail(ctx, RM_EINVAL, "bad arguments");
+    if (!is_device_ptr(E) || !is_device_ptr(R_out))
+        return fail(ctx, RM_EINVAL, "E and R_out must be device pointers");
+    CK(cudaSetDevice(ctx->opts.device));
+    const PwHost &P = ctx->pw[pw];
+    for (int e0 = 0; e0 < n_E; e0 += MAX_BLOCK_E) {
+        const int nb = std::min(MAX_BLOCK_E, n_E - e0);
+        rc = form_r_block(ctx, P, E + e0, nb, R_out + (size_t)e0 * P.n * P.n);
+        if (rc) return rc;
+    }
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_sync(rm_ctx *ctx)
+{
+    if (!ctx) return RM_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RM_SUCCESS;
+}
+
+extern "C" long long rm_launch_count(rm_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" const char *rm_strerror(int code)
+{
+    switch (code) {
+    case RM_SUCCESS: return "success";
+    case RM_EINVAL: return "invalid argument";
+    case RM_ENOMEM: return "out of memory";
+    case RM_ECUDA: return "CUDA runtime error";
+    case RM_EGRID: return "energy grid differs from the registered grid";
+    case RM_ENOTLOADED: return "partial wave not loaded";
+    case RM_EUNSUPPORTED: return "unsupported option for this size or mode";
+    case RM_ETIMEOUT: return "bounded device wait timed out";
+    case RM_ETHRESHOLD: return "energy on a channel threshold";
+    case RM_ENEAR_POLE: return "energy on an R-matrix pole";
+    case RM_ESINGULAR: return "matching system singular";
+    case RM_ECF_NOCONV: return "Coulomb continued fraction did not converge";
+    default: return "unknown code";
+    }
+}
+
+extern "C" const char *rm_last_error(rm_ctx *ctx) { return ctx ? ctx->err : "NULL context"; }

@@ -1,0 +1,270 @@
+// Steps (c) and (d) for n <= SOLVE_SMALL_MAXN channels: one CTA per energy,
+// everything in shared memory, FP64.
+//
+// (c) Matching (Section "Overview", Eq. match): with unknowns X (n x n_o),
+//   psi_ij = s_i delta_ij + ghat_i X_ij, ghat = c (open) or theta (closed),
+//   psi(a) = R (a psi'(a) - b psi(a)) gives
+//   [diag(ghat) - R diag(a ghat' - b ghat)] X = -[diag(s) - R diag(a s' - b s)] P,
+// P selecting open columns; K = X[open rows].
+// The unknowns are ordered closed-first, so after Gaussian elimination with
+// partial pivoting on the augmented matrix [A | B] the open unknowns are the
+// trailing n_o rows of the triangular system: back-substitution runs over
+// those rows only (the closed amplitudes are never formed).
+//
+// (d) T = 2iK(1 - iK)^{-1} (Section "Glossary of terms") in real form. K is
+// symmetric, so with M = 1 + K^2 (SPD), X = M^{-1} K and Y = M^{-1} K^2 = K X:
+//   T = -2Y + 2iX,  |T_ab|^2 = 4 (X_ab^2 + Y_ab^2).
+// M is factored by Cholesky. Then for target levels I <= J, one thread owns
+// Omega_IJ(E) and adds g sum_{a in I, b in J} |T_ab|^2 in a fixed order, so
+// the accumulation is deterministic (no atomics).
+#include <math.h>
+
+#include "rm_internal.cuh"
+
+namespace rmgb {
+namespace {
+
+constexpr int SOLVE_SMALL_MAXN = 96;
+constexpr int NT = 256;
+
+__global__ void __launch_bounds__(NT) solve_small_kernel(
+    PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
+    const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
+    int *__restrict__ n_open_out, double *__restrict__ omega, int n_tri)
+{
+    extern __shared__ double sm[];
+    __shared__ int col_chan[SOLVE_SMALL_MAXN];   // unknown column -> channel
+    __shared__ int open_pos[SOLVE_SMALL_MAXN];   // channel -> open position (-1 closed)
+    __shared__ int s_no, s_piv, s_bad;
+    __shared__ double s_pivinv;
+
+    const int e = blockIdx.x;
+    const int n = pw.n;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const double x = E[e];
+    const ChanFn *cf = cfa + (size_t)e * n;
+    const double *R = Ra + (size_t)e * n * n;
+
+    if (tid == 0) {
+        int no = 0;
+        for (int i = 0; i < n; ++i) no += (x - pw.e_thr[i] > 0.0);
+        const int nc = n - no;
+        int pc = 0, po = 0;
+        for (int i = 0; i < n; ++i) {
+            if (x - pw.e_thr[i] > 0.0) {
+                open_pos[i] = po;
+                col_chan[nc + po] = i;
+                ++po;
+            } else {
+                open_pos[i] = -1;
+                col_chan[pc++] = i;
+            }
+        }
+        s_no = no;
+        s_bad = 0;
+        if (n_open_out) n_open_out[e] = no;
+    }
+    __syncthreads();
+    const int no = s_no, nc = n - no;
+    if (status[e] != RM_OK || no == 0) return;
+
+    const int w = n + no;        // augmented width
+    const int ld = w + 1;        // padded row stride
+    double *M = sm;
+    const double a = pw.a, b = pw.b;
+
+    // ---- assemble [A | B] -------------------------------------------------
+    for (int q = tid; q < n * w; q += NT) {
+        const int r = q / w, c = q - (q / w) * w;
+        double v;
+        if (c < n) {
+            const int j = col_chan[c];
+            const ChanFn cj = cf[j];
+            v = -R[r * n + j] * (a * cj.ghp - b * cj.gh);
+            if (r == j) v += cj.gh;
+        } else {
+            const int o = col_chan[nc + (c - n)];
+            const ChanFn co = cf[o];
+            v = R[r * n + o] * (a * co.sp - b * co.s);
+            if (r == o) v -= co.s;
+        }
+        M[r * ld + c] = v;
+    }
+    __syncthreads();
+
+    // ---- forward elimination with partial pivoting -------------------------
+    for (int c = 0; c < n; ++c) {
+        if (warp == 0) {
+            double best = -1.0;
+            int bi = c;
+            for (int r = c + lane; r < n; r += 32) {
+                const double v = fabs(M[r * ld + c]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                s_piv = bi;
+                const double pv = M[bi * ld + c];
+                if (!(best > 0.0) || !isfinite(pv)) s_bad = 1;
+                s_pivinv = 1.0 / pv;
+            }
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != c) {
+            for (int q = c + tid; q < w; q += NT) {
+                const double t = M[c * ld + q];
+                M[c * ld + q] = M[p * ld + q];
+                M[p * ld + q] = t;
+            }
+            __syncthreads();
+        }
+        // multipliers into column c (below the pivot), then the trailing update
+        const double pinv = s_pivinv;
+        for (int r = c + 1 + tid; r < n; r += NT) M[r * ld + c] *= pinv;
+        __syncthreads();
+        const int rows = n - c - 1, cols = w - c - 1;
+        for (int q = tid; q < rows * cols; q += NT) {
+            const int r = c + 1 + q / cols, cc = c + 1 + (q - (q / cols) * cols);
+            M[r * ld + cc] = fma(-M[r * ld + c], M[c * ld + cc], M[r * ld + cc]);
+        }
+        __syncthreads();
+    }
+    if (s_bad) {
+        if (tid == 0) status[e] = RM_ESINGULAR;
+        return;
+    }
+
+    // ---- back-substitution over the trailing open rows ----------------------
+    // x_t = (y_t - sum_{u>t} U_tu x_u) / U_tt for t = n-1 .. nc, in place in the
+    // right-hand-side columns; one thread per right-hand side.
+    for (int qq = tid; qq < no; qq += NT) {
+        const int cq = n + qq;
+        for (int t = n - 1; t >= nc; --t) {
+            double s = M[t * ld + cq];
+            for (int u = t + 1; u < n; ++u) s = fma(-M[t * ld + u], M[u * ld + cq], s);
+            M[t * ld + cq] = s / M[t * ld + t];
+        }
+    }
+    __syncthreads();
+
+    // ---- K, optional output, symmetrised copy ------------------------------
+    // Shared layout: [augmented region, n(2n+2) doubles][Ks]; once K is copied
+    // out, the Cholesky factor and X reuse the augmented region.
+    const int lk = no + 1;
+    double *Ks = sm + (size_t)n * (2 * n + 2);
+    double *Lc = sm;                         // Cholesky factor of 1 + K^2
+    double *Xm = sm + (size_t)no * lk;       // X = M^{-1} K
+    for (int q = tid; q < no * no; q += NT) {
+        const int p = q / no, r = q - (q / no) * no;
+        const double kpr = M[(nc + p) * ld + n + r];
+        const double krp = M[(nc + r) * ld + n + p];
+        Ks[p * lk + r] = 0.5 * (kpr + krp);
+        if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
+    }
+    __syncthreads();
+    if (!omega) return;
+
+    // ---- M = 1 + K^2, Cholesky ----------------------------------------------
+    for (int q = tid; q < no * no; q += NT) {
+        const int p = q / no, r = q - (q / no) * no;
+        double s = (p == r) ? 1.0 : 0.0;
+        for (int u = 0; u < no; ++u) s = fma(Ks[p * lk + u], Ks[u * lk + r], s);
+        Lc[p * lk + r] = s;
+    }
+    __syncthreads();
+    for (int c = 0; c < no; ++c) {
+        if (tid == 0) Lc[c * lk + c] = sqrt(Lc[c * lk + c]);
+        __syncthreads();
+        const double dinv = 1.0 / Lc[c * lk + c];
+        for (int r = c + 1 + tid; r < no; r += NT) Lc[r * lk + c] *= dinv;
+        __syncthreads();
+        const int m = no - c - 1;
+        for (int q = tid; q < m * m; q += NT) {
+            const int r = c + 1 + q / m, s2 = c + 1 + (q - (q / m) * m);
+            if (s2 <= r) Lc[r * lk + s2] = fma(-Lc[r * lk + c], Lc[s2 * lk + c], Lc[r * lk + s2]);
+        }
+        __syncthreads();
+    }
+    // X = (L L^T)^{-1} K: one thread per column
+    for (int r = tid; r < no; r += NT) {
+        for (int p = 0; p < no; ++p) {
+            double s = Ks[p * lk + r];
+            for (int u = 0; u < p; ++u) s = fma(-Lc[p * lk + u], Xm[u * lk + r], s);
+            Xm[p * lk + r] = s / Lc[p * lk + p];
+        }
+        for (int p = no - 1; p >= 0; --p) {
+            double s = Xm[p * lk + r];
+            for (int u = p + 1; u < no; ++u) s = fma(-Lc[u * lk + p], Xm[u * lk + r], s);
+            Xm[p * lk + r] = s / Lc[p * lk + p];
+        }
+    }
+    __syncthreads();
+    // |T|^2 = 4 (X^2 + Y^2), Y = K X; stored over Lc
+    double *T2 = Lc;
+    for (int q = tid; q < no * no; q += NT) {
+        const int p = q / no, r = q - (q / no) * no;
+        double y = 0.0;
+        for (int u = 0; u < no; ++u) y = fma(Ks[p * lk + u], Xm[u * lk + r], y);
+        const double xv = Xm[p * lk + r];
+        T2[p * lk + r] = 4.0 * (xv * xv + y * y);
+    }
+    __syncthreads();
+
+    // ---- Omega_IJ += g sum |T_ab|^2 over a in I, b in J ---------------------
+    const int nl = pw.n_levels;
+    const int npair = nl * (nl + 1) / 2;
+    double *om = omega + (size_t)e * n_tri;
+    const double g = pw.g;
+    for (int q = tid; q < npair; q += NT) {
+        // invert the row-wise triangular index q -> (I, J)
+        int I = 0, rem = q;
+        while (rem >= nl - I) { rem -= nl - I; ++I; }
+        const int J = I + rem;
+        if (!(x - pw.lev_thr[I] > 0.0) || !(x - pw.lev_thr[J] > 0.0)) continue;
+        double s = 0.0;
+        for (int ia = pw.lev_start[I]; ia < pw.lev_start[I + 1]; ++ia) {
+            const int pa = open_pos[pw.lev_chan[ia]];
+            for (int ib = pw.lev_start[J]; ib < pw.lev_start[J + 1]; ++ib) {
+                const int pb = open_pos[pw.lev_chan[ib]];
+                s += T2[pa * lk + pb];
+            }
+        }
+        om[q] += g * s;
+    }
+}
+
+}  // namespace
+
+int solve_small_max_n() { return SOLVE_SMALL_MAXN; }
+
+size_t solve_small_smem(int n)
+{
+    const size_t aug = (size_t)n * (2 * n + 2);
+    const size_t ks = (size_t)n * (n + 1);
+    return (aug + ks) * sizeof(double);
+}
+
+cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
+                               const MqdtFn *mq, const double *R, int mqdt, int *status,
+                               double *K_out, int *n_open_out, double *omega, int n_tri,
+                               cudaStream_t s)
+{
+    (void)mq;
+    if (mqdt) return cudaErrorNotSupported;
+    if (pw.n > SOLVE_SMALL_MAXN) return cudaErrorInvalidValue;
+    if (nE == 0) return cudaSuccess;
+    const size_t smem = solve_small_smem(pw.n);
+    cudaError_t err = cudaFuncSetAttribute(solve_small_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    solve_small_kernel<<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega, n_tri);
+    return cudaGetLastError();
+}
+
+}  // namespace rmgb

@@ -1,0 +1,68 @@
+"""C-ABI library: builds, loads, exports every declared symbol (CPU only).
+
+No compute call is made here; on a machine without a GPU rm_create must fail
+cleanly with RM_ECUDA rather than crash.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1909_07321_gb300 import build as libbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rmgb.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rm_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def so():
+    path = libbuild.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_boundary():
+    names = _declared()
+    for must in ["rm_create", "rm_destroy", "rm_load_poles", "rm_set_channels",
+                 "rm_solve_energies", "rm_collision_strengths", "rm_strerror", "rm_last_error"]:
+        assert must in names
+
+
+def test_every_declared_symbol_exported(so):
+    missing = [n for n in _declared() if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_defaults(so):
+    from paper_1909_07321_gb300 import rmgb
+    for code in [0, -1, -2, -3, -4, -5, -6, -7, 1, 2, 3, 4, 99]:
+        assert isinstance(rmgb.rm_strerror(code), str) and rmgb.rm_strerror(code)
+    o = rmgb.rm_default_opts()
+    assert o.precision == rmgb.RM_FP64 and o.eps_thr == 1e-10 and o.delta_pole == 1e-3
+    assert o.nu_margin == 0.1 and o.fnumin == 0.0
+
+
+def test_create_without_gpu_fails_cleanly(so):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    from paper_1909_07321_gb300 import rmgb
+    with pytest.raises(rmgb.RmError) as ei:
+        rmgb.rm_create()
+    assert ei.value.code in (rmgb.RM_ECUDA, rmgb.RM_EINVAL)
+
+
+def test_null_context_is_rejected(so):
+    from paper_1909_07321_gb300 import rmgb
+    L = rmgb.lib()
+    assert L.rm_solve_energies(None, 0, 1, None, 0, None, None, None) == rmgb.RM_EINVAL
+    assert L.rm_collision_strengths(None, None, 0) == rmgb.RM_EINVAL
+    assert L.rm_sync(None) == rmgb.RM_EINVAL
+    L.rm_destroy(None)
+    assert L.rm_last_error(None)
