@@ -17,7 +17,8 @@
 //      for an attractive potential. Forward Lentz only finds the depth n at
 //      which the fraction settles; the value is then taken bottom-up from
 //      depth 2n + 20, which avoids the rounding that forward Lentz accumulates
-//      on the slowly converging fractions near threshold (|eta| >> 1, rho << 1).
+//      on the slowly converging fractions near threshold (|eta| >> 1, rho << 1)
+//      (double precision loses ~1e-10 there otherwise).
 //   4. The Wronskian q (F^2 + G^2) = 1 fixes |F_0|; G_0 = (F_0' - p F_0)/q.
 //   5. G is carried up to l by the l-recurrences (stable: G is dominant upwards).
 //   Energy normalisation: s = F/sqrt(k), s' = sqrt(k) F', c = G/sqrt(k), c' = sqrt(k) G'.
@@ -82,51 +83,49 @@ __device__ Cf1 cf1_lentz(int l, double eta, double rho)
     return {f, sgn, 0};
 }
 
-// p + iq = H+'/H+ at l = 0: i(1 - eta/rho) + (i/rho) K(a_m / b_m),
+// p + iq = H+'/H+ at l = 0: i(1 - eta/rho) + (i/rho) K,  K = K(a_m / b_m),
 // a_m = (m + i eta)(m - 1 + i eta), b_m = 2(rho - eta) + 2 i m.
+// The depth is found by forward Lentz on the tail K' = b_1 + K_{m>=2}(a_m / b_m)
+// (|b_1| >= 2, so no scaled-tiny start is needed); the value is then taken
+// bottom-up from depth 2n + 20.
 __device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
 {
     const double br = 2.0 * (rho - eta);
-    // forward Lentz, only to find the depth
-    double fr = TINY, fi = 0.0, Cr = fr, Ci = 0.0, Dr = 0.0, Di = 0.0;
-    int n = 1;
+    double Cr = br, Ci = 2.0, Dr = 0.0, Di = 0.0;
+    int n = 2;
     for (; n < CF_MAXIT; ++n) {
-        double m = n;
-        double ar = m * (m - 1.0) - eta * eta;
-        double ai = eta * (2.0 * m - 1.0);
-        double bi = 2.0 * m;
-        // D = b + a D
+        const double m = n;
+        const double ar = m * (m - 1.0) - eta * eta;
+        const double ai = eta * (2.0 * m - 1.0);
+        const double bi = 2.0 * m;
+        // D = 1 / (b + a D)
         double tr = br + (ar * Dr - ai * Di);
         double ti = bi + (ar * Di + ai * Dr);
         if (tr == 0.0 && ti == 0.0) tr = TINY;
+        const double dm = 1.0 / (tr * tr + ti * ti);
+        Dr = tr * dm;
+        Di = -ti * dm;
         // C = b + a / C
-        double cm = 1.0 / (Cr * Cr + Ci * Ci);
+        const double cm = 1.0 / (Cr * Cr + Ci * Ci);
         double ur = br + (ar * Cr + ai * Ci) * cm;
         double ui = bi + (ai * Cr - ar * Ci) * cm;
         if (ur == 0.0 && ui == 0.0) ur = TINY;
         Cr = ur;
         Ci = ui;
-        double dm = 1.0 / (tr * tr + ti * ti);
-        Dr = tr * dm;
-        Di = -ti * dm;
-        double er = Cr * Dr - Ci * Di;
-        double ei = Cr * Di + Ci * Dr;
-        double nfr = fr * er - fi * ei;
-        fi = fr * ei + fi * er;
-        fr = nfr;
+        const double er = Cr * Dr - Ci * Di;
+        const double ei = Cr * Di + Ci * Dr;
         if (fabs(er - 1.0) + fabs(ei) < CF_TOL) break;
     }
     if (n >= CF_MAXIT) return 0;
-    // bottom-up evaluation from depth 2n + 20
     const int N = 2 * n + 20;
     double vr = 0.0, vi = 0.0;
     for (int m_ = N; m_ >= 1; --m_) {
-        double m = m_;
-        double ar = m * (m - 1.0) - eta * eta;
-        double ai = eta * (2.0 * m - 1.0);
-        double dr = br + vr;
-        double di = 2.0 * m + vi;
-        double dm = 1.0 / (dr * dr + di * di);
+        const double m = m_;
+        const double ar = m * (m - 1.0) - eta * eta;
+        const double ai = eta * (2.0 * m - 1.0);
+        const double dr = br + vr;
+        const double di = 2.0 * m + vi;
+        const double dm = 1.0 / (dr * dr + di * di);
         vr = (ar * dr + ai * di) * dm;
         vi = (ai * dr - ar * di) * dm;
     }
@@ -136,30 +135,29 @@ __device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
 }
 
 // Closed-channel log-derivative (r-units) at l = L0 from CF2 at imaginary k.
+// Depth from forward Lentz on the tail b_1 - a_2/(b_2 - a_3/(...)).
 __device__ int cf2_closed(int L0, double nu, double kap, double a, double *y)
 {
     const double base = kap * a - nu;
     auto an = [&](int m) { return (L0 + m - nu) * (m - 1.0 - L0 - nu); };
-    // forward Lentz on K(A_n / b_n), A_1 = a_1, A_n = -a_n, b_n = 2(base + n)
-    double f = TINY, C = f, D = 0.0;
-    int n = 1;
+    double C = 2.0 * (base + 1.0), D = 0.0;
+    if (C == 0.0) C = TINY;
+    int n = 2;
     for (; n < CF_MAXIT; ++n) {
-        double A = (n == 1) ? an(1) : -an(n);
-        double B = 2.0 * (base + n);
+        const double A = -an(n);
+        const double B = 2.0 * (base + n);
         D = B + A * D;
         if (D == 0.0) D = TINY;
         C = B + A / C;
         if (C == 0.0) C = TINY;
         D = 1.0 / D;
-        double delta = C * D;
-        f *= delta;
-        if (fabs(delta - 1.0) < CF_TOL) break;
+        if (fabs(C * D - 1.0) < CF_TOL) break;
     }
     if (n >= CF_MAXIT) return 0;
     const int N = 2 * n + 20;
     double v = 0.0;
     for (int m = N; m >= 2; --m) v = -an(m) / (2.0 * (base + m) + v);
-    double phi = an(1) / (2.0 * (base + 1.0) + v);
+    const double phi = an(1) / (2.0 * (base + 1.0) + v);
     *y = -kap + (nu + phi) / a;
     return 1;
 }
