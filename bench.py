@@ -178,7 +178,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
-    pws, Eall = synth.workload_64ch(N_E * world)
+    pws, Eall = synth.workload_64ch(args.energies * world)
     pw = pws[0]
     E = np.ascontiguousarray(Eall[rank::world])
     n, N = pw["W"].shape
@@ -302,6 +302,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=list(PREC))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--energies", type=int, default=N_E,
+                    help="energies per GPU (smaller only for profiler captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

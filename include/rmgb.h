@@ -123,7 +123,7 @@ int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, doub
  * (RM_EGRID otherwise). Optional outputs (NULL to skip), all device:
  *   K_out      [n_E][n_ch*n_ch]: K_ab at K_out[e*n_ch*n_ch + a*n_ch + b],
  *              a, b < n_open[e] (open channels in ascending order)
- *   n_open_out [n_E]
+ *   n_open_out [n_E] number of channels with E > e_i (every energy)
  *   status_out [n_E] per-energy RM_OK / RM_E* (non-negative) codes
  * Asynchronous on the context stream. Errors: RM_EINVAL, RM_ENOTLOADED,
  * RM_EGRID, RM_EUNSUPPORTED, RM_ENOMEM, RM_ECUDA. */

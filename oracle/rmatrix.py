@@ -245,17 +245,19 @@ def solve_energy(pw, E, mode=MODE_DIRECT, eps_thr=1e-10, fnumin=0.0, margin=0.1)
 
 def solve_energies(pw, E, mode=MODE_DIRECT, **kw):
     """All energies of one partial wave. Returns dict with status (n_E,),
-    n_open (n_E,), K (list of arrays or None), omega (n_E, n_tri)."""
+    n_open (n_E,) = number of channels with E > e_i (for every energy, failed
+    or not), K (list of arrays or None), omega (n_E, n_tri)."""
     E = np.asarray(E, dtype=np.float64)
     nlev = int(pw["n_levels"])
     om = np.zeros((E.size, nlev * (nlev + 1) // 2))
     st = np.zeros(E.size, dtype=np.int32)
     no = np.zeros(E.size, dtype=np.int32)
     Ks = []
+    e_thr = np.asarray(pw["e_thr"], dtype=np.float64)
     for m, Em in enumerate(E):
         s, K, oi, row = solve_energy(pw, float(Em), mode, **kw)
         st[m] = s
-        no[m] = 0 if oi is None else len(oi)
+        no[m] = int(np.sum(Em - e_thr > 0))
         Ks.append(K)
         om[m] = row
     return dict(status=st, n_open=no, K=Ks, omega=om)
