@@ -174,6 +174,34 @@ int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *R_out);
 int rm_profile_enable(rm_ctx *ctx, int enable);
 int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms);
 
+/* Allocation-free K-matrices (no counterpart in the paper: a deployment
+ * convenience). For callers that cannot let the library call cudaMalloc --
+ * code whose GPU memory belongs entirely to another allocator, or a
+ * latency-bound loop that cannot take the device-wide synchronisation of
+ * cudaMalloc/cudaFree. Needs no context; computes, like rm_solve_energies in
+ * RM_DIRECT mode with RM_FP64 formation, the open-channel K-matrices of one
+ * partial wave at n_E energies, and writes no Omega.
+ * Inputs, all device memory of `device`: E_k [n_poles] sorted ascending (the
+ * near-pole check assumes it), W [n_ch][n_poles] row-major, e_thr [n_ch],
+ * l [n_ch], E [n_E]; scalars z, a, b, eps_thr as in rm_set_channels /
+ * rm_load_poles / rm_opts. Outputs (device): K_out [n_E][n_ch*n_ch] (NULL to
+ * skip), n_open_out [n_E] (NULL to skip), status_out [n_E] (required).
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * The library allocates nothing for it: its workspace is one static 32 MiB
+ * device array per GPU, held from library load until process exit. The
+ * first call on a device looks up that array's device address; make that
+ * first call before any stream capture. Every call shares the array, so
+ * calls whose work overlaps on the GPU (different streams, threads or
+ * processes sharing a context) race and must be serialised by the caller.
+ * Limits: n_ch <= 96 (RM_EUNSUPPORTED beyond). errbuf (may be NULL) receives
+ * a one-line reason on error. Returns RM_SUCCESS, RM_EINVAL,
+ * RM_EUNSUPPORTED or RM_ECUDA. */
+int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E, const double *E_k,
+                          const double *W, const double *e_thr, const int *l, double z,
+                          double a, double b, const double *E, double eps_thr, double *K_out,
+                          int *n_open_out, int *status_out, void *stream, char *errbuf,
+                          size_t errlen);
+
 /* Waits for all work enqueued on the context's stream. */
 int rm_sync(rm_ctx *ctx);
 
