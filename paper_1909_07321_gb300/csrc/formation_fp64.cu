@@ -1,9 +1,10 @@
 // Step (a), FP64: R_ij(E) = (1/2a) sum_k w_ik w_jk / (E_k - E)  (Section "Overview",
-// Eq. rmatrix), one symmetric n x n matrix per energy, written in full.
+// Eq. rmatrix), the upper triangle of each energy's R in the packed layout
+// (tri_idx, stride tri_ld(n)).
 //
 // This is the plain-FP64 baseline the mixed-precision path is measured
 // against. Only the upper triangle is computed (tiles with tile_j >= tile_i)
-// and mirrored, so every R is exactly symmetric. d_k = 1/(E_k - E) is formed
+// and stored, so every R is exactly symmetric. d_k = 1/(E_k - E) is formed
 // once per (tile, k) in shared memory and folded into the j-operand.
 #include "rm_internal.cuh"
 
@@ -27,9 +28,7 @@ __global__ void form_r_naive(PwDev pw, const double *__restrict__ E, int nE,
     double acc = 0.0;
     for (int k = 0; k < pw.N; ++k) acc = fma(wi[k], wj[k] / (pw.Ek[k] - x), acc);
     acc *= 0.5 / pw.a;
-    double *Re = R + (size_t)e * n * n;
-    Re[i * n + j] = acc;
-    Re[j * n + i] = acc;
+    R[(size_t)e * tri_ld(n) + tri_idx(i, j, n)] = acc;
 }
 
 constexpr int TB = 64;   // output tile
@@ -89,18 +88,14 @@ __global__ void __launch_bounds__(256) form_r_tiled(PwDev pw, const double *__re
         __syncthreads();
     }
     const double h = 0.5 / pw.a;
-    double *Re = R + (size_t)e * n * n;
+    double *Re = R + (size_t)e * tri_ld(n);
 #pragma unroll
     for (int a = 0; a < TT; ++a) {
         const int i = i0 + ty * TT + a;
 #pragma unroll
         for (int b = 0; b < TT; ++b) {
             const int j = j0 + tx * TT + b;
-            if (i < n && j < n && i <= j) {
-                const double v = acc[a][b] * h;
-                Re[(size_t)i * n + j] = v;
-                Re[(size_t)j * n + i] = v;
-            }
+            if (i < n && j < n && i <= j) Re[tri_idx(i, j, n)] = acc[a][b] * h;
         }
     }
 }

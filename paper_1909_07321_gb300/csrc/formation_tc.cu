@@ -1,0 +1,550 @@
+// Step (a) in mixed precision on tcgen05 tensor cores (Section "Overview",
+// Eq. rmatrix, split as the spec precision plan asks: bulk products in
+// low precision with FP32 accumulation, near-pole terms in FP64).
+//
+// For every energy e of a block and every channel pair p = (i <= j):
+//   R_packed[e][p] = sum_k D[e][k] P[p][k],   D[e][k] = 1/(E_k - E_e),
+//                                             P[p][k] = w_ik w_jk / (2a),
+// one GEMM over all energies of the block (M = energies, N = pairs,
+// K = poles). Both operands are split x = hi + lo with hi, lo in the MMA
+// input type (bf16, or tf32 carried in fp32), and the product is taken as
+// hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory; lo*lo is
+// dropped. Terms with |E_k - E_e| < delta are zeroed in D and added later in
+// FP64 by the near-pole fix-up kernel.
+//
+// Kernel layout (one persistent CTA per SM, 192 threads):
+//   warp 0, one lane : TMA producer (D tile 128 x BK, P tile 256 x BK, hi and
+//                      lo, 128-byte swizzle) into a 2-stage ring,
+//   warp 1           : allocates 512 TMEM columns; one lane issues
+//                      tcgen05.mma (M = 128, N = 256) into one of two
+//                      accumulators,
+//   warps 2..5       : epilogue; each reads its 32-lane quadrant of the
+//                      accumulator with tcgen05.ld, converts to FP64 and
+//                      stores R_packed rows.
+// Every mbarrier wait is bounded (about 2 s by %globaltimer); a wait that
+// gives up sets *err_flag, and every role then drains and exits, so the host
+// sees an error instead of a hung GPU.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "rm_internal.cuh"
+
+namespace rmgb {
+namespace {
+
+constexpr int BM = 128;            // energies per tile (TMEM lanes)
+constexpr int BN = 256;            // pairs per tile (TMEM columns)
+constexpr int STAGES = 2;
+constexpr int NTHREADS = 192;
+constexpr int ROW_BYTES = 128;     // one K-row of an operand tile (swizzle span)
+constexpr int A_TILE = BM * ROW_BYTES;   // 16 KB
+constexpr int B_TILE = BN * ROW_BYTES;   // 32 KB
+constexpr int STAGE_BYTES = 2 * (A_TILE + B_TILE);   // hi + lo of both: 96 KB
+constexpr int TMEM_COLS = 512;     // two 256-column accumulators
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits until the phase of `bar` with the given parity has completed. Gives
+// up (returns false, sets *err when err is not null) after WAIT_LIMIT_NS, or
+// as soon as another role has set *err.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63) == 0) {
+            if (err && *(volatile int *)err) return false;
+            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                if (err) atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, uint64_t *bar,
+                                            int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// K-major operand in 128-byte-swizzled rows (as the TMA writes it): 8-row
+// groups 1024 bytes apart (stride-dimension offset), fixed-constant field 1,
+// swizzle mode 2 (128 B).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
+{
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B format
+// (bits 7-9, 10-12: bf16 = 1 for kind::f16, tf32 = 2 for kind::tf32), both
+// K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+template <int KIND> __device__ __forceinline__ uint32_t idesc()
+{
+    constexpr uint32_t fmt = (KIND == TC_BF16X3) ? 1u : 2u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
+                                     uint32_t accumulate)
+{
+    if constexpr (KIND == TC_BF16X3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(id), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(id), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+        "%30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    form_r_tc_kernel(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
+                     const __grid_constant__ CUtensorMap tmPh, const __grid_constant__ CUtensorMap tmPl,
+                     double *__restrict__ Rp, int ldR, int nE, int n_pairs, int n_kb, int n_ntiles,
+                     int n_tiles, int *err_flag)
+{
+    extern __shared__ uint8_t smem_raw[];
+    // 1024-byte alignment for the 128-byte swizzle atoms
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint64_t *acce = accf + 2;
+    uint64_t *done = acce + 2;
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 4);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            int stage = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
+                const int m0 = (t / n_ntiles) * BM, n0 = (t % n_ntiles) * BN;
+                for (int kb = 0; kb < n_kb; ++kb) {
+                    if (!mbar_wait(&empty[stage], ph ^ 1u, err_flag)) { ok = false; break; }
+                    uint8_t *st = smem + stage * STAGE_BYTES;
+                    mbar_expect_tx(&full[stage], STAGE_BYTES);
+                    const int kx = kb * (ROW_BYTES / (KIND == TC_BF16X3 ? 2 : 4));
+                    tma_load_2d(smem_u32(st), &tmDh, &full[stage], kx, m0);
+                    tma_load_2d(smem_u32(st + A_TILE), &tmDl, &full[stage], kx, m0);
+                    tma_load_2d(smem_u32(st + 2 * A_TILE), &tmPh, &full[stage], kx, n0);
+                    tma_load_2d(smem_u32(st + 2 * A_TILE + B_TILE), &tmPl, &full[stage], kx, n0);
+                    if (++stage == STAGES) { stage = 0; ph ^= 1u; }
+                }
+            }
+            if (!ok) {
+                // let copies already in flight land before the CTA exits
+                const unsigned long long t0 = globaltimer();
+                while (globaltimer() - t0 < 2000000ull) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            const uint32_t id = idesc<KIND>();
+            int stage = 0;
+            uint32_t ph = 0;
+            int acc = 0;
+            uint32_t aph = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < n_tiles; t += gridDim.x) {
+                if (!mbar_wait(&acce[acc], aph ^ 1u, err_flag)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < n_kb; ++kb) {
+                    if (!mbar_wait(&full[stage], ph, err_flag)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t st = smem_u32(smem + stage * STAGE_BYTES);
+                    const uint64_t ah = sdesc_sw128(st), al = sdesc_sw128(st + A_TILE);
+                    const uint64_t bh = sdesc_sw128(st + 2 * A_TILE);
+                    const uint64_t bl = sdesc_sw128(st + 2 * A_TILE + B_TILE);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint64_t o = (uint64_t)(ks * 32) >> 4;   // 32 bytes of K per MMA
+                        umma<KIND>(d_tmem, ah + o, bh + o, id, (kb | ks) != 0);
+                        umma<KIND>(d_tmem, ah + o, bl + o, id, 1u);
+                        umma<KIND>(d_tmem, al + o, bh + o, id, 1u);
+                    }
+                    umma_commit(&empty[stage]);
+                    if (++stage == STAGES) { stage = 0; ph ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit(&accf[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1u; }
+            }
+            // all MMAs issued by this thread complete before TMEM is freed
+            umma_commit(done);
+            mbar_wait(done, 0, nullptr);
+        }
+    } else {
+        // ---- epilogue: warps 2..5 -> TMEM lane quadrant warp % 4 ----
+        const int quad = warp & 3;
+        int acc = 0;
+        uint32_t aph = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            if (!mbar_wait(&accf[acc], aph, err_flag)) break;
+            tc_fence_after();
+            const int m0 = (t / n_ntiles) * BM, n0 = (t % n_ntiles) * BN;
+            const int e = m0 + quad * 32 + lane;
+            double *row = Rp + (size_t)e * ldR;
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem + (uint32_t)(acc * BN + c0) + ((uint32_t)(quad * 32) << 16), r);
+                if (e < nE) {
+                    const int p0 = n0 + c0;
+                    if (p0 + 32 <= n_pairs) {
+#pragma unroll
+                        for (int j = 0; j < 32; j += 2) {
+                            double2 v = make_double2((double)__uint_as_float(r[j]),
+                                                     (double)__uint_as_float(r[j + 1]));
+                            *reinterpret_cast<double2 *>(row + p0 + j) = v;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (p0 + j < n_pairs) row[p0 + j] = (double)__uint_as_float(r[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[acc]);
+            if (++acc == 2) { acc = 0; aph ^= 1u; }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// ---- operand preparation ---------------------------------------------------
+
+__device__ __forceinline__ void split_store(double x, int kind, void *hi, void *lo, size_t idx)
+{
+    const float f = (float)x;
+    if (kind == TC_BF16X3) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(f);
+        const __nv_bfloat16 l = __float2bfloat16_rn(f - __bfloat162float(h));
+        static_cast<__nv_bfloat16 *>(hi)[idx] = h;
+        static_cast<__nv_bfloat16 *>(lo)[idx] = l;
+    } else {
+        uint32_t hb;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(f));
+        const float h = __uint_as_float(hb);
+        static_cast<float *>(hi)[idx] = h;
+        static_cast<float *>(lo)[idx] = f - h;
+    }
+}
+
+__global__ void split_p_kernel(PwDev pw, int kind, int Kpad, void *Ph, void *Pl)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int np = tri_count(pw.n);
+    if (idx >= (long long)np * Kpad) return;
+    const int p = (int)(idx / Kpad), k = (int)(idx - (long long)p * Kpad);
+    // invert the row-wise pair index
+    int i = 0, rem = p;
+    while (rem >= pw.n - i) { rem -= pw.n - i; ++i; }
+    const int j = i + rem;
+    const double v = (k < pw.N) ? pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] * (0.5 / pw.a) : 0.0;
+    split_store(v, kind, Ph, Pl, (size_t)idx);
+}
+
+__global__ void split_d_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta,
+                               int kind, int Kpad, void *Dh, void *Dl)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nE * Kpad) return;
+    const int e = (int)(idx / Kpad), k = (int)(idx - (long long)e * Kpad);
+    double d = 0.0;
+    if (k < pw.N) {
+        const double den = pw.Ek[k] - E[e];
+        if (fabs(den) >= delta) d = 1.0 / den;
+    }
+    split_store(d, kind, Dh, Dl, (size_t)idx);
+}
+
+// One warp per energy: the poles within delta of E (sorted E_k, binary
+// search), then every pair adds its FP64 terms.
+__global__ void near_pole_fixup_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta,
+                                       double *__restrict__ Rp)
+{
+    const int e = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= nE) return;
+    const double x = E[e];
+    int lo = 0, hi = pw.N;
+    while (lo < hi) {          // first k with E_k > x - delta
+        const int mid = (lo + hi) >> 1;
+        if (pw.Ek[mid] <= x - delta) lo = mid + 1; else hi = mid;
+    }
+    int k0 = lo, k1 = lo;
+    while (k1 < pw.N && pw.Ek[k1] < x + delta) ++k1;
+    // same exclusion test as split_d_kernel
+    bool any = false;
+    for (int k = k0; k < k1; ++k) any |= fabs(pw.Ek[k] - x) < delta;
+    if (!any) return;
+    const int n = pw.n, np = tri_count(n);
+    const double h = 0.5 / pw.a;
+    double *row = Rp + (size_t)e * tri_ld(n);
+    for (int p = lane; p < np; p += 32) {
+        int i = 0, rem = p;
+        while (rem >= n - i) { rem -= n - i; ++i; }
+        const int j = i + rem;
+        double s = 0.0;
+        for (int k = k0; k < k1; ++k) {
+            const double den = pw.Ek[k] - x;
+            if (fabs(den) < delta) s += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+        }
+        row[p] += h * s;
+    }
+}
+
+__global__ void unpack_r_kernel(int n, int nE, const double *__restrict__ Rp, double *__restrict__ R)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nE * n * n) return;
+    const int e = (int)(idx / ((long long)n * n));
+    const int ij = (int)(idx - (long long)e * n * n);
+    const int i = ij / n, j = ij - (ij / n) * n;
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    R[idx] = Rp[(size_t)e * tri_ld(n) + tri_idx(a, b, n)];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D K-major operand map: rows x Kpad elements, box (128 bytes of K) x box_rows.
+bool make_map(CUtensorMap *m, const void *base, int kind, int Kpad, int rows, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const int es = (kind == TC_BF16X3) ? 2 : 4;
+    cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kpad * es};
+    cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / es), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, kind == TC_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                    2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int num_sms()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 1;
+        }
+    }
+    return n;
+}
+
+}  // namespace
+
+int tc_kpad(int N, int kind)
+{
+    const int bk = ROW_BYTES / ((kind == TC_BF16X3) ? 2 : 4);
+    return ((N + bk - 1) / bk) * bk;
+}
+
+cudaError_t launch_split_p(const PwDev &pw, int kind, int Kpad, void *P_hi, void *P_lo, cudaStream_t s)
+{
+    const long long total = (long long)tri_count(pw.n) * Kpad;
+    split_p_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pw, kind, Kpad, P_hi, P_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delta, int kind, int Kpad,
+                           void *D_hi, void *D_lo, cudaStream_t s)
+{
+    const long long total = (long long)nE * Kpad;
+    if (total == 0) return cudaSuccess;
+    split_d_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pw, E, nE, delta, kind, Kpad,
+                                                                    D_hi, D_lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
+                             const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
+                             int *err_flag, cudaStream_t s)
+{
+    if (nE == 0) return cudaSuccess;
+    CUtensorMap mDh, mDl, mPh, mPl;
+    if (!make_map(&mDh, D_hi, kind, Kpad, nE, BM) || !make_map(&mDl, D_lo, kind, Kpad, nE, BM) ||
+        !make_map(&mPh, P_hi, kind, Kpad, n_pairs, BN) || !make_map(&mPl, P_lo, kind, Kpad, n_pairs, BN))
+        return cudaErrorInvalidValue;
+    const int bk = ROW_BYTES / ((kind == TC_BF16X3) ? 2 : 4);
+    const int n_kb = Kpad / bk;
+    const int n_mt = (nE + BM - 1) / BM, n_nt = (n_pairs + BN - 1) / BN;
+    const int n_tiles = n_mt * n_nt;
+    const int grid = n_tiles < num_sms() ? n_tiles : num_sms();
+    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+    cudaError_t e;
+    if (kind == TC_BF16X3) {
+        e = cudaFuncSetAttribute(form_r_tc_kernel<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        form_r_tc_kernel<TC_BF16X3><<<grid, NTHREADS, smem, s>>>(mDh, mDl, mPh, mPl, Rp, ldR, nE, n_pairs,
+                                                                 n_kb, n_nt, n_tiles, err_flag);
+    } else {
+        e = cudaFuncSetAttribute(form_r_tc_kernel<TC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        form_r_tc_kernel<TC_TF32X3><<<grid, NTHREADS, smem, s>>>(mDh, mDl, mPh, mPl, Rp, ldR, nE, n_pairs,
+                                                                 n_kb, n_nt, n_tiles, err_flag);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, double delta, double *Rp,
+                                   cudaStream_t s)
+{
+    if (nE == 0) return cudaSuccess;
+    const long long threads = (long long)nE * 32;
+    near_pole_fixup_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(pw, E, nE, delta, Rp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_r(int n, int nE, const double *Rp, double *R, cudaStream_t s)
+{
+    const long long total = (long long)nE * n * n;
+    if (total == 0) return cudaSuccess;
+    unpack_r_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, nE, Rp, R);
+    return cudaGetLastError();
+}
+
+}  // namespace rmgb

@@ -56,7 +56,7 @@ extern "C" int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E,
         return say(errbuf, errlen, RM_EINVAL, "need a > 0, z >= 0, eps_thr >= 0");
     if (device < 0 || device >= MAX_DEVICES)
         return say(errbuf, errlen, RM_EINVAL, "device %ld out of range", device);
-    const size_t per_energy = (size_t)n_ch * sizeof(ChanFn) + (size_t)n_ch * n_ch * sizeof(double);
+    const size_t per_energy = (size_t)n_ch * sizeof(ChanFn) + (size_t)tri_ld(n_ch) * sizeof(double);
     if (round_up(per_energy) + 512 > NOALLOC_SCRATCH_BYTES)
         return say(errbuf, errlen, RM_EUNSUPPORTED,
                    "one energy needs %ld bytes of workspace, more than the %ld-byte static array",
@@ -84,10 +84,10 @@ extern "C" int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E,
         scratch = g_scratch_addr[device];
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // Energies per chunk that fit the workspace: [ChanFn x chunk x n][R x chunk x n x n].
+    // Energies per chunk that fit the workspace: [ChanFn x chunk x n][packed R x chunk].
     size_t chunk = (NOALLOC_SCRATCH_BYTES - 512) / (per_energy + 1);
     while (chunk > 1 && round_up(chunk * n_ch * sizeof(ChanFn)) +
-                            chunk * (size_t)n_ch * n_ch * sizeof(double) > NOALLOC_SCRATCH_BYTES)
+                            chunk * (size_t)tri_ld(n_ch) * sizeof(double) > NOALLOC_SCRATCH_BYTES)
         --chunk;
     if (chunk > 32768) chunk = 32768;
     ChanFn *cf = static_cast<ChanFn *>(scratch);

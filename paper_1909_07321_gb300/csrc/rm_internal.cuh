@@ -24,6 +24,16 @@ struct __align__(16) MqdtFn {
     int pad;
 };
 
+// R is stored per energy as its upper triangle, row-wise:
+//   R_ij (i <= j) at tri_idx(i, j, n) = i n - i(i-1)/2 + (j - i),
+// with the per-energy stride rounded up to a multiple of 4 doubles.
+__host__ __device__ __forceinline__ int tri_count(int n) { return n * (n + 1) / 2; }
+__host__ __device__ __forceinline__ int tri_ld(int n) { return (tri_count(n) + 3) & ~3; }
+__host__ __device__ __forceinline__ int tri_idx(int i, int j, int n)
+{
+    return i * n - (i * (i - 1)) / 2 + (j - i);
+}
+
 // Device-side description of one partial wave.
 struct PwDev {
     int n;             // channels
@@ -56,6 +66,25 @@ cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const C
                                const MqdtFn *mq, const double *R, int mqdt, int *status,
                                double *K_out, int *n_open_out, double *omega, int n_tri,
                                cudaStream_t s);
+// Mixed-precision formation (tensor cores). Operand kinds:
+enum TcKind { TC_BF16X3 = 0, TC_TF32X3 = 1 };
+// Split of P_pk = w_ik w_jk / (2a) into hi/lo operands, [n_pairs][Kpad] K-major.
+cudaError_t launch_split_p(const PwDev &pw, int kind, int Kpad, void *P_hi, void *P_lo,
+                           cudaStream_t s);
+// Split of D_ek = 1/(E_k - E_e) (0 when |E_k - E_e| < delta) into hi/lo, [nE][Kpad].
+cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delta, int kind,
+                           int Kpad, void *D_hi, void *D_lo, cudaStream_t s);
+// R_packed[e][p] = sum_k D[e][k] P[p][k] over the three hi/lo products.
+cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
+                             const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
+                             int *err_flag, cudaStream_t s);
+// R_packed[e][p] += (1/2a) w_ik w_jk / (E_k - E_e) over poles with |E_k - E_e| < delta (FP64).
+cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, double delta,
+                                   double *Rp, cudaStream_t s);
+// Packed -> full symmetric [nE][n][n] (inspection only).
+cudaError_t launch_unpack_r(int n, int nE, const double *Rp, double *R, cudaStream_t s);
+int tc_kpad(int N, int kind);
+
 cudaError_t launch_chanfn_export(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                  double *out, cudaStream_t s);
 

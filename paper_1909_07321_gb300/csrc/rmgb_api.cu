@@ -55,11 +55,16 @@ struct PwHost {
     int n = 0, N = 0, n_levels = 0;
     double a = 0, b = 0, z = 0, g = 0;
     DevBuf Ek, W, e_thr, l, level, lev_start, lev_chan, lev_thr;
+    // mixed-precision operand P = w_i w_j / 2a, split hi/lo (built on first use)
+    DevBuf Ph, Pl;
+    int p_kind = -1, p_kpad = 0;
     std::vector<double> h_e_thr;
     void release()
     {
-        for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr}) d->release();
+        for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl})
+            d->release();
         loaded = channels = false;
+        p_kind = -1;
     }
     PwDev dev() const
     {
@@ -95,7 +100,7 @@ struct rm_ctx {
     std::vector<double> grid_host;
     DevBuf omega;
     // workspace
-    DevBuf wsE, wsCf, wsR, wsStatus, wsMq;
+    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr;
     long long launches = 0;
     // per-phase event pairs (tracing)
     bool prof = false;
@@ -256,7 +261,8 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaSetDevice(ctx->opts.device);
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
-    for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq})
+    for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
+                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
         for (auto &pr : ctx->ev[p]) {
@@ -293,6 +299,9 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
         for (int k = 0; k < n_poles; ++k) Ws[(size_t)i * n_poles + k] = W[(size_t)i * n_poles + ord[k]];
     P.Ek.release();
     P.W.release();
+    P.Ph.release();
+    P.Pl.release();
+    P.p_kind = -1;
     CK(upload(P.Ek, Es.data(), Es.size(), ctx->stream));
     CK(upload(P.W, Ws.data(), Ws.size(), ctx->stream));
     P.n = n_ch;
@@ -362,24 +371,91 @@ int device_energies(rm_ctx *ctx, int n_E, const double *E, const double **dE)
     return RM_SUCCESS;
 }
 
+int tc_kind(int precision) { return precision == RM_BF16X3 ? TC_BF16X3 : TC_TF32X3; }
+size_t tc_esize(int kind) { return kind == TC_BF16X3 ? 2 : 4; }
+
+// Largest n_pairs x Kpad operand (hi + lo) the Khatri-Rao formation keeps per
+// partial wave; larger waves need the per-energy formulation (not built).
+constexpr size_t MAX_P_BYTES = (size_t)4 << 30;
+
+int check_precision(rm_ctx *ctx, const PwHost &P)
+{
+    if (ctx->opts.precision == RM_FP64) return RM_SUCCESS;
+    const int kind = tc_kind(ctx->opts.precision);
+    const size_t bytes = (size_t)tri_count(P.n) * tc_kpad(P.N, kind) * tc_esize(kind) * 2;
+    if (bytes > MAX_P_BYTES)
+        return fail(ctx, RM_EUNSUPPORTED,
+                    "mixed-precision formation of n_ch=%d, n_poles=%d needs %zu bytes of pair "
+                    "operands (limit %zu)", P.n, P.N, bytes, MAX_P_BYTES);
+    return RM_SUCCESS;
+}
+
 int block_energies(rm_ctx *ctx, const PwHost &P)
 {
-    const size_t per = (size_t)P.n * P.n * sizeof(double) + (size_t)P.n * sizeof(ChanFn) + 64;
+    size_t per = (size_t)tri_ld(P.n) * sizeof(double) + (size_t)P.n * sizeof(ChanFn) + 64;
+    if (ctx->opts.precision != RM_FP64) {
+        const int kind = tc_kind(ctx->opts.precision);
+        per += 2 * (size_t)tc_kpad(P.N, kind) * tc_esize(kind);
+    }
     size_t B = ctx->opts.mem_budget / per;
     if (B < 1) B = 1;
     if (B > MAX_BLOCK_E) B = MAX_BLOCK_E;
     return (int)B;
 }
 
-int form_r_block(rm_ctx *ctx, const PwHost &P, const double *E, int nE, double *R)
+// Packed R of nE energies into R (stride tri_ld(n)), in the context's precision.
+int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
 {
     const PwDev d = P.dev();
-    if (ctx->opts.precision != RM_FP64)
-        return fail(ctx, RM_EUNSUPPORTED, "formation precision %d not built yet", ctx->opts.precision);
+    if (ctx->opts.precision == RM_FP64) {
+        CK(prof_begin(ctx, RM_PH_FORM));
+        CK(launch_form_r_fp64(d, E, nE, R, ctx->stream));
+        CK(prof_end(ctx, RM_PH_FORM));
+        ctx->launches++;
+        return RM_SUCCESS;
+    }
+    const int kind = tc_kind(ctx->opts.precision);
+    const int Kpad = tc_kpad(P.N, kind);
+    const size_t es = tc_esize(kind);
+    if (P.p_kind != kind) {
+        const size_t pb = (size_t)tri_count(P.n) * Kpad * es;
+        CK(P.Ph.reserve(pb));
+        CK(P.Pl.reserve(pb));
+        CK(launch_split_p(d, kind, Kpad, P.Ph.p, P.Pl.p, ctx->stream));
+        ctx->launches++;
+        P.p_kind = kind;
+        P.p_kpad = Kpad;
+    }
+    CK(ctx->wsDh.reserve((size_t)nE * Kpad * es));
+    CK(ctx->wsDl.reserve((size_t)nE * Kpad * es));
+    if (!ctx->wsErr.p) {
+        CK(ctx->wsErr.reserve(sizeof(int)));
+        CK(cudaMemsetAsync(ctx->wsErr.p, 0, sizeof(int), ctx->stream));
+    }
     CK(prof_begin(ctx, RM_PH_FORM));
-    CK(launch_form_r_fp64(d, E, nE, R, ctx->stream));
+    CK(launch_split_d(d, E, nE, ctx->opts.delta_pole, kind, Kpad, ctx->wsDh.p, ctx->wsDl.p,
+                      ctx->stream));
+    CK(launch_form_r_tc(kind, ctx->wsDh.p, ctx->wsDl.p, P.Ph.p, P.Pl.p, nE, tri_count(P.n), Kpad, R,
+                        tri_ld(P.n), ctx->wsErr.as<int>(), ctx->stream));
     CK(prof_end(ctx, RM_PH_FORM));
-    ctx->launches++;
+    CK(prof_begin(ctx, RM_PH_FIXUP));
+    CK(launch_near_pole_fixup(d, E, nE, ctx->opts.delta_pole, R, ctx->stream));
+    CK(prof_end(ctx, RM_PH_FIXUP));
+    ctx->launches += 3;
+    return RM_SUCCESS;
+}
+
+// After a synchronisation: a tensor-core kernel that gave up a bounded wait
+// left its flag set.
+int check_device_flag(rm_ctx *ctx)
+{
+    if (!ctx->wsErr.p) return RM_SUCCESS;
+    int f = 0;
+    CK(cudaMemcpy(&f, ctx->wsErr.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) {
+        CK(cudaMemset(ctx->wsErr.p, 0, sizeof(int)));
+        return fail(ctx, RM_ETIMEOUT, "a tensor-core formation kernel gave up a bounded wait");
+    }
     return RM_SUCCESS;
 }
 
@@ -393,10 +469,12 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
     if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
     if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
     if (mode == RM_MQDT) return fail(ctx, RM_EUNSUPPORTED, "MQDT mode not built yet");
-    const PwHost &P = ctx->pw[pw];
+    PwHost &P = ctx->pw[pw];
     if (P.n > solve_small_max_n())
         return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the solver limit %d", P.n,
                     solve_small_max_n());
+    rc = check_precision(ctx, P);
+    if (rc) return rc;
     CK(cudaSetDevice(ctx->opts.device));
     const bool dev_in = is_device_ptr(E);
     // grid registration / check
@@ -422,7 +500,7 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
     if (rc) return rc;
     const int B = std::min(n_E, block_energies(ctx, P));
     CK(ctx->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
-    CK(ctx->wsR.reserve((size_t)B * P.n * P.n * sizeof(double)));
+    CK(ctx->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
     int *dstatus = status_out;
     if (!dstatus) {
         CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
@@ -467,6 +545,8 @@ extern "C" int rm_collision_strengths(rm_ctx *ctx, double *omega_out, int reset)
     if (omega_out)
         CK(cudaMemcpyAsync(omega_out, ctx->omega.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    int rc = check_device_flag(ctx);
+    if (rc) return rc;
     if (reset) {
         ctx->grid_nE = ctx->grid_nlev = ctx->grid_ntri = 0;
         ctx->grid_host.clear();
@@ -549,11 +629,18 @@ extern "C" int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *
     if (!is_device_ptr(E) || !is_device_ptr(R_out))
         return fail(ctx, RM_EINVAL, "E and R_out must be device pointers");
     CK(cudaSetDevice(ctx->opts.device));
-    const PwHost &P = ctx->pw[pw];
-    for (int e0 = 0; e0 < n_E; e0 += MAX_BLOCK_E) {
-        const int nb = std::min(MAX_BLOCK_E, n_E - e0);
-        rc = form_r_block(ctx, P, E + e0, nb, R_out + (size_t)e0 * P.n * P.n);
+    PwHost &P = ctx->pw[pw];
+    rc = check_precision(ctx, P);
+    if (rc) return rc;
+    const int B = std::min(n_E, block_energies(ctx, P));
+    CK(ctx->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
+    for (int e0 = 0; e0 < n_E; e0 += B) {
+        const int nb = std::min(B, n_E - e0);
+        rc = form_r_block(ctx, P, E + e0, nb, ctx->wsR.as<double>());
         if (rc) return rc;
+        CK(launch_unpack_r(P.n, nb, ctx->wsR.as<double>(), R_out + (size_t)e0 * P.n * P.n,
+                           ctx->stream));
+        ctx->launches++;
     }
     return RM_SUCCESS;
 }
@@ -562,7 +649,7 @@ extern "C" int rm_sync(rm_ctx *ctx)
 {
     if (!ctx) return RM_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
-    return RM_SUCCESS;
+    return check_device_flag(ctx);
 }
 
 extern "C" long long rm_launch_count(rm_ctx *ctx) { return ctx ? ctx->launches : 0; }

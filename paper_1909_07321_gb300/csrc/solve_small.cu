@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     const int lane = tid & 31, warp = tid >> 5;
     const double x = E[e];
     const ChanFn *cf = cfa + (size_t)e * n;
-    const double *R = Ra + (size_t)e * n * n;
+    const double *Rp = Ra + (size_t)e * tri_ld(n);   // packed upper triangle
 
     if (tid == 0) {
         int no = 0;
@@ -81,12 +81,12 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         if (c < n) {
             const int j = col_chan[c];
             const ChanFn cj = cf[j];
-            v = -R[r * n + j] * (a * cj.ghp - b * cj.gh);
+            v = -Rp[r <= j ? tri_idx(r, j, n) : tri_idx(j, r, n)] * (a * cj.ghp - b * cj.gh);
             if (r == j) v += cj.gh;
         } else {
             const int o = col_chan[nc + (c - n)];
             const ChanFn co = cf[o];
-            v = R[r * n + o] * (a * co.sp - b * co.s);
+            v = Rp[r <= o ? tri_idx(r, o, n) : tri_idx(o, r, n)] * (a * co.sp - b * co.s);
             if (r == o) v -= co.s;
         }
         M[r * ld + c] = v;
