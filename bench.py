@@ -38,7 +38,7 @@ N_E = 20000
 # clock over 152 SMs is 4 FP64 flops per clock per SM (2 DFMA).
 FP64_FLOPS_PER_CLK_SM = 4.0
 N_SM = 152
-PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}
+PREC = {"fp64": 0, "fp32": 1, "bf16x3": 2}   # fp32 = 3xTF32 on tensor cores
 
 
 def _peaks():
@@ -163,6 +163,37 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _time_steps(ctx, Ed, stream, flush, steps, rmgb, torch):
+    """Times `steps` full steps (reset + solve of every energy) with CUDA events
+    on the library's stream, flushing L2 before each; returns (ms per step,
+    per-phase (launches, ms), kernel launches)."""
+    ctx.profile_enable(True)
+    l0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for s in range(steps):
+        flush.zero_()
+        ev[s][0].record(stream)
+        ctx.reset_omega()
+        ctx.solve_energies(0, Ed)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    phase = {p: ctx.profile_get(p) for p in range(rmgb.RM_PH_COUNT)}
+    ctx.profile_enable(False)
+    return sum(step_ms) / len(step_ms), phase, launches
+
+
+def _solve_flops(n, n_open):
+    """Algorithmic FP64 flops of steps (c)+(d) for one energy: elimination of
+    the n x (n + n_o) system (2/3 n^3 + 2 n^2 n_o), then M = 1 + K^2 (2 n_o^3),
+    Cholesky (n_o^3/3), X = M^{-1} K (2 n_o^3), Y = K X (2 n_o^3)."""
+    no = n_open.astype(np.float64)
+    return float(np.sum(2.0 / 3.0 * n**3 + 2.0 * n * n * no + (6.0 + 1.0 / 3.0) * no**3))
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -182,18 +213,27 @@ def run_ours(args, rank, world, local_rank):
     pw = pws[0]
     E = np.ascontiguousarray(Eall[rank::world])
     n, N = pw["W"].shape
+    n_tri = pw["n_levels"] * (pw["n_levels"] + 1) // 2
     prec = PREC[args.precision]
     dist = world > 1
     if dist:
         import torch.distributed as tdist
 
-    ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, device=local_rank)
-    ctx.load_pw(0, pw)
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
     Ed = torch.tensor(E, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, device=local_rank)
+    ctx.load_pw(0, pw)
+    n_open = torch.zeros(E.size, dtype=torch.int32, device=dev)
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 1)):
-            ctx.solve_energies(0, Ed)
+            ctx.solve_energies(0, Ed, 0, None, n_open)
             ctx.reset_omega()
         torch.cuda.synchronize()
         if dist:
@@ -202,33 +242,14 @@ def run_ours(args, rank, world, local_rank):
         clk = ClockSampler("GPU-%s" % props.uuid if getattr(props, "uuid", None) else local_rank)
         clk.start()
         time.sleep(0.3)
-        ctx.profile_enable(True)
-        l0 = ctx.launch_count()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
-        torch.cuda.synchronize()
-        for s in range(args.steps):
-            flush.zero_()
-            ev[s][0].record(stream)
-            ctx.reset_omega()
-            ctx.solve_energies(0, Ed)
-            ev[s][1].record(stream)
-        torch.cuda.synchronize()
-        launches = ctx.launch_count() - l0
-        step_ms = [a.elapsed_time(b) for a, b in ev]
-        phase = {p: ctx.profile_get(p) for p in range(rmgb.RM_PH_COUNT)}
-        ctx.profile_enable(False)
+        t_step, phase, launches = _time_steps(ctx, Ed, stream, flush, args.steps, rmgb, torch)
         clocks = clk.stop()
-        t_step = sum(step_ms) / len(step_ms)
-        if dist:
-            t = torch.tensor([t_step], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            t_step = float(t.item())
+        t_step = max_over_ranks(t_step)
         value = world * E.size / (t_step * 1e-3)
+        om_main = ctx.collision_strengths()      # Omega of the last timed step
 
         # end to end through the public API with host buffers
         E_pin = torch.tensor(E, dtype=torch.float64).pin_memory()
-        n_tri = pw["n_levels"] * (pw["n_levels"] + 1) // 2
         om_pin = torch.empty((E.size, n_tri), dtype=torch.float64).pin_memory()
         ctx.collision_strengths(reset=True)
         torch.cuda.synchronize()
@@ -239,33 +260,68 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(k2):
             ctx.solve_energies(0, E_pin.numpy())
             ctx.collision_strengths(om_pin.numpy(), reset=True)
-        e2e_s = (time.perf_counter() - t0) / k2
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / k2)
     ctx.close()
+
+    # the plain FP64 GPU path on the same workload (the metric's comparison)
+    fp64 = None
+    if prec != 0 and not args.no_fp64_compare:
+        ctx64 = rmgb.Context(precision=0, stream=stream.cuda_stream, device=local_rank)
+        ctx64.load_pw(0, pw)
+        with torch.cuda.stream(stream):
+            ctx64.solve_energies(0, Ed)
+            ctx64.reset_omega()
+            t64, ph64, _ = _time_steps(ctx64, Ed, stream, flush, max(2, args.steps // 3), rmgb, torch)
+            om64 = ctx64.collision_strengths()
+        ctx64.close()
+        t64 = max_over_ranks(t64)
+        rel = np.linalg.norm(om_main - om64, axis=1) / np.maximum(np.linalg.norm(om64, axis=1), 1e-300)
+        fp64 = {"value": world * E.size / (t64 * 1e-3), "ms_per_step": t64,
+                "omega_rel_err_vs_fp64": {"median": float(np.median(rel)),
+                                          "p99": float(np.quantile(rel, 0.99)),
+                                          "max": float(rel.max())}}
 
     if rank != 0:
         return
     peaks, peak_src = _peaks()
-    # dominant kernel: R formation. Algorithmic work n(n+1)/2 MACs per pole
-    # per energy = n(n+1) N flops per energy.
-    form_n, form_ms = phase[rmgb.RM_PH_FORM]
-    flops_per_launch = n * (n + 1) * N * (E.size / max(1, form_n / args.steps))
-    achieved = flops_per_launch / (form_ms / max(form_n, 1) * 1e-3) / 1e12
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp64_peak = N_SM * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    names = {rmgb.RM_PH_NEARPOLE: "nearpole", rmgb.RM_PH_CHANFN: "chanfn", rmgb.RM_PH_FORM: "form",
+             rmgb.RM_PH_FIXUP: "fixup", rmgb.RM_PH_SOLVE: "solve", rmgb.RM_PH_SPLIT: "split"}
+    total_phase_ms = sum(v[1] for v in phase.values())
+    share = {names[p]: (phase[p][1] / total_phase_ms if total_phase_ms else None) for p in names}
+
+    def per_launch_ms(p):
+        return phase[p][1] / max(phase[p][0], 1)
+
+    # formation kernel: algorithmic n(n+1)/2 MACs per pole per energy
+    form_flops = n * (n + 1) * N * (E.size / max(1, phase[rmgb.RM_PH_FORM][0] / args.steps))
+    form_ach = form_flops / (per_launch_ms(rmgb.RM_PH_FORM) * 1e-3) / 1e12
     if prec == 0:
-        peak = N_SM * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "form_r_tiled (FP64)",
+        form_roof = {"bound": "alu", "achieved": form_ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": form_ach / fp64_peak, "traffic": None, "kernel": "form_r_tiled (FP64)",
+                     "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"}
+    else:
+        tpk = peaks["bf16_tflops"] if prec == 2 else peaks["bf16_tflops"] / 2.0
+        issued = 3.0 * form_ach
+        form_roof = {"bound": "tensor", "achieved": form_ach, "peak": tpk, "unit": "TFLOP/s",
+                     "frac": form_ach / tpk, "issued_frac": issued / tpk, "traffic": None,
+                     "kernel": "form_r_tc_kernel (%s)" % args.precision,
+                     "peak_source": ("bf16 dense burst, %s" % peak_src) if prec == 2 else
+                     ("tf32 = bf16 dense burst (%s) x nominal ratio 1/2" % peak_src)}
+    # dominant kernel by device time
+    dom = max((rmgb.RM_PH_FORM, rmgb.RM_PH_SOLVE, rmgb.RM_PH_CHANFN), key=lambda p: phase[p][1])
+    if dom == rmgb.RM_PH_FORM:
+        roof = form_roof
+    elif dom == rmgb.RM_PH_SOLVE:
+        fl = _solve_flops(n, n_open.cpu().numpy()) / max(1, phase[rmgb.RM_PH_SOLVE][0] / args.steps)
+        ach = fl / (per_launch_ms(rmgb.RM_PH_SOLVE) * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None, "kernel": "solve_small_kernel (FP64)",
                 "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"}
     else:
-        peak = peaks["bf16_tflops"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "formation",
-                "peak_source": "bf16 burst (%s)" % peak_src}
-    total_phase_ms = sum(v[1] for v in phase.values())
+        roof = {"bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": "chanfn_kernel (FP64 continued fractions)"}
     cpu = None
     if pool is not None:
         v, sample = oracle_throughput(pool, n_cores, 24)
@@ -276,16 +332,13 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_channels": n, "n_poles": N,
                        "energies_per_gpu": int(E.size), "formation": args.precision,
-                       "mode": "direct", "l2": "flushed between timed steps (256 MB write)",
+                       "near_pole_delta_ry": 1e-3, "mode": "direct",
+                       "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "energy-interleaved dp%d" % world},
-            "roofline": roof,
-            "phases_ms_per_step": {name: phase[p][1] / args.steps for name, p in
-                                   [("nearpole", rmgb.RM_PH_NEARPOLE), ("chanfn", rmgb.RM_PH_CHANFN),
-                                    ("form", rmgb.RM_PH_FORM), ("fixup", rmgb.RM_PH_FIXUP),
-                                    ("solve", rmgb.RM_PH_SOLVE)]},
-            "phase_share": {k: (phase[p][1] / total_phase_ms if total_phase_ms else None)
-                            for k, p in [("form", rmgb.RM_PH_FORM), ("solve", rmgb.RM_PH_SOLVE),
-                                         ("chanfn", rmgb.RM_PH_CHANFN)]},
+            "roofline": roof, "formation_roofline": form_roof,
+            "phases_ms_per_step": {names[p]: phase[p][1] / args.steps for p in names},
+            "phase_share": share,
+            "fp64_path": fp64,
             "cpu_baseline": cpu,
             "e2e": {"value": world * E.size / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(E.size * 8),
@@ -300,7 +353,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PREC))
+    ap.add_argument("--precision", default="bf16x3", choices=list(PREC))
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the plain FP64 path beside the chosen precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--energies", type=int, default=N_E,
                     help="energies per GPU (smaller only for profiler captures)")

@@ -167,10 +167,11 @@ int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *R_out);
  * enable. Phases: */
 #define RM_PH_NEARPOLE    0   /* near-pole check */
 #define RM_PH_CHANFN      1   /* step (b) channel functions */
-#define RM_PH_FORM        2   /* step (a) R formation (all precisions) */
+#define RM_PH_FORM        2   /* step (a) R formation kernel (all precisions) */
 #define RM_PH_FIXUP       3   /* step (a) near-pole FP64 terms (mixed precision) */
 #define RM_PH_SOLVE       4   /* steps (c)+(d) matching, T, Omega */
-#define RM_PH_COUNT       5
+#define RM_PH_SPLIT       5   /* step (a) operand split of 1/(E_k - E) (mixed precision) */
+#define RM_PH_COUNT       6
 int rm_profile_enable(rm_ctx *ctx, int enable);
 int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms);
 

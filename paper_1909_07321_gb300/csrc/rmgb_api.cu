@@ -105,7 +105,7 @@ struct rm_ctx {
     // per-phase event pairs (tracing)
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[RM_PH_COUNT];
-    size_t ev_used[RM_PH_COUNT] = {0, 0, 0, 0, 0};
+    size_t ev_used[RM_PH_COUNT] = {};
     char err[512] = "no error";
 };
 
@@ -432,9 +432,11 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
         CK(ctx->wsErr.reserve(sizeof(int)));
         CK(cudaMemsetAsync(ctx->wsErr.p, 0, sizeof(int), ctx->stream));
     }
-    CK(prof_begin(ctx, RM_PH_FORM));
+    CK(prof_begin(ctx, RM_PH_SPLIT));
     CK(launch_split_d(d, E, nE, ctx->opts.delta_pole, kind, Kpad, ctx->wsDh.p, ctx->wsDl.p,
                       ctx->stream));
+    CK(prof_end(ctx, RM_PH_SPLIT));
+    CK(prof_begin(ctx, RM_PH_FORM));
     CK(launch_form_r_tc(kind, ctx->wsDh.p, ctx->wsDl.p, P.Ph.p, P.Pl.p, nE, tri_count(P.n), Kpad, R,
                         tri_ld(P.n), ctx->wsErr.as<int>(), ctx->stream));
     CK(prof_end(ctx, RM_PH_FORM));
