@@ -162,14 +162,17 @@ __device__ int cf2_closed(int L0, double nu, double kap, double a, double *y)
     return 1;
 }
 
+// Thread (i, e) with the energy index fastest: a warp covers 32 consecutive
+// energies of one channel (same l and threshold, nearby eta and rho), so its
+// lanes take the same branch and similar continued-fraction depths.
 __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
                               ChanFn *__restrict__ out, int *__restrict__ status)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = pw.n;
     if (idx >= (long long)nE * n) return;
-    const int e = (int)(idx / n);
-    const int i = (int)(idx - (long long)e * n);
+    const int i = (int)(idx / nE);
+    const int e = (int)(idx - (long long)i * nE);
     const double eps = E[e] - pw.e_thr[i];
     const int l = pw.l[i];
     const double a = pw.a, z = pw.z;
@@ -240,7 +243,7 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
             r.ghp = y * nrm;
         }
     }
-    out[idx] = r;
+    out[(size_t)e * n + i] = r;
     if (bad != RM_OK) atomicCAS(status + e, RM_OK, bad);
 }
 

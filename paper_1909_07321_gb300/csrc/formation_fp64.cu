@@ -36,6 +36,10 @@ constexpr int TK = 16;   // pole chunk
 constexpr int TT = 4;    // outputs per thread per dimension
 
 // n >= 32: CTA per (energy, 64x64 upper tile); 256 threads x 4x4 outputs.
+// Off-diagonal tiles: thread (ty, tx) = (tid/16, tid%16) owns rows 4ty.., cols
+// 4tx... Diagonal tiles: the 32x32 quadrant below the diagonal is not needed,
+// so whole warps are assigned to the three upper quadrants (2 warps each) and
+// warps 6-7 sit out; the FP64 pipe is not spent on discarded outputs.
 __global__ void __launch_bounds__(256) form_r_tiled(PwDev pw, const double *__restrict__ E,
                                                     double *__restrict__ R)
 {
@@ -48,7 +52,17 @@ __global__ void __launch_bounds__(256) form_r_tiled(PwDev pw, const double *__re
     __shared__ double Wj[TK][TB + 1];
     __shared__ double dk[TK];
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    int tx = tid & 15, ty = tid >> 4;
+    bool active = true;
+    if (ti == tj) {
+        const int w = tid >> 5, l = tid & 31;
+        const int quad = w >> 1;             // 0: (0,0), 1: (0,1), 2: (1,1), 3: idle
+        const int sub = (w & 1) * 32 + l;    // 64 threads per 32x32 quadrant
+        const int qy = (quad == 2) ? 1 : 0, qx = (quad == 0) ? 0 : 1;
+        ty = qy * 8 + (sub >> 3);
+        tx = qx * 8 + (sub & 7);
+        active = quad < 3;
+    }
     const double x = E[e];
     double acc[TT][TT];
 #pragma unroll
@@ -73,6 +87,7 @@ __global__ void __launch_bounds__(256) form_r_tiled(PwDev pw, const double *__re
             Wj[c][r] = (gj < n && k < N) ? pw.W[(size_t)gj * N + k] * dk[c] : 0.0;
         }
         __syncthreads();
+        if (active) {
 #pragma unroll
         for (int c = 0; c < TK; ++c) {
             double av[TT], bv[TT];
@@ -85,8 +100,10 @@ __global__ void __launch_bounds__(256) form_r_tiled(PwDev pw, const double *__re
 #pragma unroll
                 for (int b = 0; b < TT; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
         }
+        }
         __syncthreads();
     }
+    if (!active) return;
     const double h = 0.5 / pw.a;
     double *Re = R + (size_t)e * tri_ld(n);
 #pragma unroll

@@ -170,12 +170,16 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     __syncthreads();
     if (!omega) return;
 
-    // ---- M = 1 + K^2, Cholesky ----------------------------------------------
-    for (int q = tid; q < no * no; q += NT) {
-        const int p = q / no, r = q - (q / no) * no;
+    // ---- M = 1 + K^2 (symmetric: upper triangle, mirrored), Cholesky --------
+    const int nsym = no * (no + 1) / 2;
+    for (int q = tid; q < nsym; q += NT) {
+        int p = 0, rem = q;
+        while (rem >= no - p) { rem -= no - p; ++p; }
+        const int r = p + rem;
         double s = (p == r) ? 1.0 : 0.0;
         for (int u = 0; u < no; ++u) s = fma(Ks[p * lk + u], Ks[u * lk + r], s);
         Lc[p * lk + r] = s;
+        Lc[r * lk + p] = s;
     }
     __syncthreads();
     for (int c = 0; c < no; ++c) {
@@ -185,9 +189,13 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         for (int r = c + 1 + tid; r < no; r += NT) Lc[r * lk + c] *= dinv;
         __syncthreads();
         const int m = no - c - 1;
-        for (int q = tid; q < m * m; q += NT) {
-            const int r = c + 1 + q / m, s2 = c + 1 + (q - (q / m) * m);
-            if (s2 <= r) Lc[r * lk + s2] = fma(-Lc[r * lk + c], Lc[s2 * lk + c], Lc[r * lk + s2]);
+        const int mt = m * (m + 1) / 2;
+        for (int q = tid; q < mt; q += NT) {
+            // lower-triangle element (r, s2), c < s2 <= r, of the trailing block
+            int rr = 0, rem = q;
+            while (rem > rr) { rem -= rr + 1; ++rr; }
+            const int r = c + 1 + rr, s2 = c + 1 + rem;
+            Lc[r * lk + s2] = fma(-Lc[r * lk + c], Lc[s2 * lk + c], Lc[r * lk + s2]);
         }
         __syncthreads();
     }
@@ -205,14 +213,19 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         }
     }
     __syncthreads();
-    // |T|^2 = 4 (X^2 + Y^2), Y = K X; stored over Lc
+    // |T|^2 = 4 (X^2 + Y^2) with Y = K X; X and Y are symmetric (functions of
+    // K), so the upper triangle is computed and mirrored. Stored over Lc.
     double *T2 = Lc;
-    for (int q = tid; q < no * no; q += NT) {
-        const int p = q / no, r = q - (q / no) * no;
+    for (int q = tid; q < nsym; q += NT) {
+        int p = 0, rem = q;
+        while (rem >= no - p) { rem -= no - p; ++p; }
+        const int r = p + rem;
         double y = 0.0;
         for (int u = 0; u < no; ++u) y = fma(Ks[p * lk + u], Xm[u * lk + r], y);
-        const double xv = Xm[p * lk + r];
-        T2[p * lk + r] = 4.0 * (xv * xv + y * y);
+        const double xv = 0.5 * (Xm[p * lk + r] + Xm[r * lk + p]);
+        const double t2 = 4.0 * (xv * xv + y * y);
+        T2[p * lk + r] = t2;
+        T2[r * lk + p] = t2;
     }
     __syncthreads();
 
