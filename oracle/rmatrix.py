@@ -125,6 +125,15 @@ def match_direct(R, cf, a, b=0.0):
     return X[oi, :], oi
 
 
+def sincos_pi(nu):
+    """sin(pi nu), cos(pi nu) from the fractional part of nu (exact argument
+    reduction: pi*nu itself would carry an absolute rounding error ~ nu 1e-16)."""
+    m = np.round(nu)
+    f = nu - m
+    sgn = np.where(np.mod(m, 2) == 0, 1.0, -1.0)
+    return sgn * np.sin(np.pi * f), sgn * np.cos(np.pi * f)
+
+
 def mqdt_set(cf, l, fnumin=0.0, margin=0.1, sin_min=1e-3):
     """Closed channels treated by quantum-defect elimination: nu >= max(l +
     margin, fnumin) and |sin(pi nu)| >= sin_min (Section "namelist stgf MQDT
@@ -134,7 +143,7 @@ def mqdt_set(cf, l, fnumin=0.0, margin=0.1, sin_min=1e-3):
     cl = ~cf["open"]
     nu = cf["nu"]
     with np.errstate(invalid="ignore"):
-        q = cl & (nu >= np.maximum(l + margin, fnumin)) & (np.abs(np.sin(np.pi * nu)) >= sin_min)
+        q = cl & (nu >= np.maximum(l + margin, fnumin)) & (np.abs(sincos_pi(nu)[0]) >= sin_min)
     return q
 
 
@@ -160,8 +169,7 @@ def match_mqdt(R, cf, l, z, a, b=0.0, Q=None, fnumin=0.0, margin=0.1):
         fo, st = _clib.regular_analytic(np.asarray(l)[qi], z, cf["eps"][qi], a)
         f, fp = fo[:, 0], fo[:, 1]
         L = cf["L"][qi]
-        beta = np.pi * cf["nu"][qi]
-        sb, cb = np.sin(beta), np.cos(beta)
+        sb, cb = sincos_pi(cf["nu"][qi])
         th = sb / (f * L - fp)
         thp = L * th
         g = (f * cb - th) / sb
@@ -187,8 +195,8 @@ def match_mqdt(R, cf, l, z, a, b=0.0, Q=None, fnumin=0.0, margin=0.1):
     Koc = Ku[np.ix_(po, pc)]
     Kco = Ku[np.ix_(pc, po)]
     Kcc = Ku[np.ix_(pc, pc)]
-    tanb = np.tan(np.pi * cf["nu"][qi])
-    Y = _solve(Kcc + np.diag(tanb), Kco)
+    sb, cb = sincos_pi(cf["nu"][qi])
+    Y = _solve(Kcc + np.diag(sb / cb), Kco)
     if Y is None:
         return None, Ku, oi, qi
     return Koo - Koc @ Y, Ku, oi, qi

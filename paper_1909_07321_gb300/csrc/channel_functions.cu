@@ -35,8 +35,18 @@
 // is stable upwards there. L0 = 0 unless nu <= l + 1/2, where the operator
 // would pass near its null case nu = L+1; then L0 = ceil(nu - 1/2).
 // Output pair (theta, theta') scaled to theta^2 + (a theta')^2 = 1.
+//
+// MQDT (Section "namelist stgf MQDT variables"): a closed channel with
+// nu >= max(l + nu_margin, fnumin) and |sin pi nu| >= 1e-3 is eliminated by
+// quantum-defect theory. It needs the energy-analytic regular solution
+// f -> (2 pi z)^{1/2} (2z)^l r^{l+1}/(2l+1)! (r -> 0), from its Frobenius
+// series in double-double (the series cancels by up to ~1e10 at r = a), and g
+// defined by theta ~ f cos(pi nu) - g sin(pi nu) with f'g - fg' = 1:
+//   theta-hat(a) = sin(pi nu) / (f L - f'),  theta-hat'(a) = L theta-hat(a),
+//   g = (f cos(pi nu) - theta-hat) / sin(pi nu),  g' likewise.
 #include <math.h>
 
+#include "dd.cuh"
 #include "rm_internal.cuh"
 
 namespace rmgb {
@@ -165,6 +175,44 @@ __device__ int cf2_closed(int L0, double nu, double kap, double a, double *y)
 // Thread (i, e) with the energy index fastest: a warp covers 32 consecutive
 // energies of one channel (same l and threshold, nearby eta and rho), so its
 // lanes take the same branch and similar continued-fraction depths.
+// Energy-analytic regular solution f(r), f'(r) (see above). Terms
+// t_k = c_k r^k with k(k+2l+1) c_k = -2z c_{k-1} - eps c_{k-2}, c_0 = 1.
+__device__ int regular_analytic(int l, double z, double eps, double r, double *f, double *fp)
+{
+    const dd zr = two_prod(-2.0 * z, r);                 // -2 z r
+    const dd er2 = dd_mul_d(two_prod(-eps, r), r);       // -eps r^2
+    dd tm2 = dd_make(0.0), tm1 = dd_make(1.0);
+    dd S = dd_make(1.0), Sp = dd_make((double)(l + 1));
+    double tmax = 1.0;
+    int quiet = 0;
+    for (int k = 1; k < 100000; ++k) {
+        dd t = dd_add(dd_mul(zr, tm1), dd_mul(er2, tm2));
+        t = dd_div_d(t, (double)k * (double)(k + 2 * l + 1));
+        S = dd_add(S, t);
+        Sp = dd_add(Sp, dd_mul_d(t, (double)(k + l + 1)));
+        const double at = fabs(t.hi);
+        tmax = fmax(tmax, at);
+        if (at <= 1e-33 * tmax) {
+            if (++quiet >= 3 && k > 8) {
+                double Nf = sqrt(2.0 * M_PI * z);
+                for (int j = 0; j < l; ++j) Nf *= 2.0 * z;
+                for (int j = 2; j <= 2 * l + 1; ++j) Nf /= (double)j;
+                double rl = 1.0;
+                for (int j = 0; j < l; ++j) rl *= r;
+                *f = Nf * rl * r * dd_to_d(S);
+                *fp = Nf * rl * dd_to_d(Sp);
+                return 1;
+            }
+        } else {
+            quiet = 0;
+        }
+        tm2 = tm1;
+        tm1 = t;
+    }
+    return 0;
+}
+
+template <bool MQDT>
 __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
                               ChanFn *__restrict__ out, int *__restrict__ status)
 {
@@ -176,7 +224,7 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
     const double eps = E[e] - pw.e_thr[i];
     const int l = pw.l[i];
     const double a = pw.a, z = pw.z;
-    ChanFn r = {0.0, 0.0, 0.0, 0.0};
+    ChanFn r = {0.0, 0.0, 0.0, 0.0, 0.0, CH_CLOSED, 0};
     int bad = RM_OK;
     if (fabs(eps) < o.eps_thr) {
         bad = RM_ETHRESHOLD;
@@ -219,6 +267,7 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
             r.sp = scale * Fpl * sk;
             r.gh = G / sk;
             r.ghp = Gp * sk;
+            r.kind = CH_OPEN;
         }
     } else {
         const double kap = sqrt(-eps);
@@ -241,6 +290,24 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
             const double nrm = 1.0 / sqrt(1.0 + (a * y) * (a * y));
             r.gh = nrm;
             r.ghp = y * nrm;
+            if (MQDT && nu >= fmax(l + o.nu_margin, o.fnumin)) {
+                double sb, cb;
+                sincospi(nu, &sb, &cb);
+                if (fabs(sb) >= 1e-3) {
+                    double f, fp;
+                    if (!regular_analytic(l, z, eps, a, &f, &fp)) {
+                        bad = RM_ECF_NOCONV;
+                    } else {
+                        const double th = sb / (f * y - fp), thp = y * th;
+                        r.gh = (f * cb - th) / sb;
+                        r.ghp = (fp * cb - thp) / sb;
+                        r.s = f;
+                        r.sp = fp;
+                        r.tanb = sb / cb;
+                        r.kind = CH_MQDT;
+                    }
+                }
+            }
         }
     }
     out[(size_t)e * n + i] = r;
@@ -280,14 +347,16 @@ __global__ void export_kernel(PwDev pw, const double *__restrict__ E, int nE,
 }  // namespace
 
 cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
-                          ChanFn *cf, MqdtFn *mq, int *status, cudaStream_t s)
+                          ChanFn *cf, int *status, cudaStream_t s)
 {
-    (void)mq;
-    if (mqdt) return cudaErrorNotSupported;
     const long long total = (long long)nE * pw.n;
     if (total == 0) return cudaSuccess;
     const int bs = 128;
-    chanfn_kernel<<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(pw, E, nE, o, cf, status);
+    const unsigned grid = (unsigned)((total + bs - 1) / bs);
+    if (mqdt)
+        chanfn_kernel<true><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status);
+    else
+        chanfn_kernel<false><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status);
     return cudaGetLastError();
 }
 

@@ -9,18 +9,15 @@
 namespace rmgb {
 
 // Boundary data of one channel at one energy (step (b)).
-//   open:   (gh, ghp) = (c, c'),  (s, sp) = (s, s')   energy-normalised Coulomb
-//   closed: (gh, ghp) = (theta, theta') with theta^2 + (a theta')^2 = 1, s = sp = 0
+//   open (CH_OPEN):        (gh, ghp) = (c, c'),  (s, sp) = (s, s')   energy-normalised Coulomb
+//   closed (CH_CLOSED):    (gh, ghp) = (theta, theta') with theta^2 + (a theta')^2 = 1, s = sp = 0
+//   MQDT-eliminated closed (CH_MQDT): (gh, ghp) = (g, g'), (s, sp) = (f, f'),
+//                          tanb = tan(pi nu)
+enum ChanKind { CH_OPEN = 0, CH_CLOSED = 1, CH_MQDT = 2 };
 struct __align__(16) ChanFn {
     double gh, ghp, s, sp;
-};
-
-// MQDT extra data of a closed channel (only filled in MQDT mode):
-//   q != 0 marks a channel eliminated by quantum-defect theory; then
-//   (f, fp) replaces (s, s'), (g, gp) replaces (theta, theta'), tanb = tan(pi nu).
-struct __align__(16) MqdtFn {
-    double f, fp, g, gp, tanb;
-    int q;
+    double tanb;
+    int kind;
     int pad;
 };
 
@@ -56,16 +53,16 @@ struct Opts {
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----------
 
+// mqdt != 0: closed channels in the quantum-defect set get CH_MQDT data.
 cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
-                          ChanFn *cf, MqdtFn *mq, int *status, cudaStream_t s);
+                          ChanFn *cf, int *status, cudaStream_t s);
 cudaError_t launch_nearpole(const PwDev &pw, const double *E, int nE, int *status,
                             cudaStream_t s);
 cudaError_t launch_form_r_fp64(const PwDev &pw, const double *E, int nE, double *R,
                                cudaStream_t s);
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
-                               const MqdtFn *mq, const double *R, int mqdt, int *status,
-                               double *K_out, int *n_open_out, double *omega, int n_tri,
-                               cudaStream_t s);
+                               const double *R, int *status, double *K_out, int *n_open_out,
+                               double *omega, int n_tri, cudaStream_t s);
 // Mixed-precision formation (tensor cores). Operand kinds:
 enum TcKind { TC_BF16X3 = 0, TC_TF32X3 = 1 };
 // Split of P_pk = w_ik w_jk / (2a) into hi/lo operands, [n_pairs][Kpad] K-major.

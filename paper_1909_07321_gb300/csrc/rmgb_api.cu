@@ -470,7 +470,6 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
     if (rc) return rc;
     if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
     if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
-    if (mode == RM_MQDT) return fail(ctx, RM_EUNSUPPORTED, "MQDT mode not built yet");
     PwHost &P = ctx->pw[pw];
     if (P.n > solve_small_max_n())
         return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the solver limit %d", P.n,
@@ -519,14 +518,14 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
         CK(launch_nearpole(d, Eb, nb, sb, ctx->stream));
         CK(prof_end(ctx, RM_PH_NEARPOLE));
         CK(prof_begin(ctx, RM_PH_CHANFN));
-        CK(launch_chanfn(d, Eb, nb, o, 0, ctx->wsCf.as<ChanFn>(), nullptr, sb, ctx->stream));
+        CK(launch_chanfn(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, ctx->stream));
         CK(prof_end(ctx, RM_PH_CHANFN));
         ctx->launches += 2;
         rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
         if (rc) return rc;
         CK(prof_begin(ctx, RM_PH_SOLVE));
-        CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), nullptr, ctx->wsR.as<double>(), 0,
-                              sb, K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr,
+        CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb,
+                              K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr,
                               n_open_out ? n_open_out + e0 : nullptr,
                               ctx->omega.as<double>() + (size_t)e0 * ntri, ntri, ctx->stream));
         CK(prof_end(ctx, RM_PH_SOLVE));
@@ -616,8 +615,7 @@ extern "C" int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *
     }
     CK(cudaMemsetAsync(st, 0, (size_t)n_E * sizeof(int), ctx->stream));
     const PwDev d = P.dev();
-    CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ctx->wsCf.as<ChanFn>(), nullptr, st,
-                     ctx->stream));
+    CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ctx->wsCf.as<ChanFn>(), st, ctx->stream));
     CK(launch_chanfn_export(d, E, n_E, ctx->wsCf.as<ChanFn>(), out, ctx->stream));
     ctx->launches += 2;
     return RM_SUCCESS;

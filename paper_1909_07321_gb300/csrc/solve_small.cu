@@ -1,15 +1,20 @@
 // Steps (c) and (d) for n <= SOLVE_SMALL_MAXN channels: one CTA per energy,
 // everything in shared memory, FP64.
 //
-// (c) Matching (Section "Overview", Eq. match): with unknowns X (n x n_o),
-//   psi_ij = s_i delta_ij + ghat_i X_ij, ghat = c (open) or theta (closed),
-//   psi(a) = R (a psi'(a) - b psi(a)) gives
-//   [diag(ghat) - R diag(a ghat' - b ghat)] X = -[diag(s) - R diag(a s' - b s)] P,
-// P selecting open columns; K = X[open rows].
-// The unknowns are ordered closed-first, so after Gaussian elimination with
-// partial pivoting on the augmented matrix [A | B] the open unknowns are the
-// trailing n_o rows of the triangular system: back-substitution runs over
-// those rows only (the closed amplitudes are never formed).
+// (c) Matching (Section "Overview", Eq. match). Channels split into the set P
+// whose amplitudes are unknowns of K (open channels, plus in MQDT mode the
+// closed channels eliminated by quantum-defect theory) and the remaining
+// closed channels, which keep their decaying boundary condition. With
+// psi_ij = S_i delta_ij + Ghat_i X_ij (S, Ghat = s, c open; f, g MQDT; theta
+// decaying, no S), psi(a) = R (a psi'(a) - b psi(a)) gives
+//   [diag(Ghat) - R diag(a Ghat' - b Ghat)] X = -[diag(S) - R diag(a S' - b S)] P.
+// Unknowns are ordered decaying-closed first, so after Gaussian elimination
+// with partial pivoting of [A | B] the P unknowns are the trailing rows of
+// the triangular system: back-substitution runs over those rows only, giving
+// K_u = X[P rows] (the physical K in direct mode).
+// MQDT (Section "namelist stgf MQDT variables", iqdt): with o = open and
+// c = eliminated channels of P,
+//   K = K_oo - K_oc (K_cc + diag(tan pi nu))^{-1} K_co.
 //
 // (d) T = 2iK(1 - iK)^{-1} (Section "Glossary of terms") in real form. K is
 // symmetric, so with M = 1 + K^2 (SPD), X = M^{-1} K and Y = M^{-1} K^2 = K X:
@@ -27,6 +32,76 @@ namespace {
 constexpr int SOLVE_SMALL_MAXN = 96;
 constexpr int NT = 256;
 
+struct ElimShared {
+    int piv;
+    int bad;
+    double pivinv;
+};
+
+// In-place Gaussian elimination with partial pivoting of the first `rows`
+// columns of the rows x w matrix M (row stride ld), whole block. Sets
+// sh->bad on a zero or non-finite pivot.
+__device__ void block_eliminate(double *M, int ld, int rows, int w, ElimShared *sh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int c = 0; c < rows; ++c) {
+        if (warp == 0) {
+            double best = -1.0;
+            int bi = c;
+            for (int r = c + lane; r < rows; r += 32) {
+                const double v = fabs(M[r * ld + c]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                sh->piv = bi;
+                const double pv = M[bi * ld + c];
+                if (!(best > 0.0) || !isfinite(pv)) sh->bad = 1;
+                sh->pivinv = 1.0 / pv;
+            }
+        }
+        __syncthreads();
+        const int p = sh->piv;
+        if (p != c) {
+            for (int q = c + tid; q < w; q += NT) {
+                const double t = M[c * ld + q];
+                M[c * ld + q] = M[p * ld + q];
+                M[p * ld + q] = t;
+            }
+            __syncthreads();
+        }
+        const double pinv = sh->pivinv;
+        for (int r = c + 1 + tid; r < rows; r += NT) M[r * ld + c] *= pinv;
+        __syncthreads();
+        const int nr = rows - c - 1, nc = w - c - 1;
+        for (int q = tid; q < nr * nc; q += NT) {
+            const int r = c + 1 + q / nc, cc = c + 1 + (q - (q / nc) * nc);
+            M[r * ld + cc] = fma(-M[r * ld + c], M[c * ld + cc], M[r * ld + cc]);
+        }
+        __syncthreads();
+    }
+}
+
+// Back-substitution of the upper-triangular rows x rows system in M for the
+// n_rhs right-hand sides in columns rhs0.., over rows t = rows-1 .. row_lo,
+// in place; one thread per right-hand side.
+__device__ void block_backsub(double *M, int ld, int rows, int rhs0, int n_rhs, int row_lo)
+{
+    for (int qq = threadIdx.x; qq < n_rhs; qq += NT) {
+        const int cq = rhs0 + qq;
+        for (int t = rows - 1; t >= row_lo; --t) {
+            double s = M[t * ld + cq];
+            for (int u = t + 1; u < rows; ++u) s = fma(-M[t * ld + u], M[u * ld + cq], s);
+            M[t * ld + cq] = s / M[t * ld + t];
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
     const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
@@ -34,42 +109,58 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
 {
     extern __shared__ double sm[];
     __shared__ int col_chan[SOLVE_SMALL_MAXN];   // unknown column -> channel
-    __shared__ int open_pos[SOLVE_SMALL_MAXN];   // channel -> open position (-1 closed)
-    __shared__ int s_no, s_piv, s_bad;
-    __shared__ double s_pivinv;
+    __shared__ int open_pos[SOLVE_SMALL_MAXN];   // channel -> open position (-1 otherwise)
+    __shared__ int qpos[SOLVE_SMALL_MAXN];       // MQDT channel k -> its position in P
+    __shared__ int opos[SOLVE_SMALL_MAXN];       // open channel k -> its position in P
+    __shared__ int s_no, s_np, s_nq;
+    __shared__ ElimShared esh;
 
     const int e = blockIdx.x;
     const int n = pw.n;
     const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
     const double x = E[e];
     const ChanFn *cf = cfa + (size_t)e * n;
     const double *Rp = Ra + (size_t)e * tri_ld(n);   // packed upper triangle
+    const bool ok_status = status[e] == RM_OK;
 
     if (tid == 0) {
         int no = 0;
         for (int i = 0; i < n; ++i) no += (x - pw.e_thr[i] > 0.0);
-        const int nc = n - no;
-        int pc = 0, po = 0;
-        for (int i = 0; i < n; ++i) {
-            if (x - pw.e_thr[i] > 0.0) {
-                open_pos[i] = po;
-                col_chan[nc + po] = i;
-                ++po;
-            } else {
-                open_pos[i] = -1;
-                col_chan[pc++] = i;
-            }
-        }
-        s_no = no;
-        s_bad = 0;
         if (n_open_out) n_open_out[e] = no;
+        s_no = no;
+        esh.bad = 0;
+        if (ok_status) {
+            int np = 0;
+            for (int i = 0; i < n; ++i) np += (cf[i].kind != CH_CLOSED);
+            const int ncl = n - np;
+            int pc = 0, pp = 0, po = 0, pq = 0;
+            for (int i = 0; i < n; ++i) {
+                const int k = cf[i].kind;
+                if (k == CH_CLOSED) {
+                    col_chan[pc++] = i;
+                    open_pos[i] = -1;
+                } else {
+                    col_chan[ncl + pp] = i;
+                    if (k == CH_OPEN) {
+                        open_pos[i] = po;
+                        opos[po++] = pp;
+                    } else {
+                        open_pos[i] = -1;
+                        qpos[pq++] = pp;
+                    }
+                    ++pp;
+                }
+            }
+            s_np = np;
+            s_nq = pq;
+        }
     }
     __syncthreads();
-    const int no = s_no, nc = n - no;
-    if (status[e] != RM_OK || no == 0) return;
+    const int no = s_no;
+    if (!ok_status || no == 0) return;
+    const int np = s_np, nq = s_nq, ncl = n - np;
 
-    const int w = n + no;        // augmented width
+    const int w = n + np;        // augmented width
     const int ld = w + 1;        // padded row stride
     double *M = sm;
     const double a = pw.a, b = pw.b;
@@ -84,7 +175,7 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
             v = -Rp[r <= j ? tri_idx(r, j, n) : tri_idx(j, r, n)] * (a * cj.ghp - b * cj.gh);
             if (r == j) v += cj.gh;
         } else {
-            const int o = col_chan[nc + (c - n)];
+            const int o = col_chan[ncl + (c - n)];
             const ChanFn co = cf[o];
             v = Rp[r <= o ? tri_idx(r, o, n) : tri_idx(o, r, n)] * (a * co.sp - b * co.s);
             if (r == o) v -= co.s;
@@ -93,82 +184,78 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     }
     __syncthreads();
 
-    // ---- forward elimination with partial pivoting -------------------------
-    for (int c = 0; c < n; ++c) {
-        if (warp == 0) {
-            double best = -1.0;
-            int bi = c;
-            for (int r = c + lane; r < n; r += 32) {
-                const double v = fabs(M[r * ld + c]);
-                if (v > best) { best = v; bi = r; }
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-                const double ob = __shfl_down_sync(0xffffffffu, best, off);
-                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) {
-                s_piv = bi;
-                const double pv = M[bi * ld + c];
-                if (!(best > 0.0) || !isfinite(pv)) s_bad = 1;
-                s_pivinv = 1.0 / pv;
-            }
-        }
-        __syncthreads();
-        const int p = s_piv;
-        if (p != c) {
-            for (int q = c + tid; q < w; q += NT) {
-                const double t = M[c * ld + q];
-                M[c * ld + q] = M[p * ld + q];
-                M[p * ld + q] = t;
-            }
-            __syncthreads();
-        }
-        // multipliers into column c (below the pivot), then the trailing update
-        const double pinv = s_pivinv;
-        for (int r = c + 1 + tid; r < n; r += NT) M[r * ld + c] *= pinv;
-        __syncthreads();
-        const int rows = n - c - 1, cols = w - c - 1;
-        for (int q = tid; q < rows * cols; q += NT) {
-            const int r = c + 1 + q / cols, cc = c + 1 + (q - (q / cols) * cols);
-            M[r * ld + cc] = fma(-M[r * ld + c], M[c * ld + cc], M[r * ld + cc]);
-        }
-        __syncthreads();
-    }
-    if (s_bad) {
+    block_eliminate(M, ld, n, w, &esh);
+    if (esh.bad) {
         if (tid == 0) status[e] = RM_ESINGULAR;
         return;
     }
+    block_backsub(M, ld, n, n, np, ncl);   // K_u = rows ncl.. of the RHS columns
 
-    // ---- back-substitution over the trailing open rows ----------------------
-    // x_t = (y_t - sum_{u>t} U_tu x_u) / U_tt for t = n-1 .. nc, in place in the
-    // right-hand-side columns; one thread per right-hand side.
-    for (int qq = tid; qq < no; qq += NT) {
-        const int cq = n + qq;
-        for (int t = n - 1; t >= nc; --t) {
-            double s = M[t * ld + cq];
-            for (int u = t + 1; u < n; ++u) s = fma(-M[t * ld + u], M[u * ld + cq], s);
-            M[t * ld + cq] = s / M[t * ld + t];
-        }
-    }
-    __syncthreads();
-
-    // ---- K, optional output, symmetrised copy ------------------------------
-    // Shared layout: [augmented region, n(2n+2) doubles][Ks]; once K is copied
-    // out, the Cholesky factor and X reuse the augmented region.
+    // Shared layout: [region A: n(2n+2) doubles][region B: n(n+1) doubles].
+    double *Ks = sm + (size_t)n * (2 * n + 2);   // region B
     const int lk = no + 1;
-    double *Ks = sm + (size_t)n * (2 * n + 2);
-    double *Lc = sm;                         // Cholesky factor of 1 + K^2
-    double *Xm = sm + (size_t)no * lk;       // X = M^{-1} K
-    for (int q = tid; q < no * no; q += NT) {
-        const int p = q / no, r = q - (q / no) * no;
-        const double kpr = M[(nc + p) * ld + n + r];
-        const double krp = M[(nc + r) * ld + n + p];
-        Ks[p * lk + r] = 0.5 * (kpr + krp);
-        if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
+    if (nq == 0) {
+        // direct mode (or no eliminated channel at this energy): K = K_u
+        for (int q = tid; q < no * no; q += NT) {
+            const int p = q / no, r = q - (q / no) * no;
+            const double kpr = M[(ncl + p) * ld + n + r];
+            const double krp = M[(ncl + r) * ld + n + p];
+            Ks[p * lk + r] = 0.5 * (kpr + krp);
+            if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
+        }
+        __syncthreads();
+    } else {
+        // ---- MQDT elimination of the nq channels --------------------------
+        const int lu = np + 1;
+        double *Ku = Ks;           // K_u (np x np) in region B
+        for (int q = tid; q < np * np; q += NT) {
+            const int p = q / np, r = q - (q / np) * np;
+            Ku[p * lu + r] = M[(ncl + p) * ld + n + r];
+        }
+        __syncthreads();
+        // [K_cc + diag(tan pi nu) | K_co] in region A
+        const int w2 = nq + no, ld2 = w2 + 1;
+        double *C = sm;
+        for (int q = tid; q < nq * w2; q += NT) {
+            const int i = q / w2, j = q - (q / w2) * w2;
+            double v;
+            if (j < nq) {
+                v = Ku[qpos[i] * lu + qpos[j]];
+                if (i == j) v += cf[col_chan[ncl + qpos[i]]].tanb;
+            } else {
+                v = Ku[qpos[i] * lu + opos[j - nq]];
+            }
+            C[i * ld2 + j] = v;
+        }
+        __syncthreads();
+        block_eliminate(C, ld2, nq, w2, &esh);
+        if (esh.bad) {
+            if (tid == 0) status[e] = RM_ESINGULAR;
+            return;
+        }
+        block_backsub(C, ld2, nq, nq, no, 0);   // Y = (K_cc + tan)^{-1} K_co
+        // K = K_oo - K_oc Y, after [C | Y] in region A
+        double *Kd = sm + (size_t)nq * ld2;
+        for (int q = tid; q < no * no; q += NT) {
+            const int s = q / no, t = q - (q / no) * no;
+            double v = Ku[opos[s] * lu + opos[t]];
+            for (int i = 0; i < nq; ++i) v = fma(-Ku[opos[s] * lu + qpos[i]], C[i * ld2 + nq + t], v);
+            Kd[s * lk + t] = v;
+        }
+        __syncthreads();
+        for (int q = tid; q < no * no; q += NT) {
+            const int p = q / no, r = q - (q / no) * no;
+            const double kpr = Kd[p * lk + r];
+            Ks[p * lk + r] = 0.5 * (kpr + Kd[r * lk + p]);   // overwrites K_u, no longer read
+            if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     if (!omega) return;
+
+    // Cholesky factor and X reuse region A.
+    double *Lc = sm;
+    double *Xm = sm + (size_t)no * lk;
 
     // ---- M = 1 + K^2 (symmetric: upper triangle, mirrored), Cholesky --------
     const int nsym = no * (no + 1) / 2;
@@ -264,12 +351,9 @@ size_t solve_small_smem(int n)
 }
 
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
-                               const MqdtFn *mq, const double *R, int mqdt, int *status,
-                               double *K_out, int *n_open_out, double *omega, int n_tri,
-                               cudaStream_t s)
+                               const double *R, int *status, double *K_out, int *n_open_out,
+                               double *omega, int n_tri, cudaStream_t s)
 {
-    (void)mq;
-    if (mqdt) return cudaErrorNotSupported;
     if (pw.n > SOLVE_SMALL_MAXN) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
     const size_t smem = solve_small_smem(pw.n);
