@@ -83,6 +83,9 @@ typedef struct rm_opts {
                                the legacy default stream); NULL = a non-blocking
                                stream the context creates and owns */
     size_t mem_budget;      /* bytes of per-call device workspace (0 = 1 GiB) */
+    double mqdt_kappa_a_max;/* MQDT: closed channels with kappa a above this keep the
+                               decaying condition (default 5; eliminating them costs
+                               ~exp(2 kappa a) in precision) */
 } rm_opts;
 
 /* Fills *opts with the defaults above. */

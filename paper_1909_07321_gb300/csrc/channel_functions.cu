@@ -37,8 +37,10 @@
 // Output pair (theta, theta') scaled to theta^2 + (a theta')^2 = 1.
 //
 // MQDT (Section "namelist stgf MQDT variables"): a closed channel with
-// nu >= max(l + nu_margin, fnumin) and |sin pi nu| >= 1e-3 is eliminated by
-// quantum-defect theory. It needs the energy-analytic regular solution
+// nu >= max(l + nu_margin, fnumin), |sin pi nu| >= 1e-3 and kappa a <=
+// kappa_a_max is eliminated by quantum-defect theory (more deeply closed
+// channels make f and g differ by exp(2 kappa a) at r = a, and the
+// elimination would lose that factor in precision). It needs the energy-analytic regular solution
 // f -> (2 pi z)^{1/2} (2z)^l r^{l+1}/(2l+1)! (r -> 0), from its Frobenius
 // series in double-double (the series cancels by up to ~1e10 at r = a), and g
 // defined by theta ~ f cos(pi nu) - g sin(pi nu) with f'g - fg' = 1:
@@ -290,7 +292,7 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
             const double nrm = 1.0 / sqrt(1.0 + (a * y) * (a * y));
             r.gh = nrm;
             r.ghp = y * nrm;
-            if (MQDT && nu >= fmax(l + o.nu_margin, o.fnumin)) {
+            if (MQDT && nu >= fmax(l + o.nu_margin, o.fnumin) && kap * a <= o.kappa_a_max) {
                 double sb, cb;
                 sincospi(nu, &sb, &cb);
                 if (fabs(sb) >= 1e-3) {

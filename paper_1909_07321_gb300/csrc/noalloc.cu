@@ -103,7 +103,7 @@ extern "C" int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E,
     d.W = W;
     d.e_thr = e_thr;
     d.l = l;
-    Opts o = {eps_thr, 0.0, 0.0, 0.1};
+    Opts o = {eps_thr, 0.0, 0.0, 0.1, 5.0};
     // status must start at zero (kernels only record the first failure)
     cudaError_t err = cudaMemsetAsync(status_out, 0, (size_t)n_E * sizeof(int), s);
     for (int e0 = 0; err == cudaSuccess && e0 < n_E; e0 += (int)chunk) {

@@ -48,7 +48,7 @@ struct PwDev {
 };
 
 struct Opts {
-    double eps_thr, delta_pole, fnumin, nu_margin;
+    double eps_thr, delta_pole, fnumin, nu_margin, kappa_a_max;
 };
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----------

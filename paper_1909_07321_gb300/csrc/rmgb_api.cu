@@ -202,6 +202,7 @@ Opts make_opts(const rm_opts &o)
     r.delta_pole = o.delta_pole;
     r.fnumin = o.fnumin;
     r.nu_margin = o.nu_margin;
+    r.kappa_a_max = o.mqdt_kappa_a_max;
     return r;
 }
 
@@ -221,6 +222,7 @@ extern "C" void rm_default_opts(rm_opts *o)
     o->device = 0;
     o->stream = nullptr;
     o->mem_budget = 0;
+    o->mqdt_kappa_a_max = 5.0;
 }
 
 extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
@@ -231,6 +233,7 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
     if (opts) o = *opts; else rm_default_opts(&o);
     if (o.mem_budget == 0) o.mem_budget = (size_t)1 << 30;
     if (!(o.eps_thr >= 0) || !(o.delta_pole >= 0) || !std::isfinite(o.fnumin) ||
+        !(o.mqdt_kappa_a_max >= 0) ||
         !std::isfinite(o.nu_margin) ||
         (o.precision != RM_FP64 && o.precision != RM_FP32 && o.precision != RM_BF16X3))
         return RM_EINVAL;

@@ -34,7 +34,8 @@ class RmOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("delta_pole", ctypes.c_double),
                 ("eps_thr", ctypes.c_double), ("fnumin", ctypes.c_double),
                 ("nu_margin", ctypes.c_double), ("device", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t)]
+                ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
+                ("mqdt_kappa_a_max", ctypes.c_double)]
 
 
 class RmError(RuntimeError):

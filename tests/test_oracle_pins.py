@@ -319,7 +319,10 @@ def test_k_invariant_under_theta_scaling():
 def test_mqdt_equals_direct():
     pw = _mixed_pw()
     n_q = 0
-    for E in np.linspace(0.05, 2.2, 31):
+    # a coarse grid plus energies just below each threshold (the Rydberg
+    # region where closed channels are eliminated by quantum-defect theory)
+    below = np.concatenate([t - np.array([0.001, 0.002, 0.005, 0.01, 0.03]) for t in pw["e_thr"][1:]])
+    for E in np.concatenate([np.linspace(0.05, 2.2, 31), below]):
         cf = oracle.channel_functions(float(E), pw["e_thr"], pw["l"], pw["z"], pw["a"])
         R = oracle.r_matrix(float(E), pw["E_k"], pw["W"], pw["a"])
         Kd, _ = oracle.match_direct(R, cf, pw["a"])
@@ -340,7 +343,7 @@ def test_mqdt_two_channel_vs_mpmath():
     l = np.array([1, 2])
     cf = oracle.channel_functions(E, e_thr, l, z, a)
     Kd, _ = oracle.match_direct(R, cf, a)
-    Km, _, _, qi = oracle.match_mqdt(R, cf, l, z, a)
+    Km, _, _, qi = oracle.match_mqdt(R, cf, l, z, a, kappa_a_max=10.0)   # kappa a = 8.9 here
     assert len(qi) == 1
     with mp.workdps(40):
         k = mp.sqrt(mp.mpf(E) - mp.mpf("0.5"))
