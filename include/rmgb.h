@@ -82,11 +82,19 @@ typedef struct rm_opts {
     void *stream;           /* cudaStream_t to enqueue on (cudaStreamLegacy for
                                the legacy default stream); NULL = a non-blocking
                                stream the context creates and owns */
-    size_t mem_budget;      /* bytes of per-call device workspace (0 = 1 GiB) */
+    size_t mem_budget;      /* bytes of per-call device workspace (0 = 8 GiB, at most
+                               half the free device memory) */
     double mqdt_kappa_a_max;/* MQDT: closed channels with kappa a above this keep the
                                decaying condition (default 5; eliminating them costs
                                ~exp(2 kappa a) in precision) */
+    int solver;             /* matching solver: RM_SOLVER_AUTO (default: shared
+                               memory up to 96 channels, global memory above),
+                               RM_SOLVER_SMALL, RM_SOLVER_LARGE */
 } rm_opts;
+
+#define RM_SOLVER_AUTO    0
+#define RM_SOLVER_SMALL   1
+#define RM_SOLVER_LARGE   2
 
 /* Fills *opts with the defaults above. */
 void rm_default_opts(rm_opts *opts);

@@ -88,4 +88,10 @@ cudaError_t launch_chanfn_export(const PwDev &pw, const double *E, int nE, const
 // Largest channel count the shared-memory solver takes.
 int solve_small_max_n();
 
+// Global-memory solver for any channel count (steps (c) and (d)).
+size_t solve_large_bytes_per_energy(int n);
+cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
+                               const double *R, int *status, double *K_out, int *n_open_out,
+                               double *omega, int n_tri, void *ws, int *launches, cudaStream_t s);
+
 }  // namespace rmgb

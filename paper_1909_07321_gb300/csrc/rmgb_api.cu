@@ -100,7 +100,7 @@ struct rm_ctx {
     std::vector<double> grid_host;
     DevBuf omega;
     // workspace
-    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr;
+    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL;
     long long launches = 0;
     // per-phase event pairs (tracing)
     bool prof = false;
@@ -223,6 +223,7 @@ extern "C" void rm_default_opts(rm_opts *o)
     o->stream = nullptr;
     o->mem_budget = 0;
     o->mqdt_kappa_a_max = 5.0;
+    o->solver = RM_SOLVER_AUTO;
 }
 
 extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
@@ -231,7 +232,7 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
     *out = nullptr;
     rm_opts o;
     if (opts) o = *opts; else rm_default_opts(&o);
-    if (o.mem_budget == 0) o.mem_budget = (size_t)1 << 30;
+    if (o.solver < RM_SOLVER_AUTO || o.solver > RM_SOLVER_LARGE) return RM_EINVAL;
     if (!(o.eps_thr >= 0) || !(o.delta_pole >= 0) || !std::isfinite(o.fnumin) ||
         !(o.mqdt_kappa_a_max >= 0) ||
         !std::isfinite(o.nu_margin) ||
@@ -240,6 +241,12 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
     if (cudaSetDevice(o.device) != cudaSuccess) {
         cudaGetLastError();
         return RM_ECUDA;
+    }
+    if (o.mem_budget == 0) {
+        size_t fr = 0, tot = 0;
+        o.mem_budget = (size_t)8 << 30;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr / 2 < o.mem_budget) o.mem_budget = fr / 2;
+        cudaGetLastError();
     }
     rm_ctx *ctx = new (std::nothrow) rm_ctx();
     if (!ctx) return RM_ENOMEM;
@@ -265,7 +272,7 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
     for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
-                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr})
+                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
         for (auto &pr : ctx->ev[p]) {
@@ -393,9 +400,17 @@ int check_precision(rm_ctx *ctx, const PwHost &P)
     return RM_SUCCESS;
 }
 
+bool use_large(rm_ctx *ctx, const PwHost &P)
+{
+    if (ctx->opts.solver == RM_SOLVER_LARGE) return true;
+    if (ctx->opts.solver == RM_SOLVER_SMALL) return false;
+    return P.n > solve_small_max_n();
+}
+
 int block_energies(rm_ctx *ctx, const PwHost &P)
 {
     size_t per = (size_t)tri_ld(P.n) * sizeof(double) + (size_t)P.n * sizeof(ChanFn) + 64;
+    if (use_large(ctx, P)) per += solve_large_bytes_per_energy(P.n);
     if (ctx->opts.precision != RM_FP64) {
         const int kind = tc_kind(ctx->opts.precision);
         per += 2 * (size_t)tc_kpad(P.N, kind) * tc_esize(kind);
@@ -474,8 +489,9 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
     if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
     if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
     PwHost &P = ctx->pw[pw];
-    if (P.n > solve_small_max_n())
-        return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the solver limit %d", P.n,
+    const bool large = use_large(ctx, P);
+    if (!large && P.n > solve_small_max_n())
+        return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the shared-memory solver limit %d", P.n,
                     solve_small_max_n());
     rc = check_precision(ctx, P);
     if (rc) return rc;
@@ -505,6 +521,7 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
     const int B = std::min(n_E, block_energies(ctx, P));
     CK(ctx->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
     CK(ctx->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
+    if (large) CK(ctx->wsL.reserve(solve_large_bytes_per_energy(P.n) * (size_t)B + 256));
     int *dstatus = status_out;
     if (!dstatus) {
         CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
@@ -527,12 +544,20 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
         rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
         if (rc) return rc;
         CK(prof_begin(ctx, RM_PH_SOLVE));
-        CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb,
-                              K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr,
-                              n_open_out ? n_open_out + e0 : nullptr,
-                              ctx->omega.as<double>() + (size_t)e0 * ntri, ntri, ctx->stream));
+        double *Kb = K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr;
+        int *nob = n_open_out ? n_open_out + e0 : nullptr;
+        double *omb = ctx->omega.as<double>() + (size_t)e0 * ntri;
+        if (large) {
+            int L = 0;
+            CK(launch_solve_large(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
+                                  omb, ntri, ctx->wsL.p, &L, ctx->stream));
+            ctx->launches += L;
+        } else {
+            CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
+                                  omb, ntri, ctx->stream));
+            ctx->launches++;
+        }
         CK(prof_end(ctx, RM_PH_SOLVE));
-        ctx->launches++;
     }
     return RM_SUCCESS;
 }

@@ -35,7 +35,7 @@ class RmOpts(ctypes.Structure):
                 ("eps_thr", ctypes.c_double), ("fnumin", ctypes.c_double),
                 ("nu_margin", ctypes.c_double), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
-                ("mqdt_kappa_a_max", ctypes.c_double)]
+                ("mqdt_kappa_a_max", ctypes.c_double), ("solver", ctypes.c_int)]
 
 
 class RmError(RuntimeError):
