@@ -194,6 +194,38 @@ def _solve_flops(n, n_open):
     return float(np.sum(2.0 / 3.0 * n**3 + 2.0 * n * n * no + (6.0 + 1.0 / 3.0) * no**3))
 
 
+def run_serving(args, prec):
+    """Poisson stream of partial-wave x energy-batch requests through the
+    continuous-batching server (mixed-precision formation); p50/p99 latency."""
+    from paper_1909_07321_gb300 import serving, synth
+    specs = synth.serving_requests(args.serving_requests, args.serving_rate,
+                                   n_range=(50, 200), ne_range=(256, 2048), n_sets=16)
+    pws = {}
+    reqs = []
+    for sp in specs:
+        if sp["set_id"] not in pws:
+            pws[sp["set_id"]] = synth.serving_pole_set(sp["set_id"], sp["n"])
+        reqs.append(serving.Request(sp["id"], sp["set_id"], pws[sp["set_id"]], sp["E"], sp["mode"],
+                                    sp["t_arrival"]))
+    srv = serving.Server(n_slots=4, precision=prec, slot_workspace=1 << 30, cache_sets=4)
+    try:
+        # warm the slots (kernels loaded, workspaces sized) outside the measurement
+        warm = [serving.Request(-1 - i, r.set_id, r.pw, r.E[:64], r.mode, 0.0)
+                for i, r in enumerate(reqs[:4])]
+        srv.run(warm)
+        srv.run(reqs)
+    finally:
+        srv.close()
+    st = serving.latency_stats(reqs)
+    return {"workload": ("Poisson arrivals at %.0f/s; requests of 50-200 channels (pool of 16 "
+                         "pole sets, 25-35 poles per channel), 256-2048 energies on 0-8 Ry, "
+                         "half MQDT; 4 slots" % args.serving_rate),
+            "formation": [k for k, v in PREC.items() if v == prec][0],
+            "requests": st["requests"], "energy_solves": st["energy_solves"],
+            "energy_solves_per_s": st["energy_solves_per_s"],
+            "p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"], "mean_ms": 1e3 * st["mean_s"]}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -281,6 +313,10 @@ def run_ours(args, rank, world, local_rank):
                                           "p99": float(np.quantile(rel, 0.99)),
                                           "max": float(rel.max())}}
 
+    serving_line = None
+    if rank == 0 and world == 1 and args.serving_requests > 0:
+        serving_line = run_serving(args, prec if prec != 0 else 2)
+
     if rank != 0:
         return
     peaks, peak_src = _peaks()
@@ -339,6 +375,7 @@ def run_ours(args, rank, world, local_rank):
             "phases_ms_per_step": {names[p]: phase[p][1] / args.steps for p in names},
             "phase_share": share,
             "fp64_path": fp64,
+            "serving": serving_line,
             "cpu_baseline": cpu,
             "e2e": {"value": world * E.size / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(E.size * 8),
@@ -357,6 +394,9 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path beside the chosen precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=48,
+                    help="requests in the serving leg (0 to skip)")
+    ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrival rate (1/s)")
     ap.add_argument("--energies", type=int, default=N_E,
                     help="energies per GPU (smaller only for profiler captures)")
     args = ap.parse_args()

@@ -119,3 +119,37 @@ def random_pw(seed, n, n_poles, z=1.0, a=20.0, e_max=1.5, sigma=0.1, pole_lo=-1.
     E_k = jittered_poles(rng, n_poles, pole_lo, pole_hi)
     W = rng.normal(0.0, sigma, (n, n_poles))
     return _pw(E_k, W, a, e_thr, l, z, np.arange(n), n, 1.0, b)
+
+
+def serving_pole_set(set_id, n, base_seed=SEED0 + 4):
+    """Pole set `set_id` of the serving pool: n channels (4 per level, levels at
+    linspace(0, 6) Ry), N = U{25..35} n poles on [-5, 200] Ry, w ~ N(0, 0.03^2),
+    z = 2, a = 20. Draw order: N/n, l, jitter, W."""
+    rng = np.random.default_rng(np.random.PCG64(base_seed * 1000 + set_id))
+    per = int(rng.integers(25, 36))
+    n_lev = (n + 3) // 4
+    level, l, e_thr = _leveled_channels(rng, n, np.linspace(0.0, 6.0, n_lev))
+    E_k = jittered_poles(rng, per * n, -5.0, 200.0)
+    W = rng.normal(0.0, 0.03, (n, per * n))
+    return _pw(E_k, W, 20.0, e_thr, l, 2.0, level, n_lev, 1.0)
+
+
+def serving_requests(n_req, rate_hz, n_range=(50, 1500), ne_range=(256, 8192), n_sets=64,
+                     mqdt_fraction=0.5, seed=SEED0 + 4):
+    """Poisson stream of requests: arrival times (s), pole-set id from a pool of
+    n_sets (each set has a fixed channel count drawn from n_range), an energy
+    batch of U{ne_range} midpoint energies on [0, 8] Ry with a random offset,
+    and the matching mode (MQDT with probability mqdt_fraction).
+    Returns a list of dicts; pole sets are built lazily by serving_pole_set."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    set_n = rng.integers(n_range[0], n_range[1] + 1, n_sets)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_req))
+    out = []
+    for i in range(n_req):
+        sid = int(rng.integers(0, n_sets))
+        ne = int(rng.integers(ne_range[0], ne_range[1] + 1))
+        lo = float(rng.uniform(0.0, 0.5 * 8.0 / ne))
+        E = lo + midpoint_grid(0.0, 8.0, ne)
+        out.append(dict(id=i, t_arrival=float(t[i]), set_id=sid, n=int(set_n[sid]), E=E,
+                        mode=int(rng.random() < mqdt_fraction)))
+    return out
