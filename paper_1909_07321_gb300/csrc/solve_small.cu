@@ -74,13 +74,14 @@ __device__ void block_eliminate(double *M, int ld, int rows, int w, ElimShared *
             }
             __syncthreads();
         }
+        // trailing update with the multiplier formed on the fly (the
+        // multipliers themselves are not needed: every right-hand side is in
+        // the augmented matrix), so no separate scaling pass and barrier
         const double pinv = sh->pivinv;
-        for (int r = c + 1 + tid; r < rows; r += NT) M[r * ld + c] *= pinv;
-        __syncthreads();
         const int nr = rows - c - 1, nc = w - c - 1;
         for (int q = tid; q < nr * nc; q += NT) {
             const int r = c + 1 + q / nc, cc = c + 1 + (q - (q / nc) * nc);
-            M[r * ld + cc] = fma(-M[r * ld + c], M[c * ld + cc], M[r * ld + cc]);
+            M[r * ld + cc] = fma(-M[r * ld + c] * pinv, M[c * ld + cc], M[r * ld + cc]);
         }
         __syncthreads();
     }

@@ -235,3 +235,24 @@ def test_invalid_arguments(rt):
         lev[0] = 99
         with pytest.raises(rmgb.RmError):
             rmgb.rm_set_channels(ctx.h, 0, pw["e_thr"], pw["l"], 1.0, lev, 3, 1.0)
+
+
+def test_neutral_target_z0(rt):
+    """Neutral target (z = 0): Riccati-Bessel open channels (eta = 0) and
+    modified-spherical-Bessel closed channels (nu = 0), through both solvers."""
+    pw = synth.random_pw(90, 6, 120, z=0.0, a=12.0, e_max=1.2, l_max=4)
+    E = synth.midpoint_grid(0.01, 1.6, 300)
+    ref = oracle.solve_energies(pw, E)
+    assert (ref["status"] == 0).all()
+    _compare(_gpu_solve(rt, pw, E), ref)
+    torch, rmgb = rt
+    n = pw["W"].shape[0]
+    with rmgb.Context(solver=2) as ctx:
+        ctx.load_pw(0, pw)
+        K = torch.zeros((E.size, n * n), dtype=torch.float64, device="cuda")
+        no = torch.zeros(E.size, dtype=torch.int32, device="cuda")
+        st = torch.zeros(E.size, dtype=torch.int32, device="cuda")
+        ctx.solve_energies(0, torch.tensor(E, device="cuda"), 0, K, no, st)
+        res = dict(K=K.cpu().numpy().reshape(E.size, n, n), n_open=no.cpu().numpy(),
+                   status=st.cpu().numpy(), omega=ctx.collision_strengths())
+    _compare(res, ref)
