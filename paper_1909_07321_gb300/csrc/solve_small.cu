@@ -74,14 +74,18 @@ __device__ void block_eliminate(double *M, int ld, int rows, int w, ElimShared *
             }
             __syncthreads();
         }
-        // trailing update with the multiplier formed on the fly (the
-        // multipliers themselves are not needed: every right-hand side is in
-        // the augmented matrix), so no separate scaling pass and barrier
+        // trailing update; G threads share a row and form its multiplier once
+        // (the multipliers are not stored: every right-hand side is in the
+        // augmented matrix), so there is no separate scaling pass or barrier
+        constexpr int G = 4;
         const double pinv = sh->pivinv;
-        const int nr = rows - c - 1, nc = w - c - 1;
-        for (int q = tid; q < nr * nc; q += NT) {
-            const int r = c + 1 + q / nc, cc = c + 1 + (q - (q / nc) * nc);
-            M[r * ld + cc] = fma(-M[r * ld + c] * pinv, M[c * ld + cc], M[r * ld + cc]);
+        const int nr = rows - c - 1;
+        const double *prow = M + c * ld;
+        for (int q = tid; q < nr * G; q += NT) {
+            const int r = c + 1 + q / G, j = q - (q / G) * G;
+            double *row = M + r * ld;
+            const double f = row[c] * pinv;
+            for (int cc = c + 1 + j; cc < w; cc += G) row[cc] = fma(-f, prow[cc], row[cc]);
         }
         __syncthreads();
     }
