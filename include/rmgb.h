@@ -60,7 +60,8 @@ extern "C" {
 /* Precision of the R-matrix formation (step (a)). Channel functions, the
  * matching solve, T and Omega are always FP64. */
 #define RM_FP64           0   /* FP64 formation */
-#define RM_FP32           1   /* FP32 products and accumulation, near-pole terms in FP64 */
+#define RM_FP32           1   /* tensor cores: tf32 hi/lo split, 3 products, FP32
+                                 accumulate; near-pole terms in FP64 */
 #define RM_BF16X3         2   /* tensor cores: bf16 hi/lo split, 3 products, FP32
                                  accumulate; near-pole terms in FP64 */
 
@@ -90,11 +91,27 @@ typedef struct rm_opts {
     int solver;             /* matching solver: RM_SOLVER_AUTO (default: shared
                                memory up to 96 channels, global memory above),
                                RM_SOLVER_SMALL, RM_SOLVER_LARGE */
+    int formulation;        /* mixed-precision formation (Eq. rmatrix on tensor cores):
+                               RM_FORM_AUTO (default: pair operand while it is small,
+                               per-energy GEMM above), RM_FORM_PAIRS, RM_FORM_ENERGY */
 } rm_opts;
 
 #define RM_SOLVER_AUTO    0
 #define RM_SOLVER_SMALL   1
 #define RM_SOLVER_LARGE   2
+
+/* Mixed-precision formulations of the formation:
+ *   RM_FORM_PAIRS:  one GEMM per block of energies, R_packed[e][ij] =
+ *                   sum_k d_k(E_e) (w_ik w_jk / 2a); the pair operand takes
+ *                   n(n+1)/2 x N hi/lo elements (at most 4 GB), so it serves
+ *                   up to a few hundred channels;
+ *   RM_FORM_ENERGY: one GEMM per energy, R(E) = W diag(d(E)) W^T / 2a, with
+ *                   the scaled operand formed on the fly; any n up to 8192;
+ *                   FP32 accumulation is cut every 4096 poles and the
+ *                   segments are summed in FP64. */
+#define RM_FORM_AUTO      0
+#define RM_FORM_PAIRS     1
+#define RM_FORM_ENERGY    2
 
 /* Fills *opts with the defaults above. */
 void rm_default_opts(rm_opts *opts);

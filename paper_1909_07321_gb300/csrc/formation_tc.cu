@@ -24,12 +24,10 @@
 // Every mbarrier wait is bounded (about 2 s by %globaltimer); a wait that
 // gives up sets *err_flag, and every role then drains and exits, so the host
 // sees an error instead of a hung GPU.
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
-#include "rm_internal.cuh"
+#include "tc_sm103.cuh"
 
 namespace rmgb {
 namespace {
@@ -38,149 +36,11 @@ constexpr int BM = 128;            // energies per tile (TMEM lanes)
 constexpr int BN = 256;            // pairs per tile (TMEM columns)
 constexpr int STAGES = 2;
 constexpr int NTHREADS = 192;
-constexpr int ROW_BYTES = 128;     // one K-row of an operand tile (swizzle span)
+constexpr int ROW_BYTES = TC_ROW_BYTES;
 constexpr int A_TILE = BM * ROW_BYTES;   // 16 KB
 constexpr int B_TILE = BN * ROW_BYTES;   // 32 KB
 constexpr int STAGE_BYTES = 2 * (A_TILE + B_TILE);   // hi + lo of both: 96 KB
 constexpr int TMEM_COLS = 512;     // two 256-column accumulators
-constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Waits until the phase of `bar` with the given parity has completed. Gives
-// up (returns false, sets *err when err is not null) after WAIT_LIMIT_NS, or
-// as soon as another role has set *err.
-__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63) == 0) {
-            if (err && *(volatile int *)err) return false;
-            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-                if (err) atomicExch(err, 1);
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *tm, uint64_t *bar,
-                                            int x, int y)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"((uint64_t)tm), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// K-major operand in 128-byte-swizzled rows (as the TMA writes it): 8-row
-// groups 1024 bytes apart (stride-dimension offset), fixed-constant field 1,
-// swizzle mode 2 (128 B).
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr)
-{
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// Instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B format
-// (bits 7-9, 10-12: bf16 = 1 for kind::f16, tf32 = 2 for kind::tf32), both
-// K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-template <int KIND> __device__ __forceinline__ uint32_t idesc()
-{
-    constexpr uint32_t fmt = (KIND == TC_BF16X3) ? 1u : 2u;
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(BN >> 3) << 17) |
-           ((uint32_t)(BM >> 4) << 24);
-}
-
-template <int KIND>
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id,
-                                     uint32_t accumulate)
-{
-    if constexpr (KIND == TC_BF16X3) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(id), "r"(accumulate)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(id), "r"(accumulate)
-            : "memory");
-    }
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                     smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-        "%30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 template <int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
     form_r_tc_kernel(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
@@ -212,11 +72,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tmem_alloc(tmem_slot, TMEM_COLS);
     }
     tc_fence_before();
     __syncthreads();
@@ -245,15 +101,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (!ok) {
                 // let copies already in flight land before the CTA exits
-                const unsigned long long t0 = globaltimer();
-                while (globaltimer() - t0 < 2000000ull) {
-                }
+                spin_ns(2000000ull);
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer ----
-            const uint32_t id = idesc<KIND>();
+            const uint32_t id = idesc<KIND, BM, BN>();
             int stage = 0;
             uint32_t ph = 0;
             int acc = 0;
@@ -328,8 +182,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
-                     : "memory");
+        tmem_dealloc(tmem, TMEM_COLS);
 }
 
 // ---- operand preparation ---------------------------------------------------
@@ -399,19 +252,19 @@ __global__ void near_pole_fixup_kernel(PwDev pw, const double *__restrict__ E, i
     bool any = false;
     for (int k = k0; k < k1; ++k) any |= fabs(pw.Ek[k] - x) < delta;
     if (!any) return;
-    const int n = pw.n, np = tri_count(n);
+    const int n = pw.n;
     const double h = 0.5 / pw.a;
-    double *row = Rp + (size_t)e * tri_ld(n);
-    for (int p = lane; p < np; p += 32) {
-        int i = 0, rem = p;
-        while (rem >= n - i) { rem -= n - i; ++i; }
-        const int j = i + rem;
-        double s = 0.0;
-        for (int k = k0; k < k1; ++k) {
-            const double den = pw.Ek[k] - x;
-            if (fabs(den) < delta) s += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+    double *Re = Rp + (size_t)e * tri_ld(n);
+    for (int i = 0; i < n; ++i) {
+        double *row = Re + tri_idx(i, i, n);
+        for (int j = i + lane; j < n; j += 32) {
+            double s = 0.0;
+            for (int k = k0; k < k1; ++k) {
+                const double den = pw.Ek[k] - x;
+                if (fabs(den) < delta) s += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+            }
+            row[j - i] += h * s;
         }
-        row[p] += h * s;
     }
 }
 
@@ -424,53 +277,6 @@ __global__ void unpack_r_kernel(int n, int nE, const double *__restrict__ Rp, do
     const int i = ij / n, j = ij - (ij / n) * n;
     const int a = i < j ? i : j, b = i < j ? j : i;
     R[idx] = Rp[(size_t)e * tri_ld(n) + tri_idx(a, b, n)];
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-        else
-            cudaGetLastError();
-    }
-    return fn;
-}
-
-// 2-D K-major operand map: rows x Kpad elements, box (128 bytes of K) x box_rows.
-bool make_map(CUtensorMap *m, const void *base, int kind, int Kpad, int rows, int box_rows)
-{
-    auto fn = encode_fn();
-    if (!fn) return false;
-    const int es = (kind == TC_BF16X3) ? 2 : 4;
-    cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)Kpad * es};
-    cuuint32_t box[2] = {(cuuint32_t)(ROW_BYTES / es), (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, kind == TC_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
-                    2, const_cast<void *>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-int num_sms()
-{
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
-            cudaGetLastError();
-            n = 1;
-        }
-    }
-    return n;
 }
 
 }  // namespace

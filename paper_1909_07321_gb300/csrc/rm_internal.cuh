@@ -78,6 +78,21 @@ cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const
 // R_packed[e][p] += (1/2a) w_ik w_jk / (E_k - E_e) over poles with |E_k - E_e| < delta (FP64).
 cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, double delta,
                                    double *Rp, cudaStream_t s);
+// Per-energy formulation (formation_tc_energy.cu): R(E) = W diag(d(E)) W^T / 2a.
+int pe_max_n();
+// Workspace per energy: FP32 partial tiles of every K segment + d(E) in FP32.
+size_t pe_bytes_per_energy(int n, int N, int kind);
+// W in FP32 plus w split hi/lo, [n][Kpad] each.
+size_t pe_operand_bytes(int n, int N, int kind);
+cudaError_t launch_pe_prep_w(const PwDev &pw, int kind, int Kpad, float *W32, void *Wh, void *Wl,
+                             cudaStream_t s);
+cudaError_t launch_pe_d32(const PwDev &pw, const double *E, int nE, double delta, int Kpad, float *D32,
+                          cudaStream_t s);
+cudaError_t launch_form_r_pe(int kind, int n, int Kpad, const float *W32, const void *Wh, const void *Wl,
+                             const float *D32, int nE, float *part, int *err_flag, cudaStream_t s);
+// Sums the segments in FP64, adds the near-pole terms, scales by 1/2a -> packed R.
+cudaError_t launch_pe_reduce(const PwDev &pw, int kind, int Kpad, const double *E, int nE, double delta,
+                             const float *part, double *Rp, int ldR, cudaStream_t s);
 // Packed -> full symmetric [nE][n][n] (inspection only).
 cudaError_t launch_unpack_r(int n, int nE, const double *Rp, double *R, cudaStream_t s);
 int tc_kpad(int N, int kind);

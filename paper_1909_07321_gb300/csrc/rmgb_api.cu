@@ -58,13 +58,18 @@ struct PwHost {
     // mixed-precision operand P = w_i w_j / 2a, split hi/lo (built on first use)
     DevBuf Ph, Pl;
     int p_kind = -1, p_kpad = 0;
+    // per-energy formulation: W in FP32 and w split hi/lo (built on first use)
+    DevBuf W32, Wh, Wl;
+    int w_kind = -1;
     std::vector<double> h_e_thr;
     void release()
     {
-        for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl})
+        for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
+                          &Wh, &Wl})
             d->release();
         loaded = channels = false;
         p_kind = -1;
+        w_kind = -1;
     }
     PwDev dev() const
     {
@@ -100,7 +105,7 @@ struct rm_ctx {
     std::vector<double> grid_host;
     DevBuf omega;
     // workspace
-    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL;
+    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart;
     long long launches = 0;
     // per-phase event pairs (tracing)
     bool prof = false;
@@ -224,6 +229,7 @@ extern "C" void rm_default_opts(rm_opts *o)
     o->mem_budget = 0;
     o->mqdt_kappa_a_max = 5.0;
     o->solver = RM_SOLVER_AUTO;
+    o->formulation = RM_FORM_AUTO;
 }
 
 extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
@@ -233,6 +239,7 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
     rm_opts o;
     if (opts) o = *opts; else rm_default_opts(&o);
     if (o.solver < RM_SOLVER_AUTO || o.solver > RM_SOLVER_LARGE) return RM_EINVAL;
+    if (o.formulation < RM_FORM_AUTO || o.formulation > RM_FORM_ENERGY) return RM_EINVAL;
     if (!(o.eps_thr >= 0) || !(o.delta_pole >= 0) || !std::isfinite(o.fnumin) ||
         !(o.mqdt_kappa_a_max >= 0) ||
         !std::isfinite(o.nu_margin) ||
@@ -272,7 +279,7 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
     for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
-                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL})
+                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
         for (auto &pr : ctx->ev[p]) {
@@ -312,6 +319,10 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
     P.Ph.release();
     P.Pl.release();
     P.p_kind = -1;
+    P.W32.release();
+    P.Wh.release();
+    P.Wl.release();
+    P.w_kind = -1;
     CK(upload(P.Ek, Es.data(), Es.size(), ctx->stream));
     CK(upload(P.W, Ws.data(), Ws.size(), ctx->stream));
     P.n = n_ch;
@@ -384,19 +395,45 @@ int device_energies(rm_ctx *ctx, int n_E, const double *E, const double **dE)
 int tc_kind(int precision) { return precision == RM_BF16X3 ? TC_BF16X3 : TC_TF32X3; }
 size_t tc_esize(int kind) { return kind == TC_BF16X3 ? 2 : 4; }
 
-// Largest n_pairs x Kpad operand (hi + lo) the Khatri-Rao formation keeps per
-// partial wave; larger waves need the per-energy formulation (not built).
+// Largest n_pairs x Kpad operand (hi + lo) the pair formulation keeps per
+// partial wave; larger waves take the per-energy formulation.
 constexpr size_t MAX_P_BYTES = (size_t)4 << 30;
+// Automatic choice: the pair formulation up to this channel count (its tiles
+// carry no padding in the pair dimension; the per-energy tiles of 128 x 256
+// channels are mostly padding for small n).
+constexpr int AUTO_PAIRS_MAX_N = 192;
+
+size_t pair_operand_bytes(const PwHost &P, int kind)
+{
+    return (size_t)tri_count(P.n) * tc_kpad(P.N, kind) * tc_esize(kind) * 2;
+}
+
+// Formulation the context's precision and options give this partial wave.
+int formulation(rm_ctx *ctx, const PwHost &P)
+{
+    if (ctx->opts.precision == RM_FP64) return 0;
+    if (ctx->opts.formulation != RM_FORM_AUTO) return ctx->opts.formulation;
+    const int kind = tc_kind(ctx->opts.precision);
+    return (P.n <= AUTO_PAIRS_MAX_N && pair_operand_bytes(P, kind) <= MAX_P_BYTES) ? RM_FORM_PAIRS
+                                                                                   : RM_FORM_ENERGY;
+}
 
 int check_precision(rm_ctx *ctx, const PwHost &P)
 {
-    if (ctx->opts.precision == RM_FP64) return RM_SUCCESS;
+    const int f = formulation(ctx, P);
+    if (f == 0) return RM_SUCCESS;
     const int kind = tc_kind(ctx->opts.precision);
-    const size_t bytes = (size_t)tri_count(P.n) * tc_kpad(P.N, kind) * tc_esize(kind) * 2;
-    if (bytes > MAX_P_BYTES)
-        return fail(ctx, RM_EUNSUPPORTED,
-                    "mixed-precision formation of n_ch=%d, n_poles=%d needs %zu bytes of pair "
-                    "operands (limit %zu)", P.n, P.N, bytes, MAX_P_BYTES);
+    if (f == RM_FORM_PAIRS) {
+        const size_t bytes = pair_operand_bytes(P, kind);
+        if (bytes > MAX_P_BYTES)
+            return fail(ctx, RM_EUNSUPPORTED,
+                        "pair formulation of n_ch=%d, n_poles=%d needs %zu bytes of pair operands "
+                        "(limit %zu); use RM_FORM_ENERGY",
+                        P.n, P.N, bytes, MAX_P_BYTES);
+    } else if (P.n > pe_max_n()) {
+        return fail(ctx, RM_EUNSUPPORTED, "per-energy formulation takes at most %d channels (n_ch=%d)",
+                    pe_max_n(), P.n);
+    }
     return RM_SUCCESS;
 }
 
@@ -411,10 +448,10 @@ int block_energies(rm_ctx *ctx, const PwHost &P)
 {
     size_t per = (size_t)tri_ld(P.n) * sizeof(double) + (size_t)P.n * sizeof(ChanFn) + 64;
     if (use_large(ctx, P)) per += solve_large_bytes_per_energy(P.n);
-    if (ctx->opts.precision != RM_FP64) {
-        const int kind = tc_kind(ctx->opts.precision);
-        per += 2 * (size_t)tc_kpad(P.N, kind) * tc_esize(kind);
-    }
+    const int f = formulation(ctx, P);
+    const int kind = tc_kind(ctx->opts.precision);
+    if (f == RM_FORM_PAIRS) per += 2 * (size_t)tc_kpad(P.N, kind) * tc_esize(kind);
+    if (f == RM_FORM_ENERGY) per += pe_bytes_per_energy(P.n, P.N, kind);
     size_t B = ctx->opts.mem_budget / per;
     if (B < 1) B = 1;
     if (B > MAX_BLOCK_E) B = MAX_BLOCK_E;
@@ -435,6 +472,36 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
     const int kind = tc_kind(ctx->opts.precision);
     const int Kpad = tc_kpad(P.N, kind);
     const size_t es = tc_esize(kind);
+    if (!ctx->wsErr.p) {
+        CK(ctx->wsErr.reserve(sizeof(int)));
+        CK(cudaMemsetAsync(ctx->wsErr.p, 0, sizeof(int), ctx->stream));
+    }
+    if (formulation(ctx, P) == RM_FORM_ENERGY) {
+        if (P.w_kind != kind) {
+            const size_t nk = (size_t)P.n * Kpad;
+            CK(P.W32.reserve(nk * sizeof(float)));
+            CK(P.Wh.reserve(nk * es));
+            CK(P.Wl.reserve(nk * es));
+            CK(launch_pe_prep_w(d, kind, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ctx->stream));
+            ctx->launches++;
+            P.w_kind = kind;
+        }
+        CK(ctx->wsDh.reserve((size_t)nE * Kpad * sizeof(float)));
+        CK(ctx->wsPart.reserve(pe_bytes_per_energy(P.n, P.N, kind) * (size_t)nE));
+        CK(prof_begin(ctx, RM_PH_SPLIT));
+        CK(launch_pe_d32(d, E, nE, ctx->opts.delta_pole, Kpad, ctx->wsDh.as<float>(), ctx->stream));
+        CK(prof_end(ctx, RM_PH_SPLIT));
+        CK(prof_begin(ctx, RM_PH_FORM));
+        CK(launch_form_r_pe(kind, P.n, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ctx->wsDh.as<float>(), nE,
+                            ctx->wsPart.as<float>(), ctx->wsErr.as<int>(), ctx->stream));
+        CK(prof_end(ctx, RM_PH_FORM));
+        CK(prof_begin(ctx, RM_PH_FIXUP));
+        CK(launch_pe_reduce(d, kind, Kpad, E, nE, ctx->opts.delta_pole, ctx->wsPart.as<float>(), R,
+                            tri_ld(P.n), ctx->stream));
+        CK(prof_end(ctx, RM_PH_FIXUP));
+        ctx->launches += 3;
+        return RM_SUCCESS;
+    }
     if (P.p_kind != kind) {
         const size_t pb = (size_t)tri_count(P.n) * Kpad * es;
         CK(P.Ph.reserve(pb));
@@ -446,10 +513,6 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
     }
     CK(ctx->wsDh.reserve((size_t)nE * Kpad * es));
     CK(ctx->wsDl.reserve((size_t)nE * Kpad * es));
-    if (!ctx->wsErr.p) {
-        CK(ctx->wsErr.reserve(sizeof(int)));
-        CK(cudaMemsetAsync(ctx->wsErr.p, 0, sizeof(int), ctx->stream));
-    }
     CK(prof_begin(ctx, RM_PH_SPLIT));
     CK(launch_split_d(d, E, nE, ctx->opts.delta_pole, kind, Kpad, ctx->wsDh.p, ctx->wsDl.p,
                       ctx->stream));

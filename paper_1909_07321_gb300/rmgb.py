@@ -35,7 +35,8 @@ class RmOpts(ctypes.Structure):
                 ("eps_thr", ctypes.c_double), ("fnumin", ctypes.c_double),
                 ("nu_margin", ctypes.c_double), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
-                ("mqdt_kappa_a_max", ctypes.c_double), ("solver", ctypes.c_int)]
+                ("mqdt_kappa_a_max", ctypes.c_double), ("solver", ctypes.c_int),
+                ("formulation", ctypes.c_int)]
 
 
 class RmError(RuntimeError):
@@ -244,6 +245,8 @@ class Context:
         if stream is not None:
             o.stream = stream
         for k, v in kw.items():
+            if k not in [f[0] for f in RmOpts._fields_]:
+                raise TypeError("unknown rm_opts field %r" % k)
             setattr(o, k, v)
         self.h = rm_create(o)
 

@@ -46,31 +46,64 @@ def _energies(pw, E, n_rand, seed):
 
 
 PRECS = [("bf16x3", 2), ("tf32x3", 1)]
+FORMS = [("pairs", 1), ("energy", 2)]
 
 
-@pytest.mark.parametrize("name,prec", PRECS)
-def test_form_r_mixed_bound(rt, name, prec):
+def _gpu_r(rt, pw, Es, prec, form):
     torch, rmgb = rt
+    n = pw["W"].shape[0]
+    with rmgb.Context(precision=prec, formulation=form) as ctx:
+        ctx.load_pw(0, pw)
+        Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+        R = torch.zeros((Es.size, n, n), dtype=torch.float64, device="cuda")
+        ctx.form_r(0, Ed, R)
+        ctx.sync()
+        return R.cpu().numpy()
+
+
+def _check_r_bound(pw, Es, Rg, tag):
+    absW = np.abs(pw["W"])
+    for m, x in enumerate(Es):
+        Ro = oracle.r_matrix(float(x), pw["E_k"], pw["W"], pw["a"])
+        dd = np.abs(pw["E_k"] - x)
+        far = dd >= 1e-3
+        S = (absW[:, far] / dd[far]) @ absW[:, far].T / (2 * pw["a"])
+        Sn = (absW[:, ~far] / dd[~far]) @ absW[:, ~far].T / (2 * pw["a"])
+        assert np.array_equal(Rg[m], Rg[m].T)
+        err = np.abs(Rg[m] - Ro) - 1e-13 * Sn
+        assert np.all(err <= R_BOUND * S + 1e-300), (tag, x, (err / S).max())
+
+
+@pytest.mark.parametrize("fname,form", FORMS)
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_form_r_mixed_bound(rt, name, prec, fname, form):
     for pws, E in [synth.workload_small(), synth.workload_64ch()]:
         pw = pws[0]
         Es = _energies(pw, E, 80, 5)
-        n = pw["W"].shape[0]
-        with rmgb.Context(precision=prec) as ctx:
-            ctx.load_pw(0, pw)
-            Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
-            R = torch.zeros((Es.size, n, n), dtype=torch.float64, device="cuda")
-            ctx.form_r(0, Ed, R)
-            ctx.sync()
-            Rg = R.cpu().numpy()
-        absW = np.abs(pw["W"])
-        for m, x in enumerate(Es):
-            Ro = oracle.r_matrix(float(x), pw["E_k"], pw["W"], pw["a"])
-            dd = np.abs(pw["E_k"] - x)
-            far = dd >= 1e-3
-            S = (absW[:, far] / dd[far]) @ absW[:, far].T / (2 * pw["a"])
-            Sn = (absW[:, ~far] / dd[~far]) @ absW[:, ~far].T / (2 * pw["a"])
-            assert np.array_equal(Rg[m], Rg[m].T)
-            assert np.all(np.abs(Rg[m] - Ro) <= R_BOUND * S + 1e-13 * Sn + 1e-300), (name, x)
+        _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, prec, form), (name, fname))
+
+
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_form_r_energy_wide(rt, name, prec):
+    """Per-energy formulation on 300 channels and 9000 poles: several row and
+    column tiles, a ragged last tile, three K segments (the last ragged), an
+    odd energy count and energies within delta of poles."""
+    pw = synth.random_pw(301, 300, 9000, z=2.0, a=20.0, e_max=3.0, sigma=0.05, pole_lo=-5.0,
+                         pole_hi=200.0, l_max=8)
+    rng = np.random.default_rng(7)
+    Es = np.sort(np.concatenate([rng.uniform(0.01, 4.0, 6),
+                                 pw["E_k"][rng.choice(1500, 3)] + rng.uniform(-5e-4, 5e-4, 3)]))
+    _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, prec, 2), name)
+
+
+def test_form_r_energy_1000ch(rt):
+    """The 1000-channel, 30000-pole workload shape (automatic choice takes the
+    per-energy formulation): two energies, one within delta of a pole."""
+    pws, E = synth.workload_1000ch(8)
+    pw = pws[0]
+    k = int(np.searchsorted(pw["E_k"], 3.0))
+    Es = np.array([E[3], pw["E_k"][k] + 2e-4])
+    _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, 2, 0), "1000ch")
 
 
 def _first_order_k_bound(pw, x):
@@ -97,14 +130,14 @@ def _first_order_k_bound(pw, x):
     return np.abs(Ainv[oi, :]) @ (R_BOUND * S) @ np.abs(d2[:, None] * P + d1[:, None] * X)
 
 
-@pytest.mark.parametrize("name,prec", PRECS)
-def test_mixed_k_and_omega_bounds(rt, name, prec):
+@pytest.mark.parametrize("name,prec,form", [("bf16x3", 2, 1), ("tf32x3", 1, 1), ("bf16x3-energy", 2, 2)])
+def test_mixed_k_and_omega_bounds(rt, name, prec, form):
     torch, rmgb = rt
     pws, E = synth.workload_64ch()
     pw = pws[0]
     Es = _energies(pw, E, 150, 6)
     n = pw["W"].shape[0]
-    with rmgb.Context(precision=prec) as ctx:
+    with rmgb.Context(precision=prec, formulation=form) as ctx:
         ctx.load_pw(0, pw)
         Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
         K = torch.zeros((Es.size, n * n), dtype=torch.float64, device="cuda")
@@ -132,7 +165,8 @@ def test_mixed_k_and_omega_bounds(rt, name, prec):
     assert np.median(eK) <= K_MED, np.median(eK)
 
 
-def test_mixed_matches_fp64_path_statuses_and_layout(rt):
+@pytest.mark.parametrize("form", [1, 2])
+def test_mixed_matches_fp64_path_statuses_and_layout(rt, form):
     """Same statuses, open counts and Omega layout as the FP64 path on a
     multi-block run (small workspace budget, ragged last block)."""
     torch, rmgb = rt
@@ -140,8 +174,8 @@ def test_mixed_matches_fp64_path_statuses_and_layout(rt):
     pw = pws[0]
     outs = []
     for prec in (0, 2):
-        per = 4 * 4 * 8 + 4 * 32 + 64 + 2 * 128 * 2
-        with rmgb.Context(precision=prec, mem_budget=per * 97) as ctx:
+        per = 4 * 4 * 8 + 4 * 48 + 64 + (2 * 128 * 2 if form == 1 else 128 * 256 * 4 + 128 * 4)
+        with rmgb.Context(precision=prec, formulation=form, mem_budget=per * 97) as ctx:
             ctx.load_pw(0, pw)
             st = torch.zeros(E.size, dtype=torch.int32, device="cuda")
             no = torch.zeros(E.size, dtype=torch.int32, device="cuda")
