@@ -187,11 +187,13 @@ def _time_steps(ctx, Ed, stream, flush, steps, rmgb, torch):
 
 
 def _solve_flops(n, n_open):
-    """Algorithmic FP64 flops of steps (c)+(d) for one energy: elimination of
-    the n x (n + n_o) system (2/3 n^3 + 2 n^2 n_o), then M = 1 + K^2 (2 n_o^3),
-    Cholesky (n_o^3/3), X = M^{-1} K (2 n_o^3), Y = K X (2 n_o^3)."""
+    """Algorithmic FP64 flops of steps (c)+(d) for one energy, as the
+    shared-memory solver takes them: elimination of the n x (n + n_o) system
+    (2/3 n^3 + n^2 n_o), back-substitution of the n_o trailing rows (n_o^3),
+    M = 1 + K^2 (upper triangle, n_o^3), M^{-1} by Gauss-Jordan (2 n_o^3),
+    X = K M^{-1} (upper triangle, n_o^3)."""
     no = n_open.astype(np.float64)
-    return float(np.sum(2.0 / 3.0 * n**3 + 2.0 * n * n * no + (6.0 + 1.0 / 3.0) * no**3))
+    return float(np.sum(2.0 / 3.0 * n**3 + n * n * no + 5.0 * no**3))
 
 
 def run_serving(args, prec):
@@ -224,6 +226,66 @@ def run_serving(args, prec):
             "requests": st["requests"], "energy_solves": st["energy_solves"],
             "energy_solves_per_s": st["energy_solves_per_s"],
             "p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"], "mean_ms": 1e3 * st["mean_s"]}
+
+
+def _pe_tiles(n):
+    """Tiles of 128 rows x 256 columns holding some (i <= j) of an n x n matrix."""
+    n_ib, n_jb = -(-n // 128), -(-n // 256)
+    return sum(min(n_ib, 2 * jb + 2) for jb in range(n_jb))
+
+
+def run_wide(args, prec, stream, flush, peaks, peak_src):
+    """The 1000-channel, 30000-pole workload (the per-energy tensor-core
+    formation): a strided sample of its energy grid through the mixed path,
+    and every 16th of those through the plain FP64 path, with the Omega error
+    of the mixed path on the common energies."""
+    import torch
+
+    from paper_1909_07321_gb300 import rmgb, synth
+    pws, Eall = synth.workload_1000ch()
+    pw = pws[0]
+    n, N = pw["W"].shape
+    idx = np.linspace(0, Eall.size - 1, args.wide_energies).round().astype(int)
+    E = np.ascontiguousarray(Eall[idx])
+    sub = np.arange(0, E.size, 16)
+    out = {"workload": ("one partial wave: 1000 channels (250 levels x 4 on 0-8 Ry, l 0-8, z=2), "
+                        "30000 poles on [-5,200] Ry, w~N(0,0.02^2), a=20; %d of its 5000 energies on "
+                        "0-10 Ry (evenly strided)" % E.size)}
+    res = {}
+    for name, pr, Es in [("mixed", prec, E), ("fp64", 0, E[sub])]:
+        ctx = rmgb.Context(precision=pr, stream=stream.cuda_stream)
+        ctx.load_pw(0, pw)
+        Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            ctx.solve_energies(0, Ed)
+            ctx.reset_omega()
+            t, ph, launches = _time_steps(ctx, Ed, stream, flush, 2, rmgb, torch)
+            om = ctx.collision_strengths()
+        ctx.close()
+        res[name] = (t, ph, om, Es.size)
+    t, ph, om, ne = res["mixed"]
+    names = {rmgb.RM_PH_CHANFN: "chanfn", rmgb.RM_PH_FORM: "form", rmgb.RM_PH_FIXUP: "reduce+nearpole",
+             rmgb.RM_PH_SOLVE: "solve", rmgb.RM_PH_SPLIT: "d(E)"}
+    form_ms = ph[rmgb.RM_PH_FORM][1] / 2
+    alg = n * (n + 1) * N * ne / (form_ms * 1e-3) / 1e12
+    tpk = peaks["bf16_tflops"] if prec == 2 else peaks["bf16_tflops"] / 2.0
+    t64, _, om64, ne64 = res["fp64"]
+    rel = np.linalg.norm(om[sub] - om64, axis=1) / np.maximum(np.linalg.norm(om64, axis=1), 1e-300)
+    out.update({
+        "mixed": {"energy_solves_per_s": ne / (t * 1e-3), "ms_per_step": t, "energies": ne,
+                  "phases_ms_per_step": {v: ph[k][1] / 2 for k, v in names.items()}},
+        "fp64_path": {"energy_solves_per_s": ne64 / (t64 * 1e-3), "ms_per_step": t64, "energies": ne64},
+        "omega_rel_err_vs_fp64": {"median": float(np.median(rel)), "max": float(rel.max())},
+        "formation_roofline": {
+            "bound": "tensor", "achieved": alg, "peak": tpk, "unit": "TFLOP/s", "frac": alg / tpk,
+            "issued_frac": 3.0 * alg / tpk,
+            "executed_frac": 3.0 * alg * _pe_tiles(n) * 128 * 256 / (n * (n + 1) / 2) / tpk,
+            "traffic": None, "kernel": "form_r_pe_kernel (%s, one GEMM per energy)" % args.precision,
+            "note": ("algorithmic n(n+1)N flops per energy; issued x3 (hi/lo products); executed "
+                     "counts the tiles of 128 x 256 that cover the upper triangle"),
+            "peak_source": ("bf16 dense burst, %s" % peak_src) if prec == 2 else
+            ("tf32 = bf16 dense burst (%s) x nominal ratio 1/2" % peak_src)}})
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -320,6 +382,9 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     peaks, peak_src = _peaks()
+    wide = None
+    if world == 1 and args.wide_energies > 0:
+        wide = run_wide(args, prec if prec != 0 else 2, stream, flush, peaks, peak_src)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = N_SM * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     names = {rmgb.RM_PH_NEARPOLE: "nearpole", rmgb.RM_PH_CHANFN: "chanfn", rmgb.RM_PH_FORM: "form",
@@ -376,6 +441,7 @@ def run_ours(args, rank, world, local_rank):
             "phase_share": share,
             "fp64_path": fp64,
             "serving": serving_line,
+            "wide_1000ch": wide,
             "cpu_baseline": cpu,
             "e2e": {"value": world * E.size / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(E.size * 8),
@@ -397,6 +463,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests in the serving leg (0 to skip)")
     ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrival rate (1/s)")
+    ap.add_argument("--wide-energies", type=int, default=256,
+                    help="energies of the 1000-channel leg (0 to skip)")
     ap.add_argument("--energies", type=int, default=N_E,
                     help="energies per GPU (smaller only for profiler captures)")
     args = ap.parse_args()

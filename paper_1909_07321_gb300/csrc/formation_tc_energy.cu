@@ -357,39 +357,23 @@ __global__ void pe_prep_w_kernel(PwDev pw, int kind, int Kpad, float *W32, void 
     }
 }
 
-// Per energy block: d_k(E_e) in FP32, 0 where |E_k - E_e| < delta or k >= N.
+// Per energy block: d_k(E_e) in FP32, 0 where |E_k - E_e| < delta or k >= N;
+// the thread of k = 0 also records the pole range [k0, k1) that can lie
+// within delta of E_e (sorted E_k, binary search) for the reduction.
 __global__ void pe_d32_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta, int Kpad,
-                              float *D32)
+                              float *D32, int2 *np_range)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long long)nE * Kpad) return;
     const int e = (int)(idx / Kpad), k = (int)(idx - (long long)e * Kpad);
+    const double x = E[e];
     float d = 0.f;
     if (k < pw.N) {
-        const double den = pw.Ek[k] - E[e];
+        const double den = pw.Ek[k] - x;
         if (fabs(den) >= delta) d = (float)(1.0 / den);
     }
     D32[idx] = d;
-}
-
-// One block per (row i, energy e): R_ij for j >= i = (1/2a) [sum over
-// segments of the FP32 partials (in FP64, segment order) + the FP64 terms of
-// the poles within delta of E].
-__global__ void pe_reduce_kernel(PwDev pw, const double *__restrict__ E, double delta,
-                                 const float *__restrict__ part, const PeGeom g, double *__restrict__ Rp,
-                                 int ldR)
-{
-    const int i = blockIdx.x, e = blockIdx.y;
-    const int n = pw.n;
-    __shared__ int s_off[PE_MAX_JB];
-    __shared__ int s_k0, s_k1;
-    const double x = E[e];
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int jb = 0; jb < g.n_jb; ++jb) {
-            s_off[jb] = acc;
-            acc += pe_col_tiles(jb, g.n_ib);
-        }
+    if (k == 0) {
         int lo = 0, hi = pw.N;
         while (lo < hi) {   // first k with E_k > x - delta
             const int mid = (lo + hi) >> 1;
@@ -397,26 +381,49 @@ __global__ void pe_reduce_kernel(PwDev pw, const double *__restrict__ E, double 
         }
         int k1 = lo;
         while (k1 < pw.N && pw.Ek[k1] < x + delta) ++k1;
-        s_k0 = lo;
-        s_k1 = k1;
+        np_range[e] = make_int2(lo, k1);
+    }
+}
+
+// R_ij for j >= i = (1/2a) [sum over segments of the FP32 partials (in FP64,
+// segment order) + the FP64 terms of the poles within delta of E]. Block
+// (energy e, band of PE_RROWS rows); threads along j, so both the partial
+// rows and the packed output rows are read and written contiguously.
+constexpr int PE_RROWS = 4;
+__global__ void __launch_bounds__(256)
+    pe_reduce_kernel(PwDev pw, const double *__restrict__ E, double delta, const int2 *__restrict__ np_range,
+                     const float *__restrict__ part, const PeGeom g, double *__restrict__ Rp, int ldR)
+{
+    const int e = blockIdx.x;
+    const int n = pw.n;
+    __shared__ int s_off[PE_MAX_JB];
+    if (threadIdx.x < g.n_jb) {
+        int acc = 0;
+        for (int jb = 0; jb < (int)threadIdx.x; ++jb) acc += pe_col_tiles(jb, g.n_ib);
+        s_off[threadIdx.x] = acc;
     }
     __syncthreads();
-    const int ib = i / PE_BM, il = i - ib * PE_BM;
-    const int k0 = s_k0, k1 = s_k1;
+    const double x = E[e];
+    const int2 kr = np_range[e];
     const double h = 0.5 / pw.a;
     const size_t seg_stride = (size_t)g.nE * g.n_tiles * PE_BM * PE_BN;
-    double *out = Rp + (size_t)e * ldR + tri_idx(i, i, n);
-    for (int j = i + threadIdx.x; j < n; j += blockDim.x) {
-        const int jb = j / PE_BN;
-        const int t = s_off[jb] + ib;
-        const float *p = part + (((size_t)e * g.n_tiles + t) * PE_BM + il) * PE_BN + (j - jb * PE_BN);
-        double s = 0.0;
-        for (int sg = 0; sg < g.n_seg; ++sg) s += (double)p[sg * seg_stride];
-        for (int k = k0; k < k1; ++k) {
-            const double den = pw.Ek[k] - x;   // same exclusion test as pe_d32_kernel
-            if (fabs(den) < delta) s += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+    double *Re = Rp + (size_t)e * ldR;
+    const int i0 = blockIdx.y * PE_RROWS;
+    for (int i = i0; i < min(n, i0 + PE_RROWS); ++i) {
+        const int ib = i / PE_BM, il = i - ib * PE_BM;
+        double *out = Re + tri_idx(i, i, n);
+        for (int j = i + threadIdx.x; j < n; j += blockDim.x) {
+            const int jb = j / PE_BN;
+            const float *p =
+                part + (((size_t)e * g.n_tiles + s_off[jb] + ib) * PE_BM + il) * PE_BN + (j - jb * PE_BN);
+            double s = 0.0;
+            for (int sg = 0; sg < g.n_seg; ++sg) s += (double)__ldg(p + sg * seg_stride);
+            for (int k = kr.x; k < kr.y; ++k) {
+                const double den = pw.Ek[k] - x;   // same exclusion test as pe_d32_kernel
+                if (fabs(den) < delta) s += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+            }
+            out[j - i] = h * s;
         }
-        out[j - i] = h * s;
     }
 }
 
@@ -447,7 +454,8 @@ size_t pe_bytes_per_energy(int n, int N, int kind)
 {
     const int Kpad = tc_kpad(N, kind);
     const PeGeom g = pe_geom(n, Kpad, kind, 1);
-    return (size_t)g.n_seg * g.n_tiles * PE_BM * PE_BN * sizeof(float) + (size_t)Kpad * sizeof(float);
+    return (size_t)g.n_seg * g.n_tiles * PE_BM * PE_BN * sizeof(float) + (size_t)Kpad * sizeof(float) +
+           sizeof(int2);
 }
 
 size_t pe_operand_bytes(int n, int N, int kind)
@@ -470,7 +478,8 @@ cudaError_t launch_pe_d32(const PwDev &pw, const double *E, int nE, double delta
 {
     const long long total = (long long)nE * Kpad;
     if (total == 0) return cudaSuccess;
-    pe_d32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pw, E, nE, delta, Kpad, D32);
+    int2 *np_range = reinterpret_cast<int2 *>(D32 + (size_t)nE * Kpad);
+    pe_d32_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pw, E, nE, delta, Kpad, D32, np_range);
     return cudaGetLastError();
 }
 
@@ -502,11 +511,13 @@ cudaError_t launch_form_r_pe(int kind, int n, int Kpad, const float *W32, const 
 }
 
 cudaError_t launch_pe_reduce(const PwDev &pw, int kind, int Kpad, const double *E, int nE, double delta,
-                             const float *part, double *Rp, int ldR, cudaStream_t s)
+                             const float *D32, const float *part, double *Rp, int ldR, cudaStream_t s)
 {
     if (nE == 0) return cudaSuccess;
     const PeGeom g = pe_geom(pw.n, Kpad, kind, nE);
-    pe_reduce_kernel<<<dim3((unsigned)pw.n, (unsigned)nE), 128, 0, s>>>(pw, E, delta, part, g, Rp, ldR);
+    const int2 *np_range = reinterpret_cast<const int2 *>(D32 + (size_t)nE * Kpad);
+    pe_reduce_kernel<<<dim3((unsigned)nE, (unsigned)((pw.n + PE_RROWS - 1) / PE_RROWS)), 256, 0, s>>>(
+        pw, E, delta, np_range, part, g, Rp, ldR);
     return cudaGetLastError();
 }
 

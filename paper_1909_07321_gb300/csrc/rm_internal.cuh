@@ -80,7 +80,8 @@ cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, dou
                                    double *Rp, cudaStream_t s);
 // Per-energy formulation (formation_tc_energy.cu): R(E) = W diag(d(E)) W^T / 2a.
 int pe_max_n();
-// Workspace per energy: FP32 partial tiles of every K segment + d(E) in FP32.
+// Workspace per energy: FP32 partial tiles of every K segment + d(E) in FP32
+// (D32 holds [nE][Kpad] floats followed by nE int2 near-pole ranges).
 size_t pe_bytes_per_energy(int n, int N, int kind);
 // W in FP32 plus w split hi/lo, [n][Kpad] each.
 size_t pe_operand_bytes(int n, int N, int kind);
@@ -92,7 +93,7 @@ cudaError_t launch_form_r_pe(int kind, int n, int Kpad, const float *W32, const 
                              const float *D32, int nE, float *part, int *err_flag, cudaStream_t s);
 // Sums the segments in FP64, adds the near-pole terms, scales by 1/2a -> packed R.
 cudaError_t launch_pe_reduce(const PwDev &pw, int kind, int Kpad, const double *E, int nE, double delta,
-                             const float *part, double *Rp, int ldR, cudaStream_t s);
+                             const float *D32, const float *part, double *Rp, int ldR, cudaStream_t s);
 // Packed -> full symmetric [nE][n][n] (inspection only).
 cudaError_t launch_unpack_r(int n, int nE, const double *Rp, double *R, cudaStream_t s);
 int tc_kpad(int N, int kind);

@@ -486,7 +486,7 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
             ctx->launches++;
             P.w_kind = kind;
         }
-        CK(ctx->wsDh.reserve((size_t)nE * Kpad * sizeof(float)));
+        CK(ctx->wsDh.reserve((size_t)nE * Kpad * sizeof(float) + (size_t)nE * sizeof(int2)));
         CK(ctx->wsPart.reserve(pe_bytes_per_energy(P.n, P.N, kind) * (size_t)nE));
         CK(prof_begin(ctx, RM_PH_SPLIT));
         CK(launch_pe_d32(d, E, nE, ctx->opts.delta_pole, Kpad, ctx->wsDh.as<float>(), ctx->stream));
@@ -496,7 +496,8 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
                             ctx->wsPart.as<float>(), ctx->wsErr.as<int>(), ctx->stream));
         CK(prof_end(ctx, RM_PH_FORM));
         CK(prof_begin(ctx, RM_PH_FIXUP));
-        CK(launch_pe_reduce(d, kind, Kpad, E, nE, ctx->opts.delta_pole, ctx->wsPart.as<float>(), R,
+        CK(launch_pe_reduce(d, kind, Kpad, E, nE, ctx->opts.delta_pole, ctx->wsDh.as<float>(),
+                            ctx->wsPart.as<float>(), R,
                             tri_ld(P.n), ctx->stream));
         CK(prof_end(ctx, RM_PH_FIXUP));
         ctx->launches += 3;

@@ -17,9 +17,11 @@
 //   K = K_oo - K_oc (K_cc + diag(tan pi nu))^{-1} K_co.
 //
 // (d) T = 2iK(1 - iK)^{-1} (Section "Glossary of terms") in real form. K is
-// symmetric, so with M = 1 + K^2 (SPD), X = M^{-1} K and Y = M^{-1} K^2 = K X:
+// symmetric, so with M = 1 + K^2 (SPD), X = M^{-1} K and Y = M^{-1} K^2 =
+// 1 - M^{-1}:
 //   T = -2Y + 2iX,  |T_ab|^2 = 4 (X_ab^2 + Y_ab^2).
-// M is factored by Cholesky. Then for target levels I <= J, one thread owns
+// M^{-1} by Gauss-Jordan; X from one product (upper triangle: X is
+// symmetric). Then for target levels I <= J, one thread owns
 // Omega_IJ(E) and adds g sum_{a in I, b in J} |T_ab|^2 in a fixed order, so
 // the accumulation is deterministic (no atomics).
 #include <math.h>
@@ -107,6 +109,92 @@ __device__ void block_backsub(double *M, int ld, int rows, int rhs0, int n_rhs, 
     __syncthreads();
 }
 
+// In-place Gauss-Jordan inverse with partial pivoting of the m x m matrix A
+// (row stride ld). piv and fcol are shared scratch of m entries. Sets
+// sh->bad on a zero or non-finite pivot.
+__device__ void gj_inverse(double *A, int ld, int m, int *piv, double *fcol, ElimShared *sh)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int k = 0; k < m; ++k) {
+        if (warp == 0) {
+            double best = -1.0;
+            int bi = k;
+            for (int r = k + lane; r < m; r += 32) {
+                const double v = fabs(A[r * ld + k]);
+                if (v > best) { best = v; bi = r; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const double ob = __shfl_down_sync(0xffffffffu, best, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                sh->piv = bi;
+                piv[k] = bi;
+                const double pv = A[bi * ld + k];
+                if (!(best > 0.0) || !isfinite(pv)) sh->bad = 1;
+                sh->pivinv = 1.0 / pv;
+            }
+        }
+        __syncthreads();
+        if (sh->bad) return;
+        const int p = sh->piv;
+        const double pinv = sh->pivinv;
+        // pivot column as it will be after the row interchange (0 for row k)
+        for (int r = tid; r < m; r += NT) {
+            const int src = (r == k) ? p : ((r == p) ? k : r);
+            fcol[r] = (r == k) ? 0.0 : A[src * ld + k];
+        }
+        __syncthreads();
+        // interchange rows k and p, scale the pivot row (its pivot entry becomes 1/pivot)
+        for (int c = tid; c < m; c += NT) {
+            double vk = A[k * ld + c];
+            if (p != k) {
+                const double vp = A[p * ld + c];
+                A[p * ld + c] = vk;
+                vk = vp;
+            }
+            A[k * ld + c] = (c == k) ? pinv : vk * pinv;
+        }
+        __syncthreads();
+        constexpr int G = 4;
+        const double *prow = A + k * ld;
+        for (int q = tid; q < m * G; q += NT) {
+            const int r = q / G, j = q - (q / G) * G;
+            if (r == k) continue;
+            const double f = fcol[r];
+            double *row = A + r * ld;
+            for (int c = j; c < m; c += G) row[c] = fma(-f, prow[c], (c == k) ? 0.0 : row[c]);
+        }
+        __syncthreads();
+    }
+    // undo the row interchanges as column interchanges, in reverse order
+    for (int r = tid; r < m; r += NT) {
+        double *row = A + r * ld;
+        for (int k = m - 1; k >= 0; --k) {
+            const int p = piv[k];
+            if (p != k) {
+                const double t = row[k];
+                row[k] = row[p];
+                row[p] = t;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Row-wise upper-triangle index q -> (p, r), p <= r < m.
+__device__ __forceinline__ void tri_pair(int q, int m, int &p, int &r)
+{
+    const double t = (double)(2 * m + 1);
+    int pp = (int)((t - sqrt(t * t - 8.0 * (double)q)) * 0.5);
+    if (pp < 0) pp = 0;
+    while (pp > 0 && pp * m - (pp * (pp - 1)) / 2 > q) --pp;
+    while ((pp + 1) * m - ((pp + 1) * pp) / 2 <= q) ++pp;
+    p = pp;
+    r = pp + (q - (pp * m - (pp * (pp - 1)) / 2));
+}
+
 __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
     const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
@@ -117,6 +205,8 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     __shared__ int open_pos[SOLVE_SMALL_MAXN];   // channel -> open position (-1 otherwise)
     __shared__ int qpos[SOLVE_SMALL_MAXN];       // MQDT channel k -> its position in P
     __shared__ int opos[SOLVE_SMALL_MAXN];       // open channel k -> its position in P
+    __shared__ int piv[SOLVE_SMALL_MAXN];
+    __shared__ double fcol[SOLVE_SMALL_MAXN];
     __shared__ int s_no, s_np, s_nq;
     __shared__ ElimShared esh;
 
@@ -258,64 +348,34 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     }
     if (!omega) return;
 
-    // Cholesky factor and X reuse region A.
-    double *Lc = sm;
-    double *Xm = sm + (size_t)no * lk;
+    // M^{-1} and |T|^2 reuse region A.
+    double *Mi = sm;
+    double *T2 = sm + (size_t)no * lk;
 
-    // ---- M = 1 + K^2 (symmetric: upper triangle, mirrored), Cholesky --------
+    // ---- M = 1 + K^2 (upper triangle, mirrored), inverted in place ----------
     const int nsym = no * (no + 1) / 2;
     for (int q = tid; q < nsym; q += NT) {
-        int p = 0, rem = q;
-        while (rem >= no - p) { rem -= no - p; ++p; }
-        const int r = p + rem;
+        int p, r;
+        tri_pair(q, no, p, r);
         double s = (p == r) ? 1.0 : 0.0;
         for (int u = 0; u < no; ++u) s = fma(Ks[p * lk + u], Ks[u * lk + r], s);
-        Lc[p * lk + r] = s;
-        Lc[r * lk + p] = s;
+        Mi[p * lk + r] = s;
+        Mi[r * lk + p] = s;
     }
     __syncthreads();
-    for (int c = 0; c < no; ++c) {
-        if (tid == 0) Lc[c * lk + c] = sqrt(Lc[c * lk + c]);
-        __syncthreads();
-        const double dinv = 1.0 / Lc[c * lk + c];
-        for (int r = c + 1 + tid; r < no; r += NT) Lc[r * lk + c] *= dinv;
-        __syncthreads();
-        const int m = no - c - 1;
-        const int mt = m * (m + 1) / 2;
-        for (int q = tid; q < mt; q += NT) {
-            // lower-triangle element (r, s2), c < s2 <= r, of the trailing block
-            int rr = 0, rem = q;
-            while (rem > rr) { rem -= rr + 1; ++rr; }
-            const int r = c + 1 + rr, s2 = c + 1 + rem;
-            Lc[r * lk + s2] = fma(-Lc[r * lk + c], Lc[s2 * lk + c], Lc[r * lk + s2]);
-        }
-        __syncthreads();
+    gj_inverse(Mi, lk, no, piv, fcol, &esh);
+    if (esh.bad) {
+        if (tid == 0) status[e] = RM_ESINGULAR;
+        return;
     }
-    // X = (L L^T)^{-1} K: one thread per column
-    for (int r = tid; r < no; r += NT) {
-        for (int p = 0; p < no; ++p) {
-            double s = Ks[p * lk + r];
-            for (int u = 0; u < p; ++u) s = fma(-Lc[p * lk + u], Xm[u * lk + r], s);
-            Xm[p * lk + r] = s / Lc[p * lk + p];
-        }
-        for (int p = no - 1; p >= 0; --p) {
-            double s = Xm[p * lk + r];
-            for (int u = p + 1; u < no; ++u) s = fma(-Lc[u * lk + p], Xm[u * lk + r], s);
-            Xm[p * lk + r] = s / Lc[p * lk + p];
-        }
-    }
-    __syncthreads();
-    // |T|^2 = 4 (X^2 + Y^2) with Y = K X; X and Y are symmetric (functions of
-    // K), so the upper triangle is computed and mirrored. Stored over Lc.
-    double *T2 = Lc;
+    // |T|^2 = 4 (X^2 + Y^2), X = K M^{-1}, Y = 1 - M^{-1}; upper triangle, mirrored
     for (int q = tid; q < nsym; q += NT) {
-        int p = 0, rem = q;
-        while (rem >= no - p) { rem -= no - p; ++p; }
-        const int r = p + rem;
-        double y = 0.0;
-        for (int u = 0; u < no; ++u) y = fma(Ks[p * lk + u], Xm[u * lk + r], y);
-        const double xv = 0.5 * (Xm[p * lk + r] + Xm[r * lk + p]);
-        const double t2 = 4.0 * (xv * xv + y * y);
+        int p, r;
+        tri_pair(q, no, p, r);
+        double xv = 0.0;
+        for (int u = 0; u < no; ++u) xv = fma(Ks[p * lk + u], Mi[u * lk + r], xv);
+        const double yv = ((p == r) ? 1.0 : 0.0) - 0.5 * (Mi[p * lk + r] + Mi[r * lk + p]);
+        const double t2 = 4.0 * (xv * xv + yv * yv);
         T2[p * lk + r] = t2;
         T2[r * lk + p] = t2;
     }
@@ -327,10 +387,8 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     double *om = omega + (size_t)e * n_tri;
     const double g = pw.g;
     for (int q = tid; q < npair; q += NT) {
-        // invert the row-wise triangular index q -> (I, J)
-        int I = 0, rem = q;
-        while (rem >= nl - I) { rem -= nl - I; ++I; }
-        const int J = I + rem;
+        int I, J;
+        tri_pair(q, nl, I, J);
         if (!(x - pw.lev_thr[I] > 0.0) || !(x - pw.lev_thr[J] > 0.0)) continue;
         double s = 0.0;
         for (int ia = pw.lev_start[I]; ia < pw.lev_start[I + 1]; ++ia) {
