@@ -618,7 +618,7 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
             ctx->launches += L;
         } else {
             CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, ctx->stream));
+                                  omb, ntri, mode == RM_MQDT, ctx->stream));
             ctx->launches++;
         }
         CK(prof_end(ctx, RM_PH_SOLVE));

@@ -110,9 +110,9 @@ __device__ void block_backsub(double *M, int ld, int rows, int rhs0, int n_rhs, 
 }
 
 // In-place Gauss-Jordan inverse with partial pivoting of the m x m matrix A
-// (row stride ld). piv and fcol are shared scratch of m entries. Sets
-// sh->bad on a zero or non-finite pivot.
-__device__ void gj_inverse(double *A, int ld, int m, int *piv, double *fcol, ElimShared *sh)
+// (row stride ld). piv is shared scratch of m entries. Sets sh->bad on a zero
+// or non-finite pivot.
+__device__ void gj_inverse(double *A, int ld, int m, int *piv, ElimShared *sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k = 0; k < m; ++k) {
@@ -140,12 +140,6 @@ __device__ void gj_inverse(double *A, int ld, int m, int *piv, double *fcol, Eli
         if (sh->bad) return;
         const int p = sh->piv;
         const double pinv = sh->pivinv;
-        // pivot column as it will be after the row interchange (0 for row k)
-        for (int r = tid; r < m; r += NT) {
-            const int src = (r == k) ? p : ((r == p) ? k : r);
-            fcol[r] = (r == k) ? 0.0 : A[src * ld + k];
-        }
-        __syncthreads();
         // interchange rows k and p, scale the pivot row (its pivot entry becomes 1/pivot)
         for (int c = tid; c < m; c += NT) {
             double vk = A[k * ld + c];
@@ -157,14 +151,21 @@ __device__ void gj_inverse(double *A, int ld, int m, int *piv, double *fcol, Eli
             A[k * ld + c] = (c == k) ? pinv : vk * pinv;
         }
         __syncthreads();
+        // every other row: G threads share it; each reads the multiplier
+        // A[r][k] before any of them overwrites that column (groups never
+        // straddle a warp, so a warp barrier orders the two)
         constexpr int G = 4;
         const double *prow = A + k * ld;
-        for (int q = tid; q < m * G; q += NT) {
+        for (int q0 = 0; q0 < m * G; q0 += NT) {
+            const int q = q0 + tid;
             const int r = q / G, j = q - (q / G) * G;
-            if (r == k) continue;
-            const double f = fcol[r];
-            double *row = A + r * ld;
-            for (int c = j; c < m; c += G) row[c] = fma(-f, prow[c], (c == k) ? 0.0 : row[c]);
+            const bool act = q < m * G && r != k;
+            const double f = act ? A[r * ld + k] : 0.0;
+            __syncwarp();
+            if (act) {
+                double *row = A + r * ld;
+                for (int c = j; c < m; c += G) row[c] = fma(-f, prow[c], (c == k) ? 0.0 : row[c]);
+            }
         }
         __syncthreads();
     }
@@ -186,8 +187,8 @@ __device__ void gj_inverse(double *A, int ld, int m, int *piv, double *fcol, Eli
 // Row-wise upper-triangle index q -> (p, r), p <= r < m.
 __device__ __forceinline__ void tri_pair(int q, int m, int &p, int &r)
 {
-    const double t = (double)(2 * m + 1);
-    int pp = (int)((t - sqrt(t * t - 8.0 * (double)q)) * 0.5);
+    const float t = (float)(2 * m + 1);
+    int pp = (int)((t - sqrtf(fmaxf(t * t - 8.0f * (float)q, 0.0f))) * 0.5f);
     if (pp < 0) pp = 0;
     while (pp > 0 && pp * m - (pp * (pp - 1)) / 2 > q) --pp;
     while ((pp + 1) * m - ((pp + 1) * pp) / 2 <= q) ++pp;
@@ -198,7 +199,7 @@ __device__ __forceinline__ void tri_pair(int q, int m, int &p, int &r)
 __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
     const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
-    int *__restrict__ n_open_out, double *__restrict__ omega, int n_tri)
+    int *__restrict__ n_open_out, double *__restrict__ omega, int n_tri, int mqdt_layout)
 {
     extern __shared__ double sm[];
     __shared__ int col_chan[SOLVE_SMALL_MAXN];   // unknown column -> channel
@@ -206,7 +207,6 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     __shared__ int qpos[SOLVE_SMALL_MAXN];       // MQDT channel k -> its position in P
     __shared__ int opos[SOLVE_SMALL_MAXN];       // open channel k -> its position in P
     __shared__ int piv[SOLVE_SMALL_MAXN];
-    __shared__ double fcol[SOLVE_SMALL_MAXN];
     __shared__ int s_no, s_np, s_nq;
     __shared__ ElimShared esh;
 
@@ -286,20 +286,41 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     }
     block_backsub(M, ld, n, n, np, ncl);   // K_u = rows ncl.. of the RHS columns
 
-    // Shared layout: [region A: n(2n+2) doubles][region B: n(n+1) doubles].
-    double *Ks = sm + (size_t)n * (2 * n + 2);   // region B
     const int lk = no + 1;
+    double *Kp;   // K (no x no, symmetrised), row stride kld
+    double *Mi;   // M = 1 + K^2, then M^{-1} (no x no), row stride mld
+    int kld, mld;
     if (nq == 0) {
-        // direct mode (or no eliminated channel at this energy): K = K_u
-        for (int q = tid; q < no * no; q += NT) {
-            const int p = q / no, r = q - (q / no) * no;
-            const double kpr = M[(ncl + p) * ld + n + r];
-            const double krp = M[(ncl + r) * ld + n + p];
-            Ks[p * lk + r] = 0.5 * (kpr + krp);
-            if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
+        // Direct mode (or no eliminated channel at this energy): K = K_u sits
+        // in rows ncl.. / columns n.. of the augmented matrix; it is
+        // symmetrised in place, and M takes columns 0.. of the same rows (the
+        // eliminated part is no longer read). Only the augmented matrix is
+        // needed in shared memory.
+        Kp = M + ncl * ld + n;
+        kld = ld;
+        Mi = M + ncl * ld;
+        mld = ld;
+        const int nsym0 = no * (no + 1) / 2;
+        for (int q = tid; q < nsym0; q += NT) {
+            int p, r;
+            tri_pair(q, no, p, r);
+            const double kpr = Kp[p * kld + r], krp = Kp[r * kld + p];
+            if (K_out) {
+                K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
+                K_out[(size_t)e * n * n + (size_t)r * n + p] = krp;
+            }
+            const double v = 0.5 * (kpr + krp);
+            Kp[p * kld + r] = v;
+            Kp[r * kld + p] = v;
         }
         __syncthreads();
     } else {
+        if (!mqdt_layout) {   // direct-mode launch: never produced by the channel kernel
+            if (tid == 0) status[e] = RM_ESINGULAR;
+            return;
+        }
+        // Shared layout: [region A: n(2n+2) doubles][region B: n(n+1) doubles].
+        double *Ks = sm + (size_t)n * (2 * n + 2);   // region B
         // ---- MQDT elimination of the nq channels --------------------------
         const int lu = np + 1;
         double *Ku = Ks;           // K_u (np x np) in region B
@@ -332,10 +353,10 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         // K = K_oo - K_oc Y, after [C | Y] in region A
         double *Kd = sm + (size_t)nq * ld2;
         for (int q = tid; q < no * no; q += NT) {
-            const int s = q / no, t = q - (q / no) * no;
-            double v = Ku[opos[s] * lu + opos[t]];
-            for (int i = 0; i < nq; ++i) v = fma(-Ku[opos[s] * lu + qpos[i]], C[i * ld2 + nq + t], v);
-            Kd[s * lk + t] = v;
+            const int s2 = q / no, t = q - (q / no) * no;
+            double v = Ku[opos[s2] * lu + opos[t]];
+            for (int i = 0; i < nq; ++i) v = fma(-Ku[opos[s2] * lu + qpos[i]], C[i * ld2 + nq + t], v);
+            Kd[s2 * lk + t] = v;
         }
         __syncthreads();
         for (int q = tid; q < no * no; q += NT) {
@@ -345,12 +366,12 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
             if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
         }
         __syncthreads();
+        Kp = Ks;
+        kld = lk;
+        Mi = sm;
+        mld = lk;
     }
     if (!omega) return;
-
-    // M^{-1} and |T|^2 reuse region A.
-    double *Mi = sm;
-    double *T2 = sm + (size_t)no * lk;
 
     // ---- M = 1 + K^2 (upper triangle, mirrored), inverted in place ----------
     const int nsym = no * (no + 1) / 2;
@@ -358,30 +379,20 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         int p, r;
         tri_pair(q, no, p, r);
         double s = (p == r) ? 1.0 : 0.0;
-        for (int u = 0; u < no; ++u) s = fma(Ks[p * lk + u], Ks[u * lk + r], s);
-        Mi[p * lk + r] = s;
-        Mi[r * lk + p] = s;
+        for (int u = 0; u < no; ++u) s = fma(Kp[p * kld + u], Kp[u * kld + r], s);
+        Mi[p * mld + r] = s;
+        Mi[r * mld + p] = s;
     }
     __syncthreads();
-    gj_inverse(Mi, lk, no, piv, fcol, &esh);
+    gj_inverse(Mi, mld, no, piv, &esh);
     if (esh.bad) {
         if (tid == 0) status[e] = RM_ESINGULAR;
         return;
     }
-    // |T|^2 = 4 (X^2 + Y^2), X = K M^{-1}, Y = 1 - M^{-1}; upper triangle, mirrored
-    for (int q = tid; q < nsym; q += NT) {
-        int p, r;
-        tri_pair(q, no, p, r);
-        double xv = 0.0;
-        for (int u = 0; u < no; ++u) xv = fma(Ks[p * lk + u], Mi[u * lk + r], xv);
-        const double yv = ((p == r) ? 1.0 : 0.0) - 0.5 * (Mi[p * lk + r] + Mi[r * lk + p]);
-        const double t2 = 4.0 * (xv * xv + yv * yv);
-        T2[p * lk + r] = t2;
-        T2[r * lk + p] = t2;
-    }
-    __syncthreads();
 
-    // ---- Omega_IJ += g sum |T_ab|^2 over a in I, b in J ---------------------
+    // ---- Omega_IJ += g sum_{a in I, b in J} |T_ab|^2 -------------------------
+    // |T_ab|^2 = 4 (X_ab^2 + Y_ab^2), X = K M^{-1}, Y = 1 - M^{-1}, each pair
+    // formed where it is summed (taken with a <= b: both are symmetric).
     const int nl = pw.n_levels;
     const int npair = nl * (nl + 1) / 2;
     double *om = omega + (size_t)e * n_tri;
@@ -392,10 +403,15 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         if (!(x - pw.lev_thr[I] > 0.0) || !(x - pw.lev_thr[J] > 0.0)) continue;
         double s = 0.0;
         for (int ia = pw.lev_start[I]; ia < pw.lev_start[I + 1]; ++ia) {
-            const int pa = open_pos[pw.lev_chan[ia]];
+            const int pa0 = open_pos[pw.lev_chan[ia]];
             for (int ib = pw.lev_start[J]; ib < pw.lev_start[J + 1]; ++ib) {
-                const int pb = open_pos[pw.lev_chan[ib]];
-                s += T2[pa * lk + pb];
+                const int pb0 = open_pos[pw.lev_chan[ib]];
+                const int pa = min(pa0, pb0), pb = max(pa0, pb0);
+                double xv = 0.0;
+                for (int u = 0; u < no; ++u) xv = fma(Kp[pa * kld + u], Mi[u * mld + pb], xv);
+                const double yv =
+                    ((pa == pb) ? 1.0 : 0.0) - 0.5 * (Mi[pa * mld + pb] + Mi[pb * mld + pa]);
+                s += 4.0 * (xv * xv + yv * yv);
             }
         }
         om[q] += g * s;
@@ -406,8 +422,11 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
 
 int solve_small_max_n() { return SOLVE_SMALL_MAXN; }
 
-size_t solve_small_smem(int n)
+// Direct mode needs only the augmented matrix n x (2n + 1); MQDT mode also
+// holds K_u and the elimination system.
+size_t solve_small_smem(int n, int mqdt)
 {
+    if (!mqdt) return (size_t)n * (2 * n + 1) * sizeof(double);
     const size_t aug = (size_t)n * (2 * n + 2);
     const size_t ks = (size_t)n * (n + 1);
     return (aug + ks) * sizeof(double);
@@ -415,15 +434,16 @@ size_t solve_small_smem(int n)
 
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
-                               double *omega, int n_tri, cudaStream_t s)
+                               double *omega, int n_tri, int mqdt, cudaStream_t s)
 {
     if (pw.n > SOLVE_SMALL_MAXN) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
-    const size_t smem = solve_small_smem(pw.n);
+    const size_t smem = solve_small_smem(pw.n, mqdt);
     cudaError_t err = cudaFuncSetAttribute(solve_small_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    solve_small_kernel<<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega, n_tri);
+    solve_small_kernel<<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega, n_tri,
+                                            mqdt ? 1 : 0);
     return cudaGetLastError();
 }
 
