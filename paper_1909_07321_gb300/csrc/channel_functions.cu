@@ -49,6 +49,7 @@
 #include <math.h>
 
 #include "dd.cuh"
+#include "rcp.cuh"
 #include "rm_internal.cuh"
 
 namespace rmgb {
@@ -70,27 +71,28 @@ __device__ Cf1 cf1_lentz(int l, double eta, double rho)
 {
     const double irho = 1.0 / rho;
     double L1 = l + 1.0;
-    double S = L1 * irho + eta / L1;
+    double er = eta / L1;            // eta / (l + n), carried to the next iteration
+    double S = L1 * irho + er;
     double f = (S == 0.0) ? TINY : S;
     double C = f, D = 0.0;
     int sgn = 1;
     for (int n = 1; n < CF_MAXIT; ++n) {
-        double Ln = l + n;
-        double Ln1 = Ln + 1.0;
-        double Snext = Ln1 * irho + eta / Ln1;
-        double er = eta / Ln;
-        double an = -(1.0 + er * er);
-        double bn = S + Snext;
-        D = bn + an * D;
+        const double Ln1 = l + n + 1.0;
+        const double er1 = eta * rcp_nr(Ln1);
+        const double Snext = Ln1 * irho + er1;
+        const double an = -fma(er, er, 1.0);
+        const double bn = S + Snext;
+        D = fma(an, D, bn);
         if (D == 0.0) D = TINY;
-        C = bn + an / C;
+        C = fma(an, rcp_nr(C), bn);
         if (C == 0.0) C = TINY;
-        D = 1.0 / D;
+        D = rcp_nr(D);
         if (D < 0.0) sgn = -sgn;
-        double delta = C * D;
+        const double delta = C * D;
         f *= delta;
         if (fabs(delta - 1.0) < CF_TOL) return {f, sgn, 1};
         S = Snext;
+        er = er1;
     }
     return {f, sgn, 0};
 }
@@ -114,11 +116,11 @@ __device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
         double tr = br + (ar * Dr - ai * Di);
         double ti = bi + (ar * Di + ai * Dr);
         if (tr == 0.0 && ti == 0.0) tr = TINY;
-        const double dm = 1.0 / (tr * tr + ti * ti);
+        const double dm = rcp_nr(tr * tr + ti * ti);
         Dr = tr * dm;
         Di = -ti * dm;
         // C = b + a / C
-        const double cm = 1.0 / (Cr * Cr + Ci * Ci);
+        const double cm = rcp_nr(Cr * Cr + Ci * Ci);
         double ur = br + (ar * Cr + ai * Ci) * cm;
         double ui = bi + (ai * Cr - ar * Ci) * cm;
         if (ur == 0.0 && ui == 0.0) ur = TINY;
@@ -137,7 +139,7 @@ __device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
         const double ai = eta * (2.0 * m - 1.0);
         const double dr = br + vr;
         const double di = 2.0 * m + vi;
-        const double dm = 1.0 / (dr * dr + di * di);
+        const double dm = rcp_nr(dr * dr + di * di);
         vr = (ar * dr + ai * di) * dm;
         vi = (ai * dr - ar * di) * dm;
     }
@@ -158,17 +160,17 @@ __device__ int cf2_closed(int L0, double nu, double kap, double a, double *y)
     for (; n < CF_MAXIT; ++n) {
         const double A = -an(n);
         const double B = 2.0 * (base + n);
-        D = B + A * D;
+        D = fma(A, D, B);
         if (D == 0.0) D = TINY;
-        C = B + A / C;
+        C = fma(A, rcp_nr(C), B);
         if (C == 0.0) C = TINY;
-        D = 1.0 / D;
+        D = rcp_nr(D);
         if (fabs(C * D - 1.0) < CF_TOL) break;
     }
     if (n >= CF_MAXIT) return 0;
     const int N = 2 * n + 20;
     double v = 0.0;
-    for (int m = N; m >= 2; --m) v = -an(m) / (2.0 * (base + m) + v);
+    for (int m = N; m >= 2; --m) v = -an(m) * rcp_nr(2.0 * (base + m) + v);
     const double phi = an(1) / (2.0 * (base + 1.0) + v);
     *y = -kap + (nu + phi) / a;
     return 1;
