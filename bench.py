@@ -322,7 +322,8 @@ def run_ours(args, rank, world, local_rank):
 
     Ed = torch.tensor(E, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
-    ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, device=local_rank)
+    sp = 1 if (prec != 0 and args.matching == "fp32") else 0
+    ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, device=local_rank, solve_precision=sp)
     ctx.load_pw(0, pw)
     n_open = torch.zeros(E.size, dtype=torch.int32, device=dev)
     with torch.cuda.stream(stream):
@@ -433,6 +434,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_channels": n, "n_poles": N,
                        "energies_per_gpu": int(E.size), "formation": args.precision,
+                       "matching": args.matching if prec != 0 else "fp64",
                        "near_pole_delta_ry": 1e-3, "mode": "direct",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "energy-interleaved dp%d" % world},
@@ -463,6 +465,8 @@ def main():
     ap.add_argument("--serving-requests", type=int, default=48,
                     help="requests in the serving leg (0 to skip)")
     ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrival rate (1/s)")
+    ap.add_argument("--matching", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of the matching elimination on the mixed path")
     ap.add_argument("--wide-energies", type=int, default=256,
                     help="energies of the 1000-channel leg (0 to skip)")
     ap.add_argument("--energies", type=int, default=N_E,

@@ -94,6 +94,10 @@ typedef struct rm_opts {
     int formulation;        /* mixed-precision formation (Eq. rmatrix on tensor cores):
                                RM_FORM_AUTO (default: pair operand while it is small,
                                per-energy GEMM above), RM_FORM_PAIRS, RM_FORM_ENERGY */
+    int solve_precision;    /* matching elimination (step (c)): RM_FP64 (default) or
+                               RM_FP32 (direct mode, shared-memory solver: the system
+                               is eliminated in FP32; T and Omega stay FP64). Other
+                               cases run in FP64 whatever this asks */
 } rm_opts;
 
 #define RM_SOLVER_AUTO    0

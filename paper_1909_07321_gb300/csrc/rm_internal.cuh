@@ -61,10 +61,11 @@ cudaError_t launch_nearpole(const PwDev &pw, const double *E, int nE, int *statu
 cudaError_t launch_form_r_fp64(const PwDev &pw, const double *E, int nE, double *R,
                                cudaStream_t s);
 // mqdt != 0: the channel data may hold MQDT-eliminated channels (larger
-// shared-memory layout).
+// shared-memory layout). f32 != 0 (direct mode only): the matching system is
+// eliminated in FP32.
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
-                               double *omega, int n_tri, int mqdt, cudaStream_t s);
+                               double *omega, int n_tri, int mqdt, int f32, cudaStream_t s);
 // Mixed-precision formation (tensor cores). Operand kinds:
 enum TcKind { TC_BF16X3 = 0, TC_TF32X3 = 1 };
 // Split of P_pk = w_ik w_jk / (2a) into hi/lo operands, [n_pairs][Kpad] K-major.

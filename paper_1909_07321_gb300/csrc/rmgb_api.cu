@@ -230,6 +230,7 @@ extern "C" void rm_default_opts(rm_opts *o)
     o->mqdt_kappa_a_max = 5.0;
     o->solver = RM_SOLVER_AUTO;
     o->formulation = RM_FORM_AUTO;
+    o->solve_precision = RM_FP64;
 }
 
 extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
@@ -240,6 +241,7 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
     if (opts) o = *opts; else rm_default_opts(&o);
     if (o.solver < RM_SOLVER_AUTO || o.solver > RM_SOLVER_LARGE) return RM_EINVAL;
     if (o.formulation < RM_FORM_AUTO || o.formulation > RM_FORM_ENERGY) return RM_EINVAL;
+    if (o.solve_precision != RM_FP64 && o.solve_precision != RM_FP32) return RM_EINVAL;
     if (!(o.eps_thr >= 0) || !(o.delta_pole >= 0) || !std::isfinite(o.fnumin) ||
         !(o.mqdt_kappa_a_max >= 0) ||
         !std::isfinite(o.nu_margin) ||
@@ -618,7 +620,8 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
             ctx->launches += L;
         } else {
             CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, mode == RM_MQDT, ctx->stream));
+                                  omb, ntri, mode == RM_MQDT,
+                                  mode == RM_DIRECT && ctx->opts.solve_precision == RM_FP32, ctx->stream));
             ctx->launches++;
         }
         CK(prof_end(ctx, RM_PH_SOLVE));

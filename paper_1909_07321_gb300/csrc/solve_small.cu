@@ -26,6 +26,8 @@
 // the accumulation is deterministic (no atomics).
 #include <math.h>
 
+#include <type_traits>
+
 #include "rm_internal.cuh"
 
 namespace rmgb {
@@ -41,28 +43,30 @@ struct ElimShared {
 };
 
 // In-place Gaussian elimination with partial pivoting of the first `rows`
-// columns of the rows x w matrix M (row stride ld), whole block. Sets
-// sh->bad on a zero or non-finite pivot.
-__device__ void block_eliminate(double *M, int ld, int rows, int w, ElimShared *sh)
+// columns of the rows x w matrix M (row stride ld), whole block, in the
+// element type T (double, or float for the FP32 matching). Sets sh->bad on a
+// zero or non-finite pivot.
+template <typename T>
+__device__ void block_eliminate(T *M, int ld, int rows, int w, ElimShared *sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int c = 0; c < rows; ++c) {
         if (warp == 0) {
-            double best = -1.0;
+            T best = -1;
             int bi = c;
             for (int r = c + lane; r < rows; r += 32) {
-                const double v = fabs(M[r * ld + c]);
+                const T v = fabs(M[r * ld + c]);
                 if (v > best) { best = v; bi = r; }
             }
             for (int off = 16; off > 0; off >>= 1) {
-                const double ob = __shfl_down_sync(0xffffffffu, best, off);
+                const T ob = __shfl_down_sync(0xffffffffu, best, off);
                 const int oi = __shfl_down_sync(0xffffffffu, bi, off);
                 if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
             }
             if (lane == 0) {
                 sh->piv = bi;
-                const double pv = M[bi * ld + c];
-                if (!(best > 0.0) || !isfinite(pv)) sh->bad = 1;
+                const double pv = (double)M[bi * ld + c];
+                if (!(best > 0) || !isfinite(pv)) sh->bad = 1;
                 sh->pivinv = 1.0 / pv;
             }
         }
@@ -70,7 +74,7 @@ __device__ void block_eliminate(double *M, int ld, int rows, int w, ElimShared *
         const int p = sh->piv;
         if (p != c) {
             for (int q = c + tid; q < w; q += NT) {
-                const double t = M[c * ld + q];
+                const T t = M[c * ld + q];
                 M[c * ld + q] = M[p * ld + q];
                 M[p * ld + q] = t;
             }
@@ -80,13 +84,13 @@ __device__ void block_eliminate(double *M, int ld, int rows, int w, ElimShared *
         // (the multipliers are not stored: every right-hand side is in the
         // augmented matrix), so there is no separate scaling pass or barrier
         constexpr int G = 4;
-        const double pinv = sh->pivinv;
+        const T pinv = (T)sh->pivinv;
         const int nr = rows - c - 1;
-        const double *prow = M + c * ld;
+        const T *prow = M + c * ld;
         for (int q = tid; q < nr * G; q += NT) {
             const int r = c + 1 + q / G, j = q - (q / G) * G;
-            double *row = M + r * ld;
-            const double f = row[c] * pinv;
+            T *row = M + r * ld;
+            const T f = row[c] * pinv;
             for (int cc = c + 1 + j; cc < w; cc += G) row[cc] = fma(-f, prow[cc], row[cc]);
         }
         __syncthreads();
@@ -96,12 +100,13 @@ __device__ void block_eliminate(double *M, int ld, int rows, int w, ElimShared *
 // Back-substitution of the upper-triangular rows x rows system in M for the
 // n_rhs right-hand sides in columns rhs0.., over rows t = rows-1 .. row_lo,
 // in place; one thread per right-hand side.
-__device__ void block_backsub(double *M, int ld, int rows, int rhs0, int n_rhs, int row_lo)
+template <typename T>
+__device__ void block_backsub(T *M, int ld, int rows, int rhs0, int n_rhs, int row_lo)
 {
     for (int qq = threadIdx.x; qq < n_rhs; qq += NT) {
         const int cq = rhs0 + qq;
         for (int t = rows - 1; t >= row_lo; --t) {
-            double s = M[t * ld + cq];
+            T s = M[t * ld + cq];
             for (int u = t + 1; u < rows; ++u) s = fma(-M[t * ld + u], M[u * ld + cq], s);
             M[t * ld + cq] = s / M[t * ld + t];
         }
@@ -196,6 +201,18 @@ __device__ __forceinline__ void tri_pair(int q, int m, int &p, int &r)
     r = pp + (q - (pp * m - (pp * (pp - 1)) / 2));
 }
 
+// Shared-memory bytes of region A in the FP32-matching layout: the float
+// augmented matrix n x (2n + 1), later M^{-1} (at most n x (n + 1) doubles).
+__host__ __device__ inline size_t f32_region_a(int n)
+{
+    const size_t aug = (size_t)n * (2 * n + 1) * sizeof(float);
+    const size_t mi = (size_t)n * (n + 1) * sizeof(double);
+    return ((aug > mi ? aug : mi) + 15) & ~(size_t)15;
+}
+
+// F32: the matching system is eliminated in FP32 (direct mode only; the T
+// step and Omega stay FP64).
+template <bool F32>
 __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
     const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
@@ -257,7 +274,8 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
 
     const int w = n + np;        // augmented width
     const int ld = w + 1;        // padded row stride
-    double *M = sm;
+    using Real = typename std::conditional<F32, float, double>::type;
+    Real *M = reinterpret_cast<Real *>(sm);
     const double a = pw.a, b = pw.b;
 
     // ---- assemble [A | B] -------------------------------------------------
@@ -275,30 +293,56 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
             v = Rp[r <= o ? tri_idx(r, o, n) : tri_idx(o, r, n)] * (a * co.sp - b * co.s);
             if (r == o) v -= co.s;
         }
-        M[r * ld + c] = v;
+        M[r * ld + c] = (Real)v;
     }
     __syncthreads();
 
-    block_eliminate(M, ld, n, w, &esh);
+    block_eliminate<Real>(M, ld, n, w, &esh);
     if (esh.bad) {
         if (tid == 0) status[e] = RM_ESINGULAR;
         return;
     }
-    block_backsub(M, ld, n, n, np, ncl);   // K_u = rows ncl.. of the RHS columns
+    block_backsub<Real>(M, ld, n, n, np, ncl);   // K_u = rows ncl.. of the RHS columns
 
     const int lk = no + 1;
     double *Kp;   // K (no x no, symmetrised), row stride kld
     double *Mi;   // M = 1 + K^2, then M^{-1} (no x no), row stride mld
     int kld, mld;
-    if (nq == 0) {
+    if (F32) {
+        if (nq > 0) {   // FP32 matching is launched for direct mode only
+            if (tid == 0) status[e] = RM_ESINGULAR;
+            return;
+        }
+        // K (FP64) into region B, then M^{-1} over the float matrix in region A
+        Kp = reinterpret_cast<double *>(reinterpret_cast<char *>(sm) + f32_region_a(n));
+        kld = lk;
+        const int nsym0 = no * (no + 1) / 2;
+        for (int q = tid; q < nsym0; q += NT) {
+            int p, r;
+            tri_pair(q, no, p, r);
+            const double kpr = (double)M[(ncl + p) * ld + n + r];
+            const double krp = (double)M[(ncl + r) * ld + n + p];
+            if (K_out) {
+                K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
+                K_out[(size_t)e * n * n + (size_t)r * n + p] = krp;
+            }
+            const double v = 0.5 * (kpr + krp);
+            Kp[p * kld + r] = v;
+            Kp[r * kld + p] = v;
+        }
+        __syncthreads();
+        Mi = sm;
+        mld = lk;
+    } else if (nq == 0) {
+        double *Md = reinterpret_cast<double *>(sm);
         // Direct mode (or no eliminated channel at this energy): K = K_u sits
         // in rows ncl.. / columns n.. of the augmented matrix; it is
         // symmetrised in place, and M takes columns 0.. of the same rows (the
         // eliminated part is no longer read). Only the augmented matrix is
         // needed in shared memory.
-        Kp = M + ncl * ld + n;
+        Kp = Md + ncl * ld + n;
         kld = ld;
-        Mi = M + ncl * ld;
+        Mi = Md + ncl * ld;
         mld = ld;
         const int nsym0 = no * (no + 1) / 2;
         for (int q = tid; q < nsym0; q += NT) {
@@ -321,12 +365,13 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         }
         // Shared layout: [region A: n(2n+2) doubles][region B: n(n+1) doubles].
         double *Ks = sm + (size_t)n * (2 * n + 2);   // region B
+        const Real *Mq = M;
         // ---- MQDT elimination of the nq channels --------------------------
         const int lu = np + 1;
         double *Ku = Ks;           // K_u (np x np) in region B
         for (int q = tid; q < np * np; q += NT) {
             const int p = q / np, r = q - (q / np) * np;
-            Ku[p * lu + r] = M[(ncl + p) * ld + n + r];
+            Ku[p * lu + r] = (double)Mq[(ncl + p) * ld + n + r];
         }
         __syncthreads();
         // [K_cc + diag(tan pi nu) | K_co] in region A
@@ -344,12 +389,12 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
             C[i * ld2 + j] = v;
         }
         __syncthreads();
-        block_eliminate(C, ld2, nq, w2, &esh);
+        block_eliminate<double>(C, ld2, nq, w2, &esh);
         if (esh.bad) {
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        block_backsub(C, ld2, nq, nq, no, 0);   // Y = (K_cc + tan)^{-1} K_co
+        block_backsub<double>(C, ld2, nq, nq, no, 0);   // Y = (K_cc + tan)^{-1} K_co
         // K = K_oo - K_oc Y, after [C | Y] in region A
         double *Kd = sm + (size_t)nq * ld2;
         for (int q = tid; q < no * no; q += NT) {
@@ -423,9 +468,11 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
 int solve_small_max_n() { return SOLVE_SMALL_MAXN; }
 
 // Direct mode needs only the augmented matrix n x (2n + 1); MQDT mode also
-// holds K_u and the elimination system.
-size_t solve_small_smem(int n, int mqdt)
+// holds K_u and the elimination system; FP32 matching keeps the float matrix
+// (then M^{-1}) beside K.
+size_t solve_small_smem(int n, int mqdt, int f32)
 {
+    if (f32) return f32_region_a(n) + (size_t)n * (n + 1) * sizeof(double);
     if (!mqdt) return (size_t)n * (2 * n + 1) * sizeof(double);
     const size_t aug = (size_t)n * (2 * n + 2);
     const size_t ks = (size_t)n * (n + 1);
@@ -434,16 +481,25 @@ size_t solve_small_smem(int n, int mqdt)
 
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
-                               double *omega, int n_tri, int mqdt, cudaStream_t s)
+                               double *omega, int n_tri, int mqdt, int f32, cudaStream_t s)
 {
-    if (pw.n > SOLVE_SMALL_MAXN) return cudaErrorInvalidValue;
+    if (pw.n > SOLVE_SMALL_MAXN || (f32 && mqdt)) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
-    const size_t smem = solve_small_smem(pw.n, mqdt);
-    cudaError_t err = cudaFuncSetAttribute(solve_small_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    solve_small_kernel<<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega, n_tri,
-                                            mqdt ? 1 : 0);
+    const size_t smem = solve_small_smem(pw.n, mqdt, f32);
+    cudaError_t err;
+    if (f32) {
+        err = cudaFuncSetAttribute(solve_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+        if (err != cudaSuccess) return err;
+        solve_small_kernel<true><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
+                                                      n_tri, 0);
+    } else {
+        err = cudaFuncSetAttribute(solve_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem);
+        if (err != cudaSuccess) return err;
+        solve_small_kernel<false><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
+                                                       n_tri, mqdt ? 1 : 0);
+    }
     return cudaGetLastError();
 }
 

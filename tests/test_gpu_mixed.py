@@ -106,8 +106,10 @@ def test_form_r_energy_1000ch(rt):
     _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, 2, 0), "1000ch")
 
 
-def _first_order_k_bound(pw, x):
-    """Elementwise first-order bound on |dK| from |dR| <= R_BOUND S (oracle quantities)."""
+def _first_order_k_bound(pw, x, u_solve=0.0):
+    """Elementwise first-order bound on |dK| from |dR| <= R_BOUND S (oracle
+    quantities); with u_solve > 0 also the backward error of an elimination
+    in that unit roundoff, |dA| <= 2 n u_solve |A|, |dB| <= 2 n u_solve |B|."""
     a, b = pw["a"], pw.get("b", 0.0)
     cf = oracle.channel_functions(float(x), pw["e_thr"], pw["l"], pw["z"], a)
     R = oracle.r_matrix(float(x), pw["E_k"], pw["W"], a)
@@ -127,17 +129,28 @@ def _first_order_k_bound(pw, x):
     far = dd >= 1e-3
     S = (absW[:, far] / dd[far]) @ absW[:, far].T / (2 * a)
     Ainv = np.linalg.inv(A)
-    return np.abs(Ainv[oi, :]) @ (R_BOUND * S) @ np.abs(d2[:, None] * P + d1[:, None] * X)
+    bound = np.abs(Ainv[oi, :]) @ (R_BOUND * S) @ np.abs(d2[:, None] * P + d1[:, None] * X)
+    if u_solve:
+        g = 2.0 * op.size * u_solve
+        bound += np.abs(Ainv[oi, :]) @ (g * (np.abs(A) @ np.abs(X) + np.abs(B)))
+    return bound
 
 
-@pytest.mark.parametrize("name,prec,form", [("bf16x3", 2, 1), ("tf32x3", 1, 1), ("bf16x3-energy", 2, 2)])
-def test_mixed_k_and_omega_bounds(rt, name, prec, form):
+U32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("name,prec,form,sp", [("bf16x3", 2, 1, 0), ("tf32x3", 1, 1, 0),
+                                               ("bf16x3-energy", 2, 2, 0),
+                                               ("bf16x3+fp32-matching", 2, 1, 1)])
+def test_mixed_k_and_omega_bounds(rt, name, prec, form, sp):
+    """K and Omega of the mixed path within the propagated bounds; with FP32
+    matching (sp = 1) the elimination's backward error joins the R error."""
     torch, rmgb = rt
     pws, E = synth.workload_64ch()
     pw = pws[0]
     Es = _energies(pw, E, 150, 6)
     n = pw["W"].shape[0]
-    with rmgb.Context(precision=prec, formulation=form) as ctx:
+    with rmgb.Context(precision=prec, formulation=form, solve_precision=sp) as ctx:
         ctx.load_pw(0, pw)
         Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
         K = torch.zeros((Es.size, n * n), dtype=torch.float64, device="cuda")
@@ -156,7 +169,7 @@ def test_mixed_k_and_omega_bounds(rt, name, prec, form):
         k = no[m]
         Ko = ref["K"][m]
         dK = np.abs(K[m, :k, :k] - Ko)
-        bK = _first_order_k_bound(pw, Es[m])
+        bK = _first_order_k_bound(pw, Es[m], U32 if sp else 0.0)
         assert np.all(dK <= 3.0 * bK + 1e-12 * max(1.0, np.abs(Ko).max())), (name, Es[m])
         eK.append(np.linalg.norm(dK) / max(np.linalg.norm(Ko), 1e-300))
         Bf = 3.0 * np.linalg.norm(bK)
