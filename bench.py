@@ -186,14 +186,42 @@ def _time_steps(ctx, Ed, stream, flush, steps, rmgb, torch):
     return sum(step_ms) / len(step_ms), phase, launches
 
 
-def _solve_flops(n, n_open):
-    """Algorithmic FP64 flops of steps (c)+(d) for one energy, as the
-    shared-memory solver takes them: elimination of the n x (n + n_o) system
-    (2/3 n^3 + n^2 n_o), back-substitution of the n_o trailing rows (n_o^3),
-    M = 1 + K^2 (upper triangle, n_o^3), M^{-1} by Gauss-Jordan (2 n_o^3),
-    X = K M^{-1} (upper triangle, n_o^3)."""
+def _solve_flops(n, n_open, f32):
+    """Algorithmic flops of steps (c)+(d) for the energies given, as the
+    shared-memory solver takes them, split (FP64, FP32): elimination of the
+    n x (n + n_o) system (2/3 n^3 + n^2 n_o) and back-substitution of the n_o
+    trailing rows (n_o^3), in FP32 when f32; then FP64 M = 1 + K^2 (upper
+    triangle, n_o^3), M^{-1} by Gauss-Jordan (2 n_o^3), X = K M^{-1} for the
+    upper triangle (n_o^3)."""
     no = n_open.astype(np.float64)
-    return float(np.sum(2.0 / 3.0 * n**3 + n * n * no + 5.0 * no**3))
+    elim = float(np.sum(2.0 / 3.0 * n**3 + n * n * no + no**3))
+    t = float(np.sum(4.0 * no**3))
+    return (t, elim) if f32 else (t + elim, 0.0)
+
+
+# FP64 operations (FMA, multiply, add, compare: one each; the reciprocal of
+# the continued fractions: 4; an IEEE division or square root counted as 8)
+# per iteration of the channel-function recurrences, counted from the kernel.
+CHANFN_OPS = {"cf1": 23, "cf2_fwd": 45, "cf2_bwd": 20, "open_l": 90, "open_fixed": 130,
+              "closed_fwd": 22, "closed_bwd": 14, "ladder": 36, "closed_fixed": 70}
+CF2_FAST_DEPTH = 32   # CF2 settling within this many forward steps has no backward pass
+
+
+def _chanfn_ops(work):
+    """FP64 operations of step (b) from the per-(energy, channel) iteration
+    counts {kind, CF1 iterations n1, CF2 forward iterations n2, l steps}."""
+    w = work.reshape(-1, 4).astype(np.float64)
+    op, cl = w[:, 0] == 0, w[:, 0] == 1
+    c = CHANFN_OPS
+    o = w[op]
+    slow_o = o[:, 2] > CF2_FAST_DEPTH
+    ops_open = (c["cf1"] * o[:, 1] + c["cf2_fwd"] * (o[:, 2] - 1)
+                + c["cf2_bwd"] * (2 * o[:, 2] + 20) * slow_o + c["open_l"] * o[:, 3] + c["open_fixed"])
+    k = w[cl]
+    slow_c = k[:, 2] > CF2_FAST_DEPTH
+    ops_closed = (c["closed_fwd"] * (k[:, 2] - 1) + c["closed_bwd"] * (2 * k[:, 2] + 19) * slow_c
+                  + c["ladder"] * k[:, 3] + c["closed_fixed"])
+    return float(ops_open.sum() + ops_closed.sum())
 
 
 def run_serving(args, prec):
@@ -342,6 +370,10 @@ def run_ours(args, rank, world, local_rank):
         t_step = max_over_ranks(t_step)
         value = world * E.size / (t_step * 1e-3)
         om_main = ctx.collision_strengths()      # Omega of the last timed step
+        work = torch.zeros((E.size, n, 4), dtype=torch.int32, device=dev)
+        ctx.channel_work(0, Ed, work)
+        torch.cuda.synchronize()
+        chan_ops = _chanfn_ops(work.cpu().numpy())
 
         # end to end through the public API with host buffers
         E_pin = torch.tensor(E, dtype=torch.float64).pin_memory()
@@ -411,19 +443,32 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": "form_r_tc_kernel (%s)" % args.precision,
                      "peak_source": ("bf16 dense burst, %s" % peak_src) if prec == 2 else
                      ("tf32 = bf16 dense burst (%s) x nominal ratio 1/2" % peak_src)}
+    # channel functions: FP64 operations counted from the recurrence depths
+    fp64_op_peak = N_SM * FP64_FLOPS_PER_CLK_SM / 2.0 * sm_mhz * 1e6 / 1e12
+    chan_ach = chan_ops / (phase[rmgb.RM_PH_CHANFN][1] / args.steps * 1e-3) / 1e12
+    chan_roof = {"bound": "alu", "achieved": chan_ach, "peak": fp64_op_peak, "unit": "TFP64op/s",
+                 "frac": chan_ach / fp64_op_peak, "traffic": None,
+                 "kernel": "chanfn_kernel (FP64 continued fractions)",
+                 "ops_per_step": chan_ops,
+                 "peak_source": "FP64 pipe 2 op/clk/SM x 152 SMs at the sampled SM clock"}
+    # matching + T + Omega
+    f32 = sp == 1
+    fl64, fl32 = _solve_flops(n, n_open.cpu().numpy(), f32)
+    t_solve = phase[rmgb.RM_PH_SOLVE][1] / args.steps * 1e-3
+    ach = fl64 / t_solve / 1e12
+    solve_roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                  "frac": ach / fp64_peak, "traffic": None,
+                  "kernel": "solve_small_kernel (%s elimination, FP64 T)" % ("FP32" if f32 else "FP64"),
+                  "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"}
+    if f32:
+        fp32_peak = N_SM * 256.0 * sm_mhz * 1e6 / 1e12
+        solve_roof["fp32_elimination"] = {"achieved": fl32 / t_solve / 1e12, "peak": fp32_peak,
+                                          "frac": fl32 / t_solve / 1e12 / fp32_peak,
+                                          "unit": "TFLOP/s",
+                                          "peak_source": "FP32 128 FMA/clk/SM x 152 SMs"}
     # dominant kernel by device time
     dom = max((rmgb.RM_PH_FORM, rmgb.RM_PH_SOLVE, rmgb.RM_PH_CHANFN), key=lambda p: phase[p][1])
-    if dom == rmgb.RM_PH_FORM:
-        roof = form_roof
-    elif dom == rmgb.RM_PH_SOLVE:
-        fl = _solve_flops(n, n_open.cpu().numpy()) / max(1, phase[rmgb.RM_PH_SOLVE][0] / args.steps)
-        ach = fl / (per_launch_ms(rmgb.RM_PH_SOLVE) * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None, "kernel": "solve_small_kernel (FP64)",
-                "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "kernel": "chanfn_kernel (FP64 continued fractions)"}
+    roof = {rmgb.RM_PH_FORM: form_roof, rmgb.RM_PH_SOLVE: solve_roof, rmgb.RM_PH_CHANFN: chan_roof}[dom]
     cpu = None
     if pool is not None:
         v, sample = oracle_throughput(pool, n_cores, 24)
@@ -439,6 +484,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "energy-interleaved dp%d" % world},
             "roofline": roof, "formation_roofline": form_roof,
+            "rooflines": {"chanfn": chan_roof, "solve": solve_roof, "formation": form_roof},
             "phases_ms_per_step": {names[p]: phase[p][1] / args.steps for p in names},
             "phase_share": share,
             "fp64_path": fp64,

@@ -186,6 +186,17 @@ int rm_grid_shape(rm_ctx *ctx, int *n_E, int *n_tri);
 int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *E, double *out,
                          int *status);
 
+/* Inspection of step (b)'s arithmetic (no counterpart in the paper: it lets
+ * a caller account for the work of the continued fractions): for `pw` at
+ * n_E energies E (device) in direct mode, writes work (device,
+ * [n_E][n_ch][4] ints): {kind, CF1 iterations, CF2 forward iterations n2, l
+ * steps}, kind 0 = open (CF1 at l, CF2 at l = 0, l downward and upward
+ * recurrence steps), 1 = closed (its CF2 at L0, then l - L0 ladder steps),
+ * -1 = on a threshold. A CF2 with n2 > 32 is re-evaluated backwards from
+ * depth 2 n2 + 20; one with n2 <= 32 is taken from its forward value.
+ * Asynchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ECUDA. */
+int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, int *work);
+
 /* Inspection of step (a), for tests: R-matrices of `pw` at n_E energies E
  * (device), with the context's formation precision, written to R_out
  * (device, [n_E][n_ch][n_ch], full symmetric matrix). Asynchronous.

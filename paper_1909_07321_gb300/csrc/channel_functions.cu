@@ -58,11 +58,17 @@ namespace {
 constexpr int CF_MAXIT = 1 << 20;
 constexpr double TINY = 1e-300;
 constexpr double CF_TOL = 4e-16;
+// A CF2 that settles within this many forward steps is taken from its
+// forward Lentz value (few roundings, and a fast-converging fraction leaves
+// no significant tail); slower ones are re-evaluated backwards from depth
+// 2n + 20.
+constexpr int CF2_FAST_DEPTH = 32;
 
 struct Cf1 {
     double f;
     int sgn;
     int ok;
+    int iters;
 };
 
 // f_l = S_{l+1} + K(a_n / b_n), a_n = -(1 + eta^2/(l+n)^2), b_n = S_{l+n} + S_{l+n+1},
@@ -90,22 +96,24 @@ __device__ Cf1 cf1_lentz(int l, double eta, double rho)
         if (D < 0.0) sgn = -sgn;
         const double delta = C * D;
         f *= delta;
-        if (fabs(delta - 1.0) < CF_TOL) return {f, sgn, 1};
+        if (fabs(delta - 1.0) < CF_TOL) return {f, sgn, 1, n};
         S = Snext;
         er = er1;
     }
-    return {f, sgn, 0};
+    return {f, sgn, 0, CF_MAXIT};
 }
 
 // p + iq = H+'/H+ at l = 0: i(1 - eta/rho) + (i/rho) K,  K = K(a_m / b_m),
 // a_m = (m + i eta)(m - 1 + i eta), b_m = 2(rho - eta) + 2 i m.
-// The depth is found by forward Lentz on the tail K' = b_1 + K_{m>=2}(a_m / b_m)
-// (|b_1| >= 2, so no scaled-tiny start is needed); the value is then taken
-// bottom-up from depth 2n + 20.
-__device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
+// Forward Lentz on the tail K' = b_1 + K_{m>=2}(a_m / b_m) (|b_1| >= 2, so
+// no scaled-tiny start is needed) gives K = a_1 / K' when it settles within
+// CF2_FAST_DEPTH steps; otherwise its depth n sets a bottom-up evaluation
+// from depth 2n + 20.
+__device__ int cf2_open_l0(double eta, double rho, double *p, double *q, int *depth)
 {
     const double br = 2.0 * (rho - eta);
     double Cr = br, Ci = 2.0, Dr = 0.0, Di = 0.0;
+    double fr = br, fi = 2.0;   // K' by forward Lentz
     int n = 2;
     for (; n < CF_MAXIT; ++n) {
         const double m = n;
@@ -128,11 +136,23 @@ __device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
         Ci = ui;
         const double er = Cr * Dr - Ci * Di;
         const double ei = Cr * Di + Ci * Dr;
+        const double gr = fr * er - fi * ei;
+        fi = fr * ei + fi * er;
+        fr = gr;
         if (fabs(er - 1.0) + fabs(ei) < CF_TOL) break;
     }
+    *depth = n;
     if (n >= CF_MAXIT) return 0;
-    const int N = 2 * n + 20;
     double vr = 0.0, vi = 0.0;
+    if (n <= CF2_FAST_DEPTH) {
+        // K = a_1 / K',  a_1 = -eta^2 + i eta
+        const double ar = -eta * eta, ai = eta;
+        const double dm = rcp_nr(fr * fr + fi * fi);
+        *p = -((ai * fr - ar * fi) * dm) / rho;
+        *q = (1.0 - eta / rho) + ((ar * fr + ai * fi) * dm) / rho;
+        return 1;
+    }
+    const int N = 2 * n + 20;
     for (int m_ = N; m_ >= 1; --m_) {
         const double m = m_;
         const double ar = m * (m - 1.0) - eta * eta;
@@ -149,13 +169,16 @@ __device__ int cf2_open_l0(double eta, double rho, double *p, double *q)
 }
 
 // Closed-channel log-derivative (r-units) at l = L0 from CF2 at imaginary k.
-// Depth from forward Lentz on the tail b_1 - a_2/(b_2 - a_3/(...)).
-__device__ int cf2_closed(int L0, double nu, double kap, double a, double *y)
+// Forward Lentz on the tail K' = b_1 - a_2/(b_2 - a_3/(...)) gives
+// Phi = a_1 / K' when it settles within CF2_FAST_DEPTH steps; otherwise its
+// depth n sets a bottom-up evaluation from depth 2n + 20.
+__device__ int cf2_closed(int L0, double nu, double kap, double a, double *y, int *depth)
 {
     const double base = kap * a - nu;
     auto an = [&](int m) { return (L0 + m - nu) * (m - 1.0 - L0 - nu); };
     double C = 2.0 * (base + 1.0), D = 0.0;
     if (C == 0.0) C = TINY;
+    double f = C;   // K' by forward Lentz
     int n = 2;
     for (; n < CF_MAXIT; ++n) {
         const double A = -an(n);
@@ -165,9 +188,16 @@ __device__ int cf2_closed(int L0, double nu, double kap, double a, double *y)
         C = fma(A, rcp_nr(C), B);
         if (C == 0.0) C = TINY;
         D = rcp_nr(D);
-        if (fabs(C * D - 1.0) < CF_TOL) break;
+        const double delta = C * D;
+        f *= delta;
+        if (fabs(delta - 1.0) < CF_TOL) break;
     }
+    *depth = n;
     if (n >= CF_MAXIT) return 0;
+    if (n <= CF2_FAST_DEPTH) {
+        *y = -kap + (nu + an(1) / f) / a;
+        return 1;
+    }
     const int N = 2 * n + 20;
     double v = 0.0;
     for (int m = N; m >= 2; --m) v = -an(m) * rcp_nr(2.0 * (base + m) + v);
@@ -216,9 +246,13 @@ __device__ int regular_analytic(int l, double z, double eps, double r, double *f
     return 0;
 }
 
-template <bool MQDT>
+// STATS: instead of the channel data, record per (energy, channel) the
+// iteration counts of the continued fractions: {kind, CF1 iterations, CF2
+// forward iterations (the backward pass then takes 2n + 20 steps), l - L0
+// ladder steps for a closed channel or l for an open one}.
+template <bool MQDT, bool STATS>
 __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
-                              ChanFn *__restrict__ out, int *__restrict__ status)
+                              ChanFn *__restrict__ out, int *__restrict__ status, int4 *__restrict__ work)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = pw.n;
@@ -238,7 +272,9 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
         const double rho = k * a;
         Cf1 c1 = cf1_lentz(l, eta, rho);
         double p, q;
-        int ok2 = cf2_open_l0(eta, rho, &p, &q);
+        int d2 = 0;
+        int ok2 = cf2_open_l0(eta, rho, &p, &q, &d2);
+        if (STATS) work[(size_t)e * n + i] = make_int4(CH_OPEN, c1.iters, d2, l);
         if (!c1.ok || !ok2) {
             bad = RM_ECF_NOCONV;
         } else {
@@ -282,7 +318,10 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
             L0 = L0 < 0 ? 0 : (L0 > l ? l : L0);
         }
         double y;
-        if (!cf2_closed(L0, nu, kap, a, &y)) {
+        int d2 = 0;
+        const int okc = cf2_closed(L0, nu, kap, a, &y, &d2);
+        if (STATS) work[(size_t)e * n + i] = make_int4(CH_CLOSED, 0, d2, l - L0);
+        if (!okc) {
             bad = RM_ECF_NOCONV;
         } else {
             for (int L = L0; L < l; ++L) {
@@ -313,6 +352,10 @@ __global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Op
                 }
             }
         }
+    }
+    if (STATS) {
+        if (fabs(eps) < o.eps_thr) work[(size_t)e * n + i] = make_int4(-1, 0, 0, 0);
+        return;
     }
     out[(size_t)e * n + i] = r;
     if (bad != RM_OK) atomicCAS(status + e, RM_OK, bad);
@@ -358,9 +401,20 @@ cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &
     const int bs = 128;
     const unsigned grid = (unsigned)((total + bs - 1) / bs);
     if (mqdt)
-        chanfn_kernel<true><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status);
+        chanfn_kernel<true, false><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status, nullptr);
     else
-        chanfn_kernel<false><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status);
+        chanfn_kernel<false, false><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chanfn_work(const PwDev &pw, const double *E, int nE, const Opts &o, int4 *work,
+                               cudaStream_t s)
+{
+    const long long total = (long long)nE * pw.n;
+    if (total == 0) return cudaSuccess;
+    const int bs = 128;
+    chanfn_kernel<false, true><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(pw, E, nE, o, nullptr,
+                                                                                nullptr, work);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,10 @@ cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &
                           ChanFn *cf, int *status, cudaStream_t s);
 cudaError_t launch_nearpole(const PwDev &pw, const double *E, int nE, int *status,
                             cudaStream_t s);
+// Iteration counts of step (b) (direct mode), [nE][n] int4 {kind, CF1
+// iterations, CF2 forward iterations, recurrence steps in l}.
+cudaError_t launch_chanfn_work(const PwDev &pw, const double *E, int nE, const Opts &o, int4 *work,
+                               cudaStream_t s);
 cudaError_t launch_form_r_fp64(const PwDev &pw, const double *E, int nE, double *R,
                                cudaStream_t s);
 // mqdt != 0: the channel data may hold MQDT-eliminated channels (larger

@@ -716,6 +716,20 @@ extern "C" int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *
     return RM_SUCCESS;
 }
 
+extern "C" int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, int *work)
+{
+    int rc = check_pw(ctx, pw, true);
+    if (rc) return rc;
+    if (n_E <= 0 || !E || !work) return fail(ctx, RM_EINVAL, "bad arguments");
+    if (!is_device_ptr(E) || !is_device_ptr(work))
+        return fail(ctx, RM_EINVAL, "E and work must be device pointers");
+    CK(cudaSetDevice(ctx->opts.device));
+    const PwDev d = ctx->pw[pw].dev();
+    CK(launch_chanfn_work(d, E, n_E, make_opts(ctx->opts), reinterpret_cast<int4 *>(work), ctx->stream));
+    ctx->launches++;
+    return RM_SUCCESS;
+}
+
 extern "C" int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *R_out)
 {
     int rc = check_pw(ctx, pw, false);

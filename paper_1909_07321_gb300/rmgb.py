@@ -61,6 +61,7 @@ _SIGS = {
     "rm_grid_shape": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rm_channel_functions": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "rm_form_r": (_I, [_VP, _I, _I, _VP, _VP]),
+    "rm_channel_work": (_I, [_VP, _I, _I, _VP, _VP]),
     "rm_sync": (_I, [_VP]),
     "rm_reset_omega": (_I, [_VP]),
     "rm_profile_enable": (_I, [_VP, _I]),
@@ -184,6 +185,11 @@ def rm_channel_functions(ctx, pw, E, out, status=None):
                                                   _ptr(out, np.float64), _ptr(status, np.int32)))
 
 
+def rm_channel_work(ctx, pw, E, work):
+    return _check(ctx, lib().rm_channel_work(ctx, pw, int(E.shape[0]), _ptr(E, np.float64),
+                                             _ptr(work, np.int32)))
+
+
 def rm_form_r(ctx, pw, E, R_out):
     return _check(ctx, lib().rm_form_r(ctx, pw, int(E.shape[0]), _ptr(E, np.float64),
                                        _ptr(R_out, np.float64)))
@@ -283,6 +289,9 @@ class Context:
 
     def form_r(self, pw, E, R_out):
         return rm_form_r(self.h, pw, E, R_out)
+
+    def channel_work(self, pw, E, work):
+        return rm_channel_work(self.h, pw, E, work)
 
     def sync(self):
         return rm_sync(self.h)

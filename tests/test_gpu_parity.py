@@ -256,3 +256,22 @@ def test_neutral_target_z0(rt):
         res = dict(K=K.cpu().numpy().reshape(E.size, n, n), n_open=no.cpu().numpy(),
                    status=st.cpu().numpy(), omega=ctx.collision_strengths())
     _compare(res, ref)
+
+
+def test_channel_work_counts(rt):
+    """The iteration-count inspection agrees with the channel classification
+    and reports converged depths."""
+    torch, rmgb = rt
+    pws, E = synth.workload_64ch(500)
+    pw = pws[0]
+    n = pw["W"].shape[0]
+    with rmgb.Context() as ctx:
+        ctx.load_pw(0, pw)
+        w = torch.zeros((E.size, n, 4), dtype=torch.int32, device="cuda")
+        ctx.channel_work(0, torch.tensor(E, device="cuda"), w)
+        w = w.cpu().numpy()
+    open_ = E[:, None] > pw["e_thr"][None, :]
+    assert np.array_equal(w[..., 0], np.where(open_, 0, 1))
+    assert (w[..., 1][open_] >= 1).all() and (w[..., 1][~open_] == 0).all()
+    assert (w[..., 2] >= 2).all() and (w[..., 2] < 1 << 20).all()
+    assert np.array_equal(w[..., 3][open_], np.broadcast_to(pw["l"], open_.shape)[open_])
