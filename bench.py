@@ -201,9 +201,11 @@ def _solve_flops(n, n_open, f32):
 
 # FP64 operations (FMA, multiply, add, compare: one each; the reciprocal of
 # the continued fractions: 4; an IEEE division or square root counted as 8)
-# per iteration of the channel-function recurrences, counted from the kernel.
-CHANFN_OPS = {"cf1": 23, "cf2_fwd": 45, "cf2_bwd": 20, "open_l": 90, "open_fixed": 130,
-              "closed_fwd": 22, "closed_bwd": 14, "ladder": 36, "closed_fixed": 70}
+# per iteration of the channel-function recurrences (Wallis forms, with the
+# rescaling and convergence test of every 8th step spread over 8 steps),
+# counted from the kernel.
+CHANFN_OPS = {"cf1": 17, "cf2_fwd": 28, "cf2_bwd": 15, "open_l": 90, "open_fixed": 130,
+              "closed_fwd": 14, "closed_bwd": 10, "ladder": 36, "closed_fixed": 70}
 CF2_FAST_DEPTH = 32   # CF2 settling within this many forward steps has no backward pass
 
 

@@ -71,137 +71,198 @@ struct Cf1 {
     int iters;
 };
 
+// The continued fractions are evaluated through their numerators and
+// denominators (Wallis recurrences), A_n = b_n A_{n-1} + a_n A_{n-2} and the
+// same for B, forwards for the convergents A_n / B_n, or backwards,
+// (p, q) <- (a_m q, p + b_m q) from (0, 1) at depth N, for the tail value
+// p / q. Each step is then one or two dependent FMAs instead of a reciprocal
+// chain, which matters because the deep fractions near thresholds are serial
+// chains of hundreds to thousands of steps. Every 8 steps the quantities are
+// rescaled by a power of two (exact; the ratios are unchanged) and the
+// forward convergence test is applied.
+constexpr int CF_CHECK = 8;
+
+// 2^k with k chosen so that s * 2^k lies in [1, 2) (s > 0 finite; clamped
+// to the normal range).
+__device__ __forceinline__ double pow2_rescale(double s)
+{
+    const int ex = (int)((__double_as_longlong(s) >> 52) & 0x7ff);
+    int se = 2046 - ex;
+    se = se < 1 ? 1 : (se > 2046 ? 2046 : se);
+    return __longlong_as_double((long long)se << 52);
+}
+
 // f_l = S_{l+1} + K(a_n / b_n), a_n = -(1 + eta^2/(l+n)^2), b_n = S_{l+n} + S_{l+n+1},
-// S_L = L/rho + eta/L.
+// S_L = L/rho + eta/L. sign(F_l) = sign(B_n): the ratios B_{n-1}/B_n are
+// ratios of a solution of the l-recurrence that vanishes at l; for large n it
+// is a positive multiple of F_l G_{l+n}, and G > 0 deep in the barrier.
 __device__ Cf1 cf1_lentz(int l, double eta, double rho)
 {
     const double irho = 1.0 / rho;
-    double L1 = l + 1.0;
+    const double L1 = l + 1.0;
     double er = eta / L1;            // eta / (l + n), carried to the next iteration
     double S = L1 * irho + er;
-    double f = (S == 0.0) ? TINY : S;
-    double C = f, D = 0.0;
-    int sgn = 1;
+    double A2 = 1.0, B2 = 0.0;       // A_{n-2}, B_{n-2}
+    double A1 = S, B1 = 1.0;         // A_{n-1}, B_{n-1}
     for (int n = 1; n < CF_MAXIT; ++n) {
         const double Ln1 = l + n + 1.0;
         const double er1 = eta * rcp_nr(Ln1);
         const double Snext = Ln1 * irho + er1;
         const double an = -fma(er, er, 1.0);
         const double bn = S + Snext;
-        D = fma(an, D, bn);
-        if (D == 0.0) D = TINY;
-        C = fma(an, rcp_nr(C), bn);
-        if (C == 0.0) C = TINY;
-        D = rcp_nr(D);
-        if (D < 0.0) sgn = -sgn;
-        const double delta = C * D;
-        f *= delta;
-        if (fabs(delta - 1.0) < CF_TOL) return {f, sgn, 1, n};
+        const double A = fma(bn, A1, an * A2);
+        const double B = fma(bn, B1, an * B2);
+        A2 = A1;
+        B2 = B1;
+        A1 = A;
+        B1 = B;
         S = Snext;
         er = er1;
+        if (n % CF_CHECK == 0) {
+            const double sc = pow2_rescale(fmax(fmax(fabs(A1), fabs(B1)), fmax(fabs(A2), fabs(B2))));
+            A1 *= sc;
+            B1 *= sc;
+            A2 *= sc;
+            B2 *= sc;
+            const double f = A1 / B1, fp = A2 / B2;
+            if (fabs(f - fp) < CF_TOL * fabs(fp)) return {f, B1 < 0.0 ? -1 : 1, 1, n};
+        }
     }
-    return {f, sgn, 0, CF_MAXIT};
+    return {0.0, 1, 0, CF_MAXIT};
 }
 
 // p + iq = H+'/H+ at l = 0: i(1 - eta/rho) + (i/rho) K,  K = K(a_m / b_m),
 // a_m = (m + i eta)(m - 1 + i eta), b_m = 2(rho - eta) + 2 i m.
-// Forward Lentz on the tail K' = b_1 + K_{m>=2}(a_m / b_m) (|b_1| >= 2, so
-// no scaled-tiny start is needed) gives K = a_1 / K' when it settles within
-// CF2_FAST_DEPTH steps; otherwise its depth n sets a bottom-up evaluation
-// from depth 2n + 20.
+// The forward convergents of the tail K' = b_1 + K_{m>=2}(a_m / b_m) give
+// K = a_1 / K' when they settle within CF2_FAST_DEPTH steps; otherwise the
+// depth n reached sets a backward evaluation of K from depth 2n + 20.
 __device__ int cf2_open_l0(double eta, double rho, double *p, double *q, int *depth)
 {
     const double br = 2.0 * (rho - eta);
-    double Cr = br, Ci = 2.0, Dr = 0.0, Di = 0.0;
-    double fr = br, fi = 2.0;   // K' by forward Lentz
+    double A2r = 1.0, A2i = 0.0, B2r = 0.0, B2i = 0.0;
+    double A1r = br, A1i = 2.0, B1r = 1.0, B1i = 0.0;
+    double fr = br, fi = 2.0;
     int n = 2;
+    bool conv = false;
     for (; n < CF_MAXIT; ++n) {
         const double m = n;
         const double ar = m * (m - 1.0) - eta * eta;
         const double ai = eta * (2.0 * m - 1.0);
         const double bi = 2.0 * m;
-        // D = 1 / (b + a D)
-        double tr = br + (ar * Dr - ai * Di);
-        double ti = bi + (ar * Di + ai * Dr);
-        if (tr == 0.0 && ti == 0.0) tr = TINY;
-        const double dm = rcp_nr(tr * tr + ti * ti);
-        Dr = tr * dm;
-        Di = -ti * dm;
-        // C = b + a / C
-        const double cm = rcp_nr(Cr * Cr + Ci * Ci);
-        double ur = br + (ar * Cr + ai * Ci) * cm;
-        double ui = bi + (ai * Cr - ar * Ci) * cm;
-        if (ur == 0.0 && ui == 0.0) ur = TINY;
-        Cr = ur;
-        Ci = ui;
-        const double er = Cr * Dr - Ci * Di;
-        const double ei = Cr * Di + Ci * Dr;
-        const double gr = fr * er - fi * ei;
-        fi = fr * ei + fi * er;
-        fr = gr;
-        if (fabs(er - 1.0) + fabs(ei) < CF_TOL) break;
+        const double tAr = fma(ar, A2r, -ai * A2i), tAi = fma(ar, A2i, ai * A2r);
+        const double tBr = fma(ar, B2r, -ai * B2i), tBi = fma(ar, B2i, ai * B2r);
+        const double Ar = fma(br, A1r, fma(-bi, A1i, tAr));
+        const double Ai = fma(br, A1i, fma(bi, A1r, tAi));
+        const double Br = fma(br, B1r, fma(-bi, B1i, tBr));
+        const double Bi = fma(br, B1i, fma(bi, B1r, tBi));
+        A2r = A1r; A2i = A1i; B2r = B1r; B2i = B1i;
+        A1r = Ar; A1i = Ai; B1r = Br; B1i = Bi;
+        if (n % CF_CHECK == 0) {
+            const double mx = fmax(fmax(fmax(fabs(A1r), fabs(A1i)), fmax(fabs(B1r), fabs(B1i))),
+                                   fmax(fmax(fabs(A2r), fabs(A2i)), fmax(fabs(B2r), fabs(B2i))));
+            const double sc = pow2_rescale(mx);
+            A1r *= sc; A1i *= sc; B1r *= sc; B1i *= sc;
+            A2r *= sc; A2i *= sc; B2r *= sc; B2i *= sc;
+            const double d1 = 1.0 / (B1r * B1r + B1i * B1i), d2 = 1.0 / (B2r * B2r + B2i * B2i);
+            fr = (A1r * B1r + A1i * B1i) * d1;
+            fi = (A1i * B1r - A1r * B1i) * d1;
+            const double gr = (A2r * B2r + A2i * B2i) * d2;
+            const double gi = (A2i * B2r - A2r * B2i) * d2;
+            if (fabs(fr - gr) + fabs(fi - gi) < CF_TOL * (fabs(gr) + fabs(gi))) {
+                conv = true;
+                break;
+            }
+        }
     }
     *depth = n;
-    if (n >= CF_MAXIT) return 0;
-    double vr = 0.0, vi = 0.0;
+    if (!conv) return 0;
     if (n <= CF2_FAST_DEPTH) {
         // K = a_1 / K',  a_1 = -eta^2 + i eta
         const double ar = -eta * eta, ai = eta;
-        const double dm = rcp_nr(fr * fr + fi * fi);
+        const double dm = 1.0 / (fr * fr + fi * fi);
         *p = -((ai * fr - ar * fi) * dm) / rho;
         *q = (1.0 - eta / rho) + ((ar * fr + ai * fi) * dm) / rho;
         return 1;
     }
     const int N = 2 * n + 20;
+    double pr = 0.0, pi = 0.0, qr = 1.0, qi = 0.0;
     for (int m_ = N; m_ >= 1; --m_) {
         const double m = m_;
         const double ar = m * (m - 1.0) - eta * eta;
         const double ai = eta * (2.0 * m - 1.0);
-        const double dr = br + vr;
-        const double di = 2.0 * m + vi;
-        const double dm = rcp_nr(dr * dr + di * di);
-        vr = (ar * dr + ai * di) * dm;
-        vi = (ai * dr - ar * di) * dm;
+        const double bi = 2.0 * m;
+        // (p, q) <- (a_m q, p + b_m q)
+        const double npr = fma(ar, qr, -ai * qi), npi = fma(ar, qi, ai * qr);
+        const double nqr = fma(br, qr, fma(-bi, qi, pr));
+        const double nqi = fma(br, qi, fma(bi, qr, pi));
+        pr = npr; pi = npi; qr = nqr; qi = nqi;
+        if (m_ % CF_CHECK == 0) {
+            const double sc = pow2_rescale(fmax(fmax(fabs(pr), fabs(pi)), fmax(fabs(qr), fabs(qi))));
+            pr *= sc; pi *= sc; qr *= sc; qi *= sc;
+        }
     }
+    const double dm = 1.0 / (qr * qr + qi * qi);
+    const double vr = (pr * qr + pi * qi) * dm, vi = (pi * qr - pr * qi) * dm;
     *p = -vi / rho;
     *q = (1.0 - eta / rho) + vr / rho;
     return 1;
 }
 
 // Closed-channel log-derivative (r-units) at l = L0 from CF2 at imaginary k.
-// Forward Lentz on the tail K' = b_1 - a_2/(b_2 - a_3/(...)) gives
-// Phi = a_1 / K' when it settles within CF2_FAST_DEPTH steps; otherwise its
-// depth n sets a bottom-up evaluation from depth 2n + 20.
+// The forward convergents of the tail K' = b_1 - a_2/(b_2 - a_3/(...)) give
+// Phi = a_1 / K' when they settle within CF2_FAST_DEPTH steps; otherwise the
+// depth n reached sets a backward evaluation from depth 2n + 20.
 __device__ int cf2_closed(int L0, double nu, double kap, double a, double *y, int *depth)
 {
     const double base = kap * a - nu;
     auto an = [&](int m) { return (L0 + m - nu) * (m - 1.0 - L0 - nu); };
-    double C = 2.0 * (base + 1.0), D = 0.0;
-    if (C == 0.0) C = TINY;
-    double f = C;   // K' by forward Lentz
+    double A2 = 1.0, B2 = 0.0, A1 = 2.0 * (base + 1.0), B1 = 1.0;
+    double f = A1;
     int n = 2;
+    bool conv = false;
     for (; n < CF_MAXIT; ++n) {
-        const double A = -an(n);
-        const double B = 2.0 * (base + n);
-        D = fma(A, D, B);
-        if (D == 0.0) D = TINY;
-        C = fma(A, rcp_nr(C), B);
-        if (C == 0.0) C = TINY;
-        D = rcp_nr(D);
-        const double delta = C * D;
-        f *= delta;
-        if (fabs(delta - 1.0) < CF_TOL) break;
+        const double num = -an(n);
+        const double den = 2.0 * (base + n);
+        const double A = fma(den, A1, num * A2);
+        const double B = fma(den, B1, num * B2);
+        A2 = A1;
+        B2 = B1;
+        A1 = A;
+        B1 = B;
+        if (n % CF_CHECK == 0) {
+            const double sc = pow2_rescale(fmax(fmax(fabs(A1), fabs(B1)), fmax(fabs(A2), fabs(B2))));
+            A1 *= sc;
+            B1 *= sc;
+            A2 *= sc;
+            B2 *= sc;
+            f = A1 / B1;
+            const double fp = A2 / B2;
+            if (fabs(f - fp) < CF_TOL * fabs(fp)) {
+                conv = true;
+                break;
+            }
+        }
     }
     *depth = n;
-    if (n >= CF_MAXIT) return 0;
+    if (!conv) return 0;
     if (n <= CF2_FAST_DEPTH) {
         *y = -kap + (nu + an(1) / f) / a;
         return 1;
     }
     const int N = 2 * n + 20;
-    double v = 0.0;
-    for (int m = N; m >= 2; --m) v = -an(m) * rcp_nr(2.0 * (base + m) + v);
-    const double phi = an(1) / (2.0 * (base + 1.0) + v);
+    double pp = 0.0, qq = 1.0;
+    for (int m = N; m >= 2; --m) {
+        // (p, q) <- (num_m q, p + den_m q)
+        const double np_ = -an(m) * qq;
+        qq = fma(2.0 * (base + m), qq, pp);
+        pp = np_;
+        if (m % CF_CHECK == 0) {
+            const double sc = pow2_rescale(fmax(fabs(pp), fabs(qq)));
+            pp *= sc;
+            qq *= sc;
+        }
+    }
+    const double phi = an(1) / (2.0 * (base + 1.0) + pp / qq);
     *y = -kap + (nu + phi) / a;
     return 1;
 }
@@ -250,8 +311,16 @@ __device__ int regular_analytic(int l, double z, double eps, double r, double *f
 // iteration counts of the continued fractions: {kind, CF1 iterations, CF2
 // forward iterations (the backward pass then takes 2n + 20 steps), l - L0
 // ladder steps for a closed channel or l for an open one}.
+#ifndef RM_CHANFN_BS
+#define RM_CHANFN_BS 128
+#endif
+#ifndef RM_CHANFN_MINB
+#define RM_CHANFN_MINB 1
+#endif
+constexpr int CHANFN_BS = RM_CHANFN_BS;   // threads per block of the channel kernel
+
 template <bool MQDT, bool STATS>
-__global__ void chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
+__global__ void __launch_bounds__(CHANFN_BS, RM_CHANFN_MINB) chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
                               ChanFn *__restrict__ out, int *__restrict__ status, int4 *__restrict__ work)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -398,7 +467,7 @@ cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &
 {
     const long long total = (long long)nE * pw.n;
     if (total == 0) return cudaSuccess;
-    const int bs = 128;
+    const int bs = CHANFN_BS;
     const unsigned grid = (unsigned)((total + bs - 1) / bs);
     if (mqdt)
         chanfn_kernel<true, false><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status, nullptr);
@@ -412,7 +481,7 @@ cudaError_t launch_chanfn_work(const PwDev &pw, const double *E, int nE, const O
 {
     const long long total = (long long)nE * pw.n;
     if (total == 0) return cudaSuccess;
-    const int bs = 128;
+    const int bs = CHANFN_BS;
     chanfn_kernel<false, true><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(pw, E, nE, o, nullptr,
                                                                                 nullptr, work);
     return cudaGetLastError();
