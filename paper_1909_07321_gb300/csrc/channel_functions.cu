@@ -62,7 +62,10 @@ constexpr double CF_TOL = 4e-16;
 // forward Lentz value (few roundings, and a fast-converging fraction leaves
 // no significant tail); slower ones are re-evaluated backwards from depth
 // 2n + 20.
-constexpr int CF2_FAST_DEPTH = 32;
+#ifndef RM_CF2_FAST_DEPTH
+#define RM_CF2_FAST_DEPTH 32
+#endif
+constexpr int CF2_FAST_DEPTH = RM_CF2_FAST_DEPTH;
 
 struct Cf1 {
     double f;
@@ -318,14 +321,43 @@ __device__ int regular_analytic(int l, double z, double eps, double r, double *f
 #define RM_CHANFN_MINB 1
 #endif
 constexpr int CHANFN_BS = RM_CHANFN_BS;   // threads per block of the channel kernel
+constexpr double CHANFN_DEEP_EPS = 2.5e-5;   // |eps| / max(z^2, 1) below this: a deep pair
+constexpr int CHANFN_DEEP_CAP = 1 << 14;     // capacity of the deep-pair list
 
-template <bool MQDT, bool STATS>
-__global__ void __launch_bounds__(CHANFN_BS, RM_CHANFN_MINB) chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
-                              ChanFn *__restrict__ out, int *__restrict__ status, int4 *__restrict__ work)
+// Pairs (energy, channel) this close to their threshold have the deepest
+// continued fractions (depth ~ 3 / sqrt(|eps| / z^2): about 600 to tens of
+// thousands of steps, each a serial chain of dependent FP64 operations that
+// no parallel split evaluates as accurately). They are listed, their
+// energies marked, and a separate kernel (on a second stream) evaluates them
+// while the main stream forms R and solves every unmarked energy; the marked
+// energies are solved after it.
+__device__ __forceinline__ bool chanfn_deep(double eps, double z, double eps_thr)
+{
+    return fabs(eps) < CHANFN_DEEP_EPS * fmax(z * z, 1.0) && fabs(eps) >= eps_thr;
+}
+
+__global__ void chanfn_deep_mark_kernel(PwDev pw, const double *__restrict__ E, int nE, double eps_thr,
+                                        int *__restrict__ count, int *__restrict__ list,
+                                        int *__restrict__ defer)
 {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nE * pw.n) return;
+    const int i = (int)(idx / nE);
+    const int e = (int)(idx - (long long)i * nE);
+    if (chanfn_deep(E[e] - pw.e_thr[i], pw.z, eps_thr)) {
+        const int k = atomicAdd(count, 1);
+        if (k < CHANFN_DEEP_CAP) list[k] = (int)idx;
+        defer[e] = 1;
+    }
+}
+
+// Channel data of pair idx = i nE + e.
+template <bool MQDT, bool STATS>
+__device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int nE, const Opts &o,
+                            ChanFn *__restrict__ out, int *__restrict__ status, int4 *__restrict__ work,
+                            long long idx)
+{
     const int n = pw.n;
-    if (idx >= (long long)nE * n) return;
     const int i = (int)(idx / nE);
     const int e = (int)(idx - (long long)i * nE);
     const double eps = E[e] - pw.e_thr[i];
@@ -430,6 +462,37 @@ __global__ void __launch_bounds__(CHANFN_BS, RM_CHANFN_MINB) chanfn_kernel(PwDev
     if (bad != RM_OK) atomicCAS(status + e, RM_OK, bad);
 }
 
+// With deep_count != nullptr, the listed deep pairs are skipped (when the
+// list did not overflow): chanfn_deep_kernel takes them.
+template <bool MQDT, bool STATS>
+__global__ void __launch_bounds__(CHANFN_BS, RM_CHANFN_MINB)
+    chanfn_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o, ChanFn *__restrict__ out,
+                  int *__restrict__ status, int4 *__restrict__ work, const int *__restrict__ deep_count)
+{
+    const int n = pw.n;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)nE * n) return;
+    if (deep_count && *deep_count <= CHANFN_DEEP_CAP) {
+        const int i0 = (int)(idx / nE);
+        const int e0 = (int)(idx - (long long)i0 * nE);
+        if (chanfn_deep(E[e0] - pw.e_thr[i0], pw.z, o.eps_thr)) return;
+    }
+    chanfn_pair<MQDT, STATS>(pw, E, nE, o, out, status, work, idx);
+}
+
+// One thread per listed deep pair.
+template <bool MQDT>
+__global__ void __launch_bounds__(64)
+    chanfn_deep_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o, ChanFn *__restrict__ out,
+                       int *__restrict__ status, const int *__restrict__ deep_count,
+                       const int *__restrict__ list)
+{
+    const int cnt = *deep_count;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cnt > CHANFN_DEEP_CAP || k >= cnt) return;
+    chanfn_pair<MQDT, false>(pw, E, nE, o, out, status, nullptr, list[k]);
+}
+
 __global__ void nearpole_kernel(PwDev pw, const double *__restrict__ E, int nE,
                                 int *__restrict__ status)
 {
@@ -463,27 +526,52 @@ __global__ void export_kernel(PwDev pw, const double *__restrict__ E, int nE,
 }  // namespace
 
 cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
-                          ChanFn *cf, int *status, cudaStream_t s)
+                          ChanFn *cf, int *status, const int *deep_ws, cudaStream_t s)
 {
     const long long total = (long long)nE * pw.n;
     if (total == 0) return cudaSuccess;
-    const int bs = CHANFN_BS;
-    const unsigned grid = (unsigned)((total + bs - 1) / bs);
+    const unsigned grid = (unsigned)((total + CHANFN_BS - 1) / CHANFN_BS);
     if (mqdt)
-        chanfn_kernel<true, false><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status, nullptr);
+        chanfn_kernel<true, false><<<grid, CHANFN_BS, 0, s>>>(pw, E, nE, o, cf, status, nullptr, deep_ws);
     else
-        chanfn_kernel<false, false><<<grid, bs, 0, s>>>(pw, E, nE, o, cf, status, nullptr);
+        chanfn_kernel<false, false><<<grid, CHANFN_BS, 0, s>>>(pw, E, nE, o, cf, status, nullptr, deep_ws);
     return cudaGetLastError();
 }
+
+size_t chanfn_deep_ws_bytes(int nE) { return (size_t)(1 + CHANFN_DEEP_CAP + nE) * sizeof(int); }
+
+cudaError_t launch_chanfn_deep_mark(const PwDev &pw, const double *E, int nE, const Opts &o, int *deep_ws,
+                                    cudaStream_t s)
+{
+    const long long total = (long long)nE * pw.n;
+    cudaError_t e = cudaMemsetAsync(deep_ws, 0, chanfn_deep_ws_bytes(nE), s);
+    if (e != cudaSuccess || total == 0) return e;
+    chanfn_deep_mark_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        pw, E, nE, o.eps_thr, deep_ws, deep_ws + 1, deep_ws + 1 + CHANFN_DEEP_CAP);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chanfn_deep(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt, ChanFn *cf,
+                               int *status, const int *deep_ws, cudaStream_t s)
+{
+    if ((long long)nE * pw.n == 0) return cudaSuccess;
+    const unsigned grid = (CHANFN_DEEP_CAP + 63) / 64;
+    if (mqdt)
+        chanfn_deep_kernel<true><<<grid, 64, 0, s>>>(pw, E, nE, o, cf, status, deep_ws, deep_ws + 1);
+    else
+        chanfn_deep_kernel<false><<<grid, 64, 0, s>>>(pw, E, nE, o, cf, status, deep_ws, deep_ws + 1);
+    return cudaGetLastError();
+}
+
+int chanfn_deep_cap() { return CHANFN_DEEP_CAP; }
 
 cudaError_t launch_chanfn_work(const PwDev &pw, const double *E, int nE, const Opts &o, int4 *work,
                                cudaStream_t s)
 {
     const long long total = (long long)nE * pw.n;
     if (total == 0) return cudaSuccess;
-    const int bs = CHANFN_BS;
-    chanfn_kernel<false, true><<<(unsigned)((total + bs - 1) / bs), bs, 0, s>>>(pw, E, nE, o, nullptr,
-                                                                                nullptr, work);
+    chanfn_kernel<false, true><<<(unsigned)((total + CHANFN_BS - 1) / CHANFN_BS), CHANFN_BS, 0, s>>>(
+        pw, E, nE, o, nullptr, nullptr, work, nullptr);
     return cudaGetLastError();
 }
 

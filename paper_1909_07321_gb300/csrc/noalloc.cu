@@ -111,12 +111,12 @@ extern "C" int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E,
         const double *Eb = E + e0;
         int *sb = status_out + e0;
         err = launch_nearpole(d, Eb, nb, sb, s);
-        if (err == cudaSuccess) err = launch_chanfn(d, Eb, nb, o, 0, cf, sb, s);
+        if (err == cudaSuccess) err = launch_chanfn(d, Eb, nb, o, 0, cf, sb, nullptr, s);
         if (err == cudaSuccess) err = launch_form_r_fp64(d, Eb, nb, R, s);
         if (err == cudaSuccess)
             err = launch_solve_small(d, Eb, nb, cf, R, sb,
                                      K_out ? K_out + (size_t)e0 * n_ch * n_ch : nullptr,
-                                     n_open_out ? n_open_out + e0 : nullptr, nullptr, 0, 0, 0, s);
+                                     n_open_out ? n_open_out + e0 : nullptr, nullptr, 0, 0, 0, nullptr, 0, s);
     }
     if (err != cudaSuccess) {
         if (errbuf && errlen) snprintf(errbuf, errlen, "CUDA error: %s", cudaGetErrorString(err));

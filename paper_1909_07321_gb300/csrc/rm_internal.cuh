@@ -54,8 +54,21 @@ struct Opts {
 // ---- launchers (each returns cudaGetLastError() of its launch) ----------
 
 // mqdt != 0: closed channels in the quantum-defect set get CH_MQDT data.
+// deep_ws (or nullptr): the list written by launch_chanfn_deep_mark; the
+// listed deep pairs are then left to launch_chanfn_deep.
 cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
-                          ChanFn *cf, int *status, cudaStream_t s);
+                          ChanFn *cf, int *status, const int *deep_ws, cudaStream_t s);
+// Near-threshold (deep) pairs: deep_ws = [count][list of CAP pair indices][nE
+// energy marks], chanfn_deep_ws_bytes(nE) bytes. The mark launch zeroes it
+// and fills it; the deep launch evaluates the listed pairs. If the list
+// overflowed (count > chanfn_deep_cap()), nothing is left out and nothing is
+// deferred.
+size_t chanfn_deep_ws_bytes(int nE);
+int chanfn_deep_cap();
+cudaError_t launch_chanfn_deep_mark(const PwDev &pw, const double *E, int nE, const Opts &o, int *deep_ws,
+                                    cudaStream_t s);
+cudaError_t launch_chanfn_deep(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt, ChanFn *cf,
+                               int *status, const int *deep_ws, cudaStream_t s);
 cudaError_t launch_nearpole(const PwDev &pw, const double *E, int nE, int *status,
                             cudaStream_t s);
 // Iteration counts of step (b) (direct mode), [nE][n] int4 {kind, CF1
@@ -67,9 +80,12 @@ cudaError_t launch_form_r_fp64(const PwDev &pw, const double *E, int nE, double 
 // mqdt != 0: the channel data may hold MQDT-eliminated channels (larger
 // shared-memory layout). f32 != 0 (direct mode only): the matching system is
 // eliminated in FP32.
+// deep_ws (or nullptr): pass 0 leaves out the energies marked by
+// launch_chanfn_deep_mark, pass 1 solves only those.
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
-                               double *omega, int n_tri, int mqdt, int f32, cudaStream_t s);
+                               double *omega, int n_tri, int mqdt, int f32, const int *deep_ws, int pass,
+                               cudaStream_t s);
 // Mixed-precision formation (tensor cores). Operand kinds:
 enum TcKind { TC_BF16X3 = 0, TC_TF32X3 = 1 };
 // Split of P_pk = w_ik w_jk / (2a) into hi/lo operands, [n_pairs][Kpad] K-major.

@@ -105,7 +105,10 @@ struct rm_ctx {
     std::vector<double> grid_host;
     DevBuf omega;
     // workspace
-    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart;
+    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep;
+    // side stream for the deep channel pairs, with fork / join events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     long long launches = 0;
     // per-phase event pairs (tracing)
     bool prof = false;
@@ -270,6 +273,15 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
         }
         ctx->own_stream = true;
     }
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        rm_destroy(ctx);
+        return RM_ECUDA;
+    }
     *out = ctx;
     return RM_SUCCESS;
 }
@@ -281,13 +293,19 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
     for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
-                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart})
+                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
         for (auto &pr : ctx->ev[p]) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -603,8 +621,23 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
         CK(prof_begin(ctx, RM_PH_NEARPOLE));
         CK(launch_nearpole(d, Eb, nb, sb, ctx->stream));
         CK(prof_end(ctx, RM_PH_NEARPOLE));
+        // Deep (near-threshold) channel pairs go to the side stream, and the
+        // energies holding them are solved after it joins (shared-memory
+        // solver only).
+        const bool split = !large;
+        int *deep = nullptr;
+        if (split) {
+            CK(ctx->wsDeep.reserve(chanfn_deep_ws_bytes(B)));
+            deep = ctx->wsDeep.as<int>();
+            CK(launch_chanfn_deep_mark(d, Eb, nb, o, deep, ctx->stream));
+            CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+            CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+            CK(launch_chanfn_deep(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, deep, ctx->side));
+            CK(cudaEventRecord(ctx->ev_join, ctx->side));
+            ctx->launches += 2;
+        }
         CK(prof_begin(ctx, RM_PH_CHANFN));
-        CK(launch_chanfn(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, ctx->stream));
+        CK(launch_chanfn(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, deep, ctx->stream));
         CK(prof_end(ctx, RM_PH_CHANFN));
         ctx->launches += 2;
         rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
@@ -619,10 +652,13 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
                                   omb, ntri, ctx->wsL.p, &L, ctx->stream));
             ctx->launches += L;
         } else {
+            const int f32 = mode == RM_DIRECT && ctx->opts.solve_precision == RM_FP32;
             CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, mode == RM_MQDT,
-                                  mode == RM_DIRECT && ctx->opts.solve_precision == RM_FP32, ctx->stream));
-            ctx->launches++;
+                                  omb, ntri, mode == RM_MQDT, f32, deep, 0, ctx->stream));
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+            CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
+                                  omb, ntri, mode == RM_MQDT, f32, deep, 1, ctx->stream));
+            ctx->launches += 2;
         }
         CK(prof_end(ctx, RM_PH_SOLVE));
     }
@@ -710,7 +746,7 @@ extern "C" int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *
     }
     CK(cudaMemsetAsync(st, 0, (size_t)n_E * sizeof(int), ctx->stream));
     const PwDev d = P.dev();
-    CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ctx->wsCf.as<ChanFn>(), st, ctx->stream));
+    CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ctx->wsCf.as<ChanFn>(), st, nullptr, ctx->stream));
     CK(launch_chanfn_export(d, E, n_E, ctx->wsCf.as<ChanFn>(), out, ctx->stream));
     ctx->launches += 2;
     return RM_SUCCESS;

@@ -216,8 +216,15 @@ template <bool F32>
 __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
     const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
-    int *__restrict__ n_open_out, double *__restrict__ omega, int n_tri, int mqdt_layout)
+    int *__restrict__ n_open_out, double *__restrict__ omega, int n_tri, int mqdt_layout,
+    const int *__restrict__ deep_ws, int deep_cap, int pass)
 {
+    // Energies holding a deep (near-threshold) channel pair are solved in
+    // pass 1, after their channel data is complete; the others in pass 0.
+    if (deep_ws) {
+        const bool deferred = deep_ws[0] <= deep_cap && deep_ws[1 + deep_cap + blockIdx.x] != 0;
+        if (pass == 0 ? deferred : !deferred) return;
+    }
     extern __shared__ double sm[];
     __shared__ int col_chan[SOLVE_SMALL_MAXN];   // unknown column -> channel
     __shared__ int open_pos[SOLVE_SMALL_MAXN];   // channel -> open position (-1 otherwise)
@@ -481,24 +488,26 @@ size_t solve_small_smem(int n, int mqdt, int f32)
 
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
-                               double *omega, int n_tri, int mqdt, int f32, cudaStream_t s)
+                               double *omega, int n_tri, int mqdt, int f32, const int *deep_ws, int pass,
+                               cudaStream_t s)
 {
     if (pw.n > SOLVE_SMALL_MAXN || (f32 && mqdt)) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
     const size_t smem = solve_small_smem(pw.n, mqdt, f32);
+    const int cap = chanfn_deep_cap();
     cudaError_t err;
     if (f32) {
         err = cudaFuncSetAttribute(solve_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem);
         if (err != cudaSuccess) return err;
         solve_small_kernel<true><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
-                                                      n_tri, 0);
+                                                      n_tri, 0, deep_ws, cap, pass);
     } else {
         err = cudaFuncSetAttribute(solve_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem);
         if (err != cudaSuccess) return err;
         solve_small_kernel<false><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
-                                                       n_tri, mqdt ? 1 : 0);
+                                                       n_tri, mqdt ? 1 : 0, deep_ws, cap, pass);
     }
     return cudaGetLastError();
 }
