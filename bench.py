@@ -191,11 +191,11 @@ def _solve_flops(n, n_open, f32):
     shared-memory solver takes them, split (FP64, FP32): elimination of the
     n x (n + n_o) system (2/3 n^3 + n^2 n_o) and back-substitution of the n_o
     trailing rows (n_o^3), in FP32 when f32; then FP64 M = 1 + K^2 (upper
-    triangle, n_o^3), M^{-1} by Gauss-Jordan (2 n_o^3), X = K M^{-1} for the
-    upper triangle (n_o^3)."""
+    triangle, n_o^3), M^{-1} by the symmetric sweep (n_o^3), X = K M^{-1} for
+    the upper triangle (n_o^3)."""
     no = n_open.astype(np.float64)
     elim = float(np.sum(2.0 / 3.0 * n**3 + n * n * no + no**3))
-    t = float(np.sum(4.0 * no**3))
+    t = float(np.sum(3.0 * no**3))
     return (t, elim) if f32 else (t + elim, 0.0)
 
 
