@@ -23,6 +23,11 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
                         unitarity of S
   k_mqdt                identity with k_direct (exact elimination identity)
   t_matrix / omega      optical theorem, symmetric Omega, real-form |T|^2
+  qdt (coarse-mesh      tests/test_oracle_qdt.py: every energy a node equals the
+  interpolation)        plain MQDT solve; a node matrix linear in energy is
+                        reproduced exactly (also when extrapolating); error
+                        of S_u interpolation falls as h^2; segment and
+                        qetest rules on hand-made grids
   cross-threshold K, Omega beyond these checks: parity unpinned (the paper
                         prints no K or Omega values for any system).
 """
