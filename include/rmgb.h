@@ -162,6 +162,38 @@ int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, doub
 int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
                       double *K_out, int *n_open_out, int *status_out);
 
+/* MQDT coarse-mesh interpolation (Section "namelist stgf MQDT variables":
+ * imode = -1, ieq, qetest, iqdt). Accumulates g |T|^2 into Omega for the
+ * n_E fine energies E (HOST array, strictly ascending; registered as the
+ * grid like rm_solve_energies) without solving the matching system at each:
+ *   1. the fine mesh is cut into segments of consecutive energies with the
+ *      same channel classes (open; closed and eliminated by MQDT: nu >=
+ *      max(l + nu_margin, fnumin), kappa a <= mqdt_kappa_a_max; other closed);
+ *   2. nodes per segment: its first and last energies, plus every |ieq|-th
+ *      fine energy (ieq < 0) or the points of the ieq-point grid spanning
+ *      [E_0, E_{n_E - 1}] that fall inside it (ieq > 0); nodes where an
+ *      eliminated channel has |sin pi nu| < 1e-3, nodes on a pole and nodes
+ *      whose solve fails are left out;
+ *   3. at every node the unphysical K_u (RM_MQDT channel functions, the
+ *      context's formation precision, FP64 matching) is solved, and for
+ *      iqdt = 1 turned into S_u = (1 + i K_u)(1 - i K_u)^{-1};
+ *   4. at every fine energy K_u (iqdt = 2) or S_u (iqdt = 1) is interpolated
+ *      linearly in energy between the nearest nodes of its segment (linearly
+ *      extrapolated beyond its outer nodes, constant with one node), at the
+ *      last energy that moved more than qetest Ry since the previous
+ *      re-interpolation (qetest <= 0: at the energy itself), and the closed
+ *      channels are eliminated with nu of the fine energy:
+ *        K = K_oo - K_oc (K_cc + tan pi nu)^{-1} K_co, or
+ *        S = S_oo - S_oc (S_cc - exp(-2 i pi nu))^{-1} S_co, T = S - 1.
+ * n_open_out (device, [n_E], nullable), status_out (device, [n_E], nullable):
+ * RM_ETHRESHOLD on a threshold, RM_ESINGULAR where a segment has no usable
+ * node or the elimination is singular. At most 96 channels. Synchronises
+ * the context stream once (after the node solves).
+ * Errors: RM_EINVAL (E on the device, not ascending, ieq = 0, iqdt not 1 or
+ * 2), RM_ENOTLOADED, RM_EGRID, RM_EUNSUPPORTED, RM_ENOMEM, RM_ECUDA. */
+int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double *E, int ieq, double qetest,
+                          int iqdt, int *n_open_out, int *status_out);
+
 /* Copies the accumulated collision strengths to omega_out (host,
  * [n_E][n_levels*(n_levels+1)/2], upper triangle row-wise: (I, J), I <= J,
  * at I*n_levels - I*(I-1)/2 + (J - I)); entries of levels closed at E are 0.

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/rmgb.h"
 
 namespace rmgb {
@@ -81,11 +83,14 @@ cudaError_t launch_form_r_fp64(const PwDev &pw, const double *E, int nE, double 
 // shared-memory layout). f32 != 0 (direct mode only): the matching system is
 // eliminated in FP32.
 // deep_ws (or nullptr): pass 0 leaves out the energies marked by
-// launch_chanfn_deep_mark, pass 1 solves only those.
+// launch_chanfn_deep_mark, pass 1 solves only those. ku_out (or nullptr,
+// FP64 matching): instead of K, T and Omega, write the unphysical K_u of the
+// P channels (open and MQDT-eliminated, channel order) to ku_out [nE][n][n]
+// (row stride n) and its order to ku_np [nE].
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
                                double *omega, int n_tri, int mqdt, int f32, const int *deep_ws, int pass,
-                               cudaStream_t s);
+                               cudaStream_t s, double *ku_out = nullptr, int *ku_np = nullptr);
 // Mixed-precision formation (tensor cores). Operand kinds:
 enum TcKind { TC_BF16X3 = 0, TC_TF32X3 = 1 };
 // Split of P_pk = w_ik w_jk / (2a) into hi/lo operands, [n_pairs][Kpad] K-major.
@@ -132,5 +137,48 @@ size_t solve_large_bytes_per_energy(int n);
 cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
                                double *omega, int n_tri, void *ws, int *launches, cudaStream_t s);
+
+// ---- MQDT coarse-mesh interpolation (qdt.cu) ------------------------------------
+enum QdtClass : signed char { QDT_OPEN = 0, QDT_ELIM = 1, QDT_DECAY = 2 };
+enum QdtFlag { QDT_FLAG_OK = 0, QDT_FLAG_THRESHOLD = 1, QDT_FLAG_NONODE = 2 };
+
+// Host view of one partial wave's channels and the MQDT options.
+struct QdtChannels {
+    int n, N;
+    const double *e_thr;   // [n]
+    const int *l;          // [n]
+    const double *E_k;     // [N] sorted
+    double z, a, eps_thr, nu_margin, fnumin, kappa_a_max;
+};
+
+// Segments of fine energies with equal channel classes, their valid nodes,
+// and the energy at which each fine energy is interpolated (qetest).
+struct QdtPlan {
+    std::vector<int> seg;                      // [n_E] segment or -1 (on a threshold)
+    std::vector<int> i0, i1;                   // fine index range per segment
+    std::vector<std::vector<signed char>> cls; // classes per segment
+    std::vector<double> e_int;                 // [n_E]
+    std::vector<double> node_x;                // valid nodes, segment by segment
+    std::vector<int> node_seg, seg_node0, seg_nnodes;
+};
+
+// Interpolation of one fine energy: K_u or S_u = (1 - t) node a + t node b.
+struct QdtFine {
+    int a, b;
+    double t;
+    int flag;
+};
+
+// RM_EINVAL if ieq == 0 or E is not strictly ascending.
+int qdt_plan(const QdtChannels &c, const double *E, int n_E, int ieq, double qetest, QdtPlan &pl);
+// Weights over the nodes with node_ok != 0 (failed nodes left out).
+void qdt_weights(const QdtPlan &pl, const std::vector<int> &node_ok, int n_E, std::vector<QdtFine> &fine);
+// Node K_u [nn][n][n] -> S_u = 2 (1 - i K_u)^{-1} - 1 (complex, same layout).
+cudaError_t launch_qdt_s_from_k(int n, int n_nodes, const double *Ku, const int *np_node, int *status,
+                                double2 *Su, cudaStream_t s);
+// Fine energies: interpolation, elimination at the fine energy, Omega.
+cudaError_t launch_qdt_fine(int iqdt, const PwDev &pw, const double *E, int nE, const Opts &o,
+                            const QdtFine *fine, const double *Ku, const double2 *Su, const int *node_status,
+                            int *status, int *n_open_out, double *omega, int n_tri, cudaStream_t s);
 
 }  // namespace rmgb

@@ -61,7 +61,8 @@ struct PwHost {
     // per-energy formulation: W in FP32 and w split hi/lo (built on first use)
     DevBuf W32, Wh, Wl;
     int w_kind = -1;
-    std::vector<double> h_e_thr;
+    std::vector<double> h_e_thr, h_Ek;   // host copies (thresholds, sorted poles)
+    std::vector<int> h_l;
     void release()
     {
         for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
@@ -106,6 +107,8 @@ struct rm_ctx {
     DevBuf omega;
     // workspace
     DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep;
+    // coarse-mesh interpolation: node energies, statuses + orders, K_u, S_u, fine plan
+    DevBuf wsQn, wsQst, wsQk, wsQs, wsQf;
     // side stream for the deep channel pairs, with fork / join events
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -293,7 +296,8 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
     for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
-                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep})
+                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsQn,
+                      &ctx->wsQst, &ctx->wsQk, &ctx->wsQs, &ctx->wsQf})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
         for (auto &pr : ctx->ev[p]) {
@@ -344,6 +348,7 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
     P.Wl.release();
     P.w_kind = -1;
     CK(upload(P.Ek, Es.data(), Es.size(), ctx->stream));
+    P.h_Ek = Es;
     CK(upload(P.W, Ws.data(), Ws.size(), ctx->stream));
     P.n = n_ch;
     P.N = n_poles;
@@ -388,6 +393,7 @@ extern "C" int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const i
     CK(upload(P.lev_chan, chan.data(), chan.size(), ctx->stream));
     CK(upload(P.lev_thr, lev_thr.data(), lev_thr.size(), ctx->stream));
     P.h_e_thr.assign(e_thr, e_thr + n);
+    P.h_l.assign(l, l + n);
     P.z = z;
     P.g = g_weight;
     P.n_levels = n_levels;
@@ -565,23 +571,12 @@ int check_device_flag(rm_ctx *ctx)
 
 }  // namespace
 
-extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
-                                 double *K_out, int *n_open_out, int *status_out)
+namespace {
+
+// Registers the energy grid of the Omega accumulator (first call) or checks
+// that this call uses the registered one.
+int register_grid(rm_ctx *ctx, const PwHost &P, int n_E, const double *E, bool dev_in)
 {
-    int rc = check_pw(ctx, pw, true);
-    if (rc) return rc;
-    if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
-    if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
-    PwHost &P = ctx->pw[pw];
-    const bool large = use_large(ctx, P);
-    if (!large && P.n > solve_small_max_n())
-        return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the shared-memory solver limit %d", P.n,
-                    solve_small_max_n());
-    rc = check_precision(ctx, P);
-    if (rc) return rc;
-    CK(cudaSetDevice(ctx->opts.device));
-    const bool dev_in = is_device_ptr(E);
-    // grid registration / check
     const int ntri = P.n_levels * (P.n_levels + 1) / 2;
     if (ctx->grid_nE == 0) {
         CK(ctx->omega.reserve((size_t)n_E * ntri * sizeof(double)));
@@ -599,19 +594,21 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
             memcmp(E, ctx->grid_host.data(), (size_t)n_E * sizeof(double)) != 0)
             return fail(ctx, RM_EGRID, "energies differ from the registered grid");
     }
-    const double *dE;
-    rc = device_energies(ctx, n_E, E, &dE);
-    if (rc) return rc;
+    return RM_SUCCESS;
+}
+
+// Steps (b)-(d) for n_E device energies dE, block by block; dstatus must be
+// zeroed. omega: Omega rows of these energies (nullptr: no accumulation).
+// ku_out / ku_np (shared-memory solver, MQDT mode): K_u instead of K, T, Omega.
+int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, double *K_out, int *n_open_out,
+                 int *dstatus, double *omega, double *ku_out = nullptr, int *ku_np = nullptr)
+{
+    const bool large = use_large(ctx, P);
+    const int ntri = P.n_levels * (P.n_levels + 1) / 2;
     const int B = std::min(n_E, block_energies(ctx, P));
     CK(ctx->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
     CK(ctx->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
     if (large) CK(ctx->wsL.reserve(solve_large_bytes_per_energy(P.n) * (size_t)B + 256));
-    int *dstatus = status_out;
-    if (!dstatus) {
-        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
-        dstatus = ctx->wsStatus.as<int>();
-    }
-    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ctx->stream));
     const PwDev d = P.dev();
     const Opts o = make_opts(ctx->opts);
     for (int e0 = 0; e0 < n_E; e0 += B) {
@@ -640,28 +637,149 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
         CK(launch_chanfn(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, deep, ctx->stream));
         CK(prof_end(ctx, RM_PH_CHANFN));
         ctx->launches += 2;
-        rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
+        int rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
         if (rc) return rc;
         CK(prof_begin(ctx, RM_PH_SOLVE));
         double *Kb = K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr;
         int *nob = n_open_out ? n_open_out + e0 : nullptr;
-        double *omb = ctx->omega.as<double>() + (size_t)e0 * ntri;
+        double *omb = omega ? omega + (size_t)e0 * ntri : nullptr;
         if (large) {
             int L = 0;
             CK(launch_solve_large(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
                                   omb, ntri, ctx->wsL.p, &L, ctx->stream));
             ctx->launches += L;
         } else {
-            const int f32 = mode == RM_DIRECT && ctx->opts.solve_precision == RM_FP32;
+            const int f32 = mode == RM_DIRECT && ctx->opts.solve_precision == RM_FP32 && !ku_out;
+            double *kub = ku_out ? ku_out + (size_t)e0 * P.n * P.n : nullptr;
+            int *kunb = ku_np ? ku_np + e0 : nullptr;
             CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, mode == RM_MQDT, f32, deep, 0, ctx->stream));
+                                  omb, ntri, mode == RM_MQDT, f32, deep, 0, ctx->stream, kub, kunb));
             CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
             CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, mode == RM_MQDT, f32, deep, 1, ctx->stream));
+                                  omb, ntri, mode == RM_MQDT, f32, deep, 1, ctx->stream, kub, kunb));
             ctx->launches += 2;
         }
         CK(prof_end(ctx, RM_PH_SOLVE));
     }
+    return RM_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
+                                 double *K_out, int *n_open_out, int *status_out)
+{
+    int rc = check_pw(ctx, pw, true);
+    if (rc) return rc;
+    if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
+    if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
+    PwHost &P = ctx->pw[pw];
+    const bool large = use_large(ctx, P);
+    if (!large && P.n > solve_small_max_n())
+        return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the shared-memory solver limit %d", P.n,
+                    solve_small_max_n());
+    rc = check_precision(ctx, P);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->opts.device));
+    const bool dev_in = is_device_ptr(E);
+    rc = register_grid(ctx, P, n_E, E, dev_in);
+    if (rc) return rc;
+    const double *dE;
+    rc = device_energies(ctx, n_E, E, &dE);
+    if (rc) return rc;
+    int *dstatus = status_out;
+    if (!dstatus) {
+        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        dstatus = ctx->wsStatus.as<int>();
+    }
+    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ctx->stream));
+    return solve_blocks(ctx, P, dE, n_E, mode, K_out, n_open_out, dstatus, ctx->omega.as<double>());
+}
+
+extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double *E, int ieq, double qetest,
+                                     int iqdt, int *n_open_out, int *status_out)
+{
+    int rc = check_pw(ctx, pw, true);
+    if (rc) return rc;
+    if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
+    if (is_device_ptr(E)) return fail(ctx, RM_EINVAL, "E must be a host array (the mesh is planned on the host)");
+    if (iqdt != 1 && iqdt != 2) return fail(ctx, RM_EINVAL, "iqdt %d (1: S matrices, 2: K matrices)", iqdt);
+    if (ieq == 0) return fail(ctx, RM_EINVAL, "ieq = 0");
+    if (!std::isfinite(qetest)) return fail(ctx, RM_EINVAL, "qetest not finite");
+    PwHost &P = ctx->pw[pw];
+    if (P.n > solve_small_max_n() || use_large(ctx, P))
+        return fail(ctx, RM_EUNSUPPORTED, "coarse-mesh interpolation takes at most %d channels (n_ch=%d)",
+                    solve_small_max_n(), P.n);
+    rc = check_precision(ctx, P);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->opts.device));
+    QdtChannels ch;
+    ch.n = P.n;
+    ch.N = P.N;
+    ch.e_thr = P.h_e_thr.data();
+    ch.l = P.h_l.data();
+    ch.E_k = P.h_Ek.data();
+    ch.z = P.z;
+    ch.a = P.a;
+    ch.eps_thr = ctx->opts.eps_thr;
+    ch.nu_margin = ctx->opts.nu_margin;
+    ch.fnumin = ctx->opts.fnumin;
+    ch.kappa_a_max = ctx->opts.mqdt_kappa_a_max;
+    QdtPlan pl;
+    if (qdt_plan(ch, E, n_E, ieq, qetest, pl) != RM_SUCCESS)
+        return fail(ctx, RM_EINVAL, "energies must be strictly ascending");
+    rc = register_grid(ctx, P, n_E, E, false);
+    if (rc) return rc;
+    // coarse nodes: K_u (and S_u) through the ordinary pipeline
+    const int nn = (int)pl.node_x.size();
+    const size_t n2 = (size_t)P.n * P.n;
+    std::vector<int> hst(nn), hnp(nn);
+    if (nn > 0) {
+        CK(ctx->wsQn.reserve((size_t)nn * sizeof(double)));
+        CK(ctx->wsQst.reserve((size_t)nn * 2 * sizeof(int)));
+        CK(ctx->wsQk.reserve((size_t)nn * n2 * sizeof(double)));
+        CK(cudaMemcpyAsync(ctx->wsQn.p, pl.node_x.data(), (size_t)nn * sizeof(double), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        int *nst = ctx->wsQst.as<int>(), *nnp = nst + nn;
+        CK(cudaMemsetAsync(nst, 0, (size_t)nn * 2 * sizeof(int), ctx->stream));
+        rc = solve_blocks(ctx, P, ctx->wsQn.as<double>(), nn, RM_MQDT, nullptr, nullptr, nst, nullptr,
+                          ctx->wsQk.as<double>(), nnp);
+        if (rc) return rc;
+        if (iqdt == 1) {
+            CK(ctx->wsQs.reserve((size_t)nn * n2 * sizeof(double2)));
+            CK(launch_qdt_s_from_k(P.n, nn, ctx->wsQk.as<double>(), nnp, nst, ctx->wsQs.as<double2>(),
+                                   ctx->stream));
+            ctx->launches++;
+        }
+        CK(cudaMemcpyAsync(hst.data(), nst, (size_t)nn * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(hnp.data(), nnp, (size_t)nn * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    std::vector<int> ok(nn);
+    for (int k = 0; k < nn; ++k) {
+        int np = 0;
+        for (signed char c : pl.cls[pl.node_seg[k]]) np += (c != QDT_DECAY);
+        ok[k] = hst[k] == RM_OK && hnp[k] == np;
+    }
+    std::vector<QdtFine> fine;
+    qdt_weights(pl, ok, n_E, fine);
+    CK(ctx->wsQf.reserve((size_t)n_E * sizeof(QdtFine)));
+    CK(cudaMemcpyAsync(ctx->wsQf.p, fine.data(), (size_t)n_E * sizeof(QdtFine), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    const double *dE;
+    rc = device_energies(ctx, n_E, E, &dE);
+    if (rc) return rc;
+    int *dstatus = status_out;
+    if (!dstatus) {
+        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        dstatus = ctx->wsStatus.as<int>();
+    }
+    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ctx->stream));
+    const int ntri = P.n_levels * (P.n_levels + 1) / 2;
+    CK(launch_qdt_fine(iqdt, P.dev(), dE, n_E, make_opts(ctx->opts), ctx->wsQf.as<QdtFine>(),
+                       ctx->wsQk.as<double>(), ctx->wsQs.as<double2>(), ctx->wsQst.as<int>(), dstatus,
+                       n_open_out, ctx->omega.as<double>(), ntri, ctx->stream));
+    ctx->launches++;
     return RM_SUCCESS;
 }
 

@@ -28,155 +28,11 @@
 
 #include <type_traits>
 
+#include "dense_smem.cuh"
 #include "rm_internal.cuh"
 
 namespace rmgb {
 namespace {
-
-constexpr int SOLVE_SMALL_MAXN = 96;
-constexpr int NT = 256;
-
-struct ElimShared {
-    int piv;
-    int bad;
-    double pivinv;
-};
-
-// In-place Gaussian elimination with partial pivoting of the first `rows`
-// columns of the rows x w matrix M (row stride ld), whole block, in the
-// element type T (double, or float for the FP32 matching). Sets sh->bad on a
-// zero or non-finite pivot.
-template <typename T>
-__device__ void block_eliminate(T *M, int ld, int rows, int w, ElimShared *sh)
-{
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int c = 0; c < rows; ++c) {
-        if (warp == 0) {
-            T best = -1;
-            int bi = c;
-            for (int r = c + lane; r < rows; r += 32) {
-                const T v = fabs(M[r * ld + c]);
-                if (v > best) { best = v; bi = r; }
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-                const T ob = __shfl_down_sync(0xffffffffu, best, off);
-                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-            }
-            if (lane == 0) {
-                sh->piv = bi;
-                const double pv = (double)M[bi * ld + c];
-                if (!(best > 0) || !isfinite(pv)) sh->bad = 1;
-                sh->pivinv = 1.0 / pv;
-            }
-        }
-        __syncthreads();
-        const int p = sh->piv;
-        if (p != c) {
-            for (int q = c + tid; q < w; q += NT) {
-                const T t = M[c * ld + q];
-                M[c * ld + q] = M[p * ld + q];
-                M[p * ld + q] = t;
-            }
-            __syncthreads();
-        }
-        // trailing update; G threads share a row and form its multiplier once
-        // (the multipliers are not stored: every right-hand side is in the
-        // augmented matrix), so there is no separate scaling pass or barrier
-        constexpr int G = 4;
-        const T pinv = (T)sh->pivinv;
-        const int nr = rows - c - 1;
-        const T *prow = M + c * ld;
-        for (int q = tid; q < nr * G; q += NT) {
-            const int r = c + 1 + q / G, j = q - (q / G) * G;
-            T *row = M + r * ld;
-            const T f = row[c] * pinv;
-            for (int cc = c + 1 + j; cc < w; cc += G) row[cc] = fma(-f, prow[cc], row[cc]);
-        }
-        __syncthreads();
-    }
-}
-
-// Back-substitution of the upper-triangular rows x rows system in M for the
-// n_rhs right-hand sides in columns rhs0.., over rows t = rows-1 .. row_lo,
-// in place; one thread per right-hand side.
-template <typename T>
-__device__ void block_backsub(T *M, int ld, int rows, int rhs0, int n_rhs, int row_lo)
-{
-    for (int qq = threadIdx.x; qq < n_rhs; qq += NT) {
-        const int cq = rhs0 + qq;
-        for (int t = rows - 1; t >= row_lo; --t) {
-            T s = M[t * ld + cq];
-            for (int u = t + 1; u < rows; ++u) s = fma(-M[t * ld + u], M[u * ld + cq], s);
-            M[t * ld + cq] = s / M[t * ld + t];
-        }
-    }
-    __syncthreads();
-}
-
-// In-place inverse of the symmetric positive definite m x m matrix A (row
-// stride ld) by the sweep operator: Gauss-Jordan elimination without
-// pivoting (which SPD matrices do not need), keeping the symmetry, so only
-// the upper triangle is read and updated (m^3 flops instead of 2 m^3). Step
-// k, with d = a_kk and v_i = a_ik / d: a_ij -= v_i v_j d (i, j != k),
-// a_ik = v_i, a_kk = -1/d; after all m steps the upper triangle holds
-// -A^{-1}, which is then negated and mirrored into the full matrix.
-// v is shared scratch of m doubles. Sets sh->bad if a pivot is not positive.
-__device__ void spd_sweep_inverse(double *A, int ld, int m, double *v, ElimShared *sh)
-{
-    const int tid = threadIdx.x;
-    constexpr int G = 8;                        // threads per pair of rows
-    const int ngroups = (m + 1) / 2;            // rows g and m-1-g share a group
-    for (int k = 0; k < m; ++k) {
-        const double d = A[k * ld + k];
-        if (!(d > 0.0) || !isfinite(d)) {       // the same value in every thread
-            if (tid == 0) sh->bad = 1;
-            return;
-        }
-        const double dinv = 1.0 / d;
-        for (int i = tid; i < m; i += NT)
-            v[i] = (i == k) ? 0.0 : ((i < k) ? A[i * ld + k] : A[k * ld + i]) * dinv;
-        __syncthreads();
-        for (int q = tid; q < ngroups * G; q += NT) {
-            const int g = q / G, t = q - (q / G) * G;
-            for (int h = 0; h < 2; ++h) {
-                const int i = h ? m - 1 - g : g;
-                if (h && i == g) break;
-                double *row = A + i * ld;
-                const double vi = v[i];
-                for (int j = i + t; j < m; j += G) {
-                    if (i == k) row[j] = (j == k) ? -dinv : v[j];
-                    else if (j == k) row[j] = vi;
-                    else row[j] = fma(-vi * d, v[j], row[j]);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    // A^{-1} = -(upper triangle), mirrored
-    for (int q = tid; q < m * m; q += NT) {
-        const int i = q / m, j = q - (q / m) * m;
-        if (i > j) A[i * ld + j] = -A[j * ld + i];
-    }
-    __syncthreads();
-    for (int q = tid; q < m * m; q += NT) {
-        const int i = q / m, j = q - (q / m) * m;
-        if (i <= j) A[i * ld + j] = -A[i * ld + j];
-    }
-    __syncthreads();
-}
-
-// Row-wise upper-triangle index q -> (p, r), p <= r < m.
-__device__ __forceinline__ void tri_pair(int q, int m, int &p, int &r)
-{
-    const float t = (float)(2 * m + 1);
-    int pp = (int)((t - sqrtf(fmaxf(t * t - 8.0f * (float)q, 0.0f))) * 0.5f);
-    if (pp < 0) pp = 0;
-    while (pp > 0 && pp * m - (pp * (pp - 1)) / 2 > q) --pp;
-    while ((pp + 1) * m - ((pp + 1) * pp) / 2 <= q) ++pp;
-    p = pp;
-    r = pp + (q - (pp * m - (pp * (pp - 1)) / 2));
-}
 
 // Shared-memory bytes of region A in the FP32-matching layout: the float
 // augmented matrix n x (2n + 1), later M^{-1} (at most n x (n + 1) doubles).
@@ -194,7 +50,8 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
     const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
     int *__restrict__ n_open_out, double *__restrict__ omega, int n_tri, int mqdt_layout,
-    const int *__restrict__ deep_ws, int deep_cap, int pass)
+    const int *__restrict__ deep_ws, int deep_cap, int pass, double *__restrict__ ku_out,
+    int *__restrict__ ku_np)
 {
     // Energies holding a deep (near-threshold) channel pair are solved in
     // pass 1, after their channel data is complete; the others in pass 0.
@@ -288,6 +145,15 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
         return;
     }
     block_backsub<Real>(M, ld, n, n, np, ncl);   // K_u = rows ncl.. of the RHS columns
+    if (ku_out) {
+        // K_u itself (P channels in channel order), for interpolation between energies
+        for (int q = tid; q < np * np; q += NT) {
+            const int p = q / np, r = q - (q / np) * np;
+            ku_out[(size_t)e * n * n + (size_t)p * n + r] = (double)M[(ncl + p) * ld + n + r];
+        }
+        if (tid == 0) ku_np[e] = np;
+        return;
+    }
 
     const int lk = no + 1;
     double *Kp;   // K (no x no, symmetrised), row stride kld
@@ -358,44 +224,13 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
             const int p = q / np, r = q - (q / np) * np;
             Ku[p * lu + r] = (double)Mq[(ncl + p) * ld + n + r];
         }
+        for (int i = tid; i < nq; i += NT) vcol[i] = cf[col_chan[ncl + qpos[i]]].tanb;
         __syncthreads();
-        // [K_cc + diag(tan pi nu) | K_co] in region A
-        const int w2 = nq + no, ld2 = w2 + 1;
-        double *C = sm;
-        for (int q = tid; q < nq * w2; q += NT) {
-            const int i = q / w2, j = q - (q / w2) * w2;
-            double v;
-            if (j < nq) {
-                v = Ku[qpos[i] * lu + qpos[j]];
-                if (i == j) v += cf[col_chan[ncl + qpos[i]]].tanb;
-            } else {
-                v = Ku[qpos[i] * lu + opos[j - nq]];
-            }
-            C[i * ld2 + j] = v;
-        }
-        __syncthreads();
-        block_eliminate<double>(C, ld2, nq, w2, &esh);
-        if (esh.bad) {
+        if (!mqdt_eliminate(Ku, lu, no, nq, qpos, opos, vcol, sm, Ks,
+                            K_out ? K_out + (size_t)e * n * n : nullptr, n, &esh)) {
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        block_backsub<double>(C, ld2, nq, nq, no, 0);   // Y = (K_cc + tan)^{-1} K_co
-        // K = K_oo - K_oc Y, after [C | Y] in region A
-        double *Kd = sm + (size_t)nq * ld2;
-        for (int q = tid; q < no * no; q += NT) {
-            const int s2 = q / no, t = q - (q / no) * no;
-            double v = Ku[opos[s2] * lu + opos[t]];
-            for (int i = 0; i < nq; ++i) v = fma(-Ku[opos[s2] * lu + qpos[i]], C[i * ld2 + nq + t], v);
-            Kd[s2 * lk + t] = v;
-        }
-        __syncthreads();
-        for (int q = tid; q < no * no; q += NT) {
-            const int p = q / no, r = q - (q / no) * no;
-            const double kpr = Kd[p * lk + r];
-            Ks[p * lk + r] = 0.5 * (kpr + Kd[r * lk + p]);   // overwrites K_u, no longer read
-            if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
-        }
-        __syncthreads();
         Kp = Ks;
         kld = lk;
         Mi = sm;
@@ -403,48 +238,9 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     }
     if (!omega) return;
 
-    // ---- M = 1 + K^2 (upper triangle, mirrored), inverted in place ----------
-    const int nsym = no * (no + 1) / 2;
-    for (int q = tid; q < nsym; q += NT) {
-        int p, r;
-        tri_pair(q, no, p, r);
-        double s = (p == r) ? 1.0 : 0.0;
-        for (int u = 0; u < no; ++u) s = fma(Kp[p * kld + u], Kp[u * kld + r], s);
-        Mi[p * mld + r] = s;
-        Mi[r * mld + p] = s;
-    }
-    __syncthreads();
-    spd_sweep_inverse(Mi, mld, no, vcol, &esh);
-    if (esh.bad) {
+    if (!t_omega(pw, x, Kp, kld, Mi, mld, no, open_pos, vcol, omega + (size_t)e * n_tri, &esh)) {
         if (tid == 0) status[e] = RM_ESINGULAR;
         return;
-    }
-
-    // ---- Omega_IJ += g sum_{a in I, b in J} |T_ab|^2 -------------------------
-    // |T_ab|^2 = 4 (X_ab^2 + Y_ab^2), X = K M^{-1}, Y = 1 - M^{-1}, each pair
-    // formed where it is summed (taken with a <= b: both are symmetric).
-    const int nl = pw.n_levels;
-    const int npair = nl * (nl + 1) / 2;
-    double *om = omega + (size_t)e * n_tri;
-    const double g = pw.g;
-    for (int q = tid; q < npair; q += NT) {
-        int I, J;
-        tri_pair(q, nl, I, J);
-        if (!(x - pw.lev_thr[I] > 0.0) || !(x - pw.lev_thr[J] > 0.0)) continue;
-        double s = 0.0;
-        for (int ia = pw.lev_start[I]; ia < pw.lev_start[I + 1]; ++ia) {
-            const int pa0 = open_pos[pw.lev_chan[ia]];
-            for (int ib = pw.lev_start[J]; ib < pw.lev_start[J + 1]; ++ib) {
-                const int pb0 = open_pos[pw.lev_chan[ib]];
-                const int pa = min(pa0, pb0), pb = max(pa0, pb0);
-                double xv = 0.0;
-                for (int u = 0; u < no; ++u) xv = fma(Kp[pa * kld + u], Mi[u * mld + pb], xv);
-                const double yv =
-                    ((pa == pb) ? 1.0 : 0.0) - 0.5 * (Mi[pa * mld + pb] + Mi[pb * mld + pa]);
-                s += 4.0 * (xv * xv + yv * yv);
-            }
-        }
-        om[q] += g * s;
     }
 }
 
@@ -467,9 +263,9 @@ size_t solve_small_smem(int n, int mqdt, int f32)
 cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
                                double *omega, int n_tri, int mqdt, int f32, const int *deep_ws, int pass,
-                               cudaStream_t s)
+                               cudaStream_t s, double *ku_out, int *ku_np)
 {
-    if (pw.n > SOLVE_SMALL_MAXN || (f32 && mqdt)) return cudaErrorInvalidValue;
+    if (pw.n > SOLVE_SMALL_MAXN || (f32 && mqdt) || (f32 && ku_out)) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
     const size_t smem = solve_small_smem(pw.n, mqdt, f32);
     const int cap = chanfn_deep_cap();
@@ -479,13 +275,13 @@ cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const C
                                    (int)smem);
         if (err != cudaSuccess) return err;
         solve_small_kernel<true><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
-                                                      n_tri, 0, deep_ws, cap, pass);
+                                                      n_tri, 0, deep_ws, cap, pass, nullptr, nullptr);
     } else {
         err = cudaFuncSetAttribute(solve_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)smem);
         if (err != cudaSuccess) return err;
         solve_small_kernel<false><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
-                                                       n_tri, mqdt ? 1 : 0, deep_ws, cap, pass);
+                                                       n_tri, mqdt ? 1 : 0, deep_ws, cap, pass, ku_out, ku_np);
     }
     return cudaGetLastError();
 }

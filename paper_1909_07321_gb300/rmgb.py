@@ -58,6 +58,7 @@ _SIGS = {
     "rm_set_channels": (_I, [_VP, _I, _VP, _VP, _D, _VP, _I, _D]),
     "rm_solve_energies": (_I, [_VP, _I, _I, _VP, _I, _VP, _VP, _VP]),
     "rm_collision_strengths": (_I, [_VP, _VP, _I]),
+    "rm_solve_energies_qdt": (_I, [_VP, _I, _I, _VP, _I, _D, _I, _VP, _VP]),
     "rm_grid_shape": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rm_channel_functions": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "rm_form_r": (_I, [_VP, _I, _I, _VP, _VP]),
@@ -163,6 +164,14 @@ def rm_solve_energies(ctx, pw, E, mode=0, K_out=None, n_open_out=None, status_ou
     return _check(ctx, lib().rm_solve_energies(ctx, pw, int(E.shape[0]), _ptr(E, np.float64), mode,
                                                _ptr(K_out, np.float64), _ptr(n_open_out, np.int32),
                                                _ptr(status_out, np.int32)))
+
+
+def rm_solve_energies_qdt(ctx, pw, E, ieq, qetest=0.0, iqdt=1, n_open_out=None, status_out=None):
+    """MQDT coarse-mesh interpolation; E must be a host array (ascending)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    return _check(ctx, lib().rm_solve_energies_qdt(ctx, pw, int(E.shape[0]), _ptr(E, np.float64), int(ieq),
+                                                   float(qetest), int(iqdt), _ptr(n_open_out, np.int32),
+                                                   _ptr(status_out, np.int32)))
 
 
 def rm_grid_shape(ctx):
@@ -286,6 +295,9 @@ class Context:
 
     def channel_functions(self, pw, E, out, status=None):
         return rm_channel_functions(self.h, pw, E, out, status)
+
+    def solve_energies_qdt(self, pw, E, ieq, qetest=0.0, iqdt=1, n_open_out=None, status_out=None):
+        return rm_solve_energies_qdt(self.h, pw, E, ieq, qetest, iqdt, n_open_out, status_out)
 
     def form_r(self, pw, E, R_out):
         return rm_form_r(self.h, pw, E, R_out)
