@@ -318,6 +318,52 @@ def run_wide(args, prec, stream, flush, peaks, peak_src):
     return out
 
 
+def run_qdt(args, prec, sp):
+    """MQDT coarse-mesh interpolation on the 64-channel workload: the full
+    per-energy MQDT solve of every energy against K_u solved at the nodes and
+    S_u interpolated to the fine energies (ieq = args.qdt_ieq), with the Omega
+    difference between the two."""
+    import torch
+
+    from paper_1909_07321_gb300 import rmgb, synth
+    pws, E = synth.workload_64ch(args.energies)
+    pw = pws[0]
+    out = {"workload": "64-channel workload in MQDT mode, %d energies; interpolation ieq = %d, iqdt = 1"
+           % (E.size, args.qdt_ieq)}
+    res = {}
+    for name in ("full", "interp"):
+        ctx = rmgb.Context(precision=prec)
+        ctx.load_pw(0, pw)
+        st = torch.zeros(E.size, dtype=torch.int32, device="cuda")
+        best = None
+        for rep in range(3):
+            if rep:
+                ctx.reset_omega()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if name == "full":
+                ctx.solve_energies(0, E, 1, None, None, st)
+            else:
+                ctx.solve_energies_qdt(0, E, args.qdt_ieq, 0.0, 1, None, st)
+            ctx.sync()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+        res[name] = (best, ctx.collision_strengths(), st.cpu().numpy())
+        ctx.close()
+    (tf, omf, stf), (ti, omi, sti) = res["full"], res["interp"]
+    ok = (stf == 0) & (sti == 0)
+    rel = np.linalg.norm(omi[ok] - omf[ok], axis=1) / np.maximum(np.linalg.norm(omf[ok], axis=1), 1e-300)
+    out.update({"full_mqdt": {"energy_solves_per_s": E.size / tf, "s": tf},
+                "interpolated": {"energy_solves_per_s": E.size / ti, "s": ti},
+                "speedup": tf / ti,
+                "omega_rel_diff_interp_vs_full": {"median": float(np.median(rel)),
+                                                  "p99": float(np.quantile(rel, 0.99)),
+                                                  "max": float(rel.max())},
+                "timing": "host wall clock around each call, best of 3 (the interpolated call "
+                          "synchronises once after its node solves)"})
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -420,6 +466,9 @@ def run_ours(args, rank, world, local_rank):
     wide = None
     if world == 1 and args.wide_energies > 0:
         wide = run_wide(args, prec if prec != 0 else 2, stream, flush, peaks, peak_src)
+    qdt_line = None
+    if world == 1 and args.qdt_ieq != 0:
+        qdt_line = run_qdt(args, prec, sp)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = N_SM * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     names = {rmgb.RM_PH_NEARPOLE: "nearpole", rmgb.RM_PH_CHANFN: "chanfn", rmgb.RM_PH_FORM: "form",
@@ -492,6 +541,7 @@ def run_ours(args, rank, world, local_rank):
             "fp64_path": fp64,
             "serving": serving_line,
             "wide_1000ch": wide,
+            "mqdt_interpolation": qdt_line,
             "cpu_baseline": cpu,
             "e2e": {"value": world * E.size / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(E.size * 8),
@@ -515,6 +565,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrival rate (1/s)")
     ap.add_argument("--matching", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the matching elimination on the mixed path")
+    ap.add_argument("--qdt-ieq", type=int, default=-25,
+                    help="node spacing of the MQDT interpolation leg (0 to skip)")
     ap.add_argument("--wide-energies", type=int, default=256,
                     help="energies of the 1000-channel leg (0 to skip)")
     ap.add_argument("--energies", type=int, default=N_E,

@@ -29,8 +29,11 @@ Readings (the paper names the controls only):
     energies and the points of the ieq-point grid spanning the whole fine
     range that fall inside it (ieq = 0 is not a valid choice).
   * A node is dropped when a channel of the eliminated set has
-    |sin pi nu| < 1e-3 there (g is not formed), or when it lies on a pole
-    (|E - E_k| < 1e-12 max(1, |E|)), or when its K_u cannot be computed; fine
+    |sin pi nu| < 1e-3 there (g is not formed), when it lies within
+    2.5e-5 max(z^2, 1) Ry of a threshold (where the Coulomb continued
+    fractions are deepest: such a node alone would cost more than the rest
+    of the mesh), on a pole (|E - E_k| < 1e-12 max(1, |E|)), or when its K_u
+    cannot be computed; fine
     energies beyond the outermost remaining node are extrapolated linearly
     from the two nearest (held constant when one remains), and a segment
     without nodes fails (RM_ESINGULAR).
@@ -45,6 +48,7 @@ from . import rmatrix as rm
 
 CL_OPEN, CL_ELIM, CL_DECAY = 0, 1, 2
 SIN_MIN = 1e-3
+NODE_MIN_EPS = 2.5e-5      # x max(z^2, 1) Ry: closest a node may lie to a threshold
 
 
 def classes(E, pw, fnumin=0.0, margin=0.1, kappa_a_max=5.0, eps_thr=1e-10):
@@ -114,12 +118,15 @@ def plan(pw, E, ieq, qetest=0.0, **kw):
 
 def node_valid(pw, x, cls_seg, **kw):
     """A node keeps the segment's classes, has |sin pi nu| >= 1e-3 for every
-    eliminated channel, and does not lie on a pole."""
+    eliminated channel, keeps 2.5e-5 max(z^2, 1) Ry from every threshold, and
+    does not lie on a pole."""
     c = classes(x, pw, **kw)
     if c is None or not np.array_equal(c, cls_seg):
         return False
     E_k = np.asarray(pw["E_k"], dtype=np.float64)
     if np.any(np.abs(x - E_k) < 1e-12 * max(1.0, abs(x))):
+        return False
+    if np.any(np.abs(x - np.asarray(pw["e_thr"])) < NODE_MIN_EPS * max(pw["z"] ** 2, 1.0)):
         return False
     el = np.nonzero(cls_seg == CL_ELIM)[0]
     if el.size:

@@ -34,27 +34,10 @@ namespace rmgb {
 namespace {
 
 constexpr double QDT_SIN_MIN = 1e-3;
-
-// Classes of the channels at energy x; false if x lies on a threshold. The
-// rules (and their floating-point evaluation) are those of the channel
-// kernel's MQDT set, without its |sin pi nu| guard.
-bool qdt_classes(const QdtChannels &c, double x, std::vector<signed char> &cls)
-{
-    cls.assign(c.n, QDT_DECAY);
-    for (int i = 0; i < c.n; ++i) {
-        const double eps = x - c.e_thr[i];
-        if (std::fabs(eps) < c.eps_thr) return false;
-        if (eps > 0.0) {
-            cls[i] = QDT_OPEN;
-        } else if (c.z > 0.0) {
-            const double kap = std::sqrt(-eps);
-            const double nu = c.z / kap;
-            if (nu >= std::fmax(c.l[i] + c.nu_margin, c.fnumin) && kap * c.a <= c.kappa_a_max)
-                cls[i] = QDT_ELIM;
-        }
-    }
-    return true;
-}
+// A node keeps this far (x max(z^2, 1) Ry) from every threshold: nearer, the
+// Coulomb continued fractions are so deep that one node would cost more than
+// the rest of the mesh (its segment end is extrapolated instead).
+constexpr double QDT_NODE_MIN_EPS = 2.5e-5;
 
 double sin_pi(double nu)
 {
@@ -66,7 +49,8 @@ double sin_pi(double nu)
 
 }  // namespace
 
-int qdt_plan(const QdtChannels &c, const double *E, int n_E, int ieq, double qetest, QdtPlan &pl)
+int qdt_plan(const QdtChannels &c, const double *E, int n_E, const signed char *cls_all, int ieq,
+             double qetest, QdtPlan &pl)
 {
     if (ieq == 0 || n_E <= 0) return RM_EINVAL;
     for (int m = 1; m < n_E; ++m)
@@ -74,28 +58,26 @@ int qdt_plan(const QdtChannels &c, const double *E, int n_E, int ieq, double qet
     pl = QdtPlan();
     pl.seg.assign(n_E, -1);
     pl.e_int.assign(E, E + n_E);
-    std::vector<signed char> prev, cur;
-    bool prev_ok = false;
+    const size_t n = (size_t)c.n;
+    int prev = -1;   // previous fine energy off a threshold, if adjacent
     for (int m = 0; m < n_E; ++m) {
-        const bool ok = qdt_classes(c, E[m], cur);
-        if (!ok) {
-            prev_ok = false;
+        const signed char *cur = cls_all + (size_t)m * n;
+        if (cur[0] == QDT_THRESHOLD) {
+            prev = -1;
             continue;
         }
-        if (prev_ok && cur == prev) {
+        if (prev >= 0 && std::equal(cur, cur + n, cls_all + (size_t)prev * n)) {
             pl.i1.back() = m;
         } else {
             pl.i0.push_back(m);
             pl.i1.push_back(m);
-            pl.cls.push_back(cur);
+            pl.cls.emplace_back(cur, cur + n);
         }
         pl.seg[m] = (int)pl.i0.size() - 1;
-        prev = cur;
-        prev_ok = true;
+        prev = m;
     }
     // nodes (candidates) and validity
     const double step = (ieq >= 2) ? (E[n_E - 1] - E[0]) / (ieq - 1) : 0.0;
-    std::vector<signed char> cx;
     for (size_t s = 0; s < pl.i0.size(); ++s) {
         const int i0 = pl.i0[s], i1 = pl.i1[s];
         std::set<double> pts = {E[i0], E[i1]};
@@ -108,14 +90,19 @@ int qdt_plan(const QdtChannels &c, const double *E, int n_E, int ieq, double qet
             }
         }
         pl.seg_node0.push_back((int)pl.node_x.size());
+        const std::vector<signed char> &cx = pl.cls[s];
         for (double x : pts) {
-            if (!qdt_classes(c, x, cx) || cx != pl.cls[s]) continue;
+            // between two fine energies of equal classes every energy has those
+            // classes (each channel goes decaying -> eliminated -> open as E rises)
             bool bad = false;
             // pole (sorted E_k): the nearest two
             const double *it = std::lower_bound(c.E_k, c.E_k + c.N, x);
             const double tol = 1e-12 * std::fmax(1.0, std::fabs(x));
             if (it != c.E_k + c.N && std::fabs(*it - x) < tol) bad = true;
             if (it != c.E_k && std::fabs(*(it - 1) - x) < tol) bad = true;
+            const double near = QDT_NODE_MIN_EPS * std::fmax(c.z * c.z, 1.0);
+            for (int i = 0; i < c.n && !bad; ++i)
+                if (std::fabs(x - c.e_thr[i]) < near) bad = true;
             // |sin pi nu| of every eliminated channel (with a relative margin, so
             // that the device's own test cannot disagree)
             for (int i = 0; i < c.n && !bad; ++i)
@@ -435,7 +422,42 @@ __global__ void __launch_bounds__(NT) qdt_fine_kernel(PwDev pw, const double *__
     }
 }
 
+// Channel classes of every (energy, channel): QDT_OPEN, QDT_ELIM (the
+// channel kernel's MQDT rules without its |sin pi nu| guard), QDT_DECAY; an
+// energy on a threshold gets QDT_THRESHOLD in its first entry.
+__global__ void qdt_class_kernel(PwDev pw, const double *__restrict__ E, int nE, Opts o,
+                                 signed char *__restrict__ cls)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nE) return;
+    const double x = E[e];
+    signed char *row = cls + (size_t)e * pw.n;
+    bool thr = false;
+    for (int i = 0; i < pw.n; ++i) {
+        const double eps = x - pw.e_thr[i];
+        signed char c = QDT_DECAY;
+        if (fabs(eps) < o.eps_thr) thr = true;
+        if (eps > 0.0) {
+            c = QDT_OPEN;
+        } else if (pw.z > 0.0) {
+            const double kap = sqrt(-eps);
+            const double nu = pw.z / kap;
+            if (nu >= fmax(pw.l[i] + o.nu_margin, o.fnumin) && kap * pw.a <= o.kappa_a_max) c = QDT_ELIM;
+        }
+        row[i] = c;
+    }
+    if (thr) row[0] = QDT_THRESHOLD;
+}
+
 }  // namespace
+
+cudaError_t launch_qdt_classes(const PwDev &pw, const double *E, int nE, const Opts &o, signed char *cls,
+                               cudaStream_t s)
+{
+    if (nE == 0) return cudaSuccess;
+    qdt_class_kernel<<<(nE + 127) / 128, 128, 0, s>>>(pw, E, nE, o, cls);
+    return cudaGetLastError();
+}
 
 size_t qdt_s_smem(int n) { return (size_t)n * (2 * n + 1) * sizeof(double2); }
 

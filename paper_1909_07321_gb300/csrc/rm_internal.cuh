@@ -139,7 +139,7 @@ cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const C
                                double *omega, int n_tri, void *ws, int *launches, cudaStream_t s);
 
 // ---- MQDT coarse-mesh interpolation (qdt.cu) ------------------------------------
-enum QdtClass : signed char { QDT_OPEN = 0, QDT_ELIM = 1, QDT_DECAY = 2 };
+enum QdtClass : signed char { QDT_OPEN = 0, QDT_ELIM = 1, QDT_DECAY = 2, QDT_THRESHOLD = 3 };
 enum QdtFlag { QDT_FLAG_OK = 0, QDT_FLAG_THRESHOLD = 1, QDT_FLAG_NONODE = 2 };
 
 // Host view of one partial wave's channels and the MQDT options.
@@ -169,8 +169,14 @@ struct QdtFine {
     int flag;
 };
 
-// RM_EINVAL if ieq == 0 or E is not strictly ascending.
-int qdt_plan(const QdtChannels &c, const double *E, int n_E, int ieq, double qetest, QdtPlan &pl);
+// Classes of every (energy, channel) on the device, [nE][n] (QDT_THRESHOLD in
+// the first entry of an energy on a threshold).
+cudaError_t launch_qdt_classes(const PwDev &pw, const double *E, int nE, const Opts &o, signed char *cls,
+                               cudaStream_t s);
+// From those classes (host copy): RM_EINVAL if ieq == 0 or E is not strictly
+// ascending.
+int qdt_plan(const QdtChannels &c, const double *E, int n_E, const signed char *cls_all, int ieq,
+             double qetest, QdtPlan &pl);
 // Weights over the nodes with node_ok != 0 (failed nodes left out).
 void qdt_weights(const QdtPlan &pl, const std::vector<int> &node_ok, int n_E, std::vector<QdtFine> &fine);
 // Node K_u [nn][n][n] -> S_u = 2 (1 - i K_u)^{-1} - 1 (complex, same layout).

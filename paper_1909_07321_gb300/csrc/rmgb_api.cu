@@ -108,7 +108,7 @@ struct rm_ctx {
     // workspace
     DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep;
     // coarse-mesh interpolation: node energies, statuses + orders, K_u, S_u, fine plan
-    DevBuf wsQn, wsQst, wsQk, wsQs, wsQf;
+    DevBuf wsQn, wsQst, wsQk, wsQs, wsQf, wsQc;
     // side stream for the deep channel pairs, with fork / join events
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -297,7 +297,7 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     for (auto &p : ctx->pw) p.release();
     for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
                       &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsQn,
-                      &ctx->wsQst, &ctx->wsQk, &ctx->wsQs, &ctx->wsQf})
+                      &ctx->wsQst, &ctx->wsQk, &ctx->wsQs, &ctx->wsQf, &ctx->wsQc})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
         for (auto &pr : ctx->ev[p]) {
@@ -725,11 +725,23 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     ch.nu_margin = ctx->opts.nu_margin;
     ch.fnumin = ctx->opts.fnumin;
     ch.kappa_a_max = ctx->opts.mqdt_kappa_a_max;
-    QdtPlan pl;
-    if (qdt_plan(ch, E, n_E, ieq, qetest, pl) != RM_SUCCESS)
-        return fail(ctx, RM_EINVAL, "energies must be strictly ascending");
+    for (int m = 1; m < n_E; ++m)
+        if (!(E[m] > E[m - 1])) return fail(ctx, RM_EINVAL, "energies must be strictly ascending");
     rc = register_grid(ctx, P, n_E, E, false);
     if (rc) return rc;
+    const double *dE;
+    rc = device_energies(ctx, n_E, E, &dE);
+    if (rc) return rc;
+    // channel classes of every fine energy on the device, then the plan
+    std::vector<signed char> hcls((size_t)n_E * P.n);
+    CK(ctx->wsQc.reserve(hcls.size()));
+    CK(launch_qdt_classes(P.dev(), dE, n_E, make_opts(ctx->opts), ctx->wsQc.as<signed char>(), ctx->stream));
+    ctx->launches++;
+    CK(cudaMemcpyAsync(hcls.data(), ctx->wsQc.p, hcls.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    QdtPlan pl;
+    if (qdt_plan(ch, E, n_E, hcls.data(), ieq, qetest, pl) != RM_SUCCESS)
+        return fail(ctx, RM_EINVAL, "energies must be strictly ascending");
     // coarse nodes: K_u (and S_u) through the ordinary pipeline
     const int nn = (int)pl.node_x.size();
     const size_t n2 = (size_t)P.n * P.n;
@@ -766,9 +778,6 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     CK(ctx->wsQf.reserve((size_t)n_E * sizeof(QdtFine)));
     CK(cudaMemcpyAsync(ctx->wsQf.p, fine.data(), (size_t)n_E * sizeof(QdtFine), cudaMemcpyHostToDevice,
                        ctx->stream));
-    const double *dE;
-    rc = device_energies(ctx, n_E, E, &dE);
-    if (rc) return rc;
     int *dstatus = status_out;
     if (!dstatus) {
         CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
