@@ -139,6 +139,9 @@ int ref_coulomb_open(int l, double eta_d, double rho_d, double *out)
         q0 = q1;
     }
     Q f = f1, p = p1, q = q1;
+    /* q (F^2 + G^2) = 1 needs q > 0; deep inside a centrifugal barrier
+     * (F / G below ~1e-33) the fraction at l has no correct digit left. */
+    if (!(q > 0)) return 1;
     Q F = qsqrt(q / ((f - p) * (f - p) + q * q));
     if (s1 < 0) F = -F;
     Q Fp = f * F;
@@ -148,6 +151,8 @@ int ref_coulomb_open(int l, double eta_d, double rho_d, double *out)
     out[1] = (double)Fp;
     out[2] = (double)G;
     out[3] = (double)Gp;
+    for (int j = 0; j < 4; ++j)
+        if (!isfinite(out[j])) return 1;
     return 0;
 }
 
