@@ -16,7 +16,12 @@ primitive.
 Parity status per function (what pins it, in tests/test_oracle_pins.py):
   coulomb functions     mpmath coulombf/coulombg, Wronskian, eta = 0 closed forms
   closed log-derivative mpmath whitw, hydrogenic integer-nu closed forms
-  regular_analytic      Gamow-factor relation to F at positive energy
+  regular_analytic      Gamow-factor relation to F at positive energy, also
+                        3e-7 Ry above threshold and inside an l = 15
+                        barrier (tests/test_oracle_threshold.py)
+  near-threshold        tests/test_oracle_threshold.py: s / sqrt(A), c sqrt(A)
+  analyticity           continue into f and g at half-integer nu across the
+                        threshold; theta ~ A f cos(pi nu) - g sin(pi nu)
   r_matrix              brute-force mpmath sum, exact symmetry, single-pole limit
   k_direct              one-channel hand formula, square well vs closed-form
                         tan(delta), 1 open + 1 closed closed form, symmetry,

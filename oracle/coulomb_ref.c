@@ -29,8 +29,11 @@
  *    of the signs of the ratios F_{L+1}/F_L over the evaluated range, because
  *    F_L > 0 once rho lies deep inside the centrifugal barrier of L.
  *  - (G'+iF')/(G+iF) = p + iq from the continued fraction of the outgoing
- *    Coulomb function H+ at the channel's own l, bottom-up, doubled depth.
- *  - The Wronskian q (F^2 + G^2) = 1 then fixes |F|, and G = (F' - pF)/q.
+ *    Coulomb function H+ at l = 0 (an attractive field puts r in no barrier
+ *    there), bottom-up, doubled depth.
+ *  - The Wronskian q (F_0^2 + G_0^2) = 1 then fixes |F_0|, and
+ *    G_0 = (F_0' - pF_0)/q; G is carried up to l by its l-recurrence (it is
+ *    the dominant solution upwards), and F_l = 1/(f_l G_l - G_l').
  *  - Whittaker log-derivative from W = e^{-x/2} x^{L+1} U(L+1-nu, 2L+2, x),
  *    U'(a,b,x) = -(a/x) [U(a,b,x) + (b-a-1) U(a+1,b,x)], with the ratio
  *    U(a+1,b,x)/U(a,b,x) taken from the recurrence of U(a+n,b,x) in n
@@ -105,48 +108,75 @@ static void cf2_at_depth(int l, Q eta, Q rho, int N, Q *p, Q *q)
     *q = (1 - eta / rho) + vr / rho;
 }
 
-/* out = {F, F', G, G'} (derivatives with respect to rho). Returns 0 on
- * success, 1 if a continued fraction did not settle within MAX_DEPTH. */
-int ref_coulomb_open(int l, double eta_d, double rho_d, double *out)
+/* f_L = F_L'/F_L and sign(F_L) by CF1 at depths doubling from beyond the
+ * turning region until three successive depths agree (so that a stretch
+ * where the truncated fraction is insensitive to depth cannot pass for
+ * convergence). Returns 1 if it does not settle within MAX_DEPTH. */
+static int cf1_converged(int L, Q eta, Q rho, double rho_d, Q *f, int *sgn)
 {
-    Q eta = eta_d, rho = rho_d;
-    /* Start beyond the turning region of each recurrence (rho for CF1,
-     * |eta| + l for CF2) and accept a value only when three successive
-     * doublings of the depth agree, so that a stretch where the truncated
-     * fraction is insensitive to depth cannot pass for convergence. */
     Q f0, f1;
     int s0, s1, M = 64 + 2 * (int)rho_d, agree = 0;
-    cf1_at_depth(l, eta, rho, M, &f0, &s0);
+    cf1_at_depth(L, eta, rho, M, &f0, &s0);
     while (agree < 2) {
         M *= 2;
         if (M > MAX_DEPTH) return 1;
-        cf1_at_depth(l, eta, rho, M, &f1, &s1);
+        cf1_at_depth(L, eta, rho, M, &f1, &s1);
         agree = (qabs(f1 - f0) <= CONV * qabs(f1) && s0 == s1) ? agree + 1 : 0;
         f0 = f1;
         s0 = s1;
     }
+    *f = f1;
+    *sgn = s1;
+    return 0;
+}
+
+/* out = {F, F', G, G'} (derivatives with respect to rho). Returns 0 on
+ * success, 1 if a continued fraction did not settle within MAX_DEPTH or lost
+ * every digit.
+ *
+ * H+'/H+ = p + iq is taken at L = 0, where an attractive field puts r = a in
+ * no barrier: at large l inside the centrifugal barrier q / |p| ~ (F/G)^2 and
+ * the fraction at l keeps correspondingly few digits. With f_0 from CF1 at 0,
+ * the Wronskian q (F_0^2 + G_0^2) = 1 gives F_0, G_0; G (dominant upwards) is
+ * carried to l by the l-recurrences (DLMF 33.4)
+ *   u_L = (S_L u_{L-1} - u'_{L-1}) / R_L,   u'_L = R_L u_{L-1} - S_L u_L,
+ *   S_L = L/rho + eta/L,  R_L = sqrt(1 + eta^2/L^2),
+ * and F_l from CF1 at l and F'G - FG' = 1: F_l = 1 / (f_l G_l - G_l'). */
+int ref_coulomb_open(int l, double eta_d, double rho_d, double *out)
+{
+    Q eta = eta_d, rho = rho_d;
+    Q fl, f0;
+    int sl, s0;
+    if (cf1_converged(l, eta, rho, rho_d, &fl, &sl)) return 1;
+    if (cf1_converged(0, eta, rho, rho_d, &f0, &s0)) return 1;
     Q p0, q0, p1, q1;
-    int N = 64 + 2 * ((int)fabs(eta_d) + l);
-    agree = 0;
-    cf2_at_depth(l, eta, rho, N, &p0, &q0);
+    int N = 64 + 2 * (int)fabs(eta_d), agree = 0;
+    cf2_at_depth(0, eta, rho, N, &p0, &q0);
     while (agree < 2) {
         N *= 2;
         if (N > MAX_DEPTH) return 1;
-        cf2_at_depth(l, eta, rho, N, &p1, &q1);
+        cf2_at_depth(0, eta, rho, N, &p1, &q1);
         Q scale = qabs(p1) + qabs(q1);
         agree = (qabs(p1 - p0) + qabs(q1 - q0) <= CONV * scale) ? agree + 1 : 0;
         p0 = p1;
         q0 = q1;
     }
-    Q f = f1, p = p1, q = q1;
-    /* q (F^2 + G^2) = 1 needs q > 0; deep inside a centrifugal barrier
-     * (F / G below ~1e-33) the fraction at l has no correct digit left. */
+    Q p = p1, q = q1;
     if (!(q > 0)) return 1;
-    Q F = qsqrt(q / ((f - p) * (f - p) + q * q));
-    if (s1 < 0) F = -F;
-    Q Fp = f * F;
-    Q G = (Fp - p * F) / q;
-    Q Gp = p * G - q * F;
+    Q F0 = qsqrt(q / ((f0 - p) * (f0 - p) + q * q));
+    if (s0 < 0) F0 = -F0;
+    Q G = (f0 - p) * F0 / q;
+    Q Gp = p * G - q * F0;
+    for (int L = 1; L <= l; ++L) {
+        Q S = (Q)L / rho + eta / (Q)L;
+        Q R = qsqrt(1 + (eta / (Q)L) * (eta / (Q)L));
+        Q Gn = (S * G - Gp) / R;
+        Gp = R * G - S * Gn;
+        G = Gn;
+    }
+    Q F = 1 / (fl * G - Gp);
+    if ((F < 0) != (sl < 0)) return 1;    /* CF1's sign and the Wronskian disagree */
+    Q Fp = fl * F;
     out[0] = (double)F;
     out[1] = (double)Fp;
     out[2] = (double)G;

@@ -97,12 +97,20 @@ def test_theta_from_f_and_g_at_half_integer_nu(z, a, l):
         assert np.max(np.abs(thp0 / th0 - Lt)) > 1e-6
 
 
-def test_oracle_reports_a_barrier_it_cannot_resolve():
-    """l = 15 at z = 1, a = 5, 3e-7 Ry above threshold: F / G ~ 1e-33 at r = a,
-    below binary128's precision, so the fraction at l cannot fix q > 0; the
-    oracle reports no convergence instead of returning NaN."""
-    import oracle
-    cf = oracle.channel_functions(3e-7, np.array([0.0, 0.5]), np.array([15, 0]), 1.0, 5.0)
-    assert cf["status"] == oracle.RM_ECF_NOCONV
-    cf = oracle.channel_functions(3e-7, np.array([0.0, 0.5]), np.array([15, 0]), 1.0, 10.0)
-    assert cf["status"] == 0 and np.all(np.isfinite(cf["c"]))
+@pytest.mark.parametrize("z,a,l", [(1.0, 5.0, 15), (1.0, 10.0, 15), (2.0, 15.0, 8), (2.0, 15.0, 0),
+                                   (1.0, 20.0, 3), (5.0, 8.0, 9)])
+def test_open_regular_solution_matches_its_power_series(z, a, l):
+    """The open-channel s, s' (continued fractions at l = 0, G carried up,
+    F_l by the Wronskian) against the energy-analytic regular solution f
+    from its power series: s = sqrt(B) f with B = A / (1 - exp(-2 pi z/k)),
+    the ratio of the two normalisations at r -> 0 (C_l(eta)^2 k^(2l+1) over
+    f's). Includes r = a deep inside an l = 15 barrier (F/G ~ 1e-35)."""
+    eps = np.array([3e-7, 4e-5, 1e-3, 0.05, 0.5])
+    s, sp, c, cp = _open(l, eps, z, a)
+    fo, st = _clib.regular_analytic(np.full(eps.size, l, np.int32), z, eps, a)
+    assert not st.any()
+    k = np.sqrt(eps)
+    sB = np.sqrt(_A(eps, l, z) / (1.0 - np.exp(-2.0 * np.pi * z / k)))
+    np.testing.assert_allclose(s, sB * fo[:, 0], rtol=1e-13)
+    np.testing.assert_allclose(sp, sB * fo[:, 1], rtol=1e-13)
+    np.testing.assert_allclose(sp * c - s * cp, 1.0, rtol=0, atol=1e-14)
