@@ -190,13 +190,16 @@ def _solve_flops(n, n_open, f32):
     """Algorithmic flops of steps (c)+(d) for the energies given, as the
     shared-memory solver takes them, split (FP64, FP32): elimination of the
     n x (n + n_o) system (2/3 n^3 + n^2 n_o) and back-substitution of the n_o
-    trailing rows (n_o^3), in FP32 when f32; then FP64 M = 1 + K^2 (upper
-    triangle, n_o^3), M^{-1} by the symmetric sweep (n_o^3), X = K M^{-1} for
-    the upper triangle (n_o^3)."""
+    trailing rows (n_o^3); then FP64: M = 1 + K^2 (upper triangle, n_o^3),
+    M^{-1} by the symmetric sweep (n_o^3), X = K M^{-1} for the upper triangle
+    (n_o^3); or, when f32, everything in FP32 with the T step as the complex
+    symmetric sweep of 1 - iK (upper triangle, n_o^3 / 2 complex FMAs =
+    4 n_o^3 flops)."""
     no = n_open.astype(np.float64)
     elim = float(np.sum(2.0 / 3.0 * n**3 + n * n * no + no**3))
-    t = float(np.sum(3.0 * no**3))
-    return (t, elim) if f32 else (t + elim, 0.0)
+    if f32:
+        return 0.0, elim + float(np.sum(4.0 * no**3))
+    return elim + float(np.sum(3.0 * no**3)), 0.0
 
 
 # FP64 operations (FMA, multiply, add, compare: one each; the reciprocal of
@@ -205,7 +208,8 @@ def _solve_flops(n, n_open, f32):
 # rescaling and convergence test of every 8th step spread over 8 steps),
 # counted from the kernel.
 CHANFN_OPS = {"cf1": 17, "cf2_fwd": 28, "cf2_bwd": 15, "open_l": 90, "open_fixed": 130,
-              "closed_fwd": 14, "closed_bwd": 10, "ladder": 36, "closed_fixed": 70}
+              "closed_fwd": 14, "closed_bwd": 10, "ladder": 36, "closed_fixed": 70,
+              "thr_interp": 16 * 10 + 40}
 CF2_FAST_DEPTH = 32   # CF2 settling within this many forward steps has no backward pass
 
 
@@ -223,7 +227,11 @@ def _chanfn_ops(work):
     slow_c = k[:, 2] > CF2_FAST_DEPTH
     ops_closed = (c["closed_fwd"] * (k[:, 2] - 1) + c["closed_bwd"] * (2 * k[:, 2] + 19) * slow_c
                   + c["ladder"] * k[:, 3] + c["closed_fixed"])
-    return float(ops_open.sum() + ops_closed.sum())
+    # near-threshold pairs: barycentric interpolation over the 16 nodes of the
+    # channel's table (a reciprocal and 5 FMAs per node) and A(eps, l)
+    ti = w[w[:, 0] == 3]
+    ops_thr = c["thr_interp"] * ti.shape[0] + 2.0 * ti[:, 3].sum()
+    return float(ops_open.sum() + ops_closed.sum() + ops_thr)
 
 
 def run_serving(args, prec):
@@ -506,17 +514,21 @@ def run_ours(args, rank, world, local_rank):
     f32 = sp == 1
     fl64, fl32 = _solve_flops(n, n_open.cpu().numpy(), f32)
     t_solve = phase[rmgb.RM_PH_SOLVE][1] / args.steps * 1e-3
-    ach = fl64 / t_solve / 1e12
-    solve_roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                  "frac": ach / fp64_peak, "traffic": None,
-                  "kernel": "solve_small_kernel (%s elimination, FP64 T)" % ("FP32" if f32 else "FP64"),
-                  "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"}
     if f32:
         fp32_peak = N_SM * 256.0 * sm_mhz * 1e6 / 1e12
-        solve_roof["fp32_elimination"] = {"achieved": fl32 / t_solve / 1e12, "peak": fp32_peak,
-                                          "frac": fl32 / t_solve / 1e12 / fp32_peak,
-                                          "unit": "TFLOP/s",
-                                          "peak_source": "FP32 128 FMA/clk/SM x 152 SMs"}
+        ach = fl32 / t_solve / 1e12
+        solve_roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                      "frac": ach / fp32_peak, "traffic": None,
+                      "kernel": "solve_small_kernel (FP32 elimination, FP32 complex T step)",
+                      "peak_source": "FP32 128 FMA/clk/SM x 152 SMs at the sampled SM clock",
+                      "note": "one CTA per energy; bound by the per-column barriers of the "
+                              "elimination and the sweep, not by the FP32 pipe"}
+    else:
+        ach = fl64 / t_solve / 1e12
+        solve_roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                      "frac": ach / fp64_peak, "traffic": None,
+                      "kernel": "solve_small_kernel (FP64 elimination, FP64 T step)",
+                      "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"}
     # dominant kernel by device time
     dom = max((rmgb.RM_PH_FORM, rmgb.RM_PH_SOLVE, rmgb.RM_PH_CHANFN), key=lambda p: phase[p][1])
     roof = {rmgb.RM_PH_FORM: form_roof, rmgb.RM_PH_SOLVE: solve_roof, rmgb.RM_PH_CHANFN: chan_roof}[dom]

@@ -94,10 +94,13 @@ typedef struct rm_opts {
     int formulation;        /* mixed-precision formation (Eq. rmatrix on tensor cores):
                                RM_FORM_AUTO (default: pair operand while it is small,
                                per-energy GEMM above), RM_FORM_PAIRS, RM_FORM_ENERGY */
-    int solve_precision;    /* matching elimination (step (c)): RM_FP64 (default) or
-                               RM_FP32 (direct mode, shared-memory solver: the system
-                               is eliminated in FP32; T and Omega stay FP64). Other
-                               cases run in FP64 whatever this asks */
+    int solve_precision;    /* steps (c)-(d): RM_FP64 (default) or RM_FP32 (direct
+                               mode, shared-memory solver: the matching system is
+                               eliminated in FP32 and T = 2(1 - iK)^{-1} - 2 comes
+                               from an FP32 complex inversion of 1 - iK, whose error
+                               is that of a perturbation of 1 - iK of Frobenius norm
+                               <= n_open 2^-24 ||1 - iK||_F; Omega is accumulated in
+                               FP64). Other cases run in FP64 whatever this asks */
 } rm_opts;
 
 #define RM_SOLVER_AUTO    0
@@ -144,7 +147,13 @@ int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const double *E_k,
  * channels of one level must share its threshold), and the statistical weight
  * g of the partial wave (e.g. (2J+1)/2). n_ch must equal the loaded n_ch.
  * Closed channels with z = 0 are supported; open channels need z >= 0.
- * Synchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
+ * For z > 0 the call also computes each channel's near-threshold table: the
+ * energy-analytic channel quantities at 16 energies straddling its
+ * threshold, from which step (b) interpolates pairs within a few node
+ * spacings of the threshold instead of running continued fractions whose
+ * length grows as 1/|E - e_i| (rm_load_poles recomputes the tables when the
+ * channels are already set). Synchronous. Errors: RM_EINVAL, RM_ENOTLOADED,
+ * RM_ENOMEM, RM_ECUDA. */
 int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, double z,
                     const int *level, int n_levels, double g_weight);
 
@@ -224,7 +233,8 @@ int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *E, double *
  * [n_E][n_ch][4] ints): {kind, CF1 iterations, CF2 forward iterations n2, l
  * steps}, kind 0 = open (CF1 at l, CF2 at l = 0, l downward and upward
  * recurrence steps), 1 = closed (its CF2 at L0, then l - L0 ladder steps),
- * -1 = on a threshold. A CF2 with n2 > 32 is re-evaluated backwards from
+ * 3 = near the threshold, interpolated from the channel's node table (no
+ * continued fraction; the l field holds l), -1 = on a threshold. A CF2 with n2 > 32 is re-evaluated backwards from
  * depth 2 n2 + 20; one with n2 <= 32 is taken from its forward value.
  * Asynchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ECUDA. */
 int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, int *work);

@@ -321,6 +321,7 @@ __device__ int regular_analytic(int l, double z, double eps, double r, double *f
 #define RM_CHANFN_MINB 1
 #endif
 constexpr int CHANFN_BS = RM_CHANFN_BS;   // threads per block of the channel kernel
+constexpr int CH_THR_INTERP = 3;          // work-record kind of an interpolated pair
 constexpr double CHANFN_DEEP_EPS = 2.5e-5;   // |eps| / max(z^2, 1) below this: a deep pair
 constexpr int CHANFN_DEEP_CAP = 1 << 14;     // capacity of the deep-pair list
 
@@ -331,9 +332,10 @@ constexpr int CHANFN_DEEP_CAP = 1 << 14;     // capacity of the deep-pair list
 // energies marked, and a separate kernel (on a second stream) evaluates them
 // while the main stream forms R and solves every unmarked energy; the marked
 // energies are solved after it.
-__device__ __forceinline__ bool chanfn_deep(double eps, double z, double eps_thr)
+__device__ __forceinline__ bool chanfn_deep(const PwDev &pw, int i, double eps, double eps_thr)
 {
-    return fabs(eps) < CHANFN_DEEP_EPS * fmax(z * z, 1.0) && fabs(eps) >= eps_thr;
+    if (!(fabs(eps) < CHANFN_DEEP_EPS * fmax(pw.z * pw.z, 1.0)) || fabs(eps) < eps_thr) return false;
+    return !(pw.thr && fabs(eps) < pw.thr[i].zone);   // covered by the channel's table
 }
 
 __global__ void chanfn_deep_mark_kernel(PwDev pw, const double *__restrict__ E, int nE, double eps_thr,
@@ -344,11 +346,119 @@ __global__ void chanfn_deep_mark_kernel(PwDev pw, const double *__restrict__ E, 
     if (idx >= (long long)nE * pw.n) return;
     const int i = (int)(idx / nE);
     const int e = (int)(idx - (long long)i * nE);
-    if (chanfn_deep(E[e] - pw.e_thr[i], pw.z, eps_thr)) {
+    if (chanfn_deep(pw, i, E[e] - pw.e_thr[i], eps_thr)) {
         const int k = atomicAdd(count, 1);
         if (k < CHANFN_DEEP_CAP) list[k] = (int)idx;
         defer[e] = 1;
     }
+}
+
+// Open channel at eps > 0 (Steed's method, steps 1-5 above): energy-
+// normalised s, s', c, c' at r = a. Returns 0 if a fraction did not converge;
+// it1 / d2: CF1 iterations and CF2 forward depth.
+__device__ __forceinline__ int open_channel(int l, double eps, double z, double a, double *s, double *sp,
+                                            double *c, double *cp, int *it1, int *d2)
+{
+    const double k = sqrt(eps);
+    const double eta = -z / k;
+    const double rho = k * a;
+    Cf1 c1 = cf1_lentz(l, eta, rho);
+    double p, q;
+    *d2 = 0;
+    const int ok2 = cf2_open_l0(eta, rho, &p, &q, d2);
+    *it1 = c1.iters;
+    if (!c1.ok || !ok2) return 0;
+    // F_l, F_l' up to a common scale, carried down to l = 0
+    const double Fl = (double)c1.sgn, Fpl = c1.f * Fl;
+    double F = Fl, Fp = Fpl;
+    for (int L = l; L >= 1; --L) {
+        const double SL = L / rho + eta / L;
+        const double RL = sqrt(1.0 + (eta / L) * (eta / L));
+        const double Fm = (SL * F + Fp) / RL;
+        Fp = SL * Fm - RL * F;
+        F = Fm;
+    }
+    const double f0 = Fp / F;
+    double F0 = sqrt(q / ((f0 - p) * (f0 - p) + q * q));
+    if (F < 0.0) F0 = -F0;
+    const double scale = F0 / F;
+    double G = scale * (Fp - p * F) / q;
+    double Gp = p * G - q * F0;
+    for (int L = 0; L < l; ++L) {
+        const double L1 = L + 1.0;
+        const double S1 = L1 / rho + eta / L1;
+        const double R1 = sqrt(1.0 + (eta / L1) * (eta / L1));
+        const double Gn = (S1 * G - Gp) / R1;
+        Gp = R1 * G - S1 * Gn;
+        G = Gn;
+    }
+    const double sk = sqrt(k);
+    *s = scale * Fl / sk;
+    *sp = scale * Fpl * sk;
+    *c = G / sk;
+    *cp = Gp * sk;
+    return 1;
+}
+
+// Closed channel at eps < 0: log-derivative y = theta'/theta of the decaying
+// solution at r = a (CF2 at l = L0, then the ladder to l). Returns 0 if the
+// fraction did not converge; d2: its forward depth, *L0o: L0.
+__device__ __forceinline__ int closed_channel(int l, double eps, double z, double a, double *y, int *d2,
+                                              int *L0o)
+{
+    const double kap = sqrt(-eps);
+    const double nu = z / kap;
+    int L0 = 0;
+    if (nu <= l + 0.5) {
+        L0 = (int)ceil(nu - 0.5);
+        L0 = L0 < 0 ? 0 : (L0 > l ? l : L0);
+    }
+    *L0o = L0;
+    *d2 = 0;
+    double yy;
+    if (!cf2_closed(L0, nu, kap, a, &yy, d2)) return 0;
+    for (int L = L0; L < l; ++L) {
+        const double L1 = L + 1.0;
+        const double T = L1 / a - z / L1;
+        const double c = eps + (z / L1) * (z / L1);
+        yy = c / (T - yy) - T;
+    }
+    *y = yy;
+    return 1;
+}
+
+// A(eps, l) = prod_{p=1..l} (1 + p^2 eps / z^2).
+__device__ __forceinline__ double a_factor(int l, double eps, double z)
+{
+    const double u = eps / (z * z);
+    double A = 1.0;
+    for (int p = 1; p <= l; ++p) A = fma(A * (double)(p * p), u, A);
+    return A;
+}
+
+// Barycentric interpolation of the table's four quantities at eps.
+__device__ __forceinline__ void thr_interp(const ThrNodes &T, double eps, double v[4])
+{
+    double num0 = 0.0, num1 = 0.0, num2 = 0.0, num3 = 0.0, den = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < THR_NODES; ++j) {
+        const double d = eps - T.x[j];
+        if (d == 0.0) {
+            for (int q = 0; q < 4; ++q) v[q] = T.y[q][j];
+            return;
+        }
+        const double t = T.w[j] * rcp_nr(d);
+        den += t;
+        num0 = fma(t, T.y[0][j], num0);
+        num1 = fma(t, T.y[1][j], num1);
+        num2 = fma(t, T.y[2][j], num2);
+        num3 = fma(t, T.y[3][j], num3);
+    }
+    const double id = 1.0 / den;
+    v[0] = num0 * id;
+    v[1] = num1 * id;
+    v[2] = num2 * id;
+    v[3] = num3 * id;
 }
 
 // Channel data of pair idx = i nE + e.
@@ -367,73 +477,60 @@ __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int n
     int bad = RM_OK;
     if (fabs(eps) < o.eps_thr) {
         bad = RM_ETHRESHOLD;
-    } else if (eps > 0.0) {
-        const double k = sqrt(eps);
-        const double eta = -z / k;
-        const double rho = k * a;
-        Cf1 c1 = cf1_lentz(l, eta, rho);
-        double p, q;
-        int d2 = 0;
-        int ok2 = cf2_open_l0(eta, rho, &p, &q, &d2);
-        if (STATS) work[(size_t)e * n + i] = make_int4(CH_OPEN, c1.iters, d2, l);
-        if (!c1.ok || !ok2) {
-            bad = RM_ECF_NOCONV;
-        } else {
-            // F_l, F_l' up to a common scale, carried down to l = 0
-            const double Fl = (double)c1.sgn, Fpl = c1.f * Fl;
-            double F = Fl, Fp = Fpl;
-            for (int L = l; L >= 1; --L) {
-                const double SL = L / rho + eta / L;
-                const double RL = sqrt(1.0 + (eta / L) * (eta / L));
-                const double Fm = (SL * F + Fp) / RL;
-                Fp = SL * Fm - RL * F;
-                F = Fm;
-            }
-            const double f0 = Fp / F;
-            double F0 = sqrt(q / ((f0 - p) * (f0 - p) + q * q));
-            if (F < 0.0) F0 = -F0;
-            const double scale = F0 / F;
-            double G = scale * (Fp - p * F) / q;
-            double Gp = p * G - q * F0;
-            for (int L = 0; L < l; ++L) {
-                const double L1 = L + 1.0;
-                const double S1 = L1 / rho + eta / L1;
-                const double R1 = sqrt(1.0 + (eta / L1) * (eta / L1));
-                const double Gn = (S1 * G - Gp) / R1;
-                Gp = R1 * G - S1 * Gn;
-                G = Gn;
-            }
-            const double sk = sqrt(k);
-            r.s = scale * Fl / sk;
-            r.sp = scale * Fpl * sk;
-            r.gh = G / sk;
-            r.ghp = Gp * sk;
+    } else if (pw.thr && fabs(eps) < pw.thr[i].zone) {
+        // near the threshold: from the channel's interpolation table
+        if (STATS) work[(size_t)e * n + i] = make_int4(CH_THR_INTERP, 0, 0, l);
+        double v[4];
+        thr_interp(pw.thr[i], eps, v);
+        const double A = a_factor(l, eps, z);
+        if (eps > 0.0) {
+            const double sA = sqrt(A), isA = 1.0 / sA;
+            r.s = v[0] * sA;
+            r.sp = v[1] * sA;
+            r.gh = v[2] * isA;
+            r.ghp = v[3] * isA;
             r.kind = CH_OPEN;
+        } else {
+            const double kap = sqrt(-eps);
+            const double nu = z / kap;
+            double sb, cb;
+            sincospi(nu, &sb, &cb);
+            if (MQDT && nu >= fmax(l + o.nu_margin, o.fnumin) && kap * a <= o.kappa_a_max && fabs(sb) >= 1e-3) {
+                // g = g~ + (1 - A) f cot(pi nu), from theta ~ f cos(pi nu) - g sin(pi nu)
+                const double ct = (1.0 - A) * cb / sb;
+                r.s = v[0];
+                r.sp = v[1];
+                r.gh = fma(ct, v[0], v[2]);
+                r.ghp = fma(ct, v[1], v[3]);
+                r.tanb = sb / cb;
+                r.kind = CH_MQDT;
+            } else {
+                const double th = fma(A * v[0], cb, -v[2] * sb);
+                const double thp = fma(A * v[1], cb, -v[3] * sb);
+                const double nrm = 1.0 / sqrt(fma(th, th, (a * thp) * (a * thp)));
+                r.gh = fabs(th) * nrm;
+                r.ghp = (th < 0.0 ? -thp : thp) * nrm;
+            }
         }
+    } else if (eps > 0.0) {
+        int it1 = 0, d2 = 0;
+        const int ok = open_channel(l, eps, z, a, &r.s, &r.sp, &r.gh, &r.ghp, &it1, &d2);
+        if (STATS) work[(size_t)e * n + i] = make_int4(CH_OPEN, it1, d2, l);
+        if (!ok) bad = RM_ECF_NOCONV;
+        else r.kind = CH_OPEN;
     } else {
-        const double kap = sqrt(-eps);
-        const double nu = z / kap;
-        int L0 = 0;
-        if (nu <= l + 0.5) {
-            L0 = (int)ceil(nu - 0.5);
-            L0 = L0 < 0 ? 0 : (L0 > l ? l : L0);
-        }
         double y;
-        int d2 = 0;
-        const int okc = cf2_closed(L0, nu, kap, a, &y, &d2);
+        int d2 = 0, L0 = 0;
+        const int okc = closed_channel(l, eps, z, a, &y, &d2, &L0);
         if (STATS) work[(size_t)e * n + i] = make_int4(CH_CLOSED, 0, d2, l - L0);
         if (!okc) {
             bad = RM_ECF_NOCONV;
         } else {
-            for (int L = L0; L < l; ++L) {
-                const double L1 = L + 1.0;
-                const double T = L1 / a - z / L1;
-                const double c = eps + (z / L1) * (z / L1);
-                y = c / (T - y) - T;
-            }
             const double nrm = 1.0 / sqrt(1.0 + (a * y) * (a * y));
             r.gh = nrm;
             r.ghp = y * nrm;
+            const double kap = sqrt(-eps);
+            const double nu = z / kap;
             if (MQDT && nu >= fmax(l + o.nu_margin, o.fnumin) && kap * a <= o.kappa_a_max) {
                 double sb, cb;
                 sincospi(nu, &sb, &cb);
@@ -462,6 +559,97 @@ __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int n
     if (bad != RM_OK) atomicCAS(status + e, RM_OK, bad);
 }
 
+// Node spacing of a channel's table: small against the energy scale on
+// which the channel functions at r = a change (~ sqrt(z) / a^1.5) and
+// against the distance z^2 / (l + 1)^2 to the nearest singularity of g~ (at
+// nu = l); the table covers |eps| < THR_ZONE h. A table is used only if
+// leave-one-out interpolation of its four innermost nodes agrees with their
+// values to THR_LOO_TOL (relative to each quantity's largest node value).
+constexpr double THR_C1 = 0.0164, THR_C2 = 0.05, THR_ZONE = 4.0, THR_LOO_TOL = 1e-9;
+
+// One block of 32 threads per channel: threads 0-7 the closed-side nodes
+// (half-integer nu, descending, so x ascends), 8-15 the open side
+// (eps = h, 2h, ... 8h); thread 0 then forms the weights and checks them.
+__global__ void __launch_bounds__(32) thr_nodes_kernel(PwDev pw, ThrNodes *__restrict__ tab)
+{
+    constexpr int M = THR_NODES / 2;
+    __shared__ double xs[THR_NODES], ys[4][THR_NODES];
+    __shared__ int okn[THR_NODES];
+    const int i = blockIdx.x, t = threadIdx.x;
+    const int l = pw.l[i];
+    const double z = pw.z, a = pw.a;
+    const double h = fmin(THR_C1 * sqrt(z) / (a * sqrt(a)), THR_C2 * z * z / ((l + 1.0) * (l + 1.0)));
+    if (t < THR_NODES) {
+        double x, v[4] = {0.0, 0.0, 0.0, 0.0};
+        int ok = 0;
+        if (t >= M) {
+            x = h * (t - M + 1);
+            int it1, d2;
+            ok = open_channel(l, x, z, a, &v[0], &v[1], &v[2], &v[3], &it1, &d2);
+            const double sA = sqrt(a_factor(l, x, z));
+            v[0] /= sA;
+            v[1] /= sA;
+            v[2] *= sA;
+            v[3] *= sA;
+        } else {
+            // node j = M - t: the half-integer nu nearest below z / sqrt(j h),
+            // at least 1 below the previous node's
+            const int j = M - t;
+            double nu = 0.0;
+            for (int q = 1; q <= j; ++q) {
+                const double c = floor(z / sqrt(h * q)) + 0.5;
+                nu = (q == 1) ? c : fmin(nu - 1.0, c);
+            }
+            x = -(z / nu) * (z / nu);
+            double y, f, fp;
+            int d2, L0;
+            ok = nu > 0.0 && closed_channel(l, x, z, a, &y, &d2, &L0) && regular_analytic(l, z, x, a, &f, &fp);
+            if (ok) {
+                // at half-integer nu, theta ~ g~ and f'g~ - f g~' = 1
+                v[2] = -1.0 / (f * y - fp);
+                v[3] = y * v[2];
+                v[0] = f;
+                v[1] = fp;
+            }
+        }
+        for (int q = 0; q < 4; ++q) ok = ok && isfinite(v[q]);
+        xs[t] = x;
+        for (int q = 0; q < 4; ++q) ys[q][t] = v[q];
+        okn[t] = ok;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    ThrNodes &T = tab[i];
+    bool valid = z > 0.0 && h > 0.0;
+    for (int j = 0; j < THR_NODES; ++j) valid = valid && okn[j];
+    for (int j = 0; j < THR_NODES; ++j) {
+        double p = 1.0;
+        for (int k = 0; k < THR_NODES; ++k)
+            if (k != j) p *= xs[j] - xs[k];
+        T.x[j] = xs[j];
+        T.w[j] = 1.0 / p;
+        for (int q = 0; q < 4; ++q) T.y[q][j] = ys[q][j];
+    }
+    if (valid) {
+        for (int q = 0; q < 4 && valid; ++q) {
+            double mx = 0.0;
+            for (int j = 0; j < THR_NODES; ++j) mx = fmax(mx, fabs(ys[q][j]));
+            for (int k = M - 2; k <= M + 1; ++k) {
+                double num = 0.0, den = 0.0;
+                for (int j = 0; j < THR_NODES; ++j) {
+                    if (j == k) continue;
+                    const double tw = T.w[j] * (xs[j] - xs[k]) / (xs[k] - xs[j]);
+                    num += tw * ys[q][j];
+                    den += tw;
+                }
+                if (!(fabs(num / den - ys[q][k]) <= THR_LOO_TOL * mx)) valid = false;
+            }
+        }
+    }
+    T.h = h;
+    T.zone = valid ? THR_ZONE * h : 0.0;
+}
+
 // With deep_count != nullptr, the listed deep pairs are skipped (when the
 // list did not overflow): chanfn_deep_kernel takes them.
 template <bool MQDT, bool STATS>
@@ -475,7 +663,7 @@ __global__ void __launch_bounds__(CHANFN_BS, RM_CHANFN_MINB)
     if (deep_count && *deep_count <= CHANFN_DEEP_CAP) {
         const int i0 = (int)(idx / nE);
         const int e0 = (int)(idx - (long long)i0 * nE);
-        if (chanfn_deep(E[e0] - pw.e_thr[i0], pw.z, o.eps_thr)) return;
+        if (chanfn_deep(pw, i0, E[e0] - pw.e_thr[i0], o.eps_thr)) return;
     }
     chanfn_pair<MQDT, STATS>(pw, E, nE, o, out, status, work, idx);
 }
@@ -564,6 +752,17 @@ cudaError_t launch_chanfn_deep(const PwDev &pw, const double *E, int nE, const O
 }
 
 int chanfn_deep_cap() { return CHANFN_DEEP_CAP; }
+
+double chanfn_deep_eps(double z) { return CHANFN_DEEP_EPS * fmax(z * z, 1.0); }
+
+cudaError_t launch_thr_nodes(const PwDev &pw, ThrNodes *tab, cudaStream_t s)
+{
+    if (pw.n == 0) return cudaSuccess;
+    PwDev d = pw;
+    d.thr = nullptr;
+    thr_nodes_kernel<<<pw.n, 32, 0, s>>>(d, tab);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_chanfn_work(const PwDev &pw, const double *E, int nE, const Opts &o, int4 *work,
                                cudaStream_t s)

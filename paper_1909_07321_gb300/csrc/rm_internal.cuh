@@ -33,6 +33,24 @@ __host__ __device__ __forceinline__ int tri_idx(int i, int j, int n)
     return i * n - (i * (i - 1)) / 2 + (j - i);
 }
 
+// Near-threshold interpolation table of one channel (step (b)). At fixed
+// r = a the pair f = s / sqrt(A), g~ = c sqrt(A) (open side, A(eps, l) =
+// prod_{p=1..l} (1 + p^2 eps / z^2)) continues analytically into the closed
+// side, where f is the energy-analytic regular solution and g~ the g of the
+// quantum-defect pair at half-integer nu; the decaying solution is then
+// theta ~ A f cos(pi nu) - g~ sin(pi nu). Values at THR_NODES energies
+// straddling the threshold (half on each side, ascending in x) give every
+// channel quantity for |eps| < zone by barycentric interpolation instead of
+// continued fractions whose depth grows as 1/|eps|. zone = 0: not covered.
+constexpr int THR_NODES = 16;
+struct ThrNodes {
+    double x[THR_NODES];        // eps of the nodes
+    double w[THR_NODES];        // barycentric weights
+    double y[4][THR_NODES];     // f, f', g~, g~'
+    double zone;
+    double h;                   // node spacing in energy
+};
+
 // Device-side description of one partial wave.
 struct PwDev {
     int n;             // channels
@@ -47,6 +65,7 @@ struct PwDev {
     const int *lev_start;  // [n_levels+1] CSR of channels per level
     const int *lev_chan;   // [n]
     const double *lev_thr; // [n_levels] threshold of each level (+inf if unused)
+    const ThrNodes *thr = nullptr;  // [n] near-threshold tables (nullptr: none)
 };
 
 struct Opts {
@@ -60,12 +79,17 @@ struct Opts {
 // listed deep pairs are then left to launch_chanfn_deep.
 cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
                           ChanFn *cf, int *status, const int *deep_ws, cudaStream_t s);
+// Near-threshold tables of the n channels (z > 0): computes tab[0..n) on the
+// stream; pw.thr is not read.
+cudaError_t launch_thr_nodes(const PwDev &pw, ThrNodes *tab, cudaStream_t s);
 // Near-threshold (deep) pairs: deep_ws = [count][list of CAP pair indices][nE
 // energy marks], chanfn_deep_ws_bytes(nE) bytes. The mark launch zeroes it
 // and fills it; the deep launch evaluates the listed pairs. If the list
 // overflowed (count > chanfn_deep_cap()), nothing is left out and nothing is
 // deferred.
 size_t chanfn_deep_ws_bytes(int nE);
+// |eps| below which a pair not covered by its channel's table is deep.
+double chanfn_deep_eps(double z);
 int chanfn_deep_cap();
 cudaError_t launch_chanfn_deep_mark(const PwDev &pw, const double *E, int nE, const Opts &o, int *deep_ws,
                                     cudaStream_t s);

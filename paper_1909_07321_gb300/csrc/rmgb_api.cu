@@ -63,11 +63,17 @@ struct PwHost {
     int w_kind = -1;
     std::vector<double> h_e_thr, h_Ek;   // host copies (thresholds, sorted poles)
     std::vector<int> h_l;
+    // near-threshold interpolation tables (z > 0), built when the wave has
+    // both its poles and its channels; use_deep: some near-threshold pairs
+    // are not covered and go to the side stream
+    DevBuf thr;
+    bool use_deep = true;
     void release()
     {
         for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
-                          &Wh, &Wl})
+                          &Wh, &Wl, &thr})
             d->release();
+        use_deep = true;
         loaded = channels = false;
         p_kind = -1;
         w_kind = -1;
@@ -90,6 +96,7 @@ struct PwHost {
         d.lev_start = lev_start.as<int>();
         d.lev_chan = lev_chan.as<int>();
         d.lev_thr = lev_thr.as<double>();
+        d.thr = thr.as<ThrNodes>();
         return d;
     }
 };
@@ -314,6 +321,29 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     delete ctx;
 }
 
+namespace {
+
+// Near-threshold tables of wave P (its poles, a and channels are set): one
+// launch, then the validity of every table is read back (once per wave).
+int build_thr(rm_ctx *ctx, PwHost &P)
+{
+    P.thr.release();
+    P.use_deep = true;
+    if (!(P.z > 0.0) || P.n == 0) return RM_SUCCESS;
+    CK(P.thr.reserve(sizeof(ThrNodes) * (size_t)P.n));
+    CK(launch_thr_nodes(P.dev(), P.thr.as<ThrNodes>(), ctx->stream));
+    ++ctx->launches;
+    std::vector<ThrNodes> h(P.n);
+    CK(cudaMemcpyAsync(h.data(), P.thr.p, sizeof(ThrNodes) * (size_t)P.n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    bool all = true;
+    for (int i = 0; i < P.n; ++i) all = all && h[i].zone >= chanfn_deep_eps(P.z);
+    P.use_deep = !all;
+    return RM_SUCCESS;
+}
+
+}  // namespace
+
 extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const double *E_k,
                              const double *W, double a, double b)
 {
@@ -356,7 +386,7 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
     P.b = b;
     P.loaded = true;
     if (!same_n) P.channels = false;
-    return RM_SUCCESS;
+    return P.channels ? build_thr(ctx, P) : RM_SUCCESS;
 }
 
 extern "C" int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, double z,
@@ -398,7 +428,7 @@ extern "C" int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const i
     P.g = g_weight;
     P.n_levels = n_levels;
     P.channels = true;
-    return RM_SUCCESS;
+    return build_thr(ctx, P);
 }
 
 namespace {
@@ -621,7 +651,7 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
         // Deep (near-threshold) channel pairs go to the side stream, and the
         // energies holding them are solved after it joins (shared-memory
         // solver only).
-        const bool split = !large;
+        const bool split = !large && P.use_deep;
         int *deep = nullptr;
         if (split) {
             CK(ctx->wsDeep.reserve(chanfn_deep_ws_bytes(B)));
@@ -654,10 +684,13 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
             int *kunb = ku_np ? ku_np + e0 : nullptr;
             CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
                                   omb, ntri, mode == RM_MQDT, f32, deep, 0, ctx->stream, kub, kunb));
-            CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-            CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, mode == RM_MQDT, f32, deep, 1, ctx->stream, kub, kunb));
-            ctx->launches += 2;
+            ++ctx->launches;
+            if (split) {
+                CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+                CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
+                                      omb, ntri, mode == RM_MQDT, f32, deep, 1, ctx->stream, kub, kunb));
+                ++ctx->launches;
+            }
         }
         CK(prof_end(ctx, RM_PH_SOLVE));
     }

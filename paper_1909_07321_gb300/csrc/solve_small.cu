@@ -24,6 +24,9 @@
 // triangle: X is symmetric). Then for target levels I <= J, one thread owns
 // Omega_IJ(E) and adds g sum_{a in I, b in J} |T_ab|^2 in a fixed order, so
 // the accumulation is deterministic (no atomics).
+// The FP32 variant (mixed-precision path) instead inverts 1 - iK in complex
+// FP32 arithmetic, T = 2(1 - iK)^{-1} - 2, which needs no product with K and
+// works with the conditioning of 1 - iK (that of 1 + K^2 is its square).
 #include <math.h>
 
 #include <type_traits>
@@ -34,17 +37,28 @@
 namespace rmgb {
 namespace {
 
-// Shared-memory bytes of region A in the FP32-matching layout: the float
-// augmented matrix n x (2n + 1), later M^{-1} (at most n x (n + 1) doubles).
+// Shared-memory bytes of the FP32 layout: region A holds the float augmented
+// matrix n x (2n + 1), later 1 - iK (complex float, n x (n + 1)); region B
+// the symmetrised K (n x n floats), later the sweep's column buffer (2n
+// complex floats).
 __host__ __device__ inline size_t f32_region_a(int n)
 {
     const size_t aug = (size_t)n * (2 * n + 1) * sizeof(float);
-    const size_t mi = (size_t)n * (n + 1) * sizeof(double);
-    return ((aug > mi ? aug : mi) + 15) & ~(size_t)15;
+    const size_t w = (size_t)n * (n + 1) * sizeof(float2);
+    return ((aug > w ? aug : w) + 15) & ~(size_t)15;
 }
 
-// F32: the matching system is eliminated in FP32 (direct mode only; the T
-// step and Omega stay FP64).
+__host__ __device__ inline size_t f32_region_b(int n)
+{
+    const size_t ks = (size_t)n * n * sizeof(float);
+    const size_t u = (size_t)2 * n * sizeof(float2);
+    return ((ks > u ? ks : u) + 15) & ~(size_t)15;
+}
+
+// F32 (direct mode only): the matching system is eliminated in FP32 and the
+// T step runs in FP32 complex arithmetic, T = 2(1 - iK)^{-1} - 2 with
+// (1 - iK)^{-1} from the complex symmetric sweep (no product with K, and the
+// conditioning of 1 - iK, not of 1 + K^2); Omega is accumulated in FP64.
 template <bool F32>
 __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
@@ -64,7 +78,6 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     __shared__ int open_pos[SOLVE_SMALL_MAXN];   // channel -> open position (-1 otherwise)
     __shared__ int qpos[SOLVE_SMALL_MAXN];       // MQDT channel k -> its position in P
     __shared__ int opos[SOLVE_SMALL_MAXN];       // open channel k -> its position in P
-    __shared__ int piv[SOLVE_SMALL_MAXN];
     __shared__ double vcol[SOLVE_SMALL_MAXN];
     __shared__ int s_no, s_np, s_nq;
     __shared__ ElimShared esh;
@@ -164,26 +177,38 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        // K (FP64) into region B, then M^{-1} over the float matrix in region A
-        Kp = reinterpret_cast<double *>(reinterpret_cast<char *>(sm) + f32_region_a(n));
-        kld = lk;
+        // K symmetrised (float) into region B; then A = 1 - iK (complex
+        // float, upper triangle) over region A, inverted by the complex
+        // symmetric sweep, and Omega from -(1 - iK)^{-1}.
+        float *Ks = reinterpret_cast<float *>(reinterpret_cast<char *>(sm) + f32_region_a(n));
         const int nsym0 = no * (no + 1) / 2;
         for (int q = tid; q < nsym0; q += NT) {
             int p, r;
             tri_pair(q, no, p, r);
-            const double kpr = (double)M[(ncl + p) * ld + n + r];
-            const double krp = (double)M[(ncl + r) * ld + n + p];
+            const float kpr = (float)M[(ncl + p) * ld + n + r];
+            const float krp = (float)M[(ncl + r) * ld + n + p];
             if (K_out) {
                 K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
                 K_out[(size_t)e * n * n + (size_t)r * n + p] = krp;
             }
-            const double v = 0.5 * (kpr + krp);
-            Kp[p * kld + r] = v;
-            Kp[r * kld + p] = v;
+            Ks[p * no + r] = 0.5f * (kpr + krp);
         }
         __syncthreads();
-        Mi = sm;
-        mld = lk;
+        if (!omega) return;
+        float2 *Wm = reinterpret_cast<float2 *>(sm);
+        const int wld = no + 1;
+        for (int q = tid; q < nsym0; q += NT) {
+            int p, r;
+            tri_pair(q, no, p, r);
+            Wm[p * wld + r] = make_float2(p == r ? 1.0f : 0.0f, -Ks[p * no + r]);
+        }
+        __syncthreads();
+        if (!csym_sweep_inverse(Wm, wld, no, reinterpret_cast<float2 *>(Ks), &esh)) {
+            if (tid == 0) status[e] = RM_ESINGULAR;
+            return;
+        }
+        omega_from_w(pw, x, Wm, wld, open_pos, omega + (size_t)e * n_tri);
+        return;
     } else if (nq == 0) {
         double *Md = reinterpret_cast<double *>(sm);
         // Direct mode (or no eliminated channel at this energy): K = K_u sits
@@ -249,11 +274,11 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
 int solve_small_max_n() { return SOLVE_SMALL_MAXN; }
 
 // Direct mode needs only the augmented matrix n x (2n + 1); MQDT mode also
-// holds K_u and the elimination system; FP32 matching keeps the float matrix
-// (then M^{-1}) beside K.
+// holds K_u and the elimination system; the FP32 layout is described at
+// f32_region_a.
 size_t solve_small_smem(int n, int mqdt, int f32)
 {
-    if (f32) return f32_region_a(n) + (size_t)n * (n + 1) * sizeof(double);
+    if (f32) return f32_region_a(n) + f32_region_b(n);
     if (!mqdt) return (size_t)n * (2 * n + 1) * sizeof(double);
     const size_t aug = (size_t)n * (2 * n + 2);
     const size_t ks = (size_t)n * (n + 1);

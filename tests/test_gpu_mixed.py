@@ -13,6 +13,10 @@ Stated bounds:
          errors there); elsewhere it is tiny. Median relative K error <= 1e-3.
   Omega: from dT = 2i(1-iK)^{-1} dK (1-iK)^{-1} and ||(1-iK)^{-1}|| <= 1,
          sum_IJ |dOmega_IJ| <= g (8 n_o B + 4 B^2) with B = ||dK bound||_F.
+         With the FP32 solve the T step inverts 1 - iK in FP32 complex
+         arithmetic: T = 2(1-iK)^{-1} - 2 moves by 2(1-iK)^{-1} dA (1-iK)^{-1}
+         for a backward error dA of that inversion, stated as
+         ||dA||_F <= n_o 2^-24 ||1 - iK||_F, which joins B.
 """
 import numpy as np
 import pytest
@@ -106,8 +110,8 @@ def test_form_r_energy_1000ch(rt):
     _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, 2, 0), "1000ch")
 
 
-def _first_order_k_bound(pw, x, u_solve=0.0):
-    """Elementwise first-order bound on |dK| from |dR| <= R_BOUND S (oracle
+def _first_order_k_bound(pw, x, u_solve=0.0, r_bound=R_BOUND):
+    """Elementwise first-order bound on |dK| from |dR| <= r_bound S (oracle
     quantities); with u_solve > 0 also the backward error of an elimination
     in that unit roundoff, |dA| <= 2 n u_solve |A|, |dB| <= 2 n u_solve |B|."""
     a, b = pw["a"], pw.get("b", 0.0)
@@ -129,7 +133,7 @@ def _first_order_k_bound(pw, x, u_solve=0.0):
     far = dd >= 1e-3
     S = (absW[:, far] / dd[far]) @ absW[:, far].T / (2 * a)
     Ainv = np.linalg.inv(A)
-    bound = np.abs(Ainv[oi, :]) @ (R_BOUND * S) @ np.abs(d2[:, None] * P + d1[:, None] * X)
+    bound = np.abs(Ainv[oi, :]) @ (r_bound * S) @ np.abs(d2[:, None] * P + d1[:, None] * X)
     if u_solve:
         g = 2.0 * op.size * u_solve
         bound += np.abs(Ainv[oi, :]) @ (g * (np.abs(A) @ np.abs(X) + np.abs(B)))
@@ -173,9 +177,57 @@ def test_mixed_k_and_omega_bounds(rt, name, prec, form, sp):
         assert np.all(dK <= 3.0 * bK + 1e-12 * max(1.0, np.abs(Ko).max())), (name, Es[m])
         eK.append(np.linalg.norm(dK) / max(np.linalg.norm(Ko), 1e-300))
         Bf = 3.0 * np.linalg.norm(bK)
+        if sp:
+            Bf += k * U32 * np.linalg.norm(np.eye(k) - 1j * Ko)
         dOm = np.abs(om[m] - ref["omega"][m]).sum()
         assert dOm <= pw["g"] * (8 * k * Bf + 4 * Bf * Bf) + 1e-12, (name, Es[m])
     assert np.median(eK) <= K_MED, np.median(eK)
+
+
+@pytest.mark.parametrize("wl", ["small", "64ch"])
+def test_fp32_solve_alone_within_bound(rt, wl):
+    """FP64 formation with the FP32 solve (matching elimination and complex
+    T step) against the oracle: K within the elimination's propagated
+    backward error, Omega within the bound with the T step's term, and the
+    per-energy Omega error small in the median (the formation's error is
+    absent here, so this isolates the solve)."""
+    torch, rmgb = rt
+    if wl == "small":
+        pws, E = synth.workload_small(2000)
+        pw = pws[0]
+        Es = E[::5]
+    else:
+        pws, E = synth.workload_64ch()
+        pw = pws[0]
+        Es = _energies(pw, E, 120, 8)
+    n = pw["W"].shape[0]
+    with rmgb.Context(precision=0, solve_precision=1) as ctx:
+        ctx.load_pw(0, pw)
+        Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+        K = torch.zeros((Es.size, n * n), dtype=torch.float64, device="cuda")
+        no = torch.zeros(Es.size, dtype=torch.int32, device="cuda")
+        st = torch.zeros(Es.size, dtype=torch.int32, device="cuda")
+        ctx.solve_energies(0, Ed, 0, K, no, st)
+        om = ctx.collision_strengths()
+    K = K.cpu().numpy().reshape(Es.size, n, n)
+    st = st.cpu().numpy()
+    ref = oracle.solve_energies(pw, Es)
+    assert np.array_equal(st, ref["status"])
+    rel = []
+    for m in range(Es.size):
+        if st[m]:
+            continue
+        Ko = ref["K"][m]
+        k = Ko.shape[0]
+        bK = _first_order_k_bound(pw, Es[m], U32, r_bound=1e-12)
+        dK = np.abs(K[m, :k, :k] - Ko)
+        assert np.all(dK <= 3.0 * bK + 1e-12 * max(1.0, np.abs(Ko).max())), (wl, Es[m])
+        B = 3.0 * np.linalg.norm(bK) + k * U32 * np.linalg.norm(np.eye(k) - 1j * Ko)
+        dOm = np.abs(om[m] - ref["omega"][m]).sum()
+        assert dOm <= pw["g"] * (8 * k * B + 4 * B * B) + 1e-12, (wl, Es[m])
+        rel.append(np.linalg.norm(om[m] - ref["omega"][m]) / max(np.linalg.norm(ref["omega"][m]), 1e-300))
+    assert len(rel) > 100
+    assert np.median(rel) < 1e-5, np.median(rel)
 
 
 @pytest.mark.parametrize("form", [1, 2])

@@ -271,7 +271,14 @@ def test_channel_work_counts(rt):
         ctx.channel_work(0, torch.tensor(E, device="cuda"), w)
         w = w.cpu().numpy()
     open_ = E[:, None] > pw["e_thr"][None, :]
-    assert np.array_equal(w[..., 0], np.where(open_, 0, 1))
-    assert (w[..., 1][open_] >= 1).all() and (w[..., 1][~open_] == 0).all()
-    assert (w[..., 2] >= 2).all() and (w[..., 2] < 1 << 20).all()
-    assert np.array_equal(w[..., 3][open_], np.broadcast_to(pw["l"], open_.shape)[open_])
+    # kind 3: within 4 node spacings of the threshold, from the channel's table
+    eps = np.abs(E[:, None] - pw["e_thr"][None, :])
+    h = np.minimum(0.0164 * np.sqrt(pw["z"]) / pw["a"] ** 1.5, 0.05 * pw["z"] ** 2 / (pw["l"] + 1.0) ** 2)
+    near = eps < 4.0 * h[None, :]
+    assert near.any() and (~near).any()
+    assert np.array_equal(w[..., 0], np.where(near, 3, np.where(open_, 0, 1)))
+    cf = ~near
+    assert (w[..., 1][open_ & cf] >= 1).all() and (w[..., 1][~open_] == 0).all()
+    assert (w[..., 2][cf] >= 2).all() and (w[..., 2] < 1 << 20).all()
+    assert (w[..., 1:3][near] == 0).all()
+    assert np.array_equal(w[..., 3][open_ | near], np.broadcast_to(pw["l"], open_.shape)[open_ | near])
