@@ -147,17 +147,7 @@ __device__ void spd_sweep_inverse(double *A, int ld, int m, double *v, ElimShare
     __syncthreads();
 }
 
-// In-place inverse of the complex symmetric m x m matrix A (upper triangle,
-// row stride ld, FP32 complex) by the sweep operator, as spd_sweep_inverse
-// but in complex arithmetic with plain transposes. Used for A = 1 - iK (K
-// real symmetric): its Hermitian part is the identity, so every Schur
-// complement has a positive definite Hermitian part and every pivot has a
-// positive real part -- no pivoting is needed. Step k, with column
-// u_i = a_ik and d = a_kk: a_ij -= (u_i / d) u_j, a_ik = u_i / d,
-// a_kk = -1/d; after all m steps the upper triangle holds -A^{-1}. The
-// threads that write column k + 1 also store it into the second half of u
-// (double buffer), so each step needs one barrier. u: shared scratch of 2m
-// complex values. Returns false (sh->bad set) on a zero or non-finite pivot.
+// Complex FP32 reciprocal (scaled against overflow) and product.
 __device__ __forceinline__ float2 crcp_f(float2 d)
 {
     const float s = fmaxf(fabsf(d.x), fabsf(d.y));
@@ -169,51 +159,6 @@ __device__ __forceinline__ float2 crcp_f(float2 d)
 __device__ __forceinline__ float2 cmul_f(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-
-__device__ bool csym_sweep_inverse(float2 *A, int ld, int m, float2 *u, ElimShared *sh)
-{
-    const int tid = threadIdx.x;
-    constexpr int G = 8;                        // threads per pair of rows
-    const int ngroups = (m + 1) / 2;            // rows g and m-1-g share a group
-    for (int i = tid; i < m; i += NT) u[i] = A[i];   // column 0 = row 0
-    __syncthreads();
-    for (int k = 0; k < m; ++k) {
-        const float2 *uc = u + (k & 1) * m;
-        float2 *un = u + ((k + 1) & 1) * m;
-        const float2 d = uc[k];
-        if (!(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y)) {
-            if (tid == 0) sh->bad = 1;          // the same value in every thread
-            return false;
-        }
-        const float2 dinv = crcp_f(d);
-        for (int q = tid; q < ngroups * G; q += NT) {
-            const int g = q / G, t = q - (q / G) * G;
-            for (int h = 0; h < 2; ++h) {
-                const int i = h ? m - 1 - g : g;
-                if (h && i == g) break;
-                float2 *row = A + i * ld;
-                const float2 vi = cmul_f(uc[i], dinv);
-                for (int j = i + t; j < m; j += G) {
-                    float2 nv;
-                    if (i == k) {
-                        nv = (j == k) ? make_float2(-dinv.x, -dinv.y) : cmul_f(uc[j], dinv);
-                    } else if (j == k) {
-                        nv = vi;
-                    } else {
-                        const float2 a = row[j], uj = uc[j];
-                        nv = make_float2(fmaf(-vi.x, uj.x, fmaf(vi.y, uj.y, a.x)),
-                                         fmaf(-vi.x, uj.y, fmaf(-vi.y, uj.x, a.y)));
-                    }
-                    row[j] = nv;
-                    if (i == k + 1) un[j] = nv;
-                    else if (j == k + 1) un[i] = nv;
-                }
-            }
-        }
-        __syncthreads();
-    }
-    return true;
 }
 
 // Row-wise upper-triangle index q -> (p, r), p <= r < m.
@@ -325,36 +270,6 @@ __device__ bool t_omega(const PwDev &pw, double x, const double *Kp, int kld, do
         om[q] += g * s;
     }
     return true;
-}
-
-// Step (d) from W = -(1 - iK)^{-1} (upper triangle of the complex symmetric
-// no x no matrix in Wm, row stride wld, as csym_sweep_inverse leaves it):
-// T = 2iK(1 - iK)^{-1} = 2(1 - iK)^{-1} - 2 = -2(W + 1), so
-// |T_ab|^2 = 4 |W_ab + delta_ab|^2, accumulated in FP64 into Omega as in
-// t_omega (one thread per level pair, fixed order).
-__device__ void omega_from_w(const PwDev &pw, double x, const float2 *Wm, int wld, const int *open_pos,
-                             double *om)
-{
-    const int nl = pw.n_levels;
-    const int npair = nl * (nl + 1) / 2;
-    const double g = pw.g;
-    for (int q = threadIdx.x; q < npair; q += NT) {
-        int I, J;
-        tri_pair(q, nl, I, J);
-        if (!(x - pw.lev_thr[I] > 0.0) || !(x - pw.lev_thr[J] > 0.0)) continue;
-        double s = 0.0;
-        for (int ia = pw.lev_start[I]; ia < pw.lev_start[I + 1]; ++ia) {
-            const int pa0 = open_pos[pw.lev_chan[ia]];
-            for (int ib = pw.lev_start[J]; ib < pw.lev_start[J + 1]; ++ib) {
-                const int pb0 = open_pos[pw.lev_chan[ib]];
-                const int pa = min(pa0, pb0), pb = max(pa0, pb0);
-                const float2 wv = Wm[pa * wld + pb];
-                const double re = (double)wv.x + ((pa == pb) ? 1.0 : 0.0), im = (double)wv.y;
-                s += 4.0 * (re * re + im * im);
-            }
-        }
-        om[q] += g * s;
-    }
 }
 
 }  // namespace

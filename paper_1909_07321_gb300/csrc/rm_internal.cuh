@@ -74,6 +74,11 @@ struct Opts {
 
 // ---- launchers (each returns cudaGetLastError() of its launch) ----------
 
+// FP32 matching and T step (direct mode, n <= solve_small_max_n()),
+// register-tiled; launch_solve_small forwards f32 launches here.
+cudaError_t launch_solve_f32(const PwDev &pw, const double *E, int nE, const ChanFn *cf, const double *R,
+                             int *status, double *K_out, int *n_open_out, double *omega, int n_tri,
+                             const int *deep_ws, int pass, cudaStream_t s);
 // mqdt != 0: closed channels in the quantum-defect set get CH_MQDT data.
 // deep_ws (or nullptr): the list written by launch_chanfn_deep_mark; the
 // listed deep pairs are then left to launch_chanfn_deep.

@@ -24,12 +24,8 @@
 // triangle: X is symmetric). Then for target levels I <= J, one thread owns
 // Omega_IJ(E) and adds g sum_{a in I, b in J} |T_ab|^2 in a fixed order, so
 // the accumulation is deterministic (no atomics).
-// The FP32 variant (mixed-precision path) instead inverts 1 - iK in complex
-// FP32 arithmetic, T = 2(1 - iK)^{-1} - 2, which needs no product with K and
-// works with the conditioning of 1 - iK (that of 1 + K^2 is its square).
+// The FP32 variant of the mixed-precision path is solve_f32.cu.
 #include <math.h>
-
-#include <type_traits>
 
 #include "dense_smem.cuh"
 #include "rm_internal.cuh"
@@ -37,29 +33,6 @@
 namespace rmgb {
 namespace {
 
-// Shared-memory bytes of the FP32 layout: region A holds the float augmented
-// matrix n x (2n + 1), later 1 - iK (complex float, n x (n + 1)); region B
-// the symmetrised K (n x n floats), later the sweep's column buffer (2n
-// complex floats).
-__host__ __device__ inline size_t f32_region_a(int n)
-{
-    const size_t aug = (size_t)n * (2 * n + 1) * sizeof(float);
-    const size_t w = (size_t)n * (n + 1) * sizeof(float2);
-    return ((aug > w ? aug : w) + 15) & ~(size_t)15;
-}
-
-__host__ __device__ inline size_t f32_region_b(int n)
-{
-    const size_t ks = (size_t)n * n * sizeof(float);
-    const size_t u = (size_t)2 * n * sizeof(float2);
-    return ((ks > u ? ks : u) + 15) & ~(size_t)15;
-}
-
-// F32 (direct mode only): the matching system is eliminated in FP32 and the
-// T step runs in FP32 complex arithmetic, T = 2(1 - iK)^{-1} - 2 with
-// (1 - iK)^{-1} from the complex symmetric sweep (no product with K, and the
-// conditioning of 1 - iK, not of 1 + K^2); Omega is accumulated in FP64.
-template <bool F32>
 __global__ void __launch_bounds__(NT) solve_small_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa,
     const double *__restrict__ Ra, int *__restrict__ status, double *__restrict__ K_out,
@@ -129,8 +102,8 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
 
     const int w = n + np;        // augmented width
     const int ld = w + 1;        // padded row stride
-    using Real = typename std::conditional<F32, float, double>::type;
-    Real *M = reinterpret_cast<Real *>(sm);
+    using Real = double;
+    Real *M = sm;
     const double a = pw.a, b = pw.b;
 
     // ---- assemble [A | B] -------------------------------------------------
@@ -172,44 +145,7 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
     double *Kp;   // K (no x no, symmetrised), row stride kld
     double *Mi;   // M = 1 + K^2, then M^{-1} (no x no), row stride mld
     int kld, mld;
-    if (F32) {
-        if (nq > 0) {   // FP32 matching is launched for direct mode only
-            if (tid == 0) status[e] = RM_ESINGULAR;
-            return;
-        }
-        // K symmetrised (float) into region B; then A = 1 - iK (complex
-        // float, upper triangle) over region A, inverted by the complex
-        // symmetric sweep, and Omega from -(1 - iK)^{-1}.
-        float *Ks = reinterpret_cast<float *>(reinterpret_cast<char *>(sm) + f32_region_a(n));
-        const int nsym0 = no * (no + 1) / 2;
-        for (int q = tid; q < nsym0; q += NT) {
-            int p, r;
-            tri_pair(q, no, p, r);
-            const float kpr = (float)M[(ncl + p) * ld + n + r];
-            const float krp = (float)M[(ncl + r) * ld + n + p];
-            if (K_out) {
-                K_out[(size_t)e * n * n + (size_t)p * n + r] = kpr;
-                K_out[(size_t)e * n * n + (size_t)r * n + p] = krp;
-            }
-            Ks[p * no + r] = 0.5f * (kpr + krp);
-        }
-        __syncthreads();
-        if (!omega) return;
-        float2 *Wm = reinterpret_cast<float2 *>(sm);
-        const int wld = no + 1;
-        for (int q = tid; q < nsym0; q += NT) {
-            int p, r;
-            tri_pair(q, no, p, r);
-            Wm[p * wld + r] = make_float2(p == r ? 1.0f : 0.0f, -Ks[p * no + r]);
-        }
-        __syncthreads();
-        if (!csym_sweep_inverse(Wm, wld, no, reinterpret_cast<float2 *>(Ks), &esh)) {
-            if (tid == 0) status[e] = RM_ESINGULAR;
-            return;
-        }
-        omega_from_w(pw, x, Wm, wld, open_pos, omega + (size_t)e * n_tri);
-        return;
-    } else if (nq == 0) {
+    if (nq == 0) {
         double *Md = reinterpret_cast<double *>(sm);
         // Direct mode (or no eliminated channel at this energy): K = K_u sits
         // in rows ncl.. / columns n.. of the augmented matrix; it is
@@ -274,11 +210,10 @@ __global__ void __launch_bounds__(NT) solve_small_kernel(
 int solve_small_max_n() { return SOLVE_SMALL_MAXN; }
 
 // Direct mode needs only the augmented matrix n x (2n + 1); MQDT mode also
-// holds K_u and the elimination system; the FP32 layout is described at
-// f32_region_a.
+// holds K_u and the elimination system.
 size_t solve_small_smem(int n, int mqdt, int f32)
 {
-    if (f32) return f32_region_a(n) + f32_region_b(n);
+    if (f32) return (size_t)n * n * sizeof(float);
     if (!mqdt) return (size_t)n * (2 * n + 1) * sizeof(double);
     const size_t aug = (size_t)n * (2 * n + 2);
     const size_t ks = (size_t)n * (n + 1);
@@ -292,22 +227,14 @@ cudaError_t launch_solve_small(const PwDev &pw, const double *E, int nE, const C
 {
     if (pw.n > SOLVE_SMALL_MAXN || (f32 && mqdt) || (f32 && ku_out)) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
-    const size_t smem = solve_small_smem(pw.n, mqdt, f32);
+    if (f32) return launch_solve_f32(pw, E, nE, cf, R, status, K_out, n_open_out, omega, n_tri, deep_ws, pass, s);
+    const size_t smem = solve_small_smem(pw.n, mqdt, 0);
     const int cap = chanfn_deep_cap();
-    cudaError_t err;
-    if (f32) {
-        err = cudaFuncSetAttribute(solve_small_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
-        if (err != cudaSuccess) return err;
-        solve_small_kernel<true><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
-                                                      n_tri, 0, deep_ws, cap, pass, nullptr, nullptr);
-    } else {
-        err = cudaFuncSetAttribute(solve_small_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem);
-        if (err != cudaSuccess) return err;
-        solve_small_kernel<false><<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega,
-                                                       n_tri, mqdt ? 1 : 0, deep_ws, cap, pass, ku_out, ku_np);
-    }
+    cudaError_t err =
+        cudaFuncSetAttribute(solve_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    solve_small_kernel<<<nE, NT, smem, s>>>(pw, E, cf, R, status, K_out, n_open_out, omega, n_tri, mqdt ? 1 : 0,
+                                            deep_ws, cap, pass, ku_out, ku_np);
     return cudaGetLastError();
 }
 
