@@ -5,15 +5,17 @@
 // (c) Matching (Section "Overview", Eq. match), as in solve_small.cu: with
 // the channels ordered closed first, then open (the set P),
 //   [diag(Ghat) - R diag(a Ghat' - b Ghat)] X = -[diag(S) - R diag(a S' - b S)] P,
-// K = X[P rows]. Thread (ty, tx) holds rows ty + 16 i and columns tx + 16 j
-// of the n x (n + n_o) augmented matrix. Gauss-Jordan elimination with
+// K = X[P rows]. Thread (tx, ty) = (tid / 16, tid % 16) holds rows ty + 16 i
+// and columns tx + 16 j of the n x (n + n_o) augmented matrix, so the 16
+// owners of a column form one half-warp. Gauss-Jordan elimination with
 // partial pivoting, the pivot rows left in place (implicit pivoting): for
-// column c the owners publish the column, every warp finds the same pivot
-// row p among the rows not yet used (largest magnitude, lowest index on
-// ties), the owners of row p publish it, and every other row r (used or not)
-// takes a_rj -= (a_rc / a_pc) a_pj for j > c. After n columns the unknowns
-// are x_c = a_{p(c), rhs} / a_{p(c), c}, with no back-substitution; only the
-// pivot column and row pass through shared memory.
+// column c its half-warp finds the pivot row p among the rows not yet used
+// (largest magnitude, lowest index on ties) by shuffles and publishes the
+// column and p; after one barrier every thread takes the pivot row's values
+// for its columns by a shuffle from the lane of its own half-warp that holds
+// row p, and every other row r (used or not) takes a_rj -= (a_rc / a_pc) a_pj
+// for j > c. After n columns the unknowns are x_c = a_{p(c), rhs} / a_{p(c), c},
+// with no back-substitution.
 //
 // (d) T = 2iK(1 - iK)^{-1} = 2(1 - iK)^{-1} - 2 (Section "Glossary of
 // terms"): 1 - iK (complex, K symmetrised) in registers in the same 16 x 16
@@ -35,8 +37,21 @@ namespace {
 constexpr int G16 = 16;                          // thread grid 16 x 16
 constexpr int MAXN = SOLVE_SMALL_MAXN;
 
+// Element k of a register array for an index k that is the same in every
+// thread of the warp: a uniform branch per case keeps the array in
+// registers (a runtime subscript would move it to local memory).
+template <int N, typename T>
+__device__ __forceinline__ T pick(const T (&v)[N], int k)
+{
+    T r = v[0];
+#pragma unroll
+    for (int q = 1; q < N; ++q)
+        if (k == q) r = v[q];
+    return r;
+}
+
 template <int TR, int TC>
-__global__ void __launch_bounds__(NT) solve_f32_kernel(
+__global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa, const double *__restrict__ Ra,
     int *__restrict__ status, double *__restrict__ K_out, int *__restrict__ n_open_out,
     double *__restrict__ omega, int n_tri, const int *__restrict__ deep_ws, int deep_cap, int pass)
@@ -46,24 +61,27 @@ __global__ void __launch_bounds__(NT) solve_f32_kernel(
         const bool deferred = deep_ws[0] <= deep_cap && deep_ws[1 + deep_cap + blockIdx.x] != 0;
         if (pass == 0 ? deferred : !deferred) return;
     }
-    extern __shared__ float Pm[];                 // K, later |T|^2 (n_o x n_o)
+    extern __shared__ double dsm[];               // [packed R of this energy][K, later |T|^2 (n_o x n_o)]
+    double *Rs = dsm;
+    float *Pm = reinterpret_cast<float *>(dsm + tri_ld(pw.n));
     __shared__ int col_chan[MAXN];                // unknown column -> channel
     __shared__ int open_pos[MAXN];                // channel -> position in P (-1: closed)
     __shared__ double colv[MAXN], dgv[MAXN];      // unknown column: a Ghat' - b Ghat, Ghat
     __shared__ double rsv[MAXN], rss[MAXN];       // right-hand side k: a S' - b S, S
     __shared__ int kind_s[MAXN];
     __shared__ float colbuf[2][G16 * TR];
-    __shared__ float rowbuf[2][G16 * TC];
-    __shared__ int done_s[G16 * TR];
+    __shared__ int pbuf[2];
     __shared__ int rowpos[G16 * TR];
     __shared__ float pivval[MAXN];
     __shared__ float2 ucol[2][G16 * TR];
+    __shared__ double lev_thr_s[MAXN];
+    __shared__ int lev_start_s[MAXN + 1], lev_chan_s[MAXN];
     __shared__ int s_no, s_np;
 
     const int e = blockIdx.x;
     const int n = pw.n;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ty = tid >> 4, tx = tid & 15;
+    const int tx = tid >> 4, ty = tid & 15;
     const double x = E[e];
     const ChanFn *cf = cfa + (size_t)e * n;
     const double *Rp = Ra + (size_t)e * tri_ld(n);
@@ -79,11 +97,21 @@ __global__ void __launch_bounds__(NT) solve_f32_kernel(
     // ---- channel order: closed first, then P (open), by warp prefix counts
     for (int i = tid; i < n; i += NT) kind_s[i] = cf[i].kind;
     for (int r = tid; r < G16 * TR; r += NT) {
-        done_s[r] = 0;
         ucol[0][r] = make_float2(0.0f, 0.0f);
         ucol[1][r] = make_float2(0.0f, 0.0f);
     }
+    // R of this energy and the level tables, by coalesced loads
+    for (int q = tid; q < tri_ld(n); q += NT) Rs[q] = Rp[q];
+    const int nl = pw.n_levels;
+    const bool lev_sm = nl <= MAXN;    // more levels than that (some without channels): read them in place
+    if (lev_sm) {
+        for (int q = tid; q < nl; q += NT) lev_thr_s[q] = pw.lev_thr[q];
+        for (int q = tid; q <= nl; q += NT) lev_start_s[q] = pw.lev_start[q];
+    }
+    for (int q = tid; q < n; q += NT) lev_chan_s[q] = pw.lev_chan[q];
     __syncthreads();
+    const double *lthr = lev_sm ? lev_thr_s : pw.lev_thr;
+    const int *lstart = lev_sm ? lev_start_s : pw.lev_start;
     if (warp == 0) {
         int ncl_run = 0, np_run = 0, no_run = 0;
         for (int base = 0; base < n; base += 32) {
@@ -145,13 +173,13 @@ __global__ void __launch_bounds__(NT) solve_f32_kernel(
             if (r < n && c < w) {
                 if (c < n) {
                     const int ch = col_chan[c];
-                    const double Rv = Rp[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)];
+                    const double Rv = Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)];
                     v = -Rv * colv[c];
                     if (r == ch) v += dgv[c];
                 } else {
                     const int k = c - n;
                     const int ch = col_chan[ncl + k];
-                    const double Rv = Rp[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)];
+                    const double Rv = Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)];
                     v = Rv * rsv[k];
                     if (r == ch) v -= rss[k];
                 }
@@ -161,72 +189,68 @@ __global__ void __launch_bounds__(NT) solve_f32_kernel(
     }
 
     // ---- Gauss-Jordan elimination, implicit partial pivoting -----------------
+    bool used[TR];
+#pragma unroll
+    for (int i = 0; i < TR; ++i) used[i] = false;
+    const unsigned hmask = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
     for (int c = 0; c < n; ++c) {
         const int buf = c & 1;
         if (tx == (c & 15)) {
+            // the column's half-warp: its values, then the pivot row by shuffles
             const int jc = c >> 4;
+            float best = -1.0f;
+            int bi = 0x7fffffff;
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
-                // select chains, not t[i][jc]: a runtime index would move the tile to local memory
-                float v = t[i][0];
-#pragma unroll
-                for (int j = 1; j < TC; ++j) v = (j == jc) ? t[i][j] : v;
+                const float v = pick<TC>(t[i], jc);
                 colbuf[buf][ty + G16 * i] = v;
+                const int r = ty + G16 * i;
+                const float av = fabsf(v);
+                if (r < n && !used[i] && (av > best || (av == best && r < bi))) {
+                    best = av;
+                    bi = r;
+                }
             }
+#pragma unroll
+            for (int off = 8; off > 0; off >>= 1) {
+                const float ob = __shfl_xor_sync(hmask, best, off, 16);
+                const int oi = __shfl_xor_sync(hmask, bi, off, 16);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (ty == 0) pbuf[buf] = bi;
         }
         __syncthreads();
-        // pivot: largest |a_rc| among unused rows, lowest row on ties (every warp alike)
-        float best = -1.0f;
-        int bi = 0x7fffffff;
-        for (int r = lane; r < n; r += 32) {
-            const float v = done_s[r] ? -1.0f : fabsf(colbuf[buf][r]);
-            if (v > best || (v == best && r < bi)) {
-                best = v;
-                bi = r;
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-            }
-        }
-        const int p = bi;
+        const int p = pbuf[buf];
         const float pv = colbuf[buf][p];
         if (!(fabsf(pv) > 0.0f) || !isfinite(pv)) {   // the same in every thread
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        if (ty == (p & 15)) {
-            const int ip = p >> 4;
-#pragma unroll
-            for (int j = 0; j < TC; ++j) {
-                float v = t[0][j];
-#pragma unroll
-                for (int i = 1; i < TR; ++i) v = (i == ip) ? t[i][j] : v;
-                const int col = tx + G16 * j;
-                if (col > c && col < w) rowbuf[buf][col] = v;
-            }
-        }
-        __syncthreads();
         if (tid == 0) {
-            done_s[p] = 1;
             rowpos[p] = c;
             pivval[c] = pv;
         }
         const float ipv = 1.0f / pv;
+        // row p's values for this thread's columns, from the lane of this
+        // half-warp that holds row p. Columns <= c and the padding take the
+        // update too: they are never read again (padding stays zero, as row
+        // p's padding is zero).
+        const int ip = p >> 4, src = (lane & 16) | (p & 15);
         float rb[TC];
 #pragma unroll
-        for (int j = 0; j < TC; ++j) {
-            const int col = tx + G16 * j;
-            rb[j] = (col > c && col < w) ? rowbuf[buf][col] : 0.0f;
+        for (int i = 0; i < TR; ++i) {
+            if (ip == i) {
+#pragma unroll
+                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(0xffffffffu, t[i][j], src);
+            }
         }
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
             const int r = ty + G16 * i;
+            if (r == p) used[i] = true;
             if (r < n && r != p) {
                 const float f = colbuf[buf][r] * ipv;
 #pragma unroll
@@ -279,9 +303,7 @@ __global__ void __launch_bounds__(NT) solve_f32_kernel(
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
                 const int r = ty + G16 * i;
-                float2 v = z[i][0];
-#pragma unroll
-                for (int j = 1; j < TR; ++j) v = (j == jk) ? z[i][j] : v;
+                const float2 v = pick<TR>(z[i], jk);
                 if (r < no) ucol[buf][r] = v;
             }
         }
@@ -300,17 +322,32 @@ __global__ void __launch_bounds__(NT) solve_f32_kernel(
         }
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
-            const int r = ty + G16 * i;
 #pragma unroll
             for (int j = 0; j < TR; ++j) {
-                const int c = tx + G16 * j;
                 float2 zz = z[i][j];
                 zz.x = fmaf(-ui[i].x, uj[j].x, fmaf(ui[i].y, uj[j].y, zz.x));
                 zz.y = fmaf(-ui[i].x, uj[j].y, fmaf(-ui[i].y, uj[j].x, zz.y));
-                if (c == k) zz = ui[i];
-                if (r == k) zz = (c == k) ? make_float2(-dinv.x, -dinv.y) : cmul_f(uj[j], dinv);
                 z[i][j] = zz;
             }
+        }
+        // column k: u_i / d; row k: u_j / d; the pivot: -1/d (uniform indices)
+        const int kk = k >> 4;
+        if (tx == (k & 15)) {
+#pragma unroll
+            for (int j = 0; j < TR; ++j)
+                if (kk == j) {
+#pragma unroll
+                    for (int i = 0; i < TR; ++i) z[i][j] = ui[i];
+                }
+        }
+        if (ty == (k & 15)) {
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+                if (kk == i) {
+#pragma unroll
+                    for (int j = 0; j < TR; ++j)
+                        z[i][j] = (tx + G16 * j == k) ? make_float2(-dinv.x, -dinv.y) : cmul_f(uj[j], dinv);
+                }
         }
     }
     __syncthreads();   // every read of K in Pm is done
@@ -329,19 +366,18 @@ __global__ void __launch_bounds__(NT) solve_f32_kernel(
     __syncthreads();
 
     // ---- Omega ----------------------------------------------------------------
-    const int nl = pw.n_levels;
     const int npair = nl * (nl + 1) / 2;
     const double g = pw.g;
     double *om = omega + (size_t)e * n_tri;
     for (int q = tid; q < npair; q += NT) {
         int I, J;
         tri_pair(q, nl, I, J);
-        if (!(x - pw.lev_thr[I] > 0.0) || !(x - pw.lev_thr[J] > 0.0)) continue;
+        if (!(x - lthr[I] > 0.0) || !(x - lthr[J] > 0.0)) continue;
         double s = 0.0;
-        for (int ia = pw.lev_start[I]; ia < pw.lev_start[I + 1]; ++ia) {
-            const int pa = open_pos[pw.lev_chan[ia]];
-            for (int ib = pw.lev_start[J]; ib < pw.lev_start[J + 1]; ++ib)
-                s += (double)Pm[pa * no + open_pos[pw.lev_chan[ib]]];
+        for (int ia = lstart[I]; ia < lstart[I + 1]; ++ia) {
+            const int pa = open_pos[lev_chan_s[ia]];
+            for (int ib = lstart[J]; ib < lstart[J + 1]; ++ib)
+                s += (double)Pm[pa * no + open_pos[lev_chan_s[ib]]];
         }
         om[q] += g * s;
     }
@@ -352,7 +388,7 @@ cudaError_t launch_tile(const PwDev &pw, const double *E, int nE, const ChanFn *
                         double *K_out, int *n_open_out, double *omega, int n_tri, const int *deep_ws, int pass,
                         cudaStream_t s)
 {
-    const size_t smem = (size_t)pw.n * pw.n * sizeof(float);
+    const size_t smem = (size_t)tri_ld(pw.n) * sizeof(double) + (size_t)pw.n * pw.n * sizeof(float);
     cudaError_t err =
         cudaFuncSetAttribute(solve_f32_kernel<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

@@ -184,7 +184,7 @@ def test_mixed_k_and_omega_bounds(rt, name, prec, form, sp):
     assert np.median(eK) <= K_MED, np.median(eK)
 
 
-@pytest.mark.parametrize("wl", ["small", "64ch"])
+@pytest.mark.parametrize("wl", ["small", "64ch", "80ch", "30ch"])
 def test_fp32_solve_alone_within_bound(rt, wl):
     """FP64 formation with the FP32 solve (matching elimination and complex
     T step) against the oracle: K within the elimination's propagated
@@ -196,10 +196,16 @@ def test_fp32_solve_alone_within_bound(rt, wl):
         pws, E = synth.workload_small(2000)
         pw = pws[0]
         Es = E[::5]
-    else:
+    elif wl == "64ch":
         pws, E = synth.workload_64ch()
         pw = pws[0]
         Es = _energies(pw, E, 120, 8)
+    else:
+        # 80 (30) channels: the 6 x 12 (2 x 4) register tiles
+        nch = 80 if wl == "80ch" else 30
+        pw = synth.random_pw(4800 + nch, nch, 30 * nch, z=2.0, a=15.0, e_max=2.0, sigma=0.05,
+                             pole_lo=-2.0, pole_hi=60.0, l_max=8)
+        Es = synth.midpoint_grid(0.01, 2.5, 4000)[::31]
     n = pw["W"].shape[0]
     with rmgb.Context(precision=0, solve_precision=1) as ctx:
         ctx.load_pw(0, pw)
