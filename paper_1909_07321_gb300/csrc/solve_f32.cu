@@ -69,8 +69,12 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     __shared__ double colv[MAXN], dgv[MAXN];      // unknown column: a Ghat' - b Ghat, Ghat
     __shared__ double rsv[MAXN], rss[MAXN];       // right-hand side k: a S' - b S, S
     __shared__ int kind_s[MAXN];
-    __shared__ float colbuf[2][G16 * TR];
+    __shared__ float colbuf[2][G16 * TR];         // multipliers a_rc / a_pc (0 for the pivot row)
     __shared__ int pbuf[2];
+    __shared__ float pvbuf[2];
+    __shared__ unsigned used_s[(G16 * TR + 31) / 32];
+    __shared__ float2 vcol[2][G16 * TR];
+    __shared__ float2 dbuf[2], dinvbuf[2];
     __shared__ int rowpos[G16 * TR];
     __shared__ float pivval[MAXN];
     __shared__ float2 ucol[2][G16 * TR];
@@ -99,7 +103,10 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     for (int r = tid; r < G16 * TR; r += NT) {
         ucol[0][r] = make_float2(0.0f, 0.0f);
         ucol[1][r] = make_float2(0.0f, 0.0f);
+        vcol[0][r] = make_float2(0.0f, 0.0f);
+        vcol[1][r] = make_float2(0.0f, 0.0f);
     }
+    if (tid < (G16 * TR + 31) / 32) used_s[tid] = 0u;
     // R of this energy and the level tables, by coalesced loads
     for (int q = tid; q < tri_ld(n); q += NT) Rs[q] = Rp[q];
     const int nl = pw.n_levels;
@@ -189,24 +196,22 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     }
 
     // ---- Gauss-Jordan elimination, implicit partial pivoting -----------------
-    bool used[TR];
-#pragma unroll
-    for (int i = 0; i < TR; ++i) used[i] = false;
     const unsigned hmask = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
     for (int c = 0; c < n; ++c) {
         const int buf = c & 1;
         if (tx == (c & 15)) {
-            // the column's half-warp: its values, then the pivot row by shuffles
+            // the column's half-warp: pivot row by shuffles, then the multipliers
             const int jc = c >> 4;
+            float v[TR];
             float best = -1.0f;
             int bi = 0x7fffffff;
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
-                const float v = pick<TC>(t[i], jc);
-                colbuf[buf][ty + G16 * i] = v;
+                v[i] = pick<TC>(t[i], jc);
                 const int r = ty + G16 * i;
-                const float av = fabsf(v);
-                if (r < n && !used[i] && (av > best || (av == best && r < bi))) {
+                const float av = fabsf(v[i]);
+                const bool used = (used_s[r >> 5] >> (r & 31)) & 1u;
+                if (r < n && !used && (av > best || (av == best && r < bi))) {
                     best = av;
                     bi = r;
                 }
@@ -220,24 +225,33 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
                     bi = oi;
                 }
             }
-            if (ty == 0) pbuf[buf] = bi;
+            const int p = bi < n ? bi : 0;
+            const float pv = __shfl_sync(hmask, pick<TR>(v, p >> 4), p & 15, 16);
+            const float ipv = 1.0f / pv;
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                const int r = ty + G16 * i;
+                colbuf[buf][r] = (r == p) ? 0.0f : v[i] * ipv;
+            }
+            if (ty == 0) {
+                pbuf[buf] = p;
+                pvbuf[buf] = pv;
+                used_s[p >> 5] |= 1u << (p & 31);
+                rowpos[p] = c;
+                pivval[c] = pv;
+            }
         }
         __syncthreads();
         const int p = pbuf[buf];
-        const float pv = colbuf[buf][p];
+        const float pv = pvbuf[buf];
         if (!(fabsf(pv) > 0.0f) || !isfinite(pv)) {   // the same in every thread
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        if (tid == 0) {
-            rowpos[p] = c;
-            pivval[c] = pv;
-        }
-        const float ipv = 1.0f / pv;
         // row p's values for this thread's columns, from the lane of this
         // half-warp that holds row p. Columns <= c and the padding take the
         // update too: they are never read again (padding stays zero, as row
-        // p's padding is zero).
+        // p's padding is zero); the pivot row's multiplier is zero.
         const int ip = p >> 4, src = (lane & 16) | (p & 15);
         float rb[TC];
 #pragma unroll
@@ -249,13 +263,9 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
         }
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
-            const int r = ty + G16 * i;
-            if (r == p) used[i] = true;
-            if (r < n && r != p) {
-                const float f = colbuf[buf][r] * ipv;
+            const float f = colbuf[buf][ty + G16 * i];
 #pragma unroll
-                for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f, rb[j], t[i][j]);
-            }
+            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f, rb[j], t[i][j]);
         }
     }
     __syncthreads();
@@ -298,26 +308,40 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     }
     for (int k = 0; k < no; ++k) {
         const int buf = k & 1;
+        const int kk = k >> 4;
         if (tx == (k & 15)) {
-            const int jk = k >> 4;
+            // column k's half-warp: u, the pivot d = u_k, and v = u / d
+            float2 u[TR];
+#pragma unroll
+            for (int i = 0; i < TR; ++i) u[i] = pick<TR>(z[i], kk);
+            const float2 uk = pick<TR>(u, kk);
+            float2 d;
+            d.x = __shfl_sync(hmask, uk.x, k & 15, 16);
+            d.y = __shfl_sync(hmask, uk.y, k & 15, 16);
+            const float2 dinv = crcp_f(d);
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
                 const int r = ty + G16 * i;
-                const float2 v = pick<TR>(z[i], jk);
-                if (r < no) ucol[buf][r] = v;
+                if (r < no) {
+                    ucol[buf][r] = u[i];
+                    vcol[buf][r] = cmul_f(u[i], dinv);
+                }
+            }
+            if (ty == 0) {
+                dbuf[buf] = d;
+                dinvbuf[buf] = dinv;
             }
         }
         __syncthreads();
-        const float2 d = ucol[buf][k];
+        const float2 d = dbuf[buf];
         if (!(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y)) {
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        const float2 dinv = crcp_f(d);
-        float2 ui[TR], uj[TR];
+        float2 vi[TR], uj[TR];
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
-            ui[i] = cmul_f(ucol[buf][ty + G16 * i], dinv);     // v_i = u_i / d
+            vi[i] = vcol[buf][ty + G16 * i];
             uj[i] = ucol[buf][tx + G16 * i];
         }
 #pragma unroll
@@ -325,28 +349,31 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
 #pragma unroll
             for (int j = 0; j < TR; ++j) {
                 float2 zz = z[i][j];
-                zz.x = fmaf(-ui[i].x, uj[j].x, fmaf(ui[i].y, uj[j].y, zz.x));
-                zz.y = fmaf(-ui[i].x, uj[j].y, fmaf(-ui[i].y, uj[j].x, zz.y));
+                zz.x = fmaf(-vi[i].x, uj[j].x, fmaf(vi[i].y, uj[j].y, zz.x));
+                zz.y = fmaf(-vi[i].x, uj[j].y, fmaf(-vi[i].y, uj[j].x, zz.y));
                 z[i][j] = zz;
             }
         }
-        // column k: u_i / d; row k: u_j / d; the pivot: -1/d (uniform indices)
-        const int kk = k >> 4;
+        // column k: u_i / d; row k: u_j / d (= v_j, the matrix being
+        // symmetric); the pivot: -1/d (uniform indices)
         if (tx == (k & 15)) {
 #pragma unroll
             for (int j = 0; j < TR; ++j)
                 if (kk == j) {
 #pragma unroll
-                    for (int i = 0; i < TR; ++i) z[i][j] = ui[i];
+                    for (int i = 0; i < TR; ++i) z[i][j] = vi[i];
                 }
         }
         if (ty == (k & 15)) {
+            const float2 dinv = dinvbuf[buf];
 #pragma unroll
             for (int i = 0; i < TR; ++i)
                 if (kk == i) {
 #pragma unroll
-                    for (int j = 0; j < TR; ++j)
-                        z[i][j] = (tx + G16 * j == k) ? make_float2(-dinv.x, -dinv.y) : cmul_f(uj[j], dinv);
+                    for (int j = 0; j < TR; ++j) {
+                        const int c = tx + G16 * j;
+                        z[i][j] = (c == k) ? make_float2(-dinv.x, -dinv.y) : vcol[buf][c];
+                    }
                 }
         }
     }
