@@ -209,7 +209,7 @@ def _solve_flops(n, n_open, f32):
 # counted from the kernel.
 CHANFN_OPS = {"cf1": 17, "cf2_fwd": 28, "cf2_bwd": 15, "open_l": 90, "open_fixed": 130,
               "closed_fwd": 14, "closed_bwd": 10, "ladder": 36, "closed_fixed": 70,
-              "thr_interp": 16 * 10 + 40}
+              "thr_interp": 16 * 10 + 40, "open_table": 4 * 2 * 11 + 60}
 CF2_FAST_DEPTH = 32   # CF2 settling within this many forward steps has no backward pass
 
 
@@ -231,7 +231,11 @@ def _chanfn_ops(work):
     # channel's table (a reciprocal and 5 FMAs per node) and A(eps, l)
     ti = w[w[:, 0] == 3]
     ops_thr = c["thr_interp"] * ti.shape[0] + 2.0 * ti[:, 3].sum()
-    return float(ops_open.sum() + ops_closed.sum() + ops_thr)
+    # open pairs from the channel's Chebyshev table: Clenshaw for four
+    # 12-term series, the segment and A(eps, l)
+    to = w[w[:, 0] == 4]
+    ops_tab = c["open_table"] * to.shape[0] + 2.0 * to[:, 3].sum()
+    return float(ops_open.sum() + ops_closed.sum() + ops_thr + ops_tab)
 
 
 def run_serving(args, prec):

@@ -151,9 +151,13 @@ int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const double *E_k,
  * energy-analytic channel quantities at 16 energies straddling its
  * threshold, from which step (b) interpolates pairs within a few node
  * spacings of the threshold instead of running continued fractions whose
- * length grows as 1/|E - e_i| (rm_load_poles recomputes the tables when the
- * channels are already set). Synchronous. Errors: RM_EINVAL, RM_ENOTLOADED,
- * RM_ENOMEM, RM_ECUDA. */
+ * length grows as 1/|E - e_i|, and its open-side table: Chebyshev expansions
+ * (12 terms) of the channel quantities in k = sqrt(E - e_i) on segments of
+ * width 0.9 / a from there to 16 Ry above threshold, each checked against
+ * direct values; open pairs in that range are evaluated from it (tables
+ * that fail a check are not used). rm_load_poles recomputes the tables when
+ * the channels are already set. Synchronous. Errors: RM_EINVAL,
+ * RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
 int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, double z,
                     const int *level, int n_levels, double g_weight);
 
@@ -233,8 +237,9 @@ int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *E, double *
  * [n_E][n_ch][4] ints): {kind, CF1 iterations, CF2 forward iterations n2, l
  * steps}, kind 0 = open (CF1 at l, CF2 at l = 0, l downward and upward
  * recurrence steps), 1 = closed (its CF2 at L0, then l - L0 ladder steps),
- * 3 = near the threshold, interpolated from the channel's node table (no
- * continued fraction; the l field holds l), -1 = on a threshold. A CF2 with n2 > 32 is re-evaluated backwards from
+ * 3 = near the threshold, interpolated from the channel's node table, 4 =
+ * open, from the channel's Chebyshev table (neither runs a continued
+ * fraction; the l field holds l), -1 = on a threshold. A CF2 with n2 > 32 is re-evaluated backwards from
  * depth 2 n2 + 20; one with n2 <= 32 is taken from its forward value.
  * Asynchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ECUDA. */
 int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, int *work);

@@ -322,6 +322,7 @@ __device__ int regular_analytic(int l, double z, double eps, double r, double *f
 #endif
 constexpr int CHANFN_BS = RM_CHANFN_BS;   // threads per block of the channel kernel
 constexpr int CH_THR_INTERP = 3;          // work-record kind of an interpolated pair
+constexpr int CH_OPEN_TABLE = 4;          // work-record kind of an open pair from its table
 constexpr double CHANFN_DEEP_EPS = 2.5e-5;   // |eps| / max(z^2, 1) below this: a deep pair
 constexpr int CHANFN_DEEP_CAP = 1 << 14;     // capacity of the deep-pair list
 
@@ -461,6 +462,40 @@ __device__ __forceinline__ void thr_interp(const ThrNodes &T, double eps, double
     v[3] = num3 * id;
 }
 
+// Node spacing of a channel's near-threshold table: small against the
+// energy scale on which the channel functions at r = a change (~ sqrt(z) /
+// a^1.5) and against the distance z^2 / (l + 1)^2 to the nearest
+// singularity of g~ (at nu = l); the table covers |eps| < THR_ZONE h. A
+// table is used only if leave-one-out interpolation of its four innermost
+// nodes agrees with their values to THR_LOO_TOL (relative to each
+// quantity's largest node value). The open-side table of the channel starts
+// where that zone ends, at k0 = sqrt(THR_ZONE h).
+constexpr double THR_C1 = 0.0164, THR_C2 = 0.05, THR_ZONE = 4.0, THR_LOO_TOL = 1e-9;
+__device__ __forceinline__ double thr_spacing(int l, double z, double a)
+{
+    return fmin(THR_C1 * sqrt(z) / (a * sqrt(a)), THR_C2 * z * z / ((l + 1.0) * (l + 1.0)));
+}
+
+// The four open-side quantities of channel i at k from its table (segment
+// q, local coordinate u in [-1, 1]), by Clenshaw's recurrence.
+__device__ __forceinline__ void otab_eval(const PwDev &pw, int i, int q, double u, double v[4])
+{
+    const double *c = pw.otab + ((size_t)i * pw.otab_nseg + q) * 4 * OTAB_M;
+    double b1[4] = {0.0, 0.0, 0.0, 0.0}, b2[4] = {0.0, 0.0, 0.0, 0.0};
+    const double u2 = 2.0 * u;
+#pragma unroll 1
+    for (int m = OTAB_M - 1; m >= 1; --m) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const double b0 = fma(u2, b1[f], c[f * OTAB_M + m] - b2[f]);
+            b2[f] = b1[f];
+            b1[f] = b0;
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) v[f] = fma(u, b1[f], c[f * OTAB_M] - b2[f]);
+}
+
 // Channel data of pair idx = i nE + e.
 template <bool MQDT, bool STATS>
 __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int nE, const Opts &o,
@@ -475,6 +510,9 @@ __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int n
     const double a = pw.a, z = pw.z;
     ChanFn r = {0.0, 0.0, 0.0, 0.0, 0.0, CH_CLOSED, 0};
     int bad = RM_OK;
+    // k - k0 on the channel's open-side table (-1: no table)
+    const double kr = (eps > 0.0 && pw.otab && !pw.otab_bad[i]) ? sqrt(eps) - sqrt(THR_ZONE * thr_spacing(l, z, a))
+                                                                 : -1.0;
     if (fabs(eps) < o.eps_thr) {
         bad = RM_ETHRESHOLD;
     } else if (pw.thr && fabs(eps) < pw.thr[i].zone) {
@@ -512,6 +550,20 @@ __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int n
                 r.ghp = (th < 0.0 ? -thp : thp) * nrm;
             }
         }
+    } else if (kr >= 0.0 && kr < pw.otab_nseg * pw.otab_dk) {
+        // open, from the channel's table (k >= k0: nearer ones are in the
+        // near-threshold zone, handled above, or the table there was refused)
+        if (STATS) work[(size_t)e * n + i] = make_int4(CH_OPEN_TABLE, 0, 0, l);
+        const int q = max(0, min((int)floor(kr / pw.otab_dk), pw.otab_nseg - 1));
+        const double u = fma(2.0 / pw.otab_dk, kr - q * pw.otab_dk, -1.0);
+        double v[4];
+        otab_eval(pw, i, q, u, v);
+        const double sA = sqrt(a_factor(l, eps, z)), isA = 1.0 / sA;
+        r.s = v[0] * sA;
+        r.sp = v[1] * sA;
+        r.gh = v[2] * isA;
+        r.ghp = v[3] * isA;
+        r.kind = CH_OPEN;
     } else if (eps > 0.0) {
         int it1 = 0, d2 = 0;
         const int ok = open_channel(l, eps, z, a, &r.s, &r.sp, &r.gh, &r.ghp, &it1, &d2);
@@ -559,14 +611,6 @@ __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int n
     if (bad != RM_OK) atomicCAS(status + e, RM_OK, bad);
 }
 
-// Node spacing of a channel's table: small against the energy scale on
-// which the channel functions at r = a change (~ sqrt(z) / a^1.5) and
-// against the distance z^2 / (l + 1)^2 to the nearest singularity of g~ (at
-// nu = l); the table covers |eps| < THR_ZONE h. A table is used only if
-// leave-one-out interpolation of its four innermost nodes agrees with their
-// values to THR_LOO_TOL (relative to each quantity's largest node value).
-constexpr double THR_C1 = 0.0164, THR_C2 = 0.05, THR_ZONE = 4.0, THR_LOO_TOL = 1e-9;
-
 // One block of 32 threads per channel: threads 0-7 the closed-side nodes
 // (half-integer nu, descending, so x ascends), 8-15 the open side
 // (eps = h, 2h, ... 8h); thread 0 then forms the weights and checks them.
@@ -578,7 +622,7 @@ __global__ void __launch_bounds__(32) thr_nodes_kernel(PwDev pw, ThrNodes *__res
     const int i = blockIdx.x, t = threadIdx.x;
     const int l = pw.l[i];
     const double z = pw.z, a = pw.a;
-    const double h = fmin(THR_C1 * sqrt(z) / (a * sqrt(a)), THR_C2 * z * z / ((l + 1.0) * (l + 1.0)));
+    const double h = thr_spacing(l, z, a);
     if (t < THR_NODES) {
         double x, v[4] = {0.0, 0.0, 0.0, 0.0};
         int ok = 0;
@@ -711,6 +755,71 @@ __global__ void export_kernel(PwDev pw, const double *__restrict__ E, int nE,
     out[4 * i + 3] = open ? c.ghp : 0.0;
 }
 
+// Segment q of channel i's open-side table: the four quantities at the
+// OTAB_M Chebyshev points x_j = cos(pi (j + 1/2) / M) of k in [q dk, (q + 1)
+// dk) (continued fractions), their Chebyshev coefficients
+// c_m = (2/M) sum_j y_j cos(pi m (j + 1/2) / M) (c_0 halved), and a check of
+// the expansion against direct values at x = -0.5 and 0.5 (relative to the
+// segment's largest node value); a failure marks the channel bad.
+constexpr double OTAB_CHECK_TOL = 1e-11;
+__global__ void __launch_bounds__(64) open_table_kernel(PwDev pw, double *__restrict__ coef, int *__restrict__ bad)
+{
+    constexpr int M = OTAB_M;
+    __shared__ double ys[4][M + 2];
+    __shared__ double cs[4][M];
+    __shared__ int okn[M + 2];
+    const int q = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
+    const int l = pw.l[i];
+    const double z = pw.z, a = pw.a, dk = pw.otab_dk;
+    if (t < M + 2) {
+        const double x = t < M ? cospi((t + 0.5) / M) : (t == M ? -0.5 : 0.5);
+        const double k = sqrt(THR_ZONE * thr_spacing(l, z, a)) + dk * (q + 0.5 * (x + 1.0));
+        const double eps = k * k;
+        double v[4];
+        int it1, d2;
+        int ok = open_channel(l, eps, z, a, &v[0], &v[1], &v[2], &v[3], &it1, &d2);
+        const double sA = sqrt(a_factor(l, eps, z));
+        v[0] /= sA;
+        v[1] /= sA;
+        v[2] *= sA;
+        v[3] *= sA;
+        for (int f = 0; f < 4; ++f) {
+            ok = ok && isfinite(v[f]);
+            ys[f][t] = v[f];
+        }
+        okn[t] = ok;
+    }
+    __syncthreads();
+    if (t < 4 * M) {
+        const int f = t / M, m = t - (t / M) * M;
+        double c = 0.0;
+        for (int j = 0; j < M; ++j) c = fma(ys[f][j], cospi(m * (j + 0.5) / M), c);
+        c *= 2.0 / M;
+        if (m == 0) c *= 0.5;
+        cs[f][m] = c;
+        coef[((size_t)i * pw.otab_nseg + q) * 4 * M + f * M + m] = c;
+    }
+    __syncthreads();
+    if (t < 8) {
+        const int f = t & 3, h = t >> 2;
+        const double x = h ? 0.5 : -0.5;
+        double b1 = 0.0, b2 = 0.0;
+        for (int m = M - 1; m >= 1; --m) {
+            const double b0 = fma(2.0 * x, b1, cs[f][m] - b2);
+            b2 = b1;
+            b1 = b0;
+        }
+        const double val = fma(x, b1, cs[f][0] - b2);
+        double mx = 0.0;
+        bool ok = okn[M + h];
+        for (int j = 0; j < M; ++j) {
+            mx = fmax(mx, fabs(ys[f][j]));
+            ok = ok && okn[j];
+        }
+        if (!ok || !(fabs(val - ys[f][M + h]) <= OTAB_CHECK_TOL * mx)) bad[i] = 1;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
@@ -754,6 +863,19 @@ cudaError_t launch_chanfn_deep(const PwDev &pw, const double *E, int nE, const O
 int chanfn_deep_cap() { return CHANFN_DEEP_CAP; }
 
 double chanfn_deep_eps(double z) { return CHANFN_DEEP_EPS * fmax(z * z, 1.0); }
+
+cudaError_t launch_open_table(const PwDev &pw, double *coef, int *bad, cudaStream_t s)
+{
+    if (pw.n == 0 || pw.otab_nseg == 0) return cudaSuccess;
+    cudaError_t err = cudaMemsetAsync(bad, 0, sizeof(int) * (size_t)pw.n, s);
+    if (err != cudaSuccess) return err;
+    PwDev d = pw;
+    d.thr = nullptr;
+    d.otab = nullptr;
+    d.otab_bad = nullptr;
+    open_table_kernel<<<dim3(pw.otab_nseg, pw.n), 64, 0, s>>>(d, coef, bad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_thr_nodes(const PwDev &pw, ThrNodes *tab, cudaStream_t s)
 {

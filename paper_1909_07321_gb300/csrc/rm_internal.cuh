@@ -66,7 +66,19 @@ struct PwDev {
     const int *lev_chan;   // [n]
     const double *lev_thr; // [n_levels] threshold of each level (+inf if unused)
     const ThrNodes *thr = nullptr;  // [n] near-threshold tables (nullptr: none)
+    // open-side tables: Chebyshev coefficients of f = s / sqrt(A), f' = s' /
+    // sqrt(A), g~ = c sqrt(A), g~' = c' sqrt(A) in k = sqrt(eps) on segments
+    // [q dk, (q + 1) dk), q < otab_nseg: otab[((i nseg + q) 4 + f) OTAB_M + m];
+    // otab_bad[i] != 0: channel i's table failed its check (nullptr: none)
+    const double *otab = nullptr;
+    const int *otab_bad = nullptr;
+    double otab_dk = 0.0;
+    int otab_nseg = 0;
 };
+
+constexpr int OTAB_M = 12;            // Chebyshev nodes per open-side segment
+constexpr double OTAB_C = 0.9;        // segment width in k: OTAB_C / a
+constexpr double OTAB_EPS_MAX = 16.0; // Ry above threshold covered by the open-side tables
 
 struct Opts {
     double eps_thr, delta_pole, fnumin, nu_margin, kappa_a_max;
@@ -87,6 +99,9 @@ cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &
 // Near-threshold tables of the n channels (z > 0): computes tab[0..n) on the
 // stream; pw.thr is not read.
 cudaError_t launch_thr_nodes(const PwDev &pw, ThrNodes *tab, cudaStream_t s);
+// Open-side tables of the n channels (z > 0) for pw.otab_dk / pw.otab_nseg:
+// coefficients into coef, failures into bad[n] (zeroed here).
+cudaError_t launch_open_table(const PwDev &pw, double *coef, int *bad, cudaStream_t s);
 // Near-threshold (deep) pairs: deep_ws = [count][list of CAP pair indices][nE
 // energy marks], chanfn_deep_ws_bytes(nE) bytes. The mark launch zeroes it
 // and fills it; the deep launch evaluates the listed pairs. If the list

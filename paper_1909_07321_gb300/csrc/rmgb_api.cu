@@ -68,12 +68,17 @@ struct PwHost {
     // are not covered and go to the side stream
     DevBuf thr;
     bool use_deep = true;
+    // open-side tables (z > 0): coefficients, failure flags, geometry
+    DevBuf otab, otab_bad;
+    double otab_dk = 0.0;
+    int otab_nseg = 0;
     void release()
     {
         for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
-                          &Wh, &Wl, &thr})
+                          &Wh, &Wl, &thr, &otab, &otab_bad})
             d->release();
         use_deep = true;
+        otab_nseg = 0;
         loaded = channels = false;
         p_kind = -1;
         w_kind = -1;
@@ -97,6 +102,12 @@ struct PwHost {
         d.lev_chan = lev_chan.as<int>();
         d.lev_thr = lev_thr.as<double>();
         d.thr = thr.as<ThrNodes>();
+        if (otab_nseg > 0) {
+            d.otab = otab.as<double>();
+            d.otab_bad = otab_bad.as<int>();
+            d.otab_dk = otab_dk;
+            d.otab_nseg = otab_nseg;
+        }
         return d;
     }
 };
@@ -328,8 +339,25 @@ namespace {
 int build_thr(rm_ctx *ctx, PwHost &P)
 {
     P.thr.release();
+    P.otab.release();
+    P.otab_bad.release();
+    P.otab_nseg = 0;
     P.use_deep = true;
     if (!(P.z > 0.0) || P.n == 0) return RM_SUCCESS;
+    // open-side tables: segments of width OTAB_C / a in k up to OTAB_EPS_MAX Ry
+    {
+        const double dk = OTAB_C / P.a;
+        const int nseg = (int)std::ceil(std::sqrt(OTAB_EPS_MAX) / dk);
+        CK(P.otab.reserve(sizeof(double) * (size_t)P.n * nseg * 4 * OTAB_M));
+        CK(P.otab_bad.reserve(sizeof(int) * (size_t)P.n));
+        PwDev d = P.dev();
+        d.otab_dk = dk;
+        d.otab_nseg = nseg;
+        CK(launch_open_table(d, P.otab.as<double>(), P.otab_bad.as<int>(), ctx->stream));
+        ++ctx->launches;
+        P.otab_dk = dk;
+        P.otab_nseg = nseg;
+    }
     CK(P.thr.reserve(sizeof(ThrNodes) * (size_t)P.n));
     CK(launch_thr_nodes(P.dev(), P.thr.as<ThrNodes>(), ctx->stream));
     ++ctx->launches;

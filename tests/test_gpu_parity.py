@@ -276,9 +276,11 @@ def test_channel_work_counts(rt):
     h = np.minimum(0.0164 * np.sqrt(pw["z"]) / pw["a"] ** 1.5, 0.05 * pw["z"] ** 2 / (pw["l"] + 1.0) ** 2)
     near = eps < 4.0 * h[None, :]
     assert near.any() and (~near).any()
-    assert np.array_equal(w[..., 0], np.where(near, 3, np.where(open_, 0, 1)))
-    cf = ~near
-    assert (w[..., 1][open_ & cf] >= 1).all() and (w[..., 1][~open_] == 0).all()
+    # kind 4: open beyond the zone, from the channel's Chebyshev table (all
+    # energies here lie within its 16 Ry)
+    assert np.array_equal(w[..., 0], np.where(near, 3, np.where(open_, 4, 1)))
+    cf = w[..., 0] == 1
+    assert (w[..., 1][cf] == 0).all()
     assert (w[..., 2][cf] >= 2).all() and (w[..., 2] < 1 << 20).all()
-    assert (w[..., 1:3][near] == 0).all()
-    assert np.array_equal(w[..., 3][open_ | near], np.broadcast_to(pw["l"], open_.shape)[open_ | near])
+    assert (w[..., 1:3][~cf] == 0).all()
+    assert np.array_equal(w[..., 3][~cf], np.broadcast_to(pw["l"], open_.shape)[~cf])

@@ -139,3 +139,34 @@ def test_k_omega_near_thresholds(rt, mode):
                             np.all(np.abs(got - exp) <= 1e-9 * np.maximum(np.abs(exp), mx))):
                 bad.append(Es[m])
     assert not bad, bad[:10]
+
+
+@pytest.mark.parametrize("ci", range(len(CONFIGS) - 1))
+def test_open_tables_vs_oracle(rt, ci):
+    """Open pairs beyond the near-threshold zone come from the channel's
+    Chebyshev table (12 terms per k-segment of width 0.9 / a, up to 16 Ry):
+    random energies up to 15 Ry above the thresholds against the oracle."""
+    torch, rmgb = rt
+    z, a, ls = CONFIGS[ci]
+    pw = _pw(z, a, ls, 900 + ci)
+    rng = np.random.default_rng(77 + ci)
+    Es = np.sort(np.concatenate([rng.uniform(0.0, 2.0, 40), rng.uniform(2.0, 16.5, 40)]))
+    with rmgb.Context() as ctx:
+        ctx.load_pw(0, pw)
+        Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+        out = torch.zeros((Es.size, 4, 4), dtype=torch.float64, device="cuda")
+        st = torch.zeros(Es.size, dtype=torch.int32, device="cuda")
+        ctx.channel_functions(0, Ed, out, st)
+        w = torch.zeros((Es.size, 4, 4), dtype=torch.int32, device="cuda")
+        ctx.channel_work(0, Ed, w)
+        g = out.cpu().numpy()
+        w = w.cpu().numpy()
+        assert not st.cpu().numpy().any()
+    _check_channel_functions(g, Es, pw, ("open table",) + CONFIGS[ci])
+    eps = Es[:, None] - pw["e_thr"][None, :]
+    h = np.array([node_spacing(z, a, int(l)) for l in pw["l"]])
+    k0 = np.sqrt(THR_ZONE * h)[None, :]
+    nseg = np.ceil(4.0 / (0.9 / a))
+    inside = (eps > 0) & (np.sqrt(np.maximum(eps, 0)) - k0 >= 0) & (np.sqrt(np.maximum(eps, 0)) - k0 < nseg * 0.9 / a)
+    assert inside.sum() > 100
+    assert np.array_equal(w[..., 0] == 4, inside)
