@@ -152,7 +152,7 @@ __device__ __forceinline__ float2 crcp_f(float2 d)
 {
     const float s = fmaxf(fabsf(d.x), fabsf(d.y));
     const float xr = d.x / s, xi = d.y / s;
-    const float t = 1.0f / (s * fmaf(xr, xr, xi * xi));
+    const float t = __frcp_rn(s * fmaf(xr, xr, xi * xi));
     return make_float2(xr * t, -xi * t);
 }
 

@@ -10,8 +10,8 @@
 // owners of a column form one half-warp. Gauss-Jordan elimination with
 // partial pivoting, the pivot rows left in place (implicit pivoting): for
 // column c its half-warp finds the pivot row p among the rows not yet used
-// (largest magnitude, lowest index on ties) by shuffles and publishes the
-// column and p; after one barrier every thread takes the pivot row's values
+// (largest magnitude to 2^-17, lowest index among those) by one max-reduction
+// and publishes the multipliers and p; after one barrier every thread takes the pivot row's values
 // for its columns by a shuffle from the lane of its own half-warp that holds
 // row p, and every other row r (used or not) takes a_rj -= (a_rc / a_pc) a_pj
 // for j > c. After n columns the unknowns are x_c = a_{p(c), rhs} / a_{p(c), c},
@@ -61,13 +61,13 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
         const bool deferred = deep_ws[0] <= deep_cap && deep_ws[1 + deep_cap + blockIdx.x] != 0;
         if (pass == 0 ? deferred : !deferred) return;
     }
-    extern __shared__ double dsm[];               // [packed R of this energy][K, later |T|^2 (n_o x n_o)]
-    double *Rs = dsm;
-    float *Pm = reinterpret_cast<float *>(dsm + tri_ld(pw.n));
+    extern __shared__ float fsm[];                // [packed R of this energy][K, later |T|^2 (n_o x n_o)]
+    float *Rs = fsm;
+    float *Pm = fsm + tri_ld(pw.n);
     __shared__ int col_chan[MAXN];                // unknown column -> channel
     __shared__ int open_pos[MAXN];                // channel -> position in P (-1: closed)
-    __shared__ double colv[MAXN], dgv[MAXN];      // unknown column: a Ghat' - b Ghat, Ghat
-    __shared__ double rsv[MAXN], rss[MAXN];       // right-hand side k: a S' - b S, S
+    __shared__ float colv[MAXN], dgv[MAXN];       // unknown column: a Ghat' - b Ghat, Ghat
+    __shared__ float rsv[MAXN], rss[MAXN];        // right-hand side k: a S' - b S, S
     __shared__ int kind_s[MAXN];
     __shared__ float colbuf[2][G16 * TR];         // multipliers a_rc / a_pc (0 for the pivot row)
     __shared__ int pbuf[2];
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     }
     if (tid < (G16 * TR + 31) / 32) used_s[tid] = 0u;
     // R of this energy and the level tables, by coalesced loads
-    for (int q = tid; q < tri_ld(n); q += NT) Rs[q] = Rp[q];
+    for (int q = tid; q < tri_ld(n); q += NT) Rs[q] = (float)Rp[q];
     const int nl = pw.n_levels;
     const bool lev_sm = nl <= MAXN;    // more levels than that (some without channels): read them in place
     if (lev_sm) {
@@ -158,16 +158,16 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     const double a = pw.a, b = pw.b;
     for (int c = tid; c < n; c += NT) {
         const ChanFn cj = cf[col_chan[c]];
-        colv[c] = a * cj.ghp - b * cj.gh;
-        dgv[c] = cj.gh;
+        colv[c] = (float)(a * cj.ghp - b * cj.gh);
+        dgv[c] = (float)cj.gh;
         if (c >= ncl) {
-            rsv[c - ncl] = a * cj.sp - b * cj.s;
-            rss[c - ncl] = cj.s;
+            rsv[c - ncl] = (float)(a * cj.sp - b * cj.s);
+            rss[c - ncl] = (float)cj.s;
         }
     }
     __syncthreads();
 
-    // ---- assemble the tile of [A | B] ----------------------------------------
+    // ---- assemble the tile of [A | B] (FP32, as it is eliminated) -----------
     const int w = n + np;
     float t[TR][TC];
 #pragma unroll
@@ -176,22 +176,20 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
 #pragma unroll
         for (int j = 0; j < TC; ++j) {
             const int c = tx + G16 * j;
-            double v = 0.0;
+            float v = 0.0f;
             if (r < n && c < w) {
                 if (c < n) {
                     const int ch = col_chan[c];
-                    const double Rv = Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)];
-                    v = -Rv * colv[c];
+                    v = -Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)] * colv[c];
                     if (r == ch) v += dgv[c];
                 } else {
                     const int k = c - n;
                     const int ch = col_chan[ncl + k];
-                    const double Rv = Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)];
-                    v = Rv * rsv[k];
+                    v = Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)] * rsv[k];
                     if (r == ch) v -= rss[k];
                 }
             }
-            t[i][j] = (float)v;
+            t[i][j] = v;
         }
     }
 
@@ -203,31 +201,22 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             // the column's half-warp: pivot row by shuffles, then the multipliers
             const int jc = c >> 4;
             float v[TR];
-            float best = -1.0f;
-            int bi = 0x7fffffff;
+            // pivot: one max-reduction over keys |v| (low 7 mantissa bits
+            // replaced by 127 - r, so rows within 2^-17 of the largest
+            // magnitude tie and the lowest one wins); unused rows only
+            unsigned key = 0u;
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
                 v[i] = pick<TC>(t[i], jc);
                 const int r = ty + G16 * i;
-                const float av = fabsf(v[i]);
                 const bool used = (used_s[r >> 5] >> (r & 31)) & 1u;
-                if (r < n && !used && (av > best || (av == best && r < bi))) {
-                    best = av;
-                    bi = r;
-                }
+                const unsigned kv = (__float_as_uint(fabsf(v[i])) & ~0x7fu) | (unsigned)(127 - r);
+                if (r < n && !used && kv > key) key = kv;
             }
-#pragma unroll
-            for (int off = 8; off > 0; off >>= 1) {
-                const float ob = __shfl_xor_sync(hmask, best, off, 16);
-                const int oi = __shfl_xor_sync(hmask, bi, off, 16);
-                if (ob > best || (ob == best && oi < bi)) {
-                    best = ob;
-                    bi = oi;
-                }
-            }
-            const int p = bi < n ? bi : 0;
+            key = __reduce_max_sync(hmask, key);
+            const int p = key ? 127 - (int)(key & 0x7fu) : 0;
             const float pv = __shfl_sync(hmask, pick<TR>(v, p >> 4), p & 15, 16);
-            const float ipv = 1.0f / pv;
+            const float ipv = __frcp_rn(pv);
 #pragma unroll
             for (int i = 0; i < TR; ++i) {
                 const int r = ty + G16 * i;
@@ -415,7 +404,7 @@ cudaError_t launch_tile(const PwDev &pw, const double *E, int nE, const ChanFn *
                         double *K_out, int *n_open_out, double *omega, int n_tri, const int *deep_ws, int pass,
                         cudaStream_t s)
 {
-    const size_t smem = (size_t)tri_ld(pw.n) * sizeof(double) + (size_t)pw.n * pw.n * sizeof(float);
+    const size_t smem = ((size_t)tri_ld(pw.n) + (size_t)pw.n * pw.n) * sizeof(float);
     cudaError_t err =
         cudaFuncSetAttribute(solve_f32_kernel<TR, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
