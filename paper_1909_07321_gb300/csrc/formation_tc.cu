@@ -218,18 +218,45 @@ __global__ void split_p_kernel(PwDev pw, int kind, int Kpad, void *Ph, void *Pl)
     split_store(v, kind, Ph, Pl, (size_t)idx);
 }
 
-__global__ void split_d_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta,
-                               int kind, int Kpad, void *Dh, void *Dl)
+// D_k(E) = 1/(E_k - E) for |E_k - E| >= delta (else 0: those terms are
+// added in FP64 by near_pole_fixup_kernel, with the same FP64 test), split
+// hi + lo. The difference is formed in FP64 and rounded once to FP32, the
+// reciprocal taken in FP32 (correctly rounded): D carries FP32 precision
+// into the split either way. Thread: two consecutive poles of one energy
+// (Kpad is even); grid: (pole pairs, energies).
+template <int KIND>
+__global__ void split_d_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta, int Kpad,
+                               void *Dh, void *Dl)
 {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)nE * Kpad) return;
-    const int e = (int)(idx / Kpad), k = (int)(idx - (long long)e * Kpad);
-    double d = 0.0;
-    if (k < pw.N) {
-        const double den = pw.Ek[k] - E[e];
-        if (fabs(den) >= delta) d = 1.0 / den;
+    const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (k >= Kpad) return;
+    for (int e = blockIdx.y; e < nE; e += gridDim.y) {
+        const double x = E[e];
+        float d[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            d[h] = 0.0f;
+            if (k + h < pw.N) {
+                const double den = pw.Ek[k + h] - x;
+                if (fabs(den) >= delta) d[h] = __frcp_rn((float)den);
+            }
+        }
+        const size_t idx = (size_t)e * Kpad + k;
+        if (KIND == TC_BF16X3) {
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(d[0], d[1]);
+            const float2 hf = __bfloat1622float2(hi);
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(d[0] - hf.x, d[1] - hf.y);
+            *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(Dh) + idx) = hi;
+            *reinterpret_cast<__nv_bfloat162 *>(static_cast<__nv_bfloat16 *>(Dl) + idx) = lo;
+        } else {
+            uint32_t h0, h1;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h0) : "f"(d[0]));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h1) : "f"(d[1]));
+            const float2 hi = make_float2(__uint_as_float(h0), __uint_as_float(h1));
+            *reinterpret_cast<float2 *>(static_cast<float *>(Dh) + idx) = hi;
+            *reinterpret_cast<float2 *>(static_cast<float *>(Dl) + idx) = make_float2(d[0] - hi.x, d[1] - hi.y);
+        }
     }
-    split_store(d, kind, Dh, Dl, (size_t)idx);
 }
 
 // One warp per energy: the poles within delta of E (sorted E_k, binary
@@ -297,10 +324,12 @@ cudaError_t launch_split_p(const PwDev &pw, int kind, int Kpad, void *P_hi, void
 cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delta, int kind, int Kpad,
                            void *D_hi, void *D_lo, cudaStream_t s)
 {
-    const long long total = (long long)nE * Kpad;
-    if (total == 0) return cudaSuccess;
-    split_d_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(pw, E, nE, delta, kind, Kpad,
-                                                                    D_hi, D_lo);
+    if ((long long)nE * Kpad == 0) return cudaSuccess;
+    const dim3 grid((unsigned)((Kpad / 2 + 255) / 256), (unsigned)(nE < 65535 ? nE : 65535));
+    if (kind == TC_BF16X3)
+        split_d_kernel<TC_BF16X3><<<grid, 256, 0, s>>>(pw, E, nE, delta, Kpad, D_hi, D_lo);
+    else
+        split_d_kernel<TC_TF32X3><<<grid, 256, 0, s>>>(pw, E, nE, delta, Kpad, D_hi, D_lo);
     return cudaGetLastError();
 }
 
