@@ -259,13 +259,15 @@ __global__ void split_d_kernel(PwDev pw, const double *__restrict__ E, int nE, d
     }
 }
 
-// One warp per energy: the poles within delta of E (sorted E_k, binary
-// search), then every pair adds its FP64 terms.
-__global__ void near_pole_fixup_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta,
-                                       double *__restrict__ Rp)
+// Near-pole terms in FP64. One thread per energy finds the poles within
+// delta of E (sorted E_k, binary search) and, if there are any, appends the
+// energy and its pole range to a list; then one warp per listed energy adds
+// every pair's FP64 terms (lanes over j). Each energy is listed once, so the
+// result does not depend on the list order.
+__global__ void near_pole_range_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta,
+                                       int *__restrict__ count, int *__restrict__ list, int2 *__restrict__ range)
 {
-    const int e = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nE) return;
     const double x = E[e];
     int lo = 0, hi = pw.N;
@@ -273,24 +275,41 @@ __global__ void near_pole_fixup_kernel(PwDev pw, const double *__restrict__ E, i
         const int mid = (lo + hi) >> 1;
         if (pw.Ek[mid] <= x - delta) lo = mid + 1; else hi = mid;
     }
-    int k0 = lo, k1 = lo;
+    int k1 = lo;
     while (k1 < pw.N && pw.Ek[k1] < x + delta) ++k1;
     // same exclusion test as split_d_kernel
     bool any = false;
-    for (int k = k0; k < k1; ++k) any |= fabs(pw.Ek[k] - x) < delta;
+    for (int k = lo; k < k1; ++k) any |= fabs(pw.Ek[k] - x) < delta;
     if (!any) return;
+    const int slot = atomicAdd(count, 1);
+    list[slot] = e;
+    range[slot] = make_int2(lo, k1);
+}
+
+__global__ void near_pole_fixup_kernel(PwDev pw, const double *__restrict__ E, double delta,
+                                       const int *__restrict__ count, const int *__restrict__ list,
+                                       const int2 *__restrict__ range, double *__restrict__ Rp)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int cnt = *count;
     const int n = pw.n;
     const double h = 0.5 / pw.a;
-    double *Re = Rp + (size_t)e * tri_ld(n);
-    for (int i = 0; i < n; ++i) {
-        double *row = Re + tri_idx(i, i, n);
-        for (int j = i + lane; j < n; j += 32) {
-            double s = 0.0;
-            for (int k = k0; k < k1; ++k) {
-                const double den = pw.Ek[k] - x;
-                if (fabs(den) < delta) s += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+    for (int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < cnt; s += nw) {
+        const int e = list[s];
+        const int2 kr = range[s];
+        const double x = E[e];
+        double *Re = Rp + (size_t)e * tri_ld(n);
+        for (int i = 0; i < n; ++i) {
+            double *row = Re + tri_idx(i, i, n);
+            for (int j = i + lane; j < n; j += 32) {
+                double acc = 0.0;
+                for (int k = kr.x; k < kr.y; ++k) {
+                    const double den = pw.Ek[k] - x;
+                    if (fabs(den) < delta) acc += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+                }
+                row[j - i] += h * acc;
             }
-            row[j - i] += h * s;
         }
     }
 }
@@ -365,12 +384,22 @@ cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, double delta, double *Rp,
+size_t near_pole_ws_bytes(int nE) { return 16 + (size_t)nE * (sizeof(int) + sizeof(int2)); }
+
+cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, double delta, double *Rp, void *ws,
                                    cudaStream_t s)
 {
     if (nE == 0) return cudaSuccess;
-    const long long threads = (long long)nE * 32;
-    near_pole_fixup_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(pw, E, nE, delta, Rp);
+    int *count = static_cast<int *>(ws);
+    int2 *range = reinterpret_cast<int2 *>(static_cast<char *>(ws) + 16);
+    int *list = reinterpret_cast<int *>(range + nE);
+    cudaError_t err = cudaMemsetAsync(count, 0, sizeof(int), s);
+    if (err != cudaSuccess) return err;
+    near_pole_range_kernel<<<(unsigned)((nE + 255) / 256), 256, 0, s>>>(pw, E, nE, delta, count, list, range);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const int warps = nE < 4 * 152 * 8 ? nE : 4 * 152 * 8;
+    near_pole_fixup_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, s>>>(pw, E, delta, count, list, range, Rp);
     return cudaGetLastError();
 }
 

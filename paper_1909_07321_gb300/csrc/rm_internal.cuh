@@ -148,8 +148,11 @@ cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const
                              const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
                              int *err_flag, cudaStream_t s);
 // R_packed[e][p] += (1/2a) w_ik w_jk / (E_k - E_e) over poles with |E_k - E_e| < delta (FP64).
-cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, double delta,
-                                   double *Rp, cudaStream_t s);
+// ws: near_pole_ws_bytes(nE) bytes of device scratch (list of the energies
+// with poles within delta, and their pole ranges).
+size_t near_pole_ws_bytes(int nE);
+cudaError_t launch_near_pole_fixup(const PwDev &pw, const double *E, int nE, double delta, double *Rp, void *ws,
+                                   cudaStream_t s);
 // Per-energy formulation (formation_tc_energy.cu): R(E) = W diag(d(E)) W^T / 2a.
 int pe_max_n();
 // Workspace per energy: FP32 partial tiles of every K segment + d(E) in FP32

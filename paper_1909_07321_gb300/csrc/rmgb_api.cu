@@ -124,7 +124,7 @@ struct rm_ctx {
     std::vector<double> grid_host;
     DevBuf omega;
     // workspace
-    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep;
+    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep, wsNear;
     // coarse-mesh interpolation: node energies, statuses + orders, K_u, S_u, fine plan
     DevBuf wsQn, wsQst, wsQk, wsQs, wsQf, wsQc;
     // side stream for the deep channel pairs, with fork / join events
@@ -314,7 +314,7 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
     for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
-                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsQn,
+                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsNear, &ctx->wsQn,
                       &ctx->wsQst, &ctx->wsQk, &ctx->wsQs, &ctx->wsQf, &ctx->wsQc})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
@@ -607,9 +607,10 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
                         tri_ld(P.n), ctx->wsErr.as<int>(), ctx->stream));
     CK(prof_end(ctx, RM_PH_FORM));
     CK(prof_begin(ctx, RM_PH_FIXUP));
-    CK(launch_near_pole_fixup(d, E, nE, ctx->opts.delta_pole, R, ctx->stream));
+    CK(ctx->wsNear.reserve(near_pole_ws_bytes(nE)));
+    CK(launch_near_pole_fixup(d, E, nE, ctx->opts.delta_pole, R, ctx->wsNear.p, ctx->stream));
     CK(prof_end(ctx, RM_PH_FIXUP));
-    ctx->launches += 3;
+    ctx->launches += 4;
     return RM_SUCCESS;
 }
 
