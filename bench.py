@@ -521,12 +521,16 @@ def run_ours(args, rank, world, local_rank):
     if f32:
         fp32_peak = N_SM * 256.0 * sm_mhz * 1e6 / 1e12
         ach = fl32 / t_solve / 1e12
+        # DRAM bytes per launch from one ncu capture of this kernel on 2000
+        # energies of the same workload (60.0 MB read, 0.39 MB written),
+        # scaled to the launch's energies
+        traffic = (60.0e6 + 0.39e6) * (E.size / 2000.0) if n == 64 else None
         solve_roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                      "frac": ach / fp32_peak, "traffic": None,
-                      "kernel": "solve_small_kernel (FP32 elimination, FP32 complex T step)",
+                      "frac": ach / fp32_peak, "traffic": traffic,
+                      "kernel": "solve_f32_kernel (FP32 Gauss-Jordan, FP32 complex T sweep, register tiles)",
                       "peak_source": "FP32 128 FMA/clk/SM x 152 SMs at the sampled SM clock",
-                      "note": "one CTA per energy; bound by the per-column barriers of the "
-                              "elimination and the sweep, not by the FP32 pipe"}
+                      "note": "one CTA per energy, n + n_o barrier steps; ncu: barrier stalls dominate, "
+                              "FMA pipe 23% busy (bound by per-step latency, not by a pipe)"}
     else:
         ach = fl64 / t_solve / 1e12
         solve_roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
