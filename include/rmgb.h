@@ -101,6 +101,15 @@ typedef struct rm_opts {
                                is that of a perturbation of 1 - iK of Frobenius norm
                                <= n_open 2^-24 ||1 - iK||_F; Omega is accumulated in
                                FP64). Other cases run in FP64 whatever this asks */
+    int channel_tables;     /* step (b): 1 builds the per-channel tables
+                               (near-threshold interpolation, open- and closed-side
+                               Chebyshev expansions; see rm_set_channels) and
+                               evaluates pairs from them (to ~1e-12); 0 evaluates
+                               every pair by its continued fractions, as
+                               rm_k_matrices_noalloc does; -1 (default): 1 with a
+                               mixed-precision formation, 0 with FP64 (whose K is
+                               meant to match to 1e-9 even where the matching
+                               amplifies channel-function errors 1e4-fold) */
 } rm_opts;
 
 #define RM_SOLVER_AUTO    0
@@ -153,11 +162,14 @@ int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const double *E_k,
  * spacings of the threshold instead of running continued fractions whose
  * length grows as 1/|E - e_i|, and its open-side table: Chebyshev expansions
  * (12 terms) of the channel quantities in k = sqrt(E - e_i) on segments of
- * width 0.9 / a from there to 16 Ry above threshold, each checked against
- * direct values; open pairs in that range are evaluated from it (tables
- * that fail a check are not used). rm_load_poles recomputes the tables when
- * the channels are already set. Synchronous. Errors: RM_EINVAL,
- * RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
+ * width 0.9 / a from there to 16 Ry above threshold, and its closed-side
+ * table: expansions of the direction of (theta, a theta') in nu on cells of
+ * 0.25 (split into up to 16 sub-segments) from 16 Ry below threshold to the
+ * near-threshold zone; each is checked against direct values, and pairs are
+ * evaluated from a table only where it passed (elsewhere the continued
+ * fractions run). rm_opts.channel_tables decides whether any of this is done.
+ * rm_load_poles recomputes the tables when the channels are already set.
+ * Synchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
 int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, double z,
                     const int *level, int n_levels, double g_weight);
 

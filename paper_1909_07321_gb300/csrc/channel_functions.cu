@@ -48,6 +48,8 @@
 //   g = (f cos(pi nu) - theta-hat) / sin(pi nu),  g' likewise.
 #include <math.h>
 
+#include <cmath>
+
 #include "dd.cuh"
 #include "rcp.cuh"
 #include "rm_internal.cuh"
@@ -323,6 +325,7 @@ __device__ int regular_analytic(int l, double z, double eps, double r, double *f
 constexpr int CHANFN_BS = RM_CHANFN_BS;   // threads per block of the channel kernel
 constexpr int CH_THR_INTERP = 3;          // work-record kind of an interpolated pair
 constexpr int CH_OPEN_TABLE = 4;          // work-record kind of an open pair from its table
+constexpr int CH_CLOSED_TABLE = 5;        // work-record kind of a closed pair from its table
 constexpr double CHANFN_DEEP_EPS = 2.5e-5;   // |eps| / max(z^2, 1) below this: a deep pair
 constexpr int CHANFN_DEEP_CAP = 1 << 14;     // capacity of the deep-pair list
 
@@ -496,6 +499,26 @@ __device__ __forceinline__ void otab_eval(const PwDev &pw, int i, int q, double 
     for (int f = 0; f < 4; ++f) v[f] = fma(u, b1[f], c[f * OTAB_M] - b2[f]);
 }
 
+// The closed-side direction (theta, a theta') of channel i at nu from its
+// table (segment q, local coordinate u), by Clenshaw's recurrence.
+__device__ __forceinline__ void ctab_eval(const PwDev &pw, int i, int q, int sub, double u, double v[2])
+{
+    const double *c = pw.ctab + (((size_t)i * pw.ctab_nseg + q) * CTAB_SUB + sub) * 2 * OTAB_M;
+    double b1[2] = {0.0, 0.0}, b2[2] = {0.0, 0.0};
+    const double u2 = 2.0 * u;
+#pragma unroll 1
+    for (int m = OTAB_M - 1; m >= 1; --m) {
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const double b0 = fma(u2, b1[f], c[f * OTAB_M + m] - b2[f]);
+            b2[f] = b1[f];
+            b1[f] = b0;
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 2; ++f) v[f] = fma(u, b1[f], c[f * OTAB_M] - b2[f]);
+}
+
 // Channel data of pair idx = i nE + e.
 template <bool MQDT, bool STATS>
 __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int nE, const Opts &o,
@@ -513,6 +536,17 @@ __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int n
     // k - k0 on the channel's open-side table (-1: no table)
     const double kr = (eps > 0.0 && pw.otab && !pw.otab_bad[i]) ? sqrt(eps) - sqrt(THR_ZONE * thr_spacing(l, z, a))
                                                                  : -1.0;
+    // cell of the channel's closed-side table (-1: none, or a cell without
+    // coefficients); closed channels of the quantum-defect set take f and g
+    int cq = -1;
+    if (eps < 0.0 && pw.ctab && -eps >= THR_ZONE * thr_spacing(l, z, a) &&
+        !(MQDT && z / sqrt(-eps) >= fmax(l + o.nu_margin, o.fnumin) && sqrt(-eps) * a <= o.kappa_a_max)) {
+        const double nr = z / sqrt(-eps) - pw.ctab_nu_lo;
+        if (nr >= 0.0 && nr < pw.ctab_nseg * pw.ctab_dnu) {
+            const int q = min((int)floor(nr / pw.ctab_dnu), pw.ctab_nseg - 1);
+            if (pw.ctab_nsub[(size_t)i * pw.ctab_nseg + q] > 0) cq = q;
+        }
+    }
     if (fabs(eps) < o.eps_thr) {
         bad = RM_ETHRESHOLD;
     } else if (pw.thr && fabs(eps) < pw.thr[i].zone) {
@@ -570,6 +604,22 @@ __device__ void chanfn_pair(const PwDev &pw, const double *__restrict__ E, int n
         if (STATS) work[(size_t)e * n + i] = make_int4(CH_OPEN, it1, d2, l);
         if (!ok) bad = RM_ECF_NOCONV;
         else r.kind = CH_OPEN;
+    } else if (cq >= 0) {
+        // closed (decaying condition), from the channel's table
+        if (STATS) work[(size_t)e * n + i] = make_int4(CH_CLOSED_TABLE, 0, 0, l);
+        const double nr = z / sqrt(-eps) - pw.ctab_nu_lo;
+        const int q = cq;
+        const int ns = pw.ctab_nsub[(size_t)i * pw.ctab_nseg + q];
+        const double w = pw.ctab_dnu / ns;
+        const double fr = nr - q * pw.ctab_dnu;
+        const int sub = min((int)floor(fr / w), ns - 1);
+        const double u = fma(2.0 / w, fr - sub * w, -1.0);
+        double v[2];
+        ctab_eval(pw, i, q, sub, u, v);
+        // theta > 0, theta^2 + (a theta')^2 = 1
+        const double nrm = 1.0 / sqrt(fma(v[0], v[0], v[1] * v[1]));
+        r.gh = fabs(v[0]) * nrm;
+        r.ghp = (v[0] < 0.0 ? -v[1] : v[1]) * nrm / a;
     } else {
         double y;
         int d2 = 0, L0 = 0;
@@ -761,7 +811,7 @@ __global__ void export_kernel(PwDev pw, const double *__restrict__ E, int nE,
 // c_m = (2/M) sum_j y_j cos(pi m (j + 1/2) / M) (c_0 halved), and a check of
 // the expansion against direct values at x = -0.5 and 0.5 (relative to the
 // segment's largest node value); a failure marks the channel bad.
-constexpr double OTAB_CHECK_TOL = 1e-11;
+constexpr double OTAB_CHECK_TOL = 1e-12;
 __global__ void __launch_bounds__(64) open_table_kernel(PwDev pw, double *__restrict__ coef, int *__restrict__ bad)
 {
     constexpr int M = OTAB_M;
@@ -820,7 +870,132 @@ __global__ void __launch_bounds__(64) open_table_kernel(PwDev pw, double *__rest
     }
 }
 
+// Cell q of channel i's closed-side table: the direction (1, a L) of
+// (theta, a theta') at the OTAB_M Chebyshev points in nu of each of ns equal
+// sub-segments, made continuous along each (each node's sign chosen to agree
+// with its neighbour's), Chebyshev coefficients, and a check of the
+// expansion's direction against direct values at x = -0.6, 0.1 and 0.7 of
+// every sub-segment (sine of the angle between them within
+// CTAB_CHECK_TOL). ns = 1, 2, 4, 8, 16 in turn; the first that passes is
+// kept, and a cell that fails at 16 gets nsub = 0: its pairs keep the
+// continued fractions. The direction turns by about pi per unit nu, but
+// where r = a lies in the classically allowed region of the decaying
+// solution (kappa a of a few) it does so through narrow peaks of its rate
+// that no modest expansion holds; deeper, it is smooth. Cells on the near
+// side of the channel's near-threshold zone are never read and not computed.
+constexpr double CTAB_CHECK_TOL = 5e-13;
+__global__ void __launch_bounds__(128) closed_table_kernel(PwDev pw, double *__restrict__ coef,
+                                                            unsigned char *__restrict__ nsub)
+{
+    constexpr int M = OTAB_M, P = M + 3;
+    __shared__ double ys[CTAB_SUB][2][P];
+    __shared__ double cs[CTAB_SUB][2][M];
+    __shared__ int okn[CTAB_SUB][P];
+    __shared__ int pass;
+    const int q = blockIdx.x, i = blockIdx.y, t = threadIdx.x;
+    const int l = pw.l[i];
+    const double z = pw.z, a = pw.a;
+    const double nu0 = pw.ctab_nu_lo + q * pw.ctab_dnu;
+    const double nu_hi = z / sqrt(THR_ZONE * thr_spacing(l, z, a));
+    double *cq = coef + ((size_t)i * pw.ctab_nseg + q) * CTAB_SUB * 2 * M;
+    unsigned char *nq = nsub + (size_t)i * pw.ctab_nseg + q;
+    if (nu0 >= nu_hi) {
+        if (t == 0) *nq = 0;
+        return;
+    }
+    for (int ns = 1; ns <= CTAB_SUB; ns *= 2) {
+        const double w = pw.ctab_dnu / ns;
+        for (int k = t; k < ns * P; k += blockDim.x) {
+            const int sb = k / P, j = k - (k / P) * P;
+            const double x = j < M ? cospi((j + 0.5) / M) : (j == M ? -0.6 : (j == M + 1 ? 0.1 : 0.7));
+            const double nu = nu0 + w * (sb + 0.5 * (x + 1.0));
+            const double kap = z / nu;
+            double y = 0.0;
+            int d2, L0;
+            const int ok = closed_channel(l, -kap * kap, z, a, &y, &d2, &L0);
+            const double nrm = 1.0 / sqrt(1.0 + (a * y) * (a * y));
+            ys[sb][0][j] = nrm;
+            ys[sb][1][j] = a * y * nrm;
+            okn[sb][j] = ok && isfinite(y);
+        }
+        if (t == 0) pass = 1;
+        __syncthreads();
+        if (t < ns) {
+            for (int j = 1; j < M; ++j) {   // nodes in order of x: continuous signs
+                const double dot = ys[t][0][j] * ys[t][0][j - 1] + ys[t][1][j] * ys[t][1][j - 1];
+                if (dot < 0.0) {
+                    ys[t][0][j] = -ys[t][0][j];
+                    ys[t][1][j] = -ys[t][1][j];
+                }
+            }
+        }
+        __syncthreads();
+        for (int k = t; k < ns * 2 * M; k += blockDim.x) {
+            const int sb = k / (2 * M), r = k - (k / (2 * M)) * 2 * M, f = r / M, m = r - (r / M) * M;
+            double c = 0.0;
+            for (int j = 0; j < M; ++j) c = fma(ys[sb][f][j], cospi(m * (j + 0.5) / M), c);
+            c *= 2.0 / M;
+            if (m == 0) c *= 0.5;
+            cs[sb][f][m] = c;
+        }
+        __syncthreads();
+        for (int k = t; k < ns * 3; k += blockDim.x) {
+            const int sb = k / 3, h = k - (k / 3) * 3;
+            const double x = h == 0 ? -0.6 : (h == 1 ? 0.1 : 0.7);
+            double v[2];
+            for (int f = 0; f < 2; ++f) {
+                double b1 = 0.0, b2 = 0.0;
+                for (int m = M - 1; m >= 1; --m) {
+                    const double b0 = fma(2.0 * x, b1, cs[sb][f][m] - b2);
+                    b2 = b1;
+                    b1 = b0;
+                }
+                v[f] = fma(x, b1, cs[sb][f][0] - b2);
+            }
+            bool ok = okn[sb][M + h];
+            for (int j = 0; j < M; ++j) ok = ok && okn[sb][j];
+            const double nv = sqrt(v[0] * v[0] + v[1] * v[1]);
+            const double sn = fabs(v[0] * ys[sb][1][M + h] - v[1] * ys[sb][0][M + h]) / nv;
+            if (!ok || !(sn <= CTAB_CHECK_TOL)) pass = 0;
+        }
+        __syncthreads();
+        if (pass) {
+            for (int k = t; k < ns * 2 * M; k += blockDim.x) {
+                const int sb = k / (2 * M), r = k - (k / (2 * M)) * 2 * M;
+                cq[sb * 2 * M + r] = cs[sb][r / M][r - (r / M) * M];
+            }
+            if (t == 0) *nq = (unsigned char)ns;
+            return;
+        }
+        __syncthreads();
+    }
+    if (t == 0) *nq = 0;
+}
+
 }  // namespace
+
+double closed_table_nu_hi(double z, double a, int l_max)
+{
+    double nu = 0.0;
+    for (int l = 0; l <= l_max; ++l) {
+        const double h = std::fmin(THR_C1 * std::sqrt(z) / (a * std::sqrt(a)), THR_C2 * z * z / ((l + 1.0) * (l + 1.0)));
+        nu = std::fmax(nu, z / std::sqrt(THR_ZONE * h));
+    }
+    return nu;
+}
+
+cudaError_t launch_closed_table(const PwDev &pw, double *coef, unsigned char *nsub, cudaStream_t s)
+{
+    if (pw.n == 0 || pw.ctab_nseg == 0) return cudaSuccess;
+    PwDev d = pw;
+    d.thr = nullptr;
+    d.otab = nullptr;
+    d.otab_bad = nullptr;
+    d.ctab = nullptr;
+    d.ctab_nsub = nullptr;
+    closed_table_kernel<<<dim3(pw.ctab_nseg, pw.n), 128, 0, s>>>(d, coef, nsub);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_chanfn(const PwDev &pw, const double *E, int nE, const Opts &o, int mqdt,
                           ChanFn *cf, int *status, const int *deep_ws, cudaStream_t s)

@@ -74,11 +74,25 @@ struct PwDev {
     const int *otab_bad = nullptr;
     double otab_dk = 0.0;
     int otab_nseg = 0;
+    // closed-side tables: Chebyshev coefficients of the direction
+    // (theta, a theta') (unnormalised, continuous in energy) in
+    // nu = z / sqrt(-eps) on cells [nu_lo + q dnu, nu_lo + (q + 1) dnu),
+    // q < ctab_nseg, each split into ctab_nsub[i nseg + q] (1, 2, 4, 8 or 16)
+    // equal sub-segments (0: the cell has no coefficients):
+    // ctab[(((i nseg + q) CTAB_SUB + s) 2 + f) OTAB_M + m]
+    const double *ctab = nullptr;
+    const unsigned char *ctab_nsub = nullptr;
+    double ctab_nu_lo = 0.0, ctab_dnu = 0.0;
+    int ctab_nseg = 0;
 };
 
 constexpr int OTAB_M = 12;            // Chebyshev nodes per open-side segment
 constexpr double OTAB_C = 0.9;        // segment width in k: OTAB_C / a
 constexpr double OTAB_EPS_MAX = 16.0; // Ry above threshold covered by the open-side tables
+constexpr double CTAB_DNU = 0.25;     // closed-side cell width in nu
+constexpr int CTAB_SUB = 16;          // at most this many sub-segments per cell
+constexpr double CTAB_EPS_MIN = -16.0; // Ry below threshold covered by the closed-side tables
+constexpr int CTAB_MAX_SEG = 4096;    // at most this many closed-side segments per channel
 
 struct Opts {
     double eps_thr, delta_pole, fnumin, nu_margin, kappa_a_max;
@@ -102,6 +116,13 @@ cudaError_t launch_thr_nodes(const PwDev &pw, ThrNodes *tab, cudaStream_t s);
 // Open-side tables of the n channels (z > 0) for pw.otab_dk / pw.otab_nseg:
 // coefficients into coef, failures into bad[n] (zeroed here).
 cudaError_t launch_open_table(const PwDev &pw, double *coef, int *bad, cudaStream_t s);
+// Closed-side tables of the n channels (z > 0) for pw.ctab_nu_lo / ctab_dnu /
+// ctab_nseg: coefficients into coef, sub-segment counts into nsub (0 for a
+// cell that failed its check).
+cudaError_t launch_closed_table(const PwDev &pw, double *coef, unsigned char *nsub, cudaStream_t s);
+// Largest nu any channel's closed-side table must reach (its near-threshold
+// zone edge), for the segment count.
+double closed_table_nu_hi(double z, double a, int l_max);
 // Near-threshold (deep) pairs: deep_ws = [count][list of CAP pair indices][nE
 // energy marks], chanfn_deep_ws_bytes(nE) bytes. The mark launch zeroes it
 // and fills it; the deep launch evaluates the listed pairs. If the list

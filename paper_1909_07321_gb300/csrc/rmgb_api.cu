@@ -72,13 +72,17 @@ struct PwHost {
     DevBuf otab, otab_bad;
     double otab_dk = 0.0;
     int otab_nseg = 0;
+    DevBuf ctab, ctab_nsub;
+    double ctab_nu_lo = 0.0;
+    int ctab_nseg = 0;
     void release()
     {
         for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
-                          &Wh, &Wl, &thr, &otab, &otab_bad})
+                          &Wh, &Wl, &thr, &otab, &otab_bad, &ctab, &ctab_nsub})
             d->release();
         use_deep = true;
         otab_nseg = 0;
+        ctab_nseg = 0;
         loaded = channels = false;
         p_kind = -1;
         w_kind = -1;
@@ -107,6 +111,13 @@ struct PwHost {
             d.otab_bad = otab_bad.as<int>();
             d.otab_dk = otab_dk;
             d.otab_nseg = otab_nseg;
+        }
+        if (ctab_nseg > 0) {
+            d.ctab = ctab.as<double>();
+            d.ctab_nsub = ctab_nsub.as<unsigned char>();
+            d.ctab_nu_lo = ctab_nu_lo;
+            d.ctab_dnu = CTAB_DNU;
+            d.ctab_nseg = ctab_nseg;
         }
         return d;
     }
@@ -255,6 +266,7 @@ extern "C" void rm_default_opts(rm_opts *o)
     o->solver = RM_SOLVER_AUTO;
     o->formulation = RM_FORM_AUTO;
     o->solve_precision = RM_FP64;
+    o->channel_tables = -1;
 }
 
 extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
@@ -266,6 +278,8 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
     if (o.solver < RM_SOLVER_AUTO || o.solver > RM_SOLVER_LARGE) return RM_EINVAL;
     if (o.formulation < RM_FORM_AUTO || o.formulation > RM_FORM_ENERGY) return RM_EINVAL;
     if (o.solve_precision != RM_FP64 && o.solve_precision != RM_FP32) return RM_EINVAL;
+    if (o.channel_tables < -1 || o.channel_tables > 1) return RM_EINVAL;
+    if (o.channel_tables == -1) o.channel_tables = o.precision == RM_FP64 ? 0 : 1;
     if (!(o.eps_thr >= 0) || !(o.delta_pole >= 0) || !std::isfinite(o.fnumin) ||
         !(o.mqdt_kappa_a_max >= 0) ||
         !std::isfinite(o.nu_margin) ||
@@ -342,8 +356,11 @@ int build_thr(rm_ctx *ctx, PwHost &P)
     P.otab.release();
     P.otab_bad.release();
     P.otab_nseg = 0;
+    P.ctab.release();
+    P.ctab_nsub.release();
+    P.ctab_nseg = 0;
     P.use_deep = true;
-    if (!(P.z > 0.0) || P.n == 0) return RM_SUCCESS;
+    if (!(P.z > 0.0) || P.n == 0 || !ctx->opts.channel_tables) return RM_SUCCESS;
     // open-side tables: segments of width OTAB_C / a in k up to OTAB_EPS_MAX Ry
     {
         const double dk = OTAB_C / P.a;
@@ -357,6 +374,29 @@ int build_thr(rm_ctx *ctx, PwHost &P)
         ++ctx->launches;
         P.otab_dk = dk;
         P.otab_nseg = nseg;
+    }
+    // closed-side tables: segments of width CTAB_DNU in nu from CTAB_EPS_MIN
+    // Ry below threshold up to the channels' near-threshold zones
+    {
+        const int l_max = *std::max_element(P.h_l.begin(), P.h_l.end());
+        const double nu_lo = P.z / std::sqrt(-CTAB_EPS_MIN);
+        const double nu_hi = closed_table_nu_hi(P.z, P.a, l_max);
+        const int nseg = std::min(CTAB_MAX_SEG, (int)std::ceil((nu_hi - nu_lo) / CTAB_DNU));
+        // at most 1 GiB of closed-side coefficients per wave (else the
+        // continued fractions serve the closed pairs)
+        const size_t bytes = sizeof(double) * (size_t)P.n * std::max(nseg, 0) * CTAB_SUB * 2 * OTAB_M;
+        if (nseg > 0 && bytes <= ((size_t)1 << 30)) {
+            CK(P.ctab.reserve(sizeof(double) * (size_t)P.n * nseg * CTAB_SUB * 2 * OTAB_M));
+            CK(P.ctab_nsub.reserve((size_t)P.n * nseg));
+            PwDev d = P.dev();
+            d.ctab_nu_lo = nu_lo;
+            d.ctab_dnu = CTAB_DNU;
+            d.ctab_nseg = nseg;
+            CK(launch_closed_table(d, P.ctab.as<double>(), P.ctab_nsub.as<unsigned char>(), ctx->stream));
+            ++ctx->launches;
+            P.ctab_nu_lo = nu_lo;
+            P.ctab_nseg = nseg;
+        }
     }
     CK(P.thr.reserve(sizeof(ThrNodes) * (size_t)P.n));
     CK(launch_thr_nodes(P.dev(), P.thr.as<ThrNodes>(), ctx->stream));

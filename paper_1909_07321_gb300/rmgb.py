@@ -36,7 +36,8 @@ class RmOpts(ctypes.Structure):
                 ("nu_margin", ctypes.c_double), ("device", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
                 ("mqdt_kappa_a_max", ctypes.c_double), ("solver", ctypes.c_int),
-                ("formulation", ctypes.c_int), ("solve_precision", ctypes.c_int)]
+                ("formulation", ctypes.c_int), ("solve_precision", ctypes.c_int),
+                ("channel_tables", ctypes.c_int)]
 
 
 class RmError(RuntimeError):

@@ -265,7 +265,7 @@ def test_channel_work_counts(rt):
     pws, E = synth.workload_64ch(500)
     pw = pws[0]
     n = pw["W"].shape[0]
-    with rmgb.Context() as ctx:
+    with rmgb.Context(channel_tables=1) as ctx:
         ctx.load_pw(0, pw)
         w = torch.zeros((E.size, n, 4), dtype=torch.int32, device="cuda")
         ctx.channel_work(0, torch.tensor(E, device="cuda"), w)
@@ -277,10 +277,17 @@ def test_channel_work_counts(rt):
     near = eps < 4.0 * h[None, :]
     assert near.any() and (~near).any()
     # kind 4: open beyond the zone, from the channel's Chebyshev table (all
-    # energies here lie within its 16 Ry)
-    assert np.array_equal(w[..., 0], np.where(near, 3, np.where(open_, 4, 1)))
-    cf = w[..., 0] == 1
-    assert (w[..., 1][cf] == 0).all()
-    assert (w[..., 2][cf] >= 2).all() and (w[..., 2] < 1 << 20).all()
+    # energies here lie within its 16 Ry); closed beyond the zone: kind 5
+    # from the closed-side table where its cell passed its check, else the
+    # continued fractions (kind 1)
+    k = w[..., 0]
+    assert np.array_equal(k[near], np.full(near.sum(), 3))
+    assert np.array_equal(k[open_ & ~near], np.full((open_ & ~near).sum(), 4))
+    cl = ~open_ & ~near
+    assert np.isin(k[cl], (1, 5)).all()
+    deep = ~open_ & (E[:, None] - pw["e_thr"][None, :] < -0.3)
+    assert (k[deep] == 5).mean() > 0.9
+    cf = k == 1
+    assert (w[..., 1][cf] == 0).all() and (w[..., 2][cf] >= 2).all() and (w[..., 2] < 1 << 20).all()
     assert (w[..., 1:3][~cf] == 0).all()
     assert np.array_equal(w[..., 3][~cf], np.broadcast_to(pw["l"], open_.shape)[~cf])

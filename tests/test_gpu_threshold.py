@@ -1,6 +1,7 @@
 """Channel functions near thresholds on the GPU against the oracle.
 
-For z > 0 the library evaluates a pair (energy, channel) within THR_ZONE
+With channel tables (the default of mixed-precision contexts, requested
+here explicitly) and z > 0 the library evaluates a pair (energy, channel) within THR_ZONE
 node spacings h of the channel's threshold by barycentric interpolation of
 the channel's node table (16 energies straddling the threshold) instead of
 continued fractions, h = min(0.0164 sqrt(z) / a^1.5, 0.05 z^2 / (l + 1)^2);
@@ -84,7 +85,7 @@ def test_channel_functions_near_thresholds(rt, ci):
     z, a, ls = CONFIGS[ci]
     pw = _pw(z, a, ls, 900 + ci)
     Es = _energies(pw, close=ci != REFUSED)
-    with rmgb.Context() as ctx:
+    with rmgb.Context(channel_tables=1) as ctx:
         ctx.load_pw(0, pw)
         Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
         out = torch.zeros((Es.size, 4, 4), dtype=torch.float64, device="cuda")
@@ -115,7 +116,7 @@ def test_k_omega_near_thresholds(rt, mode):
     pw = _pw(2.0, 15.0, (0, 3, 8, 5), 900)
     Es = _energies(pw)
     n = 4
-    with rmgb.Context() as ctx:
+    with rmgb.Context(channel_tables=1) as ctx:
         ctx.load_pw(0, pw)
         Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
         K = torch.zeros((Es.size, n * n), dtype=torch.float64, device="cuda")
@@ -151,7 +152,7 @@ def test_open_tables_vs_oracle(rt, ci):
     pw = _pw(z, a, ls, 900 + ci)
     rng = np.random.default_rng(77 + ci)
     Es = np.sort(np.concatenate([rng.uniform(0.0, 2.0, 40), rng.uniform(2.0, 16.5, 40)]))
-    with rmgb.Context() as ctx:
+    with rmgb.Context(channel_tables=1) as ctx:
         ctx.load_pw(0, pw)
         Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
         out = torch.zeros((Es.size, 4, 4), dtype=torch.float64, device="cuda")
@@ -170,3 +171,42 @@ def test_open_tables_vs_oracle(rt, ci):
     inside = (eps > 0) & (np.sqrt(np.maximum(eps, 0)) - k0 >= 0) & (np.sqrt(np.maximum(eps, 0)) - k0 < nseg * 0.9 / a)
     assert inside.sum() > 100
     assert np.array_equal(w[..., 0] == 4, inside)
+
+
+@pytest.mark.parametrize("ci", range(len(CONFIGS) - 1))
+def test_closed_tables_vs_oracle(rt, ci):
+    """Closed pairs beyond the near-threshold zone (direct mode) come from the
+    channel's table of the direction (theta, a theta') in nu (cells of 0.25
+    split into up to 16 sub-segments of 12 terms) where the cell passed its
+    check, else from the continued fractions: thresholds at 0, 5, 10, 15 Ry
+    and random energies, so that closed pairs range from 16 Ry below
+    threshold to the zone edge. All must match the oracle; deep closed pairs
+    (smooth direction) must mostly come from the table."""
+    torch, rmgb = rt
+    z, a, ls = CONFIGS[ci]
+    pw = _pw(z, a, ls, 900 + ci)
+    pw["e_thr"] = np.array([0.0, 5.0, 10.0, 15.0])
+    rng = np.random.default_rng(99 + ci)
+    Es = np.sort(np.concatenate([rng.uniform(0.01, 15.0, 60),
+                                 np.array([5.0, 10.0, 15.0]) - rng.uniform(0.005, 0.05, 3)]))
+    with rmgb.Context(channel_tables=1) as ctx:
+        ctx.load_pw(0, pw)
+        Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
+        out = torch.zeros((Es.size, 4, 4), dtype=torch.float64, device="cuda")
+        st = torch.zeros(Es.size, dtype=torch.int32, device="cuda")
+        ctx.channel_functions(0, Ed, out, st)
+        w = torch.zeros((Es.size, 4, 4), dtype=torch.int32, device="cuda")
+        ctx.channel_work(0, Ed, w)
+        g = out.cpu().numpy()
+        w = w.cpu().numpy()
+        assert not st.cpu().numpy().any()
+    _check_channel_functions(g, Es, pw, ("closed table",) + CONFIGS[ci])
+    eps = Es[:, None] - pw["e_thr"][None, :]
+    h = np.array([node_spacing(z, a, int(l)) for l in pw["l"]])
+    closed = (eps < 0) & (-eps >= THR_ZONE * h[None, :]) & (eps >= -16.0)
+    assert closed.sum() > 60
+    tab = w[..., 0] == 5
+    assert not (tab & ~closed).any()
+    assert np.isin(w[..., 0][closed], (1, 5)).all()
+    deep = closed & (np.sqrt(np.maximum(-eps, 0.0)) * a > 8.0)
+    assert tab[deep].mean() > 0.8, tab[deep].mean()

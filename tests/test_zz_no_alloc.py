@@ -35,7 +35,7 @@ def rt():
 
 def _reference_K(torch, rmgb, pw, E):
     n = pw["W"].shape[0]
-    with rmgb.Context() as ctx:
+    with rmgb.Context(channel_tables=0) as ctx:   # the same continued fractions as the call
         ctx.load_pw(0, pw)
         Ed = torch.tensor(E, dtype=torch.float64, device="cuda")
         K = torch.zeros((E.size, n * n), dtype=torch.float64, device="cuda")
