@@ -881,8 +881,9 @@ __global__ void __launch_bounds__(64) open_table_kernel(PwDev pw, double *__rest
 // continued fractions. The direction turns by about pi per unit nu, but
 // where r = a lies in the classically allowed region of the decaying
 // solution (kappa a of a few) it does so through narrow peaks of its rate
-// that no modest expansion holds; deeper, it is smooth. Cells on the near
-// side of the channel's near-threshold zone are never read and not computed.
+// that no modest expansion holds; deeper, it is smooth. So the table stops
+// at kappa a = CTAB_KA_MIN (or the near-threshold zone, if nearer); cells
+// beyond are not computed (nsub = 0).
 constexpr double CTAB_CHECK_TOL = 5e-13;
 __global__ void __launch_bounds__(128) closed_table_kernel(PwDev pw, double *__restrict__ coef,
                                                             unsigned char *__restrict__ nsub)
@@ -896,7 +897,7 @@ __global__ void __launch_bounds__(128) closed_table_kernel(PwDev pw, double *__r
     const int l = pw.l[i];
     const double z = pw.z, a = pw.a;
     const double nu0 = pw.ctab_nu_lo + q * pw.ctab_dnu;
-    const double nu_hi = z / sqrt(THR_ZONE * thr_spacing(l, z, a));
+    const double nu_hi = fmin(z / sqrt(THR_ZONE * thr_spacing(l, z, a)), z * a / CTAB_KA_MIN);
     double *cq = coef + ((size_t)i * pw.ctab_nseg + q) * CTAB_SUB * 2 * M;
     unsigned char *nq = nsub + (size_t)i * pw.ctab_nseg + q;
     if (nu0 >= nu_hi) {
@@ -981,7 +982,7 @@ double closed_table_nu_hi(double z, double a, int l_max)
         const double h = std::fmin(THR_C1 * std::sqrt(z) / (a * std::sqrt(a)), THR_C2 * z * z / ((l + 1.0) * (l + 1.0)));
         nu = std::fmax(nu, z / std::sqrt(THR_ZONE * h));
     }
-    return nu;
+    return std::fmin(nu, z * a / CTAB_KA_MIN);
 }
 
 cudaError_t launch_closed_table(const PwDev &pw, double *coef, unsigned char *nsub, cudaStream_t s)

@@ -93,6 +93,7 @@ constexpr double CTAB_DNU = 0.25;     // closed-side cell width in nu
 constexpr int CTAB_SUB = 16;          // at most this many sub-segments per cell
 constexpr double CTAB_EPS_MIN = -16.0; // Ry below threshold covered by the closed-side tables
 constexpr int CTAB_MAX_SEG = 4096;    // at most this many closed-side segments per channel
+constexpr double CTAB_KA_MIN = 6.0;   // closed-side tables only where kappa a >= this
 
 struct Opts {
     double eps_thr, delta_pole, fnumin, nu_margin, kappa_a_max;
@@ -120,8 +121,9 @@ cudaError_t launch_open_table(const PwDev &pw, double *coef, int *bad, cudaStrea
 // ctab_nseg: coefficients into coef, sub-segment counts into nsub (0 for a
 // cell that failed its check).
 cudaError_t launch_closed_table(const PwDev &pw, double *coef, unsigned char *nsub, cudaStream_t s);
-// Largest nu any channel's closed-side table must reach (its near-threshold
-// zone edge), for the segment count.
+// Largest nu any channel's closed-side table reaches (its near-threshold
+// zone edge, or kappa a = CTAB_KA_MIN if that comes first), for the cell
+// count.
 double closed_table_nu_hi(double z, double a, int l_max);
 // Near-threshold (deep) pairs: deep_ws = [count][list of CAP pair indices][nE
 // energy marks], chanfn_deep_ws_bytes(nE) bytes. The mark launch zeroes it

@@ -285,7 +285,7 @@ def test_channel_work_counts(rt):
     assert np.array_equal(k[open_ & ~near], np.full((open_ & ~near).sum(), 4))
     cl = ~open_ & ~near
     assert np.isin(k[cl], (1, 5)).all()
-    deep = ~open_ & (E[:, None] - pw["e_thr"][None, :] < -0.3)
+    deep = ~open_ & (E[:, None] - pw["e_thr"][None, :] < -(8.0 / pw["a"]) ** 2)   # kappa a > 8
     assert (k[deep] == 5).mean() > 0.9
     cf = k == 1
     assert (w[..., 1][cf] == 0).all() and (w[..., 2][cf] >= 2).all() and (w[..., 2] < 1 << 20).all()

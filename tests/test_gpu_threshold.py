@@ -210,3 +210,6 @@ def test_closed_tables_vs_oracle(rt, ci):
     assert np.isin(w[..., 0][closed], (1, 5)).all()
     deep = closed & (np.sqrt(np.maximum(-eps, 0.0)) * a > 8.0)
     assert tab[deep].mean() > 0.8, tab[deep].mean()
+    # tables stop at the cell (0.25 in nu) that reaches kappa a = 6
+    nu = z / np.sqrt(np.maximum(-eps, 1e-300))
+    assert not (tab & (nu > z * a / 6.0 + 0.25 + 1e-9)).any()
