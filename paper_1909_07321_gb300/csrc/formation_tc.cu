@@ -218,27 +218,50 @@ __global__ void split_p_kernel(PwDev pw, int kind, int Kpad, void *Ph, void *Pl)
     split_store(v, kind, Ph, Pl, (size_t)idx);
 }
 
+// A double as hi + lo floats (hi = x rounded, lo = the rest rounded).
+__device__ __forceinline__ float2 split_hl(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// E_k - E from hi + lo pairs in FP32: (hi - hi) rounds once relative to the
+// difference and (lo - lo) restores what the rounding of E_k and E dropped,
+// so the result is within ~2^-23 relative of E_k - E whenever |E_k - E| >=
+// delta >> |E| 2^-48. The near/far decision |E_k - E| < delta of the split
+// and of the FP64 near-pole terms is taken on this value, identically.
+__device__ __forceinline__ float pole_den(float2 ek, float2 e) { return (ek.x - e.x) + (ek.y - e.y); }
+
+__global__ void split_e_kernel(const double *__restrict__ E, int nE, float2 *__restrict__ e_hl)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nE) e_hl[e] = split_hl(E[e]);
+}
+
 // D_k(E) = 1/(E_k - E) for |E_k - E| >= delta (else 0: those terms are
-// added in FP64 by near_pole_fixup_kernel, with the same FP64 test), split
-// hi + lo. The difference is formed in FP64 and rounded once to FP32, the
-// reciprocal taken in FP32 (correctly rounded): D carries FP32 precision
-// into the split either way. Thread: two consecutive poles of one energy
-// (Kpad is even); grid: (pole pairs, energies).
+// added in FP64 by near_pole_fixup_kernel), split hi + lo, entirely in FP32
+// (pole_den, correctly rounded reciprocal): no FP64 pipe work, so the split
+// does not compete with the channel functions running beside it. Thread:
+// two consecutive poles of one energy (Kpad is even); grid: (pole pairs,
+// energies).
 template <int KIND>
-__global__ void split_d_kernel(PwDev pw, const double *__restrict__ E, int nE, double delta, int Kpad,
+__global__ void split_d_kernel(PwDev pw, const float2 *__restrict__ e_hl, int nE, float delta_f, int Kpad,
                                void *Dh, void *Dl)
 {
     const int k = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (k >= Kpad) return;
+    float2 ek[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) ek[h] = k + h < pw.N ? pw.Ek_hl[k + h] : make_float2(0.0f, 0.0f);
     for (int e = blockIdx.y; e < nE; e += gridDim.y) {
-        const double x = E[e];
+        const float2 x = e_hl[e];
         float d[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             d[h] = 0.0f;
             if (k + h < pw.N) {
-                const double den = pw.Ek[k + h] - x;
-                if (fabs(den) >= delta) d[h] = __frcp_rn((float)den);
+                const float den = pole_den(ek[h], x);
+                if (fabsf(den) >= delta_f) d[h] = __frcp_rn(den);
             }
         }
         const size_t idx = (size_t)e * Kpad + k;
@@ -271,15 +294,17 @@ __global__ void near_pole_range_kernel(PwDev pw, const double *__restrict__ E, i
     if (e >= nE) return;
     const double x = E[e];
     int lo = 0, hi = pw.N;
-    while (lo < hi) {          // first k with E_k > x - delta
+    while (lo < hi) {          // first k with E_k > x - 2 delta (a margin for the FP32 test)
         const int mid = (lo + hi) >> 1;
-        if (pw.Ek[mid] <= x - delta) lo = mid + 1; else hi = mid;
+        if (pw.Ek[mid] <= x - 2.0 * delta) lo = mid + 1; else hi = mid;
     }
     int k1 = lo;
-    while (k1 < pw.N && pw.Ek[k1] < x + delta) ++k1;
-    // same exclusion test as split_d_kernel
+    while (k1 < pw.N && pw.Ek[k1] < x + 2.0 * delta) ++k1;
+    // same near/far test as split_d_kernel
+    const float2 xh = split_hl(x);
+    const float df = (float)delta;
     bool any = false;
-    for (int k = lo; k < k1; ++k) any |= fabs(pw.Ek[k] - x) < delta;
+    for (int k = lo; k < k1; ++k) any |= fabsf(pole_den(pw.Ek_hl[k], xh)) < df;
     if (!any) return;
     const int slot = atomicAdd(count, 1);
     list[slot] = e;
@@ -299,14 +324,16 @@ __global__ void near_pole_fixup_kernel(PwDev pw, const double *__restrict__ E, d
         const int e = list[s];
         const int2 kr = range[s];
         const double x = E[e];
+        const float2 xh = split_hl(x);
+        const float df = (float)delta;
         double *Re = Rp + (size_t)e * tri_ld(n);
         for (int i = 0; i < n; ++i) {
             double *row = Re + tri_idx(i, i, n);
             for (int j = i + lane; j < n; j += 32) {
                 double acc = 0.0;
                 for (int k = kr.x; k < kr.y; ++k) {
-                    const double den = pw.Ek[k] - x;
-                    if (fabs(den) < delta) acc += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / den;
+                    if (fabsf(pole_den(pw.Ek_hl[k], xh)) < df)
+                        acc += pw.W[(size_t)i * pw.N + k] * pw.W[(size_t)j * pw.N + k] / (pw.Ek[k] - x);
                 }
                 row[j - i] += h * acc;
             }
@@ -341,14 +368,16 @@ cudaError_t launch_split_p(const PwDev &pw, int kind, int Kpad, void *P_hi, void
 }
 
 cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delta, int kind, int Kpad,
-                           void *D_hi, void *D_lo, cudaStream_t s)
+                           void *D_hi, void *D_lo, float2 *e_hl, cudaStream_t s)
 {
     if ((long long)nE * Kpad == 0) return cudaSuccess;
+    if (!pw.Ek_hl) return cudaErrorInvalidValue;
+    split_e_kernel<<<(unsigned)((nE + 255) / 256), 256, 0, s>>>(E, nE, e_hl);
     const dim3 grid((unsigned)((Kpad / 2 + 255) / 256), (unsigned)(nE < 65535 ? nE : 65535));
     if (kind == TC_BF16X3)
-        split_d_kernel<TC_BF16X3><<<grid, 256, 0, s>>>(pw, E, nE, delta, Kpad, D_hi, D_lo);
+        split_d_kernel<TC_BF16X3><<<grid, 256, 0, s>>>(pw, e_hl, nE, (float)delta, Kpad, D_hi, D_lo);
     else
-        split_d_kernel<TC_TF32X3><<<grid, 256, 0, s>>>(pw, E, nE, delta, Kpad, D_hi, D_lo);
+        split_d_kernel<TC_TF32X3><<<grid, 256, 0, s>>>(pw, e_hl, nE, (float)delta, Kpad, D_hi, D_lo);
     return cudaGetLastError();
 }
 

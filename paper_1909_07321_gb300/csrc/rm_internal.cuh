@@ -66,6 +66,7 @@ struct PwDev {
     const int *lev_chan;   // [n]
     const double *lev_thr; // [n_levels] threshold of each level (+inf if unused)
     const ThrNodes *thr = nullptr;  // [n] near-threshold tables (nullptr: none)
+    const float2 *Ek_hl = nullptr;  // [N] E_k as hi + lo floats (mixed-precision formation)
     // open-side tables: Chebyshev coefficients of f = s / sqrt(A), f' = s' /
     // sqrt(A), g~ = c sqrt(A), g~' = c' sqrt(A) in k = sqrt(eps) on segments
     // [q dk, (q + 1) dk), q < otab_nseg: otab[((i nseg + q) 4 + f) OTAB_M + m];
@@ -164,13 +165,15 @@ enum TcKind { TC_BF16X3 = 0, TC_TF32X3 = 1 };
 cudaError_t launch_split_p(const PwDev &pw, int kind, int Kpad, void *P_hi, void *P_lo,
                            cudaStream_t s);
 // Split of D_ek = 1/(E_k - E_e) (0 when |E_k - E_e| < delta) into hi/lo, [nE][Kpad].
-cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delta, int kind,
-                           int Kpad, void *D_hi, void *D_lo, cudaStream_t s);
+// pw.Ek_hl must be set; e_hl: nE float2 of scratch (E as hi + lo floats).
+cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delta, int kind, int Kpad,
+                           void *D_hi, void *D_lo, float2 *e_hl, cudaStream_t s);
 // R_packed[e][p] = sum_k D[e][k] P[p][k] over the three hi/lo products.
 cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
                              const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
                              int *err_flag, cudaStream_t s);
-// R_packed[e][p] += (1/2a) w_ik w_jk / (E_k - E_e) over poles with |E_k - E_e| < delta (FP64).
+// R_packed[e][p] += (1/2a) w_ik w_jk / (E_k - E_e) over poles with |E_k - E_e| < delta (FP64),
+// the near/far decision taken exactly as launch_split_d takes it (pw.Ek_hl).
 // ws: near_pole_ws_bytes(nE) bytes of device scratch (list of the energies
 // with poles within delta, and their pole ranges).
 size_t near_pole_ws_bytes(int nE);

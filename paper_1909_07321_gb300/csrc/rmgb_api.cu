@@ -55,6 +55,7 @@ struct PwHost {
     int n = 0, N = 0, n_levels = 0;
     double a = 0, b = 0, z = 0, g = 0;
     DevBuf Ek, W, e_thr, l, level, lev_start, lev_chan, lev_thr;
+    DevBuf Ek_hl;   // E_k as hi + lo floats
     // mixed-precision operand P = w_i w_j / 2a, split hi/lo (built on first use)
     DevBuf Ph, Pl;
     int p_kind = -1, p_kpad = 0;
@@ -77,7 +78,7 @@ struct PwHost {
     int ctab_nseg = 0;
     void release()
     {
-        for (DevBuf *d : {&Ek, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
+        for (DevBuf *d : {&Ek, &Ek_hl, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
                           &Wh, &Wl, &thr, &otab, &otab_bad, &ctab, &ctab_nsub})
             d->release();
         use_deep = true;
@@ -106,6 +107,7 @@ struct PwHost {
         d.lev_chan = lev_chan.as<int>();
         d.lev_thr = lev_thr.as<double>();
         d.thr = thr.as<ThrNodes>();
+        d.Ek_hl = Ek_hl.as<float2>();
         if (otab_nseg > 0) {
             d.otab = otab.as<double>();
             d.otab_bad = otab_bad.as<int>();
@@ -135,7 +137,7 @@ struct rm_ctx {
     std::vector<double> grid_host;
     DevBuf omega;
     // workspace
-    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep, wsNear;
+    DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep, wsNear, wsEhl;
     // coarse-mesh interpolation: node energies, statuses + orders, K_u, S_u, fine plan
     DevBuf wsQn, wsQst, wsQk, wsQs, wsQf, wsQc;
     // side stream for the deep channel pairs, with fork / join events
@@ -209,7 +211,7 @@ template <class T> cudaError_t upload(DevBuf &d, const T *h, size_t count, cudaS
 }
 
 // Records the start event of a traced launch of `phase` (no-op if tracing is off).
-cudaError_t prof_begin(rm_ctx *ctx, int phase)
+cudaError_t prof_begin(rm_ctx *ctx, int phase, cudaStream_t st = nullptr)
 {
     if (!ctx->prof) return cudaSuccess;
     auto &v = ctx->ev[phase];
@@ -222,15 +224,15 @@ cudaError_t prof_begin(rm_ctx *ctx, int phase)
         if (e != cudaSuccess) return e;
         v.push_back({a, b});
     }
-    return cudaEventRecord(v[u].first, ctx->stream);
+    return cudaEventRecord(v[u].first, st ? st : ctx->stream);
 }
 
-cudaError_t prof_end(rm_ctx *ctx, int phase)
+cudaError_t prof_end(rm_ctx *ctx, int phase, cudaStream_t st = nullptr)
 {
     if (!ctx->prof) return cudaSuccess;
     auto &v = ctx->ev[phase];
     size_t &u = ctx->ev_used[phase];
-    cudaError_t e = cudaEventRecord(v[u].second, ctx->stream);
+    cudaError_t e = cudaEventRecord(v[u].second, st ? st : ctx->stream);
     ++u;
     return e;
 }
@@ -328,7 +330,7 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
     for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
-                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsNear, &ctx->wsQn,
+                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsNear, &ctx->wsEhl, &ctx->wsQn,
                       &ctx->wsQst, &ctx->wsQk, &ctx->wsQs, &ctx->wsQf, &ctx->wsQc})
         d->release();
     for (int p = 0; p < RM_PH_COUNT; ++p)
@@ -446,6 +448,15 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
     P.Wl.release();
     P.w_kind = -1;
     CK(upload(P.Ek, Es.data(), Es.size(), ctx->stream));
+    {
+        std::vector<float2> hl(n_poles);
+        for (int k = 0; k < n_poles; ++k) {
+            const float h = (float)Es[k];
+            hl[k] = make_float2(h, (float)(Es[k] - (double)h));
+        }
+        P.Ek_hl.release();
+        CK(upload(P.Ek_hl, hl.data(), hl.size(), ctx->stream));
+    }
     P.h_Ek = Es;
     CK(upload(P.W, Ws.data(), Ws.size(), ctx->stream));
     P.n = n_ch;
@@ -583,13 +594,14 @@ int block_energies(rm_ctx *ctx, const PwHost &P)
 }
 
 // Packed R of nE energies into R (stride tri_ld(n)), in the context's precision.
-int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
+int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R, cudaStream_t st = nullptr)
 {
+    if (!st) st = ctx->stream;
     const PwDev d = P.dev();
     if (ctx->opts.precision == RM_FP64) {
-        CK(prof_begin(ctx, RM_PH_FORM));
-        CK(launch_form_r_fp64(d, E, nE, R, ctx->stream));
-        CK(prof_end(ctx, RM_PH_FORM));
+        CK(prof_begin(ctx, RM_PH_FORM, st));
+        CK(launch_form_r_fp64(d, E, nE, R, st));
+        CK(prof_end(ctx, RM_PH_FORM, st));
         ctx->launches++;
         return RM_SUCCESS;
     }
@@ -598,7 +610,7 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
     const size_t es = tc_esize(kind);
     if (!ctx->wsErr.p) {
         CK(ctx->wsErr.reserve(sizeof(int)));
-        CK(cudaMemsetAsync(ctx->wsErr.p, 0, sizeof(int), ctx->stream));
+        CK(cudaMemsetAsync(ctx->wsErr.p, 0, sizeof(int), st));
     }
     if (formulation(ctx, P) == RM_FORM_ENERGY) {
         if (P.w_kind != kind) {
@@ -606,24 +618,24 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
             CK(P.W32.reserve(nk * sizeof(float)));
             CK(P.Wh.reserve(nk * es));
             CK(P.Wl.reserve(nk * es));
-            CK(launch_pe_prep_w(d, kind, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ctx->stream));
+            CK(launch_pe_prep_w(d, kind, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, st));
             ctx->launches++;
             P.w_kind = kind;
         }
         CK(ctx->wsDh.reserve((size_t)nE * Kpad * sizeof(float) + (size_t)nE * sizeof(int2)));
         CK(ctx->wsPart.reserve(pe_bytes_per_energy(P.n, P.N, kind) * (size_t)nE));
-        CK(prof_begin(ctx, RM_PH_SPLIT));
-        CK(launch_pe_d32(d, E, nE, ctx->opts.delta_pole, Kpad, ctx->wsDh.as<float>(), ctx->stream));
-        CK(prof_end(ctx, RM_PH_SPLIT));
-        CK(prof_begin(ctx, RM_PH_FORM));
+        CK(prof_begin(ctx, RM_PH_SPLIT, st));
+        CK(launch_pe_d32(d, E, nE, ctx->opts.delta_pole, Kpad, ctx->wsDh.as<float>(), st));
+        CK(prof_end(ctx, RM_PH_SPLIT, st));
+        CK(prof_begin(ctx, RM_PH_FORM, st));
         CK(launch_form_r_pe(kind, P.n, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ctx->wsDh.as<float>(), nE,
-                            ctx->wsPart.as<float>(), ctx->wsErr.as<int>(), ctx->stream));
-        CK(prof_end(ctx, RM_PH_FORM));
-        CK(prof_begin(ctx, RM_PH_FIXUP));
+                            ctx->wsPart.as<float>(), ctx->wsErr.as<int>(), st));
+        CK(prof_end(ctx, RM_PH_FORM, st));
+        CK(prof_begin(ctx, RM_PH_FIXUP, st));
         CK(launch_pe_reduce(d, kind, Kpad, E, nE, ctx->opts.delta_pole, ctx->wsDh.as<float>(),
                             ctx->wsPart.as<float>(), R,
-                            tri_ld(P.n), ctx->stream));
-        CK(prof_end(ctx, RM_PH_FIXUP));
+                            tri_ld(P.n), st));
+        CK(prof_end(ctx, RM_PH_FIXUP, st));
         ctx->launches += 3;
         return RM_SUCCESS;
     }
@@ -631,26 +643,27 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R)
         const size_t pb = (size_t)tri_count(P.n) * Kpad * es;
         CK(P.Ph.reserve(pb));
         CK(P.Pl.reserve(pb));
-        CK(launch_split_p(d, kind, Kpad, P.Ph.p, P.Pl.p, ctx->stream));
+        CK(launch_split_p(d, kind, Kpad, P.Ph.p, P.Pl.p, st));
         ctx->launches++;
         P.p_kind = kind;
         P.p_kpad = Kpad;
     }
     CK(ctx->wsDh.reserve((size_t)nE * Kpad * es));
     CK(ctx->wsDl.reserve((size_t)nE * Kpad * es));
-    CK(prof_begin(ctx, RM_PH_SPLIT));
-    CK(launch_split_d(d, E, nE, ctx->opts.delta_pole, kind, Kpad, ctx->wsDh.p, ctx->wsDl.p,
-                      ctx->stream));
-    CK(prof_end(ctx, RM_PH_SPLIT));
-    CK(prof_begin(ctx, RM_PH_FORM));
+    CK(prof_begin(ctx, RM_PH_SPLIT, st));
+    CK(ctx->wsEhl.reserve((size_t)nE * sizeof(float2)));
+    CK(launch_split_d(d, E, nE, ctx->opts.delta_pole, kind, Kpad, ctx->wsDh.p, ctx->wsDl.p, ctx->wsEhl.as<float2>(),
+                      st));
+    CK(prof_end(ctx, RM_PH_SPLIT, st));
+    CK(prof_begin(ctx, RM_PH_FORM, st));
     CK(launch_form_r_tc(kind, ctx->wsDh.p, ctx->wsDl.p, P.Ph.p, P.Pl.p, nE, tri_count(P.n), Kpad, R,
-                        tri_ld(P.n), ctx->wsErr.as<int>(), ctx->stream));
-    CK(prof_end(ctx, RM_PH_FORM));
-    CK(prof_begin(ctx, RM_PH_FIXUP));
+                        tri_ld(P.n), ctx->wsErr.as<int>(), st));
+    CK(prof_end(ctx, RM_PH_FORM, st));
+    CK(prof_begin(ctx, RM_PH_FIXUP, st));
     CK(ctx->wsNear.reserve(near_pole_ws_bytes(nE)));
-    CK(launch_near_pole_fixup(d, E, nE, ctx->opts.delta_pole, R, ctx->wsNear.p, ctx->stream));
-    CK(prof_end(ctx, RM_PH_FIXUP));
-    ctx->launches += 4;
+    CK(launch_near_pole_fixup(d, E, nE, ctx->opts.delta_pole, R, ctx->wsNear.p, st));
+    CK(prof_end(ctx, RM_PH_FIXUP, st));
+    ctx->launches += 5;
     return RM_SUCCESS;
 }
 
@@ -732,12 +745,29 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
             CK(cudaEventRecord(ctx->ev_join, ctx->side));
             ctx->launches += 2;
         }
+        // With no deep pairs to wait for, the formation of R (tensor pipe,
+        // the longer chain: split, GEMM, near-pole terms) runs on the
+        // high-priority second stream and step (b) (FP64 pipe) beside it on
+        // the context's stream, filling what the formation leaves of the
+        // SMs; the solve joins both.
+        const bool beside = !P.use_deep;
+        if (beside) {
+            CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+            CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+            int rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>(), ctx->side);
+            if (rc) return rc;
+            CK(cudaEventRecord(ctx->ev_join, ctx->side));
+        }
         CK(prof_begin(ctx, RM_PH_CHANFN));
         CK(launch_chanfn(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, deep, ctx->stream));
         CK(prof_end(ctx, RM_PH_CHANFN));
         ctx->launches += 2;
-        int rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
-        if (rc) return rc;
+        if (beside) {
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+        } else {
+            int rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
+            if (rc) return rc;
+        }
         CK(prof_begin(ctx, RM_PH_SOLVE));
         double *Kb = K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr;
         int *nob = n_open_out ? n_open_out + e0 : nullptr;
