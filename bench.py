@@ -511,7 +511,7 @@ def run_ours(args, rank, world, local_rank):
     chan_ach = chan_ops / (phase[rmgb.RM_PH_CHANFN][1] / args.steps * 1e-3) / 1e12
     chan_roof = {"bound": "alu", "achieved": chan_ach, "peak": fp64_op_peak, "unit": "TFP64op/s",
                  "frac": chan_ach / fp64_op_peak, "traffic": None,
-                 "kernel": "chanfn_kernel (FP64 continued fractions)",
+                 "kernel": "chanfn_kernel (channel tables + FP64 continued fractions)",
                  "ops_per_step": chan_ops,
                  "peak_source": "FP64 pipe 2 op/clk/SM x 152 SMs at the sampled SM clock"}
     # matching + T + Omega

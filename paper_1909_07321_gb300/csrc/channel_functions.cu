@@ -46,6 +46,19 @@
 // defined by theta ~ f cos(pi nu) - g sin(pi nu) with f'g - fg' = 1:
 //   theta-hat(a) = sin(pi nu) / (f L - f'),  theta-hat'(a) = L theta-hat(a),
 //   g = (f cos(pi nu) - theta-hat) / sin(pi nu),  g' likewise.
+//
+// Channel tables (built once per partial wave from the same continued
+// fractions, when the context asks for them; see thr_nodes_kernel,
+// open_table_kernel, closed_table_kernel): at fixed r = a the pair
+// f = s / sqrt(A), g~ = c sqrt(A), A = prod_{p=1..l} (1 + p^2 eps / z^2), is
+// analytic in eps across the threshold (on the closed side f is the
+// energy-analytic regular solution and g~ the g above at half-integer nu,
+// theta ~ A f cos(pi nu) - g~ sin(pi nu)). Near a threshold the pair is
+// interpolated from 16 nodes straddling it; open pairs beyond come from
+// Chebyshev expansions in k, closed pairs deep enough (kappa a >= 6) from
+// expansions of the direction of (theta, a theta') in nu. Each table is
+// checked against direct values at build time, and pairs a table does not
+// cover keep the continued fractions.
 #include <math.h>
 
 #include <cmath>
@@ -330,12 +343,13 @@ constexpr double CHANFN_DEEP_EPS = 2.5e-5;   // |eps| / max(z^2, 1) below this: 
 constexpr int CHANFN_DEEP_CAP = 1 << 14;     // capacity of the deep-pair list
 
 // Pairs (energy, channel) this close to their threshold have the deepest
-// continued fractions (depth ~ 3 / sqrt(|eps| / z^2): about 600 to tens of
-// thousands of steps, each a serial chain of dependent FP64 operations that
-// no parallel split evaluates as accurately). They are listed, their
-// energies marked, and a separate kernel (on a second stream) evaluates them
-// while the main stream forms R and solves every unmarked energy; the marked
-// energies are solved after it.
+// continued fractions (depth ~ z / (|eps| a) steps: thousands to millions,
+// each a serial chain of dependent FP64 operations). Where the channel's
+// near-threshold table covers them they cost an interpolation; the others
+// (no tables: z = 0, an FP64 context, or a table that failed its check) are
+// listed, their energies marked, and a separate kernel (on a second stream)
+// evaluates them while the main stream forms R and solves every unmarked
+// energy; the marked energies are solved after it.
 __device__ __forceinline__ bool chanfn_deep(const PwDev &pw, int i, double eps, double eps_thr)
 {
     if (!(fabs(eps) < CHANFN_DEEP_EPS * fmax(pw.z * pw.z, 1.0)) || fabs(eps) < eps_thr) return false;
