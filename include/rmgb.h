@@ -250,8 +250,10 @@ int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *E, double *
  * steps}, kind 0 = open (CF1 at l, CF2 at l = 0, l downward and upward
  * recurrence steps), 1 = closed (its CF2 at L0, then l - L0 ladder steps),
  * 3 = near the threshold, interpolated from the channel's node table, 4 =
- * open, from the channel's Chebyshev table (neither runs a continued
- * fraction; the l field holds l), -1 = on a threshold. A CF2 with n2 > 32 is re-evaluated backwards from
+ * open, from the channel's Chebyshev table, 5 = closed, from the channel's
+ * direction table (none of these runs a continued fraction; the l field
+ * holds l), -1 = on a threshold. Kinds 3-5 occur only in contexts with
+ * channel tables (rm_opts.channel_tables). A CF2 with n2 > 32 is re-evaluated backwards from
  * depth 2 n2 + 20; one with n2 <= 32 is taken from its forward value.
  * Asynchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_ECUDA. */
 int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, int *work);
