@@ -209,7 +209,7 @@ def _solve_flops(n, n_open, f32):
 # counted from the kernel.
 CHANFN_OPS = {"cf1": 17, "cf2_fwd": 28, "cf2_bwd": 15, "open_l": 90, "open_fixed": 130,
               "closed_fwd": 14, "closed_bwd": 10, "ladder": 36, "closed_fixed": 70,
-              "thr_interp": 16 * 10 + 40, "open_table": 4 * 2 * 11 + 60}
+              "thr_interp": 16 * 10 + 40, "open_table": 4 * 2 * 11 + 60, "closed_table": 2 * 2 * 11 + 50}
 CF2_FAST_DEPTH = 32   # CF2 settling within this many forward steps has no backward pass
 
 
@@ -235,7 +235,11 @@ def _chanfn_ops(work):
     # 12-term series, the segment and A(eps, l)
     to = w[w[:, 0] == 4]
     ops_tab = c["open_table"] * to.shape[0] + 2.0 * to[:, 3].sum()
-    return float(ops_open.sum() + ops_closed.sum() + ops_thr + ops_tab)
+    # closed pairs from the channel's direction table: Clenshaw for two
+    # 12-term series and the normalisation
+    tc = w[w[:, 0] == 5]
+    ops_ctab = c["closed_table"] * tc.shape[0]
+    return float(ops_open.sum() + ops_closed.sum() + ops_thr + ops_tab + ops_ctab)
 
 
 def run_serving(args, prec):
