@@ -33,6 +33,10 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
                         reproduced exactly (also when extrapolating); error
                         of S_u interpolation falls as h^2; segment and
                         qetest rules on hand-made grids
+  propagate (outer-     tests/test_oracle_propagate.py: without coupling K at r1
+  region propagation    equals K at a; free s-wave closed form; round trip
+  with multipoles)      a -> r1 -> a; an independent RK4 converges to it at
+                        fourth order
   cross-threshold K, Omega beyond these checks: parity unpinned (the paper
                         prints no K or Omega values for any system).
 """
