@@ -173,6 +173,31 @@ int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const double *E_k,
 int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, double z,
                     const int *level, int n_levels, double g_weight);
 
+/* Outer-region propagation with the long-range multipole potential (Section
+ * "Overview": the coupled radial equations with a non-zero potential matrix
+ * U are integrated outward from the inner-region boundary r0 = a to an
+ * asymptotic radius r1, where the matching is done; namelist variable
+ * ipert). In Rydberg units the equations are
+ *   u_i'' = sum_j [ (l_i(l_i+1)/r^2 - 2z/r - (E - e_i)) delta_ij + U_ij(r) ] u_j,
+ *   U(r) = sum_{lambda=1..lambda_max} A^lambda / r^(lambda+1),
+ * A (host, [lambda_max][n_ch][n_ch] row-major, A[((lam-1)*n + i)*n + j] =
+ * A^lam_ij, each A^lam exactly symmetric; any unit factor is absorbed into A).
+ * The solution matrix Psi with Psi(a) = R(a), a Psi'(a) - b Psi(a) = 1 is
+ * integrated to r1 >= a by classical fourth-order Runge-Kutta with n_steps
+ * fixed steps (FP64, one CTA per energy), and R(r1) = Psi (r1 Psi' - b Psi)^-1
+ * replaces R in the matching of rm_solve_energies and rm_solve_energies_qdt,
+ * whose channel functions (and channel tables) are then taken at r1. The
+ * coupling beyond r1 is not included. No stabilisation is done: strongly
+ * closed channels (kappa (r1 - a) large) lose precision as in any shooting
+ * method. lambda_max = 0 switches propagation off (A, r1, n_steps ignored).
+ * rm_load_poles clears it. rm_form_r still returns R at a. At most 32
+ * channels, 1 <= lambda_max <= 4. An energy whose r1 Psi' - b Psi is
+ * singular gets RM_ESINGULAR. Synchronous when the channels are set (their
+ * tables are rebuilt for r1). Errors: RM_EINVAL (lambda_max out of range, A
+ * NULL, non-finite or not symmetric, r1 < a, n_steps < 1), RM_EUNSUPPORTED
+ * (n_ch > 32), RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
+int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const double *A, double r1, int n_steps);
+
 /* Solves n_E energies E (host or device, [n_E], Ry) of partial wave `pw` in
  * `mode` (RM_DIRECT or RM_MQDT) and adds g |T|^2 into the context's Omega
  * accumulator. The first call after creation or a reset registers the grid;
@@ -259,7 +284,8 @@ int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *E, double *
 int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, int *work);
 
 /* Inspection of step (a), for tests: R-matrices of `pw` at n_E energies E
- * (device), with the context's formation precision, written to R_out
+ * (device) at r = a (before any propagation), with the context's formation
+ * precision, written to R_out
  * (device, [n_E][n_ch][n_ch], full symmetric matrix). Asynchronous.
  * Errors: RM_EINVAL, RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
 int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *R_out);

@@ -76,11 +76,18 @@ struct PwHost {
     DevBuf ctab, ctab_nsub;
     double ctab_nu_lo = 0.0;
     int ctab_nseg = 0;
+    // outer-region propagation (rm_set_multipoles): coefficients [lmax][n][n]
+    // on the device, radius r1, RK4 steps; prop_lmax < 0: none
+    DevBuf propA;
+    int prop_lmax = -1, prop_steps = 0;
+    double prop_r1 = 0.0;
+    double a_match() const { return prop_lmax >= 0 ? prop_r1 : a; }
     void release()
     {
         for (DevBuf *d : {&Ek, &Ek_hl, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
-                          &Wh, &Wl, &thr, &otab, &otab_bad, &ctab, &ctab_nsub})
+                          &Wh, &Wl, &thr, &otab, &otab_bad, &ctab, &ctab_nsub, &propA})
             d->release();
+        prop_lmax = -1;
         use_deep = true;
         otab_nseg = 0;
         ctab_nseg = 0;
@@ -121,6 +128,14 @@ struct PwHost {
             d.ctab_dnu = CTAB_DNU;
             d.ctab_nseg = ctab_nseg;
         }
+        return d;
+    }
+    // As dev(), with a = the matching radius (r1 when the wave is propagated):
+    // for the channel functions, their tables and the matching solve.
+    PwDev dev_match() const
+    {
+        PwDev d = dev();
+        d.a = a_match();
         return d;
     }
 };
@@ -364,12 +379,13 @@ int build_thr(rm_ctx *ctx, PwHost &P)
     P.use_deep = true;
     if (!(P.z > 0.0) || P.n == 0 || !ctx->opts.channel_tables) return RM_SUCCESS;
     // open-side tables: segments of width OTAB_C / a in k up to OTAB_EPS_MAX Ry
+    // (a: the matching radius)
     {
-        const double dk = OTAB_C / P.a;
+        const double dk = OTAB_C / P.a_match();
         const int nseg = (int)std::ceil(std::sqrt(OTAB_EPS_MAX) / dk);
         CK(P.otab.reserve(sizeof(double) * (size_t)P.n * nseg * 4 * OTAB_M));
         CK(P.otab_bad.reserve(sizeof(int) * (size_t)P.n));
-        PwDev d = P.dev();
+        PwDev d = P.dev_match();
         d.otab_dk = dk;
         d.otab_nseg = nseg;
         CK(launch_open_table(d, P.otab.as<double>(), P.otab_bad.as<int>(), ctx->stream));
@@ -382,7 +398,7 @@ int build_thr(rm_ctx *ctx, PwHost &P)
     {
         const int l_max = *std::max_element(P.h_l.begin(), P.h_l.end());
         const double nu_lo = P.z / std::sqrt(-CTAB_EPS_MIN);
-        const double nu_hi = closed_table_nu_hi(P.z, P.a, l_max);
+        const double nu_hi = closed_table_nu_hi(P.z, P.a_match(), l_max);
         const int nseg = std::min(CTAB_MAX_SEG, (int)std::ceil((nu_hi - nu_lo) / CTAB_DNU));
         // at most 1 GiB of closed-side coefficients per wave (else the
         // continued fractions serve the closed pairs)
@@ -390,7 +406,7 @@ int build_thr(rm_ctx *ctx, PwHost &P)
         if (nseg > 0 && bytes <= ((size_t)1 << 30)) {
             CK(P.ctab.reserve(sizeof(double) * (size_t)P.n * nseg * CTAB_SUB * 2 * OTAB_M));
             CK(P.ctab_nsub.reserve((size_t)P.n * nseg));
-            PwDev d = P.dev();
+            PwDev d = P.dev_match();
             d.ctab_nu_lo = nu_lo;
             d.ctab_dnu = CTAB_DNU;
             d.ctab_nseg = nseg;
@@ -401,7 +417,7 @@ int build_thr(rm_ctx *ctx, PwHost &P)
         }
     }
     CK(P.thr.reserve(sizeof(ThrNodes) * (size_t)P.n));
-    CK(launch_thr_nodes(P.dev(), P.thr.as<ThrNodes>(), ctx->stream));
+    CK(launch_thr_nodes(P.dev_match(), P.thr.as<ThrNodes>(), ctx->stream));
     ++ctx->launches;
     std::vector<ThrNodes> h(P.n);
     CK(cudaMemcpyAsync(h.data(), P.thr.p, sizeof(ThrNodes) * (size_t)P.n, cudaMemcpyDeviceToHost, ctx->stream));
@@ -465,6 +481,9 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
     P.b = b;
     P.loaded = true;
     if (!same_n) P.channels = false;
+    // new poles (and a) clear any outer-region propagation
+    P.propA.release();
+    P.prop_lmax = -1;
     return P.channels ? build_thr(ctx, P) : RM_SUCCESS;
 }
 
@@ -508,6 +527,40 @@ extern "C" int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const i
     P.n_levels = n_levels;
     P.channels = true;
     return build_thr(ctx, P);
+}
+
+extern "C" int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const double *A, double r1, int n_steps)
+{
+    int rc = check_pw(ctx, pw, false);
+    if (rc) return rc;
+    PwHost &P = ctx->pw[pw];
+    const int n = P.n;
+    if (lambda_max == 0) {
+        P.prop_lmax = -1;
+        P.prop_r1 = 0.0;
+        P.prop_steps = 0;
+        return P.channels ? build_thr(ctx, P) : RM_SUCCESS;
+    }
+    if (n > PROP_MAXN) return fail(ctx, RM_EUNSUPPORTED, "propagation takes at most %d channels (n_ch=%d)",
+                                   PROP_MAXN, n);
+    if (lambda_max < 0 || lambda_max > PROP_MAX_LAMBDA)
+        return fail(ctx, RM_EINVAL, "lambda_max=%d out of [0,%d]", lambda_max, PROP_MAX_LAMBDA);
+    if (!A) return fail(ctx, RM_EINVAL, "NULL multipole coefficients");
+    if (!std::isfinite(r1) || !(r1 >= P.a)) return fail(ctx, RM_EINVAL, "r1=%g must be >= a=%g", r1, P.a);
+    if (n_steps < 1) return fail(ctx, RM_EINVAL, "n_steps=%d must be >= 1", n_steps);
+    const size_t cnt = (size_t)lambda_max * n * n;
+    if (!finite_all(A, (int)cnt)) return fail(ctx, RM_EINVAL, "non-finite multipole coefficient");
+    for (int lam = 0; lam < lambda_max; ++lam)
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < i; ++j)
+                if (A[((size_t)lam * n + i) * n + j] != A[((size_t)lam * n + j) * n + i])
+                    return fail(ctx, RM_EINVAL, "A[%d] not symmetric at (%d,%d)", lam + 1, i, j);
+    CK(cudaSetDevice(ctx->opts.device));
+    CK(upload(P.propA, A, cnt, ctx->stream));
+    P.prop_lmax = lambda_max;
+    P.prop_r1 = r1;
+    P.prop_steps = n_steps;
+    return P.channels ? build_thr(ctx, P) : RM_SUCCESS;
 }
 
 namespace {
@@ -721,7 +774,7 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
     CK(ctx->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
     CK(ctx->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
     if (large) CK(ctx->wsL.reserve(solve_large_bytes_per_energy(P.n) * (size_t)B + 256));
-    const PwDev d = P.dev();
+    const PwDev d = P.dev_match();
     const Opts o = make_opts(ctx->opts);
     for (int e0 = 0; e0 < n_E; e0 += B) {
         const int nb = std::min(B, n_E - e0);
@@ -767,6 +820,17 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
         } else {
             int rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
             if (rc) return rc;
+        }
+        if (P.prop_lmax >= 0) {
+            // R(a) -> R(r1) once every status of the block is final (the
+            // deep pairs' too), so a singular propagation never masks an
+            // earlier error
+            if (split) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+            CK(prof_begin(ctx, RM_PH_FORM));
+            CK(launch_propagate(P.dev(), Eb, nb, P.propA.as<double>(), P.prop_lmax, P.prop_r1, P.prop_steps,
+                                ctx->wsR.as<double>(), sb, ctx->stream));
+            CK(prof_end(ctx, RM_PH_FORM));
+            ++ctx->launches;
         }
         CK(prof_begin(ctx, RM_PH_SOLVE));
         double *Kb = K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr;
@@ -852,7 +916,7 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     ch.l = P.h_l.data();
     ch.E_k = P.h_Ek.data();
     ch.z = P.z;
-    ch.a = P.a;
+    ch.a = P.a_match();
     ch.eps_thr = ctx->opts.eps_thr;
     ch.nu_margin = ctx->opts.nu_margin;
     ch.fnumin = ctx->opts.fnumin;
@@ -867,7 +931,7 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     // channel classes of every fine energy on the device, then the plan
     std::vector<signed char> hcls((size_t)n_E * P.n);
     CK(ctx->wsQc.reserve(hcls.size()));
-    CK(launch_qdt_classes(P.dev(), dE, n_E, make_opts(ctx->opts), ctx->wsQc.as<signed char>(), ctx->stream));
+    CK(launch_qdt_classes(P.dev_match(), dE, n_E, make_opts(ctx->opts), ctx->wsQc.as<signed char>(), ctx->stream));
     ctx->launches++;
     CK(cudaMemcpyAsync(hcls.data(), ctx->wsQc.p, hcls.size(), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -917,7 +981,7 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     }
     CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ctx->stream));
     const int ntri = P.n_levels * (P.n_levels + 1) / 2;
-    CK(launch_qdt_fine(iqdt, P.dev(), dE, n_E, make_opts(ctx->opts), ctx->wsQf.as<QdtFine>(),
+    CK(launch_qdt_fine(iqdt, P.dev_match(), dE, n_E, make_opts(ctx->opts), ctx->wsQf.as<QdtFine>(),
                        ctx->wsQk.as<double>(), ctx->wsQs.as<double2>(), ctx->wsQst.as<int>(), dstatus,
                        n_open_out, ctx->omega.as<double>(), ntri, ctx->stream));
     ctx->launches++;
@@ -1004,7 +1068,7 @@ extern "C" int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *
         st = ctx->wsStatus.as<int>();
     }
     CK(cudaMemsetAsync(st, 0, (size_t)n_E * sizeof(int), ctx->stream));
-    const PwDev d = P.dev();
+    const PwDev d = P.dev_match();
     CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ctx->wsCf.as<ChanFn>(), st, nullptr, ctx->stream));
     CK(launch_chanfn_export(d, E, n_E, ctx->wsCf.as<ChanFn>(), out, ctx->stream));
     ctx->launches += 2;
@@ -1019,7 +1083,7 @@ extern "C" int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, in
     if (!is_device_ptr(E) || !is_device_ptr(work))
         return fail(ctx, RM_EINVAL, "E and work must be device pointers");
     CK(cudaSetDevice(ctx->opts.device));
-    const PwDev d = ctx->pw[pw].dev();
+    const PwDev d = ctx->pw[pw].dev_match();
     CK(launch_chanfn_work(d, E, n_E, make_opts(ctx->opts), reinterpret_cast<int4 *>(work), ctx->stream));
     ctx->launches++;
     return RM_SUCCESS;

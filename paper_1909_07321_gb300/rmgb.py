@@ -57,6 +57,7 @@ _SIGS = {
     "rm_destroy": (None, [_VP]),
     "rm_load_poles": (_I, [_VP, _I, _I, _I, _VP, _VP, _D, _D]),
     "rm_set_channels": (_I, [_VP, _I, _VP, _VP, _D, _VP, _I, _D]),
+    "rm_set_multipoles": (_I, [_VP, _I, _I, _VP, _D, _I]),
     "rm_solve_energies": (_I, [_VP, _I, _I, _VP, _I, _VP, _VP, _VP]),
     "rm_collision_strengths": (_I, [_VP, _VP, _I]),
     "rm_solve_energies_qdt": (_I, [_VP, _I, _I, _VP, _I, _D, _I, _VP, _VP]),
@@ -158,6 +159,19 @@ def rm_set_channels(ctx, pw, e_thr, l, z, level, n_levels, g_weight):
     level = _host(level, np.int32)
     return _check(ctx, lib().rm_set_channels(ctx, pw, _ptr(e_thr, np.float64), _ptr(l, np.int32),
                                              z, _ptr(level, np.int32), n_levels, g_weight))
+
+
+def rm_set_multipoles(ctx, pw, A, r1, n_steps):
+    """A: [lambda_max][n_ch][n_ch] (lambda_max = 0 or A None: propagation off)."""
+    if A is None:
+        return _check(ctx, lib().rm_set_multipoles(ctx, pw, 0, None, 0.0, 0))
+    if hasattr(A, "cpu"):
+        A = A.cpu().numpy()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    if A.ndim != 3:
+        raise ValueError("A must be [lambda_max][n_ch][n_ch]")
+    return _check(ctx, lib().rm_set_multipoles(ctx, pw, int(A.shape[0]), _ptr(A, np.float64), float(r1),
+                                               int(n_steps)))
 
 
 def rm_solve_energies(ctx, pw, E, mode=0, K_out=None, n_open_out=None, status_out=None):
@@ -287,6 +301,9 @@ class Context:
         """Load one partial wave given as a dict (keys of synth's partial waves)."""
         rm_load_poles(self.h, pw, d["E_k"], d["W"], d["a"], d.get("b", 0.0))
         rm_set_channels(self.h, pw, d["e_thr"], d["l"], d["z"], d["level"], d["n_levels"], d["g"])
+
+    def set_multipoles(self, pw, A, r1=0.0, n_steps=0):
+        return rm_set_multipoles(self.h, pw, A, r1, n_steps)
 
     def solve_energies(self, pw, E, mode=0, K_out=None, n_open_out=None, status_out=None):
         return rm_solve_energies(self.h, pw, E, mode, K_out, n_open_out, status_out)
