@@ -16,12 +16,17 @@ Readings (the paper prints the equation garbled and does not give U):
   * The R-matrix at a defines the solution matrix Psi (n x n) by
     Psi(a) = R(a), a Psi'(a) - b Psi(a) = 1; Psi is propagated to r1 and
         R(r1) = Psi(r1) [r1 Psi'(r1) - b Psi(r1)]^{-1},
-    which is symmetric (U symmetric). K follows from Eq. match at r = r1 with
+    which is symmetric (U symmetric). The paper integrates with Numerov's
+    method; here the integration restarts from R at sector boundaries (the
+    result does not depend on the basis of solutions Psi carries), which keeps
+    strongly closed channels from swamping the others. K follows from Eq. match at r = r1 with
     the channel functions (U = 0) at r1; the tail of U beyond r1 (ipert 3, 4)
     is not included.
-  * The propagation here is scipy's DOP853 at rtol 1e-12 on the first-order
+  * The propagation here is scipy's DOP853 at rtol 1e-13 on the first-order
     system (Psi, Psi'); the GPU integrates the same equation by RK4 with a
-    fixed number of steps.
+    fixed number of steps. (At rtol 1e-12 R over 20 a0 carries ~1e-10 of
+    error, which the matching's condition, up to ~5e4, raises to ~5e-10 in
+    K: too close to a 1e-9 comparison.)
 """
 import numpy as np
 from scipy.integrate import solve_ivp
@@ -38,14 +43,37 @@ def coupling(r, A):
     return U
 
 
-def propagate_r(R_a, a, r1, eps, l, z, A, b=0.0, rtol=1e-12):
-    """R(r1) from R(a) (see the module docstring)."""
+def propagate_r(R_a, a, r1, eps, l, z, A, b=0.0, rtol=1e-13, sector=1.0):
+    """R(r1) from R(a) (see the module docstring), sector by sector.
+
+    R(r) = Psi (r Psi' - b Psi)^{-1} does not depend on which basis of the
+    solution space Psi holds (Psi -> Psi G for any invertible G), so the
+    integration restarts from R at the end of each sector of length
+    sector / kappa_max, kappa_max^2 = max_i (l_i(l_i+1)/a^2 - eps_i): within a
+    sector no closed channel grows by more than ~e^sector against the others
+    and the columns of Psi stay independent (sector=None: one sector)."""
     R_a = np.asarray(R_a, dtype=np.float64)
-    n = R_a.shape[0]
     eps = np.asarray(eps, dtype=np.float64)
     l = np.asarray(l, dtype=np.float64)
     if r1 == a:
         return R_a.copy()
+    kmax = np.sqrt(max(0.0, float(np.max(l * (l + 1) / (a * a) - eps))))
+    if sector is None or kmax * abs(r1 - a) <= sector:
+        return _propagate_sector(R_a, a, r1, eps, l, z, A, b, rtol)
+    m = int(np.ceil(kmax * abs(r1 - a) / sector))
+    edges = a + (r1 - a) * np.arange(m + 1) / m
+    edges[-1] = r1
+    R = R_a
+    for x0, x1 in zip(edges[:-1], edges[1:]):
+        R = _propagate_sector(R, x0, x1, eps, l, z, A, b, rtol)
+        if R is None:
+            return None
+    return R
+
+
+def _propagate_sector(R_a, a, r1, eps, l, z, A, b, rtol):
+    """One sector: integrate (Psi, Psi') from a to r1 and form R(r1)."""
+    n = R_a.shape[0]
 
     def rhs(r, y):
         Psi = y[: n * n].reshape(n, n)
@@ -63,7 +91,7 @@ def propagate_r(R_a, a, r1, eps, l, z, A, b=0.0, rtol=1e-12):
     return 0.5 * (R1 + R1.T)
 
 
-def solve_energy(pw, E, A, r1, mode=rm.MODE_DIRECT, eps_thr=1e-10, fnumin=0.0, margin=0.1):
+def solve_energy(pw, E, A, r1, mode=rm.MODE_DIRECT, eps_thr=1e-10, fnumin=0.0, margin=0.1, rtol=1e-13):
     """One energy: R at a (Eq. rmatrix), propagated to r1, matched there.
     Returns (status, K, open_idx, omega_row)."""
     nlev = int(pw["n_levels"])
@@ -76,7 +104,8 @@ def solve_energy(pw, E, A, r1, mode=rm.MODE_DIRECT, eps_thr=1e-10, fnumin=0.0, m
     if cf["status"] != rm.RM_OK:
         return cf["status"], None, None, row
     R = rm.r_matrix(E, E_k, pw["W"], pw["a"])
-    R1 = propagate_r(R, pw["a"], r1, E - np.asarray(pw["e_thr"], dtype=np.float64), pw["l"], pw["z"], A, b)
+    R1 = propagate_r(R, pw["a"], r1, E - np.asarray(pw["e_thr"], dtype=np.float64), pw["l"], pw["z"], A, b,
+                     rtol=rtol)
     if R1 is None:
         return rm.RM_ESINGULAR, None, None, row
     if mode == rm.MODE_MQDT:

@@ -99,3 +99,23 @@ def test_independent_rk4_converges_to_it():
     errs = [np.abs(_rk4(R, pw["a"], 14.0, eps, l, pw["z"], A, s) - ref).max() for s in (50, 100, 200)]
     assert errs[2] < 1e-7 * np.abs(ref).max()
     assert 10.0 < errs[0] / errs[1] < 22.0 and 10.0 < errs[1] / errs[2] < 22.0, errs
+
+
+def test_sectors_do_not_change_k():
+    """R(r1) does not depend on the basis of solutions carried, so restarting
+    from R at sector boundaries (any sector length) gives the same K; with
+    strongly closed channels (kappa (r1 - a) ~ 10) the sectored results agree
+    with each other to ~1e-12."""
+    pw = _pw()
+    A = _coupling(4, 4)
+    E = 0.05                                     # three closed channels
+    eps = E - pw["e_thr"]
+    R = oracle.r_matrix(E, pw["E_k"], pw["W"], pw["a"])
+    cf = oracle.channel_functions(E, pw["e_thr"], pw["l"], pw["z"], 22.0)
+    Ks = []
+    for sector in (None, 2.0, 1.0, 0.3):
+        R1 = pr.propagate_r(R, pw["a"], 22.0, eps, pw["l"], pw["z"], A, sector=sector)
+        K, _ = oracle.match_direct(R1, cf, 22.0, 0.0)
+        Ks.append(K)
+    for K in Ks[1:]:
+        np.testing.assert_allclose(K, Ks[2], rtol=0, atol=1e-11 * np.abs(Ks[2]).max())
