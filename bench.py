@@ -380,6 +380,75 @@ def run_qdt(args, prec, sp):
     return out
 
 
+def run_propagation(args, prec, sp, fp64_peak, stream):
+    """Outer-region propagation with the multipole potential (32 channels,
+    lambda_max = 2, a = 15 -> r1 = 35 in 2000 RK4 steps): the whole solve of
+    args.prop_energies energies with propagation, the same solve without it,
+    and the propagation kernel against the FP64 pipe."""
+    import torch
+
+    from paper_1909_07321_gb300 import rmgb, synth
+    pw, A, r1, steps, E = synth.workload_multipole(args.prop_energies)
+    n = pw["W"].shape[0]
+    lmax = A.shape[0]
+    out = {"workload": "%d channels, lambda_max = %d, a = %g -> r1 = %g in %d RK4 steps, %d energies "
+                       "(0.01-2.5 Ry), formation %s" % (n, lmax, pw["a"], r1, steps, E.size, args.precision)}
+    Ed = torch.tensor(E, dtype=torch.float64, device="cuda")
+    res = {}
+    for name in ("propagated", "unpropagated"):
+        ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, solve_precision=sp)
+        ctx.load_pw(0, pw)
+        if name == "propagated":
+            ctx.set_multipoles(0, A, r1, steps)
+        with torch.cuda.stream(stream):
+            ctx.solve_energies(0, Ed)
+            ctx.reset_omega()
+            ctx.profile_enable(True)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            reps = 2
+            torch.cuda.synchronize()
+            t0.record(stream)
+            for _ in range(reps):
+                ctx.solve_energies(0, Ed)
+                ctx.reset_omega()
+            t1.record(stream)
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / reps
+            pl, pms = ctx.profile_get(rmgb.RM_PH_PROPAGATE)
+        ctx.close()
+        res[name] = (ms, pl, pms / reps)
+    # RK4 truncation: Omega with twice the steps
+    om2 = {}
+    for k, st_ in (("1x", steps), ("2x", 2 * steps)):
+        ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, solve_precision=sp)
+        ctx.load_pw(0, pw)
+        ctx.set_multipoles(0, A, r1, st_)
+        with torch.cuda.stream(stream):
+            ctx.solve_energies(0, Ed)
+            om2[k] = ctx.collision_strengths()
+        ctx.close()
+    dn = np.abs(om2["1x"] - om2["2x"]).max(axis=1) / np.maximum(np.abs(om2["2x"]).max(axis=1), 1e-300)
+    ms_p, pl, prop_ms = res["propagated"]
+    ms_u = res["unpropagated"][0]
+    # per energy and step: four products W Psi (2 n^3 flops each), the RK4
+    # combinations (14 FMA per element) and two builds of W (lambda_max FMA
+    # per element)
+    flops = E.size * steps * (8.0 * n ** 3 + (28.0 + 4.0 * lmax) * n * n)
+    ach = flops / (prop_ms * 1e-3) / 1e12
+    out.update({"propagated": {"energy_solves_per_s": E.size / (ms_p * 1e-3), "ms": ms_p},
+                "unpropagated": {"energy_solves_per_s": E.size / (ms_u * 1e-3), "ms": ms_u},
+                "propagate_ms": prop_ms, "propagate_launches_per_solve": pl / 2,
+                "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": ach / fp64_peak, "traffic": None,
+                             "kernel": "propagate_kernel (FP64 RK4, one CTA per energy)",
+                             "flops_per_launch": flops,
+                             "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"},
+                "omega_rel_change_with_2x_steps": {"median": float(np.median(dn)), "max": float(dn.max())},
+                "timing": "CUDA events on the context stream around 2 solves after one warm-up"})
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -487,6 +556,9 @@ def run_ours(args, rank, world, local_rank):
         qdt_line = run_qdt(args, prec, sp)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = N_SM * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+    prop_line = None
+    if world == 1 and args.prop_energies > 0:
+        prop_line = run_propagation(args, prec, sp, fp64_peak, stream)
     names = {rmgb.RM_PH_NEARPOLE: "nearpole", rmgb.RM_PH_CHANFN: "chanfn", rmgb.RM_PH_FORM: "form",
              rmgb.RM_PH_FIXUP: "fixup", rmgb.RM_PH_SOLVE: "solve", rmgb.RM_PH_SPLIT: "split"}
     total_phase_ms = sum(v[1] for v in phase.values())
@@ -566,6 +638,7 @@ def run_ours(args, rank, world, local_rank):
             "serving": serving_line,
             "wide_1000ch": wide,
             "mqdt_interpolation": qdt_line,
+            "multipole_propagation": prop_line,
             "cpu_baseline": cpu,
             "e2e": {"value": world * E.size / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": int(E.size * 8),
@@ -593,6 +666,8 @@ def main():
                     help="node spacing of the MQDT interpolation leg (0 to skip)")
     ap.add_argument("--wide-energies", type=int, default=256,
                     help="energies of the 1000-channel leg (0 to skip)")
+    ap.add_argument("--prop-energies", type=int, default=1024,
+                    help="energies of the multipole-propagation leg (0 to skip)")
     ap.add_argument("--energies", type=int, default=N_E,
                     help="energies per GPU (smaller only for profiler captures)")
     args = ap.parse_args()

@@ -301,7 +301,8 @@ int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *R_out);
 #define RM_PH_FIXUP       3   /* step (a) near-pole FP64 terms (mixed precision) */
 #define RM_PH_SOLVE       4   /* steps (c)+(d) matching, T, Omega */
 #define RM_PH_SPLIT       5   /* step (a) operand split of 1/(E_k - E) (mixed precision) */
-#define RM_PH_COUNT       6
+#define RM_PH_PROPAGATE   6   /* outer-region propagation a -> r1 (rm_set_multipoles) */
+#define RM_PH_COUNT       7
 int rm_profile_enable(rm_ctx *ctx, int enable);
 int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms);
 

@@ -10,8 +10,12 @@
 // a Psi'(a) - b Psi(a) = 1; Psi and Psi' are integrated to r1 by the
 // classical fourth-order Runge-Kutta method with a fixed number of steps,
 // and R(r1) = Psi(r1) [r1 Psi'(r1) - b Psi(r1)]^{-1} (symmetric; it replaces
-// R(a) in the matching, done at r1). One CTA of NT threads per energy, all
-// matrices in shared memory, FP64.
+// R(a) in the matching, done at r1). The integration restarts from R(r) at
+// sector boundaries 1 / kappa_max apart (R does not depend on the basis of
+// solutions carried), so that closed channels growing as exp(kappa r) do not
+// swamp the other columns. One CTA of NT threads per energy, FP64.
+// A step costs four products W Psi (4 n^3 FMA) and two builds of W: the
+// kernel runs on the FP64 pipe.
 #include <math.h>
 
 #include "dense_smem.cuh"
@@ -20,11 +24,97 @@
 namespace rmgb {
 namespace {
 
-// Shared memory: Psi, Psi', their RK4 accumulators, the stage inputs, W Psi
-// and W (8 n^2 doubles), then the coefficients A (lambda_max n^2).
-__global__ void __launch_bounds__(NT) propagate_kernel(PwDev pw, const double *__restrict__ E,
-                                                      const double *__restrict__ A, int lmax, double r1,
-                                                      int steps, double *__restrict__ Rp, int *__restrict__ status)
+// Elements of an n x n matrix one thread owns (q = tid + c NT, c < PROP_QN).
+constexpr int PROP_QN = (PROP_MAXN * PROP_MAXN + NT - 1) / NT;
+
+// W(r) at the owned elements into Wd: sum_lambda A^lambda r^-(lambda+1) plus
+// the diagonal l(l+1)/r^2 - 2z/r - eps.
+__device__ __forceinline__ void build_w(double *Wd, const double *As, const double *eps_s, const double *lt_s,
+                                        int n, int lmax, double z, double r, int tid)
+{
+    const int n2 = n * n;
+    const double ir = 1.0 / r;
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c) {
+        const int q = tid + c * NT;
+        if (q < n2) {
+            const int i = q / n, j = q - (q / n) * n;
+            double u = 0.0, rp = ir * ir;
+            for (int lam = 0; lam < lmax; ++lam) {
+                u = fma(As[lam * n2 + q], rp, u);
+                rp *= ir;
+            }
+            if (i == j) u += lt_s[i] * ir * ir - 2.0 * z * ir - eps_s[i];
+            Wd[q] = u;
+        }
+    }
+}
+
+// (W S) at the owned elements, the PROP_QN dot products interleaved.
+__device__ __forceinline__ void w_times(double (&kq)[PROP_QN], const double *Wd, const double *S, int n, int tid)
+{
+    const int n2 = n * n;
+    int wi[PROP_QN], sj[PROP_QN];
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c) {
+        const int q = min(tid + c * NT, n2 - 1);
+        wi[c] = (q / n) * n;
+        sj[c] = q - wi[c];
+        kq[c] = 0.0;
+    }
+#pragma unroll 2
+    for (int k = 0; k < n; ++k) {
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) kq[c] = fma(Wd[wi[c] + k], S[k * n + sj[c]], kq[c]);
+    }
+}
+
+// Psi <- Psi G^{-1}, Psi' <- Psi' G^{-1} with G = r Psi' - b Psi at the
+// owned elements (then Psi = R(r) and r Psi' - b Psi = 1), by eliminating
+// [ G^T | Psi^T ] over M (n x 2n, row stride 2n + 1; the caller's 3 n^2
+// doubles of scratch). The new Psi also goes to S. False if G is singular.
+__device__ bool restart_from_r(double (&psi)[PROP_QN], double (&dps)[PROP_QN], double *S, double *M, int n,
+                               double b, double r, ElimShared *esh, int tid)
+{
+    const int n2 = n * n, ld = 2 * n + 1;
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c) {
+        const int q = tid + c * NT;
+        if (q < n2) {
+            const int i = q / n, j = q - (q / n) * n;
+            M[j * ld + i] = r * dps[c] - b * psi[c];
+            M[j * ld + n + i] = psi[c];
+        }
+    }
+    if (tid == 0) esh->bad = 0;
+    __syncthreads();
+    block_eliminate<double>(M, ld, n, 2 * n, esh);
+    if (esh->bad) return false;
+    block_backsub<double>(M, ld, n, n, n, 0);
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c) {
+        const int q = tid + c * NT;
+        if (q < n2) {
+            const int i = q / n, j = q - (q / n) * n;
+            psi[c] = M[j * ld + n + i];
+            dps[c] = ((i == j ? 1.0 : 0.0) + b * psi[c]) / r;
+            S[q] = psi[c];
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// One CTA per energy. The solution Psi and its derivative at the owned
+// elements stay in registers with the RK4 accumulators; shared memory holds
+// what the products W S read across threads: the stage input of Psi (two
+// buffers, alternating by stage) and W (two buffers: at r0 and r0 + h/2;
+// W(r0 + h) is built over the first once stage 1 is done with it), then the
+// coefficients A. One barrier per stage.
+__global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double *__restrict__ E,
+                                                          const double *__restrict__ A, int lmax, double r1,
+                                                          int steps, double *__restrict__ Rp,
+                                                          int *__restrict__ status)
 {
     extern __shared__ double sm[];
     __shared__ double eps_s[PROP_MAXN], lt_s[PROP_MAXN];
@@ -32,9 +122,7 @@ __global__ void __launch_bounds__(NT) propagate_kernel(PwDev pw, const double *_
     const int e = blockIdx.x, tid = threadIdx.x;
     const int n = pw.n, n2 = n * n;
     if (status[e] != RM_OK) return;
-    double *Psi = sm, *P = sm + n2, *Yp = sm + 2 * n2, *Yq = sm + 3 * n2;
-    double *Tp = sm + 4 * n2, *Tq = sm + 5 * n2, *Kq = sm + 6 * n2, *Wm = sm + 7 * n2;
-    double *As = sm + 8 * n2;
+    double *S0 = sm, *S1 = sm + n2, *W0 = sm + 2 * n2, *W1 = sm + 3 * n2, *As = sm + 4 * n2;
     const double a = pw.a, b = pw.b, z = pw.z, x = E[e];
     double *Re = Rp + (size_t)e * tri_ld(n);
     for (int q = tid; q < lmax * n2; q += NT) As[q] = A[q];
@@ -42,92 +130,110 @@ __global__ void __launch_bounds__(NT) propagate_kernel(PwDev pw, const double *_
         eps_s[i] = x - pw.e_thr[i];
         lt_s[i] = (double)pw.l[i] * (pw.l[i] + 1);
     }
-    for (int q = tid; q < n2; q += NT) {
-        const int i = q / n, j = q - (q / n) * n;
-        const double r = Re[i <= j ? tri_idx(i, j, n) : tri_idx(j, i, n)];
-        Psi[q] = r;
-        P[q] = ((i == j ? 1.0 : 0.0) + b * r) / a;
+    double psi[PROP_QN], dps[PROP_QN], yp[PROP_QN], yq[PROP_QN], tq[PROP_QN], kq[PROP_QN];
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c) {
+        const int q = tid + c * NT;
+        psi[c] = dps[c] = yp[c] = yq[c] = tq[c] = 0.0;
+        if (q < n2) {
+            const int i = q / n, j = q - (q / n) * n;
+            psi[c] = Re[i <= j ? tri_idx(i, j, n) : tri_idx(j, i, n)];
+            dps[c] = ((i == j ? 1.0 : 0.0) + b * psi[c]) / a;
+            S0[q] = psi[c];
+        }
     }
     __syncthreads();
-    const double h = (r1 - a) / steps;
-    // RK4: stage inputs (Tp, Tq), slopes (Tq, W Tp); weights and offsets
-    const double cw[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-    const double dn[4] = {0.5, 0.5, 1.0, 0.0};
-    const double off[4] = {0.0, 0.5, 0.5, 1.0};
+    build_w(W0, As, eps_s, lt_s, n, lmax, z, a, tid);
+    const double h = (r1 - a) / steps, h2 = 0.5 * h, h3 = h / 3.0, h6 = h / 6.0;
+    // restart from R every `sector` steps, a sector being 1 / kappa_max long,
+    // kappa_max^2 = max_i (l_i(l_i+1)/a^2 - eps_i)
+    int sector = steps;
+    {
+        double k2 = 0.0;
+        for (int i = 0; i < n; ++i) k2 = fmax(k2, lt_s[i] / (a * a) - eps_s[i]);
+        const double m = k2 > 0.0 ? 1.0 / (sqrt(k2) * h) : (double)steps;
+        sector = m >= (double)steps ? steps : max(1, (int)m);
+    }
+    __syncthreads();
     for (int s = 0; s < steps; ++s) {
         const double r0 = a + s * h;
+        // stage 1 at r0: input Psi (S0), W0; writes the stage-2 input to S1
+        w_times(kq, W0, S0, n, tid);
 #pragma unroll
-        for (int st = 0; st < 4; ++st) {
-            const double r = r0 + off[st] * h;
-            const double *ip = st == 0 ? Psi : Tp;   // stage input
-            const double *iq = st == 0 ? P : Tq;
-            // W(r)
-            const double ir = 1.0 / r;
-            for (int q = tid; q < n2; q += NT) {
-                const int i = q / n, j = q - (q / n) * n;
-                double u = 0.0, rp = ir * ir;
-                for (int lam = 0; lam < lmax; ++lam) {
-                    u = fma(As[lam * n2 + q], rp, u);
-                    rp *= ir;
-                }
-                if (i == j) u += lt_s[i] * ir * ir - 2.0 * z * ir - eps_s[i];
-                Wm[q] = u;
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            yp[c] = fma(h6, dps[c], psi[c]);
+            yq[c] = fma(h6, kq[c], dps[c]);
+            tq[c] = fma(h2, kq[c], dps[c]);
+            if (q < n2) S1[q] = fma(h2, dps[c], psi[c]);
+        }
+        build_w(W1, As, eps_s, lt_s, n, lmax, z, r0 + h2, tid);
+        __syncthreads();
+        // stage 2 at r0 + h/2: input S1, W1; writes the stage-3 input to S0
+        w_times(kq, W1, S1, n, tid);
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            const double kp = tq[c];
+            yp[c] = fma(h3, kp, yp[c]);
+            yq[c] = fma(h3, kq[c], yq[c]);
+            tq[c] = fma(h2, kq[c], dps[c]);
+            if (q < n2) S0[q] = fma(h2, kp, psi[c]);
+        }
+        __syncthreads();
+        // stage 3 at r0 + h/2: input S0, W1; writes the stage-4 input to S1
+        // and W(r0 + h) over W0
+        w_times(kq, W1, S0, n, tid);
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            const double kp = tq[c];
+            yp[c] = fma(h3, kp, yp[c]);
+            yq[c] = fma(h3, kq[c], yq[c]);
+            tq[c] = fma(h, kq[c], dps[c]);
+            if (q < n2) S1[q] = fma(h, kp, psi[c]);
+        }
+        build_w(W0, As, eps_s, lt_s, n, lmax, z, r0 + h, tid);
+        __syncthreads();
+        // stage 4 at r0 + h: input S1, W0; the new Psi goes to S0
+        w_times(kq, W0, S1, n, tid);
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            psi[c] = fma(h6, tq[c], yp[c]);
+            dps[c] = fma(h6, kq[c], yq[c]);
+            if (q < n2) S0[q] = psi[c];
+        }
+        __syncthreads();
+        if ((s + 1) % sector == 0 && s + 1 < steps) {
+            // R(r) = Psi (r Psi' - b Psi)^{-1} does not depend on the basis
+            // of solutions Psi holds: continue from Psi = R(r),
+            // r Psi' - b Psi = 1, so that growing closed channels never
+            // swamp the other columns
+            const double r = a + (s + 1) * h;
+            if (!restart_from_r(psi, dps, S0, S1, n, b, r, &esh, tid)) {
+                if (tid == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
+                return;
             }
-            __syncthreads();
-            // W Tp
-            for (int q = tid; q < n2; q += NT) {
-                const int i = q / n, j = q - (q / n) * n;
-                double acc = 0.0;
-                for (int k = 0; k < n; ++k) acc = fma(Wm[i * n + k], ip[k * n + j], acc);
-                Kq[q] = acc;
-            }
-            __syncthreads();
-            // accumulate and form the next stage's input
-            const double wh = cw[st] * h, dh = dn[st] * h;
-            for (int q = tid; q < n2; q += NT) {
-                const double kp = iq[q], kq = Kq[q];
-                Yp[q] = (st == 0 ? Psi[q] : Yp[q]) + wh * kp;
-                Yq[q] = (st == 0 ? P[q] : Yq[q]) + wh * kq;
-                if (st < 3) {
-                    Tp[q] = Psi[q] + dh * kp;
-                    Tq[q] = P[q] + dh * kq;
-                }
-            }
+            build_w(W0, As, eps_s, lt_s, n, lmax, z, r, tid);
             __syncthreads();
         }
-        double *t0 = Psi, *t1 = P;
-        Psi = Yp;
-        P = Yq;
-        Yp = t0;
-        Yq = t1;
     }
-    // R(r1)^T = (r1 Psi' - b Psi)^{-T} Psi^T: eliminate [ (r1 Psi' - b Psi)^T | Psi^T ]
-    // (n x 2n, over Tp..Kq, which hold 3 n^2 doubles)
-    double *M = Tp;
-    const int ld = 2 * n + 1;
-    for (int q = tid; q < n2; q += NT) {
-        const int i = q / n, j = q - (q / n) * n;
-        M[j * ld + i] = r1 * P[q] - b * Psi[q];
-        M[j * ld + n + i] = Psi[q];
-    }
-    if (tid == 0) esh.bad = 0;
-    __syncthreads();
-    block_eliminate<double>(M, ld, n, 2 * n, &esh);
-    if (esh.bad) {
+    // R(r1) = Psi (r1 Psi' - b Psi)^{-1}, written symmetrised
+    if (!restart_from_r(psi, dps, S0, S1, n, b, r1, &esh, tid)) {
         if (tid == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
         return;
     }
-    block_backsub<double>(M, ld, n, n, n, 0);
     for (int q = tid; q < tri_count(n); q += NT) {
         int i, j;
         tri_pair(q, n, i, j);
-        Re[tri_idx(i, j, n)] = 0.5 * (M[i * ld + n + j] + M[j * ld + n + i]);
+        Re[tri_idx(i, j, n)] = 0.5 * (S0[i * n + j] + S0[j * n + i]);
     }
 }
 
 }  // namespace
 
-size_t propagate_smem(int n, int lmax) { return (size_t)(8 + lmax) * n * n * sizeof(double); }
+size_t propagate_smem(int n, int lmax) { return (size_t)(4 + lmax) * n * n * sizeof(double); }
 
 cudaError_t launch_propagate(const PwDev &pw, const double *E, int nE, const double *A, int lmax, double r1,
                              int steps, double *Rp, int *status, cudaStream_t s)

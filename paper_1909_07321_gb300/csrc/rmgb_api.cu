@@ -826,10 +826,10 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
             // deep pairs' too), so a singular propagation never masks an
             // earlier error
             if (split) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-            CK(prof_begin(ctx, RM_PH_FORM));
+            CK(prof_begin(ctx, RM_PH_PROPAGATE));
             CK(launch_propagate(P.dev(), Eb, nb, P.propA.as<double>(), P.prop_lmax, P.prop_r1, P.prop_steps,
                                 ctx->wsR.as<double>(), sb, ctx->stream));
-            CK(prof_end(ctx, RM_PH_FORM));
+            CK(prof_end(ctx, RM_PH_PROPAGATE));
             ++ctx->launches;
         }
         CK(prof_begin(ctx, RM_PH_SOLVE));

@@ -153,3 +153,24 @@ def serving_requests(n_req, rate_hz, n_range=(50, 1500), ne_range=(256, 8192), n
         out.append(dict(id=i, t_arrival=float(t[i]), set_id=sid, n=int(set_n[sid]), E=E,
                         mode=int(rng.random() < mqdt_fraction)))
     return out
+
+
+def workload_multipole(n_energies=2048, n=32):
+    """Outer-region propagation workload: n = 32 channels, 8 levels at
+    linspace(0, 1.4) Ry with 4 channels each, z = 2, a = 15, 30 poles per
+    channel on [-2, 60] Ry, w ~ N(0, 0.05^2); long-range coefficients
+    (Ry a0^(lambda+1)) A^1 ~ N(0, 0.5^2) between channels of different
+    levels (dipole) and A^2 ~ N(0, 0.5^2) between all channels (quadrupole),
+    symmetrised; propagation to r1 = 35 a0 in 2000 steps; energies on a
+    midpoint grid over 0.01-2.5 Ry. Draw order: l, jitter, W, A^1, A^2.
+    Returns (pw, A [2][n][n], r1, n_steps, E)."""
+    rng = np.random.Generator(np.random.PCG64(SEED0 + 5))
+    n_levels = (n + 3) // 4
+    level, l, e_thr = _leveled_channels(rng, n, np.linspace(0.0, 1.4, n_levels))
+    E_k = jittered_poles(rng, 30 * n, -2.0, 60.0)
+    W = rng.normal(0.0, 0.05, (n, 30 * n))
+    A = rng.normal(0.0, 0.5, (2, n, n))
+    A = 0.5 * (A + A.transpose(0, 2, 1))
+    A[0][level[:, None] == level[None, :]] = 0.0
+    pw = _pw(E_k, W, 15.0, e_thr, l, 2.0, level, n_levels, 1.0)
+    return pw, np.ascontiguousarray(A), 35.0, 2000, midpoint_grid(0.01, 2.5, n_energies)
