@@ -382,7 +382,7 @@ def run_qdt(args, prec, sp):
 
 def run_propagation(args, prec, sp, fp64_peak, stream):
     """Outer-region propagation with the multipole potential (32 channels,
-    lambda_max = 2, a = 15 -> r1 = 35 in 2000 RK4 steps): the whole solve of
+    lambda_max = 2, a = 15 -> r1 = 35 in 2000 Numerov steps): the whole solve of
     args.prop_energies energies with propagation, the same solve without it,
     and the propagation kernel against the FP64 pipe."""
     import torch
@@ -391,7 +391,7 @@ def run_propagation(args, prec, sp, fp64_peak, stream):
     pw, A, r1, steps, E = synth.workload_multipole(args.prop_energies)
     n = pw["W"].shape[0]
     lmax = A.shape[0]
-    out = {"workload": "%d channels, lambda_max = %d, a = %g -> r1 = %g in %d RK4 steps, %d energies "
+    out = {"workload": "%d channels, lambda_max = %d, a = %g -> r1 = %g in %d Numerov steps, %d energies "
                        "(0.01-2.5 Ry), formation %s" % (n, lmax, pw["a"], r1, steps, E.size, args.precision)}
     Ed = torch.tensor(E, dtype=torch.float64, device="cuda")
     res = {}
@@ -418,7 +418,7 @@ def run_propagation(args, prec, sp, fp64_peak, stream):
             pl, pms = ctx.profile_get(rmgb.RM_PH_PROPAGATE)
         ctx.close()
         res[name] = (ms, pl, pms / reps)
-    # RK4 truncation: Omega with twice the steps
+    # truncation: Omega with twice the steps
     om2 = {}
     for k, st_ in (("1x", steps), ("2x", 2 * steps)):
         ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, solve_precision=sp)
@@ -431,17 +431,18 @@ def run_propagation(args, prec, sp, fp64_peak, stream):
     dn = np.abs(om2["1x"] - om2["2x"]).max(axis=1) / np.maximum(np.abs(om2["2x"]).max(axis=1), 1e-300)
     ms_p, pl, prop_ms = res["propagated"]
     ms_u = res["unpropagated"][0]
-    # per energy and step: four products W Psi (2 n^3 flops each), the RK4
-    # combinations (14 FMA per element) and two builds of W (lambda_max FMA
-    # per element)
-    flops = E.size * steps * (8.0 * n ** 3 + (28.0 + 4.0 * lmax) * n * n)
+    # per energy and Numerov step: two products T X (2 n^3 flops each), the
+    # summed-form updates (12 flops per element) and one build of T (lambda_max
+    # FMA and a scaling per element); the Runge-Kutta start and the basis
+    # renormalisations are not counted
+    flops = E.size * steps * (4.0 * n ** 3 + (14.0 + 2.0 * lmax) * n * n)
     ach = flops / (prop_ms * 1e-3) / 1e12
     out.update({"propagated": {"energy_solves_per_s": E.size / (ms_p * 1e-3), "ms": ms_p},
                 "unpropagated": {"energy_solves_per_s": E.size / (ms_u * 1e-3), "ms": ms_u},
                 "propagate_ms": prop_ms, "propagate_launches_per_solve": pl / 2,
                 "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
                              "frac": ach / fp64_peak, "traffic": None,
-                             "kernel": "propagate_kernel (FP64 RK4, one CTA per energy)",
+                             "kernel": "propagate_kernel (FP64 Numerov, one CTA per energy)",
                              "flops_per_launch": flops,
                              "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"},
                 "omega_rel_change_with_2x_steps": {"median": float(np.median(dn)), "max": float(dn.max())},

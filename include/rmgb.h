@@ -174,27 +174,30 @@ int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, doub
                     const int *level, int n_levels, double g_weight);
 
 /* Outer-region propagation with the long-range multipole potential (Section
- * "Overview": the coupled radial equations with a non-zero potential matrix
- * U are integrated outward from the inner-region boundary r0 = a to an
- * asymptotic radius r1, where the matching is done; namelist variable
- * ipert). In Rydberg units the equations are
+ * "Overview": the coupled radial functions are carried by Numerov's method
+ * from the inner-region boundary r0 = a to an asymptotic radius r1, where the
+ * matching is done; namelist variables ipert and mzpts). In Rydberg units
+ * the equations are
  *   u_i'' = sum_j [ (l_i(l_i+1)/r^2 - 2z/r - (E - e_i)) delta_ij + U_ij(r) ] u_j,
  *   U(r) = sum_{lambda=1..lambda_max} A^lambda / r^(lambda+1),
  * A (host, [lambda_max][n_ch][n_ch] row-major, A[((lam-1)*n + i)*n + j] =
  * A^lam_ij, each A^lam exactly symmetric; any unit factor is absorbed into A).
  * The solution matrix Psi with Psi(a) = R(a), a Psi'(a) - b Psi(a) = 1 is
- * integrated to r1 >= a by classical fourth-order Runge-Kutta with n_steps
- * fixed steps (FP64, one CTA per energy), and R(r1) = Psi (r1 Psi' - b Psi)^-1
- * replaces R in the matching of rm_solve_energies and rm_solve_energies_qdt,
- * whose channel functions (and channel tables) are then taken at r1. The
- * coupling beyond r1 is not included. No stabilisation is done: strongly
- * closed channels (kappa (r1 - a) large) lose precision as in any shooting
- * method. lambda_max = 0 switches propagation off (A, r1, n_steps ignored).
- * rm_load_poles clears it. rm_form_r still returns R at a. At most 32
- * channels, 1 <= lambda_max <= 4. An energy whose r1 Psi' - b Psi is
- * singular gets RM_ESINGULAR. Synchronous when the channels are set (their
- * tables are rebuilt for r1). Errors: RM_EINVAL (lambda_max out of range, A
- * NULL, non-finite or not symmetric, r1 < a, n_steps < 1), RM_EUNSUPPORTED
+ * carried to r1 >= a by Numerov's method on n_steps equal steps (FP64, one
+ * CTA per energy; the first step is started by four Runge-Kutta steps of a
+ * quarter step, Psi'(r1) comes from an O(h^4) central formula, and every
+ * 1/kappa_max of radius the solution basis is renormalised so that strongly
+ * closed channels do not swamp the others), and
+ * R(r1) = Psi (r1 Psi' - b Psi)^-1 replaces R in the matching of
+ * rm_solve_energies and rm_solve_energies_qdt, whose channel functions (and
+ * channel tables) are then taken at r1. The error is O(h^4), h = (r1 - a) /
+ * n_steps; the coupling beyond r1 is not included. lambda_max = 0 switches
+ * propagation off (A, r1, n_steps ignored). rm_load_poles clears it.
+ * rm_form_r still returns R at a. At most 32 channels, 1 <= lambda_max <= 4.
+ * An energy whose r1 Psi' - b Psi (or a renormalisation) is singular gets
+ * RM_ESINGULAR. Synchronous when the channels are set (their tables are
+ * rebuilt for r1). Errors: RM_EINVAL (lambda_max out of range, A NULL,
+ * non-finite or not symmetric, r1 < a, n_steps < 2), RM_EUNSUPPORTED
  * (n_ch > 32), RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
 int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const double *A, double r1, int n_steps);
 

@@ -1,21 +1,34 @@
 // Outer-region propagation with the long-range multipole potential
-// (Section "Overview", Eq. radial with U != 0; namelist variable ipert): the
-// coupled radial functions are carried from the inner-region boundary r0 = a
-// to the asymptotic radius r1 and matched there.
+// (Section "Overview", Eq. radial with U != 0; namelist variables ipert and
+// mzpts): the coupled radial functions are carried by Numerov's method from
+// the inner-region boundary r0 = a to the asymptotic radius r1 and matched
+// there.
 //
 // In Rydberg units
 //   u_i'' = sum_j W_ij(r) u_j,  W(r) = diag(l_i(l_i+1)/r^2 - 2z/r - eps_i) + U(r),
 //   U(r) = sum_{lambda=1..lambda_max} A^lambda / r^(lambda+1)  (A^lambda symmetric).
 // The R-matrix at a fixes the solution matrix Psi by Psi(a) = R(a),
-// a Psi'(a) - b Psi(a) = 1; Psi and Psi' are integrated to r1 by the
-// classical fourth-order Runge-Kutta method with a fixed number of steps,
-// and R(r1) = Psi(r1) [r1 Psi'(r1) - b Psi(r1)]^{-1} (symmetric; it replaces
-// R(a) in the matching, done at r1). The integration restarts from R(r) at
-// sector boundaries 1 / kappa_max apart (R does not depend on the basis of
-// solutions carried), so that closed channels growing as exp(kappa r) do not
-// swamp the other columns. One CTA of NT threads per energy, FP64.
-// A step costs four products W Psi (4 n^3 FMA) and two builds of W: the
-// kernel runs on the FP64 pipe.
+// a Psi'(a) - b Psi(a) = 1, and R(r1) = Psi(r1) [r1 Psi'(r1) - b Psi(r1)]^{-1}
+// (symmetric; it replaces R(a) in the matching, done at r1).
+//
+// Numerov on the grid r_k = a + k h, h = (r1 - a) / N, with T_k = (h^2/12) W(r_k)
+// and t_k = T_k Psi_k:
+//   Psi_{k+1} - 2 Psi_k + Psi_{k-1} = t_{k+1} + 10 t_k + t_{k-1},
+// carried in summed form (D_k = Psi_k - Psi_{k-1}, which keeps the rounding
+// of the second difference from accumulating):
+//   F = Psi_k + D_k + 10 t_k + t_{k-1},   t_{k+1} = T_{k+1} (1 - T_{k+1})^{-1} F,
+//   D_{k+1} = D_k + t_{k+1} + 10 t_k + t_{k-1},   Psi_{k+1} = Psi_k + D_{k+1},
+// with T (1 - T)^{-1} F = T F + T^2 F + O(T^3 F): the truncation is O(h^6)
+// per step, the order of Numerov's own local error. Psi_1 comes from four
+// classical Runge-Kutta steps of h/4; Psi'(r1) from the O(h^4) central formula
+//   Psi'_N = (Psi_{N+1} - Psi_{N-1}) / (2h) - (t_{N+1} - t_{N-1}) / h
+// (one step past r1). The state (Psi, D, t_k, t_{k-1}) is linear in the basis
+// of solutions, and R does not depend on that basis, so every 1/kappa_max of
+// radius the state is right-multiplied by G^{-1}, G = r D/h - b Psi (about
+// r Psi' - b Psi): closed channels growing as exp(kappa r) never swamp the
+// other columns. One CTA of NT threads per energy, FP64; a step costs two
+// products T X (2 n^3 FMA) and one build of W: the kernel runs on the FP64
+// pipe.
 #include <math.h>
 
 #include "dense_smem.cuh"
@@ -26,11 +39,12 @@ namespace {
 
 // Elements of an n x n matrix one thread owns (q = tid + c NT, c < PROP_QN).
 constexpr int PROP_QN = (PROP_MAXN * PROP_MAXN + NT - 1) / NT;
+constexpr int PROP_START_SUB = 4;   // Runge-Kutta steps of h/4 to Psi_1
 
-// W(r) at the owned elements into Wd: sum_lambda A^lambda r^-(lambda+1) plus
-// the diagonal l(l+1)/r^2 - 2z/r - eps.
+// scale W(r) at the owned elements into Wd: sum_lambda A^lambda
+// r^-(lambda+1) plus the diagonal l(l+1)/r^2 - 2z/r - eps.
 __device__ __forceinline__ void build_w(double *Wd, const double *As, const double *eps_s, const double *lt_s,
-                                        int n, int lmax, double z, double r, int tid)
+                                        int n, int lmax, double z, double r, double scale, int tid)
 {
     const int n2 = n * n;
     const double ir = 1.0 / r;
@@ -45,13 +59,13 @@ __device__ __forceinline__ void build_w(double *Wd, const double *As, const doub
                 rp *= ir;
             }
             if (i == j) u += lt_s[i] * ir * ir - 2.0 * z * ir - eps_s[i];
-            Wd[q] = u;
+            Wd[q] = scale * u;
         }
     }
 }
 
-// (W S) at the owned elements, the PROP_QN dot products interleaved.
-__device__ __forceinline__ void w_times(double (&kq)[PROP_QN], const double *Wd, const double *S, int n, int tid)
+// (X S) at the owned elements, the PROP_QN dot products interleaved.
+__device__ __forceinline__ void mat_times(double (&kq)[PROP_QN], const double *X, const double *S, int n, int tid)
 {
     const int n2 = n * n;
     int wi[PROP_QN], sj[PROP_QN];
@@ -65,25 +79,90 @@ __device__ __forceinline__ void w_times(double (&kq)[PROP_QN], const double *Wd,
 #pragma unroll 2
     for (int k = 0; k < n; ++k) {
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) kq[c] = fma(Wd[wi[c] + k], S[k * n + sj[c]], kq[c]);
+        for (int c = 0; c < PROP_QN; ++c) kq[c] = fma(X[wi[c] + k], S[k * n + sj[c]], kq[c]);
     }
 }
 
-// Psi <- Psi G^{-1}, Psi' <- Psi' G^{-1} with G = r Psi' - b Psi at the
-// owned elements (then Psi = R(r) and r Psi' - b Psi = 1), by eliminating
-// [ G^T | Psi^T ] over M (n x 2n, row stride 2n + 1; the caller's 3 n^2
-// doubles of scratch). The new Psi also goes to S. False if G is singular.
-__device__ bool restart_from_r(double (&psi)[PROP_QN], double (&dps)[PROP_QN], double *S, double *M, int n,
-                               double b, double r, ElimShared *esh, int tid)
+// nsub classical Runge-Kutta steps of hh from r_start on (psi, dps) in
+// registers. Scratch S0, S1 (stage inputs of Psi), W0, W1 (W at the step's
+// start and middle); on return S0 holds Psi. Starts and ends with a barrier.
+__device__ void rk4_steps(double (&psi)[PROP_QN], double (&dps)[PROP_QN], double *S0, double *S1, double *W0,
+                          double *W1, const double *As, const double *eps_s, const double *lt_s, int n, int lmax,
+                          double z, double r_start, double hh, int nsub, int tid)
+{
+    const int n2 = n * n;
+    const double h2 = 0.5 * hh, h3 = hh / 3.0, h6 = hh / 6.0;
+    double yp[PROP_QN], yq[PROP_QN], tq[PROP_QN], kq[PROP_QN];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c)
+        if (tid + c * NT < n2) S0[tid + c * NT] = psi[c];
+    build_w(W0, As, eps_s, lt_s, n, lmax, z, r_start, 1.0, tid);
+    __syncthreads();
+    for (int s = 0; s < nsub; ++s) {
+        const double r0 = r_start + s * hh;
+        mat_times(kq, W0, S0, n, tid);                  // stage 1
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            yp[c] = fma(h6, dps[c], psi[c]);
+            yq[c] = fma(h6, kq[c], dps[c]);
+            tq[c] = fma(h2, kq[c], dps[c]);
+            if (q < n2) S1[q] = fma(h2, dps[c], psi[c]);
+        }
+        build_w(W1, As, eps_s, lt_s, n, lmax, z, r0 + h2, 1.0, tid);
+        __syncthreads();
+        mat_times(kq, W1, S1, n, tid);                  // stage 2
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            const double kp = tq[c];
+            yp[c] = fma(h3, kp, yp[c]);
+            yq[c] = fma(h3, kq[c], yq[c]);
+            tq[c] = fma(h2, kq[c], dps[c]);
+            if (q < n2) S0[q] = fma(h2, kp, psi[c]);
+        }
+        __syncthreads();
+        mat_times(kq, W1, S0, n, tid);                  // stage 3
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            const double kp = tq[c];
+            yp[c] = fma(h3, kp, yp[c]);
+            yq[c] = fma(h3, kq[c], yq[c]);
+            tq[c] = fma(hh, kq[c], dps[c]);
+            if (q < n2) S1[q] = fma(hh, kp, psi[c]);
+        }
+        build_w(W0, As, eps_s, lt_s, n, lmax, z, r0 + hh, 1.0, tid);
+        __syncthreads();
+        mat_times(kq, W0, S1, n, tid);                  // stage 4
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) {
+            const int q = tid + c * NT;
+            psi[c] = fma(h6, tq[c], yp[c]);
+            dps[c] = fma(h6, kq[c], yq[c]);
+            if (q < n2) S0[q] = psi[c];
+        }
+        __syncthreads();
+    }
+}
+
+// Writes [ G^T | 1 ] (n x 2n, row stride 2n + 1) over M from G at the owned
+// elements and leaves G^{-T} in its right half (M[j ld + n + k] =
+// (G^{-1})_kj). The caller has passed a barrier since M was last read.
+// False if G is singular.
+__device__ bool invert_owned(const double (&g)[PROP_QN], double *M, int n, ElimShared *esh, int tid)
 {
     const int n2 = n * n, ld = 2 * n + 1;
+    for (int q = tid; q < n * ld; q += NT) M[q] = 0.0;
+    __syncthreads();
 #pragma unroll
     for (int c = 0; c < PROP_QN; ++c) {
         const int q = tid + c * NT;
         if (q < n2) {
             const int i = q / n, j = q - (q / n) * n;
-            M[j * ld + i] = r * dps[c] - b * psi[c];
-            M[j * ld + n + i] = psi[c];
+            M[j * ld + i] = g[c];
+            if (i == j) M[j * ld + n + i] = 1.0;
         }
     }
     if (tid == 0) esh->bad = 0;
@@ -91,26 +170,29 @@ __device__ bool restart_from_r(double (&psi)[PROP_QN], double (&dps)[PROP_QN], d
     block_eliminate<double>(M, ld, n, 2 * n, esh);
     if (esh->bad) return false;
     block_backsub<double>(M, ld, n, n, n, 0);
-#pragma unroll
-    for (int c = 0; c < PROP_QN; ++c) {
-        const int q = tid + c * NT;
-        if (q < n2) {
-            const int i = q / n, j = q - (q / n) * n;
-            psi[c] = M[j * ld + n + i];
-            dps[c] = ((i == j ? 1.0 : 0.0) + b * psi[c]) / r;
-            S[q] = psi[c];
-        }
-    }
-    __syncthreads();
     return true;
 }
 
-// One CTA per energy. The solution Psi and its derivative at the owned
-// elements stay in registers with the RK4 accumulators; shared memory holds
-// what the products W S read across threads: the stage input of Psi (two
-// buffers, alternating by stage) and W (two buffers: at r0 and r0 + h/2;
-// W(r0 + h) is built over the first once stage 1 is done with it), then the
-// coefficients A. One barrier per stage.
+// x <- x G^{-1} at the owned elements, with G^{-T} in M (as invert_owned
+// leaves it) and SX (n^2 doubles, disjoint from M) as staging.
+__device__ void times_ginv(double (&x)[PROP_QN], const double *M, double *SX, int n, int tid)
+{
+    const int n2 = n * n, ld = 2 * n + 1;
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c)
+        if (tid + c * NT < n2) SX[tid + c * NT] = x[c];
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c) {
+        const int q = min(tid + c * NT, n2 - 1);
+        const int i = q / n, j = q - (q / n) * n;
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc = fma(SX[i * n + k], M[j * ld + n + k], acc);
+        x[c] = acc;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double *__restrict__ E,
                                                           const double *__restrict__ A, int lmax, double r1,
                                                           int steps, double *__restrict__ Rp,
@@ -122,7 +204,9 @@ __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double
     const int e = blockIdx.x, tid = threadIdx.x;
     const int n = pw.n, n2 = n * n;
     if (status[e] != RM_OK) return;
-    double *S0 = sm, *S1 = sm + n2, *W0 = sm + 2 * n2, *W1 = sm + 3 * n2, *As = sm + 4 * n2;
+    // SF (F), SG (T F), TA / TB (T_{k+1}, alternating by step), then A; the
+    // restarts use the first 4 n^2 doubles as scratch
+    double *SF = sm, *SG = sm + n2, *TA = sm + 2 * n2, *TB = sm + 3 * n2, *As = sm + 4 * n2;
     const double a = pw.a, b = pw.b, z = pw.z, x = E[e];
     double *Re = Rp + (size_t)e * tri_ld(n);
     for (int q = tid; q < lmax * n2; q += NT) As[q] = A[q];
@@ -130,22 +214,38 @@ __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double
         eps_s[i] = x - pw.e_thr[i];
         lt_s[i] = (double)pw.l[i] * (pw.l[i] + 1);
     }
-    double psi[PROP_QN], dps[PROP_QN], yp[PROP_QN], yq[PROP_QN], tq[PROP_QN], kq[PROP_QN];
+    const double h = (r1 - a) / steps, t12 = h * h / 12.0;
+    double psi[PROP_QN], dl[PROP_QN], tp[PROP_QN], tpp[PROP_QN], kq[PROP_QN];
 #pragma unroll
     for (int c = 0; c < PROP_QN; ++c) {
         const int q = tid + c * NT;
-        psi[c] = dps[c] = yp[c] = yq[c] = tq[c] = 0.0;
+        psi[c] = dl[c] = 0.0;
         if (q < n2) {
             const int i = q / n, j = q - (q / n) * n;
             psi[c] = Re[i <= j ? tri_idx(i, j, n) : tri_idx(j, i, n)];
-            dps[c] = ((i == j ? 1.0 : 0.0) + b * psi[c]) / a;
-            S0[q] = psi[c];
+            dl[c] = ((i == j ? 1.0 : 0.0) + b * psi[c]) / a;    // Psi'(a) for the starter
+            SF[q] = psi[c];
         }
     }
     __syncthreads();
-    build_w(W0, As, eps_s, lt_s, n, lmax, z, a, tid);
-    const double h = (r1 - a) / steps, h2 = 0.5 * h, h3 = h / 3.0, h6 = h / 6.0;
-    // restart from R every `sector` steps, a sector being 1 / kappa_max long,
+    // t_0 = T_0 Psi_0
+    build_w(TA, As, eps_s, lt_s, n, lmax, z, a, t12, tid);
+    __syncthreads();
+    mat_times(tpp, TA, SF, n, tid);
+    // Psi_1 (dl: Psi'(a) in, then D_1 = Psi_1 - Psi_0), t_1 = T_1 Psi_1
+    {
+        double p0[PROP_QN];
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) p0[c] = psi[c];
+        rk4_steps(psi, dl, SF, SG, TA, TB, As, eps_s, lt_s, n, lmax, z, a, h / PROP_START_SUB, PROP_START_SUB,
+                  tid);
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c) dl[c] = psi[c] - p0[c];
+    }
+    build_w(TA, As, eps_s, lt_s, n, lmax, z, a + h, t12, tid);
+    __syncthreads();
+    mat_times(tp, TA, SF, n, tid);
+    // restart every `sector` steps, a sector being 1 / kappa_max long,
     // kappa_max^2 = max_i (l_i(l_i+1)/a^2 - eps_i)
     int sector = steps;
     {
@@ -155,79 +255,78 @@ __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double
         sector = m >= (double)steps ? steps : max(1, (int)m);
     }
     __syncthreads();
-    for (int s = 0; s < steps; ++s) {
-        const double r0 = a + s * h;
-        // stage 1 at r0: input Psi (S0), W0; writes the stage-2 input to S1
-        w_times(kq, W0, S0, n, tid);
+    for (int k = 1; k <= steps; ++k) {
+        double *Tk = (k & 1) ? TB : TA;
+        // F and T_{k+1}
 #pragma unroll
         for (int c = 0; c < PROP_QN; ++c) {
             const int q = tid + c * NT;
-            yp[c] = fma(h6, dps[c], psi[c]);
-            yq[c] = fma(h6, kq[c], dps[c]);
-            tq[c] = fma(h2, kq[c], dps[c]);
-            if (q < n2) S1[q] = fma(h2, dps[c], psi[c]);
+            if (q < n2) SF[q] = psi[c] + dl[c] + fma(10.0, tp[c], tpp[c]);
         }
-        build_w(W1, As, eps_s, lt_s, n, lmax, z, r0 + h2, tid);
+        build_w(Tk, As, eps_s, lt_s, n, lmax, z, a + (k + 1) * h, t12, tid);
         __syncthreads();
-        // stage 2 at r0 + h/2: input S1, W1; writes the stage-3 input to S0
-        w_times(kq, W1, S1, n, tid);
+        // T F
+        mat_times(kq, Tk, SF, n, tid);
+#pragma unroll
+        for (int c = 0; c < PROP_QN; ++c)
+            if (tid + c * NT < n2) SG[tid + c * NT] = kq[c];
+        __syncthreads();
+        // t_{k+1} = T F + T (T F); D, Psi; shift t
+        double g2[PROP_QN];
+        mat_times(g2, Tk, SG, n, tid);
+        const bool last = k == steps;
 #pragma unroll
         for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
-            const double kp = tq[c];
-            yp[c] = fma(h3, kp, yp[c]);
-            yq[c] = fma(h3, kq[c], yq[c]);
-            tq[c] = fma(h2, kq[c], dps[c]);
-            if (q < n2) S0[q] = fma(h2, kp, psi[c]);
+            const double tn = kq[c] + g2[c];
+            const double d = dl[c] + tn + fma(10.0, tp[c], tpp[c]);
+            if (!last) {
+                dl[c] = d;
+                psi[c] += d;
+                tpp[c] = tp[c];
+                tp[c] = tn;
+            } else {
+                // Psi_N = psi (before the step) and Psi'_N from Psi_{N+1} =
+                // psi + d, Psi_{N-1} = psi - dl, t_{N+1} = tn, t_{N-1} = tpp
+                dl[c] = (d + dl[c]) / (2.0 * h) - (tn - tpp[c]) / h;
+            }
         }
-        __syncthreads();
-        // stage 3 at r0 + h/2: input S0, W1; writes the stage-4 input to S1
-        // and W(r0 + h) over W0
-        w_times(kq, W1, S0, n, tid);
+        if (k % sector == 0 && k + 1 < steps) {
+            // right-multiply the state by G^{-1}, G = r D / h - b Psi
+            const double r = a + (k + 1) * h;
+            double g[PROP_QN];
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
-            const double kp = tq[c];
-            yp[c] = fma(h3, kp, yp[c]);
-            yq[c] = fma(h3, kq[c], yq[c]);
-            tq[c] = fma(h, kq[c], dps[c]);
-            if (q < n2) S1[q] = fma(h, kp, psi[c]);
-        }
-        build_w(W0, As, eps_s, lt_s, n, lmax, z, r0 + h, tid);
-        __syncthreads();
-        // stage 4 at r0 + h: input S1, W0; the new Psi goes to S0
-        w_times(kq, W0, S1, n, tid);
-#pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
-            psi[c] = fma(h6, tq[c], yp[c]);
-            dps[c] = fma(h6, kq[c], yq[c]);
-            if (q < n2) S0[q] = psi[c];
-        }
-        __syncthreads();
-        if ((s + 1) % sector == 0 && s + 1 < steps) {
-            // R(r) = Psi (r Psi' - b Psi)^{-1} does not depend on the basis
-            // of solutions Psi holds: continue from Psi = R(r),
-            // r Psi' - b Psi = 1, so that growing closed channels never
-            // swamp the other columns
-            const double r = a + (s + 1) * h;
-            if (!restart_from_r(psi, dps, S0, S1, n, b, r, &esh, tid)) {
+            for (int c = 0; c < PROP_QN; ++c) g[c] = fma(r / h, dl[c], -b * psi[c]);
+            __syncthreads();
+            if (!invert_owned(g, sm, n, &esh, tid)) {
                 if (tid == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
                 return;
             }
-            build_w(W0, As, eps_s, lt_s, n, lmax, z, r, tid);
-            __syncthreads();
+            double *SX = sm + 3 * n2;
+            times_ginv(psi, sm, SX, n, tid);
+            times_ginv(dl, sm, SX, n, tid);
+            times_ginv(tp, sm, SX, n, tid);
+            times_ginv(tpp, sm, SX, n, tid);
         }
     }
-    // R(r1) = Psi (r1 Psi' - b Psi)^{-1}, written symmetrised
-    if (!restart_from_r(psi, dps, S0, S1, n, b, r1, &esh, tid)) {
+    // R(r1) = Psi_N (r1 Psi'_N - b Psi_N)^{-1}, written symmetrised
+    double g[PROP_QN];
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c) g[c] = fma(r1, dl[c], -b * psi[c]);
+    __syncthreads();
+    if (!invert_owned(g, sm, n, &esh, tid)) {
         if (tid == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
         return;
     }
+    double *SX = sm + 3 * n2;
+    times_ginv(psi, sm, SX, n, tid);
+#pragma unroll
+    for (int c = 0; c < PROP_QN; ++c)
+        if (tid + c * NT < n2) SX[tid + c * NT] = psi[c];
+    __syncthreads();
     for (int q = tid; q < tri_count(n); q += NT) {
         int i, j;
         tri_pair(q, n, i, j);
-        Re[tri_idx(i, j, n)] = 0.5 * (S0[i * n + j] + S0[j * n + i]);
+        Re[tri_idx(i, j, n)] = 0.5 * (SX[i * n + j] + SX[j * n + i]);
     }
 }
 
@@ -238,7 +337,7 @@ size_t propagate_smem(int n, int lmax) { return (size_t)(4 + lmax) * n * n * siz
 cudaError_t launch_propagate(const PwDev &pw, const double *E, int nE, const double *A, int lmax, double r1,
                              int steps, double *Rp, int *status, cudaStream_t s)
 {
-    if (pw.n > PROP_MAXN || lmax < 0 || lmax > PROP_MAX_LAMBDA || steps < 1) return cudaErrorInvalidValue;
+    if (pw.n > PROP_MAXN || lmax < 0 || lmax > PROP_MAX_LAMBDA || steps < 2) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
     const size_t smem = propagate_smem(pw.n, lmax);
     cudaError_t err = cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -77,7 +77,7 @@ struct PwHost {
     double ctab_nu_lo = 0.0;
     int ctab_nseg = 0;
     // outer-region propagation (rm_set_multipoles): coefficients [lmax][n][n]
-    // on the device, radius r1, RK4 steps; prop_lmax < 0: none
+    // on the device, radius r1, Numerov steps; prop_lmax < 0: none
     DevBuf propA;
     int prop_lmax = -1, prop_steps = 0;
     double prop_r1 = 0.0;
@@ -547,7 +547,7 @@ extern "C" int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const doub
         return fail(ctx, RM_EINVAL, "lambda_max=%d out of [0,%d]", lambda_max, PROP_MAX_LAMBDA);
     if (!A) return fail(ctx, RM_EINVAL, "NULL multipole coefficients");
     if (!std::isfinite(r1) || !(r1 >= P.a)) return fail(ctx, RM_EINVAL, "r1=%g must be >= a=%g", r1, P.a);
-    if (n_steps < 1) return fail(ctx, RM_EINVAL, "n_steps=%d must be >= 1", n_steps);
+    if (n_steps < 2) return fail(ctx, RM_EINVAL, "n_steps=%d must be >= 2", n_steps);
     const size_t cnt = (size_t)lambda_max * n * n;
     if (!finite_all(A, (int)cnt)) return fail(ctx, RM_EINVAL, "non-finite multipole coefficient");
     for (int lam = 0; lam < lambda_max; ++lam)

@@ -161,7 +161,8 @@ def workload_multipole(n_energies=2048, n=32):
     channel on [-2, 60] Ry, w ~ N(0, 0.05^2); long-range coefficients
     (Ry a0^(lambda+1)) A^1 ~ N(0, 0.5^2) between channels of different
     levels (dipole) and A^2 ~ N(0, 0.5^2) between all channels (quadrupole),
-    symmetrised; propagation to r1 = 35 a0 in 2000 steps; energies on a
+    symmetrised; propagation to r1 = 35 a0 in 2000 Numerov steps (the
+    paper's default outer grid has 3201 points); energies on a
     midpoint grid over 0.01-2.5 Ry. Draw order: l, jitter, W, A^1, A^2.
     Returns (pw, A [2][n][n], r1, n_steps, E)."""
     rng = np.random.Generator(np.random.PCG64(SEED0 + 5))

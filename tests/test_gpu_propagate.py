@@ -1,11 +1,12 @@
 """Outer-region propagation with the long-range multipole potential on the GPU
 (rm_set_multipoles) against the oracle (oracle/propagate.py).
 
-The GPU integrates the coupled equations from a to r1 by RK4 with a fixed
-number of steps, the oracle by DOP853 at rtol 1e-12; with a = 12, r1 = 15 and
-4000 steps (h = 7.5e-4, |W| h <~ 1e-3) the RK4 truncation is far below the
-1e-9 bar, so K and Omega must agree to 1e-9 norm-wise and per element, in
-direct and MQDT modes, with and without channel tables (built at r1).
+The GPU integrates the coupled equations from a to r1 by Numerov's method
+with a fixed number of steps, the oracle by DOP853 at rtol 1e-13 sector by
+sector; with a = 12, r1 = 15 and 4000 steps (h = 7.5e-4) the O(h^4) error of
+Numerov is ~1e-13 of R, far below the 1e-9 bar, so K and Omega must agree to
+1e-9 norm-wise and per element, in direct and MQDT modes, with and without
+channel tables (built at r1).
 """
 import numpy as np
 import pytest
@@ -135,7 +136,7 @@ def test_coupling_matters_and_off_switch(rt):
 
 def test_zero_coupling_matches_unpropagated(rt):
     """A = 0: propagation from a to r1 only carries the Coulomb functions
-    along, so K matched at r1 equals K matched at a (to the RK4 error)."""
+    along, so K matched at r1 equals K matched at a (to Numerov's error)."""
     pw = _pw()
     E = _energies(pw)
     K0, no0, st0, om0 = _gpu_solve(rt, pw, E, None, 0)
@@ -176,7 +177,7 @@ def test_set_multipoles_rejects_bad_arguments(rt):
         cases = [
             (np.zeros((5, 4, 4)), R1, STEPS, rmgb.RM_EINVAL),              # lambda_max > 4
             (A, A_ - 0.5, STEPS, rmgb.RM_EINVAL),                          # r1 < a
-            (A, R1, 0, rmgb.RM_EINVAL),                                    # no steps
+            (A, R1, 1, rmgb.RM_EINVAL),                                    # < 2 steps
             (A + np.triu(np.ones((4, 4)), 1)[None], R1, STEPS, rmgb.RM_EINVAL),  # not symmetric
             (np.full((1, 4, 4), np.nan), R1, STEPS, rmgb.RM_EINVAL),
         ]
@@ -198,9 +199,10 @@ def test_multipole_workload_sampled(rt):
     """The 32-channel multipole workload (lambda_max = 2, a = 15 -> r1 = 35),
     all 1024 energies in one launch as the benchmark runs them: FP64 with 16x
     the benchmark's steps against the oracle at 1e-9 on 8 sampled energies
-    (RK4's error in R falls 16x per halving of h: ~1e-9 at 8000 steps, ~3e-11
-    at 32000), and the benchmark's mixed configuration (bf16x3 formation,
-    FP32 solve, 2000 steps) within the mixed path's accuracy."""
+    (Numerov's error in R falls 16x per halving of h: ~7e-8 at 2000 steps,
+    ~2e-10 at 8000; at 32000 what is left, ~6e-11, is rounding on both
+    sides), and the benchmark's mixed configuration (bf16x3 formation, FP32
+    solve, 2000 steps) within the mixed path's accuracy."""
     torch, rmgb = rt
     pw, A, r1, steps, E = synth.workload_multipole(1024)
     n = pw["W"].shape[0]
