@@ -119,3 +119,87 @@ def test_sectors_do_not_change_k():
         Ks.append(K)
     for K in Ks[1:]:
         np.testing.assert_allclose(K, Ks[2], rtol=0, atol=1e-11 * np.abs(Ks[2]).max())
+
+
+def _fit_and_r1(u, du, a, r1, R_a, b):
+    """Closed-form single-channel propagation: the solution u = c1 u1 + c2 u2
+    through Psi(a) = R_a, a Psi'(a) - b Psi(a) = 1, then R(r1)."""
+    psi_a, dpsi_a = R_a, (1.0 + b * R_a) / a
+    M = np.array([[u[0](a), u[1](a)], [du[0](a), du[1](a)]])
+    c = np.linalg.solve(M, [psi_a, dpsi_a])
+    psi = c[0] * u[0](r1) + c[1] * u[1](r1)
+    dpsi = c[0] * du[0](r1) + c[1] * du[1](r1)
+    return psi / (r1 * dpsi - b * psi)
+
+
+def test_dipole_tail_bessel_closed_form():
+    """One channel, z = 0, l = 0, U = A/r^2 (lambda = 1): u'' = (A/r^2 - k^2) u
+    is solved by sqrt(r) J_nu(k r), sqrt(r) Y_nu(k r) with nu^2 = A + 1/4.
+    Fixes the power r^-(lambda+1), the sign of U and of eps, and b."""
+    sp = pytest.importorskip("scipy.special")
+    a, r1, k = 9.0, 16.0, 0.8
+    for A1, b, R_a in ((0.7, 0.0, 0.4), (2.5, 0.6, -1.3), (-0.2, -0.4, 3.0)):
+        nu = np.sqrt(A1 + 0.25)
+        u = (lambda r: np.sqrt(r) * sp.jv(nu, k * r), lambda r: np.sqrt(r) * sp.yv(nu, k * r))
+        du = (lambda r: sp.jv(nu, k * r) / (2 * np.sqrt(r)) + np.sqrt(r) * k * sp.jvp(nu, k * r),
+              lambda r: sp.yv(nu, k * r) / (2 * np.sqrt(r)) + np.sqrt(r) * k * sp.yvp(nu, k * r))
+        exact = _fit_and_r1(u, du, a, r1, R_a, b)
+        R1 = pr.propagate_r(np.array([[R_a]]), a, r1, [k * k], [0], 0.0, np.array([[[A1]]]), b)
+        assert abs(R1[0, 0] - exact) <= 1e-10 * max(1.0, abs(exact)), (A1, b, R1[0, 0], exact)
+
+
+def test_quadrupole_tail_zero_energy_closed_form():
+    """One channel, z = 0, l = 0, E = threshold, U = A/r^3 (lambda = 2, A > 0):
+    u'' = A r^-3 u is solved by sqrt(r) I_1(x), sqrt(r) K_1(x), x = 2 sqrt(A/r)
+    (u' = (Z - x Z'(x)) / (2 sqrt r))."""
+    sp = pytest.importorskip("scipy.special")
+    a, r1 = 6.0, 14.0
+    for A2, b, R_a in ((1.5, 0.0, 0.9), (4.0, 0.3, -0.5)):
+        def x(r):
+            return 2.0 * np.sqrt(A2 / r)
+        u = (lambda r: np.sqrt(r) * sp.iv(1, x(r)), lambda r: np.sqrt(r) * sp.kv(1, x(r)))
+        du = (lambda r: (sp.iv(1, x(r)) - x(r) * sp.ivp(1, x(r))) / (2 * np.sqrt(r)),
+              lambda r: (sp.kv(1, x(r)) - x(r) * sp.kvp(1, x(r))) / (2 * np.sqrt(r)))
+        exact = _fit_and_r1(u, du, a, r1, R_a, b)
+        A = np.zeros((2, 1, 1))
+        A[1, 0, 0] = A2
+        R1 = pr.propagate_r(np.array([[R_a]]), a, r1, [0.0], [0], 0.0, A, b)
+        assert abs(R1[0, 0] - exact) <= 1e-10 * max(1.0, abs(exact)), (A2, b, R1[0, 0], exact)
+
+
+_orig_coupling = pr.coupling
+_orig_propagate_r = pr.propagate_r
+
+
+def _coupling_power(r, A):
+    A = np.asarray(A, dtype=np.float64)
+    return sum(A[lam - 1] / r ** lam for lam in range(1, A.shape[0] + 1))
+
+
+def _coupling_sign(r, A):
+    return -_orig_coupling(r, A)
+
+
+def _propagate_eps_sign(R_a, a, r1, eps, l, z, A, b=0.0, **kw):
+    return _orig_propagate_r(R_a, a, r1, -np.asarray(eps, dtype=np.float64), l, z, A, b, **kw)
+
+
+def _propagate_b_sign(R_a, a, r1, eps, l, z, A, b=0.0, **kw):
+    return _orig_propagate_r(R_a, a, r1, eps, l, z, A, -b, **kw)
+
+
+@pytest.mark.parametrize("name,fn", [("coupling", _coupling_power), ("coupling", _coupling_sign),
+                                     ("propagate_r", _propagate_eps_sign),
+                                     ("propagate_r", _propagate_b_sign)],
+                         ids=["power", "u_sign", "eps_sign", "b_sign"])
+def test_propagation_mutation_is_caught(monkeypatch, name, fn):
+    """Each planted mistake fails at least one of the closed-form pins."""
+    monkeypatch.setattr(pr, name, fn)
+    caught = 0
+    for pin in (test_free_s_wave_closed_form, test_dipole_tail_bessel_closed_form,
+                test_quadrupole_tail_zero_energy_closed_form):
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught, name
