@@ -23,7 +23,8 @@
  * Conventions for every call:
  *  - Return value 0 on success, a negative RM_E* code on error; no call aborts,
  *    traps or exits. rm_last_error(ctx) gives a one-line reason.
- *  - Host pointers are read during the call and not retained. Pointers marked
+ *  - Host pointers are read during the call and not retained (except the
+ *    output of rm_collision_strengths_async, written until rm_sync). Pointers marked
  *    "device" must be device memory of the context's GPU (e.g. torch tensors).
  *  - A context is not thread-safe: use one context per host thread.
  *  - Work is enqueued on the context's stream; only rm_collision_strengths,
@@ -255,6 +256,18 @@ int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double *E, int ieq
  * RM_ECUDA. */
 int rm_collision_strengths(rm_ctx *ctx, double *omega_out, int reset);
 
+/* As rm_collision_strengths, without waiting: the copy of the accumulated
+ * collision strengths to omega_out (host, same layout; page-locked memory for
+ * the copy to overlap) is enqueued on the context's copy stream after the
+ * work already enqueued, and the call returns. omega_out is written
+ * asynchronously: the caller must not read or free it before rm_sync.
+ * reset != 0 forgets the grid as rm_collision_strengths does, and the next
+ * solves accumulate into a second device buffer while this one drains, so
+ * that a loop of solve + read-out keeps the GPU busy during the copies; with
+ * reset = 0 the next work on the context stream waits for the copy.
+ * Errors: RM_EINVAL (no grid yet, omega_out NULL), RM_ECUDA. */
+int rm_collision_strengths_async(rm_ctx *ctx, double *omega_out, int reset);
+
 /* Zeroes the Omega accumulator, keeping the registered grid. Asynchronous.
  * Errors: RM_EINVAL (no grid yet), RM_ECUDA. */
 int rm_reset_omega(rm_ctx *ctx);
@@ -337,7 +350,8 @@ int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E, const doub
                           int *n_open_out, int *status_out, void *stream, char *errbuf,
                           size_t errlen);
 
-/* Waits for all work enqueued on the context's stream. */
+/* Waits for all work enqueued on the context's stream and for the copies of
+ * rm_collision_strengths_async. */
 int rm_sync(rm_ctx *ctx);
 
 /* Number of kernels this context has launched since creation. */

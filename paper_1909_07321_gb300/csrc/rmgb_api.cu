@@ -13,6 +13,7 @@
 #include <cstring>
 #include <limits>
 #include <numeric>
+#include <utility>
 #include <vector>
 
 #include "rm_internal.cuh"
@@ -151,6 +152,14 @@ struct rm_ctx {
     int grid_nE = 0, grid_nlev = 0, grid_ntri = 0;
     std::vector<double> grid_host;
     DevBuf omega;
+    // asynchronous read-out (rm_collision_strengths_async): a second
+    // accumulator, a copy stream, and per physical buffer (cur: the active
+    // one) the event after its last copy
+    DevBuf omega_alt;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_solved = nullptr, ev_copied[2] = {nullptr, nullptr};
+    bool copied[2] = {false, false};
+    int omega_cur = 0;
     // workspace
     DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep, wsNear, wsEhl;
     // coarse-mesh interpolation: node energies, statuses + orders, K_u, S_u, fine plan
@@ -344,7 +353,14 @@ extern "C" void rm_destroy(rm_ctx *ctx)
     cudaSetDevice(ctx->opts.device);
     cudaStreamSynchronize(ctx->stream);
     for (auto &p : ctx->pw) p.release();
-    for (DevBuf *d : {&ctx->omega, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
+    if (ctx->copy) {
+        cudaStreamSynchronize(ctx->copy);
+        cudaStreamDestroy(ctx->copy);
+    }
+    if (ctx->ev_solved) cudaEventDestroy(ctx->ev_solved);
+    for (cudaEvent_t ev : ctx->ev_copied)
+        if (ev) cudaEventDestroy(ev);
+    for (DevBuf *d : {&ctx->omega, &ctx->omega_alt, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
                       &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsNear, &ctx->wsEhl, &ctx->wsQn,
                       &ctx->wsQst, &ctx->wsQk, &ctx->wsQs, &ctx->wsQf, &ctx->wsQc})
         d->release();
@@ -1009,6 +1025,40 @@ extern "C" int rm_collision_strengths(rm_ctx *ctx, double *omega_out, int reset)
     return RM_SUCCESS;
 }
 
+extern "C" int rm_collision_strengths_async(rm_ctx *ctx, double *omega_out, int reset)
+{
+    if (!ctx) return RM_EINVAL;
+    if (!omega_out) return fail(ctx, RM_EINVAL, "omega_out is NULL");
+    if (ctx->grid_nE == 0) return fail(ctx, RM_EINVAL, "no energy grid registered yet");
+    CK(cudaSetDevice(ctx->opts.device));
+    if (!ctx->copy) {
+        CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ctx->ev_solved, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_copied[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ctx->ev_copied[1], cudaEventDisableTiming));
+    }
+    const size_t bytes = (size_t)ctx->grid_nE * ctx->grid_ntri * sizeof(double);
+    const int cur = ctx->omega_cur;
+    CK(cudaEventRecord(ctx->ev_solved, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->copy, ctx->ev_solved, 0));
+    CK(cudaMemcpyAsync(omega_out, ctx->omega.p, bytes, cudaMemcpyDeviceToHost, ctx->copy));
+    CK(cudaEventRecord(ctx->ev_copied[cur], ctx->copy));
+    ctx->copied[cur] = true;
+    if (reset) {
+        // later solves accumulate into the other buffer once its own last
+        // copy is done; this one drains on the copy stream meanwhile
+        std::swap(ctx->omega, ctx->omega_alt);
+        ctx->omega_cur = cur ^ 1;
+        if (ctx->copied[cur ^ 1]) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[cur ^ 1], 0));
+        ctx->grid_nE = ctx->grid_nlev = ctx->grid_ntri = 0;
+        ctx->grid_host.clear();
+    } else {
+        // the accumulator keeps growing: nothing may touch it before the copy
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[cur], 0));
+    }
+    return RM_SUCCESS;
+}
+
 extern "C" int rm_reset_omega(rm_ctx *ctx)
 {
     if (!ctx) return RM_EINVAL;
@@ -1117,6 +1167,7 @@ extern "C" int rm_sync(rm_ctx *ctx)
 {
     if (!ctx) return RM_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->copy) CK(cudaStreamSynchronize(ctx->copy));
     return check_device_flag(ctx);
 }
 

@@ -60,6 +60,7 @@ _SIGS = {
     "rm_set_multipoles": (_I, [_VP, _I, _I, _VP, _D, _I]),
     "rm_solve_energies": (_I, [_VP, _I, _I, _VP, _I, _VP, _VP, _VP]),
     "rm_collision_strengths": (_I, [_VP, _VP, _I]),
+    "rm_collision_strengths_async": (_I, [_VP, _VP, _I]),
     "rm_solve_energies_qdt": (_I, [_VP, _I, _I, _VP, _I, _D, _I, _VP, _VP]),
     "rm_grid_shape": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rm_channel_functions": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
@@ -204,6 +205,21 @@ def rm_collision_strengths(ctx, omega_out=None, reset=False):
     return omega_out
 
 
+def rm_collision_strengths_async(ctx, omega_out, reset=False):
+    """Enqueues the copy of Omega into omega_out (host, [n_E][n_tri] float64;
+    page-locked for overlap, e.g. a pinned torch tensor's numpy view); it is
+    written by the time rm_sync returns."""
+    nE, ntri = rm_grid_shape(ctx)
+    if hasattr(omega_out, "data_ptr"):
+        ok = tuple(omega_out.shape) == (nE, ntri) and omega_out.device.type == "cpu"
+    else:
+        ok = isinstance(omega_out, np.ndarray) and omega_out.shape == (nE, ntri)
+    if not ok:
+        raise ValueError("omega_out must be a host array of shape (%d, %d)" % (nE, ntri))
+    return _check(ctx, lib().rm_collision_strengths_async(ctx, _ptr(omega_out, np.float64),
+                                                          int(bool(reset))))
+
+
 def rm_channel_functions(ctx, pw, E, out, status=None):
     return _check(ctx, lib().rm_channel_functions(ctx, pw, int(E.shape[0]), _ptr(E, np.float64),
                                                   _ptr(out, np.float64), _ptr(status, np.int32)))
@@ -310,6 +326,9 @@ class Context:
 
     def collision_strengths(self, omega_out=None, reset=False):
         return rm_collision_strengths(self.h, omega_out, reset)
+
+    def collision_strengths_async(self, omega_out, reset=False):
+        return rm_collision_strengths_async(self.h, omega_out, reset)
 
     def channel_functions(self, pw, E, out, status=None):
         return rm_channel_functions(self.h, pw, E, out, status)
