@@ -87,7 +87,10 @@ def _propagate_sector(R_a, a, r1, eps, l, z, A, b, rtol):
         return None
     Psi = sol.y[: n * n, -1].reshape(n, n)
     Pp = sol.y[n * n:, -1].reshape(n, n)
-    R1 = np.linalg.solve((r1 * Pp - b * Psi).T, Psi.T).T
+    try:
+        R1 = np.linalg.solve((r1 * Pp - b * Psi).T, Psi.T).T
+    except np.linalg.LinAlgError:
+        return None                     # r1 Psi' - b Psi singular: RM_ESINGULAR
     return 0.5 * (R1 + R1.T)
 
 
