@@ -565,7 +565,7 @@ extern "C" int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const doub
     if (!std::isfinite(r1) || !(r1 >= P.a)) return fail(ctx, RM_EINVAL, "r1=%g must be >= a=%g", r1, P.a);
     if (n_steps < 2) return fail(ctx, RM_EINVAL, "n_steps=%d must be >= 2", n_steps);
     const size_t cnt = (size_t)lambda_max * n * n;
-    if (!finite_all(A, (int)cnt)) return fail(ctx, RM_EINVAL, "non-finite multipole coefficient");
+    if (!finite_all(A, cnt)) return fail(ctx, RM_EINVAL, "non-finite multipole coefficient");
     for (int lam = 0; lam < lambda_max; ++lam)
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < i; ++j)
