@@ -218,3 +218,23 @@ def test_multipole_workload_sampled(rt):
                    for k, m in enumerate(idx) if not st[m]]
             assert np.median(rel) < 1e-5 and max(rel) < 1e-2, rel
         assert (st == 0).mean() > 0.95
+
+
+def test_small_n_batched_energies(rt):
+    """n <= 16 runs several energies per CTA (64 at n = 3): 150 energies, so
+    that the last CTA is partly empty, one of them on a pole (its status must
+    stay RM_ENEAR_POLE and its neighbours in the same CTA must be unaffected),
+    against the oracle at 1e-9."""
+    pw = _pw(n=3, seed=31, z=1.0)
+    A = _coupling(3, 2, 17)
+    rng = np.random.default_rng(5)
+    E = np.sort(rng.uniform(0.02, 1.6, 150))
+    thr = np.asarray(pw["e_thr"])
+    E = E[np.abs(E[:, None] - thr[None, :]).min(axis=1) > 5e-3]
+    pole = pw["E_k"][(pw["E_k"] > 0.1) & (pw["E_k"] < 1.5)][0]
+    E[40] = pole
+    E = np.sort(E)
+    K, no, st, om = _gpu_solve(rt, pw, E, A, 0)
+    ref = pr.solve_energies(pw, E, A, R1)
+    assert (ref["status"] != 0).sum() >= 1
+    _compare(E, K, no, st, om, ref)
