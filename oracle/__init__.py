@@ -34,9 +34,13 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
                         of S_u interpolation falls as h^2; segment and
                         qetest rules on hand-made grids
   propagate (outer-     tests/test_oracle_propagate.py: without coupling K at r1
-  region propagation    equals K at a; free s-wave closed form; round trip
-  with multipoles)      a -> r1 -> a; an independent RK4 converges to it at
-                        fourth order
+  region propagation    equals K at a; free s-wave closed form; dipole tail
+  with multipoles)      A/r^2 against Bessel J, Y of order sqrt(A + 1/4) and
+                        quadrupole tail A/r^3 at threshold against I_1, K_1
+                        (planted mistakes in the power, the signs of U, eps
+                        and b each fail one); round trip a -> r1 -> a; an
+                        independent RK4 converges to it at fourth order;
+                        sector lengths do not change K
   cross-threshold K, Omega beyond these checks: parity unpinned (the paper
                         prints no K or Omega values for any system).
 """
