@@ -294,6 +294,7 @@ class Context:
             if k not in [f[0] for f in RmOpts._fields_]:
                 raise TypeError("unknown rm_opts field %r" % k)
             setattr(o, k, v)
+        self._n_ch = {}          # channels of each loaded partial wave
         self.h = rm_create(o)
 
     def close(self):
@@ -316,9 +317,16 @@ class Context:
     def load_pw(self, pw, d):
         """Load one partial wave given as a dict (keys of synth's partial waves)."""
         rm_load_poles(self.h, pw, d["E_k"], d["W"], d["a"], d.get("b", 0.0))
+        self._n_ch[pw] = int(d["W"].shape[0]) if hasattr(d["W"], "shape") else len(d["W"])
         rm_set_channels(self.h, pw, d["e_thr"], d["l"], d["z"], d["level"], d["n_levels"], d["g"])
 
     def set_multipoles(self, pw, A, r1=0.0, n_steps=0):
+        """A: [lambda_max][n_ch][n_ch] of the loaded wave (None: propagation off)."""
+        n = getattr(self, "_n_ch", {}).get(pw)
+        if A is not None and n is not None:
+            shape = tuple(A.shape) if hasattr(A, "shape") else np.shape(A)
+            if len(shape) != 3 or shape[1:] != (n, n):
+                raise ValueError("A must be [lambda_max][%d][%d] for partial wave %d, got %s" % (n, n, pw, shape))
         return rm_set_multipoles(self.h, pw, A, r1, n_steps)
 
     def solve_energies(self, pw, E, mode=0, K_out=None, n_open_out=None, status_out=None):

@@ -66,3 +66,24 @@ def test_null_context_is_rejected(so):
     assert L.rm_sync(None) == rmgb.RM_EINVAL
     L.rm_destroy(None)
     assert L.rm_last_error(None)
+
+
+def test_null_context_rejected_by_new_calls(so):
+    from paper_1909_07321_gb300 import rmgb
+    L = rmgb.lib()
+    assert L.rm_set_multipoles(None, 0, 1, None, 10.0, 100) == rmgb.RM_EINVAL
+    assert L.rm_collision_strengths_async(None, None, 0) == rmgb.RM_EINVAL
+
+
+def test_multipole_shape_checked_before_the_library(so):
+    """The binding rejects coefficients that do not match the loaded wave's
+    channel count (the C call reads lambda_max n^2 doubles) without calling
+    the library."""
+    import numpy as np
+    from paper_1909_07321_gb300 import rmgb
+    ctx = rmgb.Context.__new__(rmgb.Context)
+    ctx.h = None
+    ctx._n_ch = {0: 4}
+    for bad in (np.zeros((2, 3, 3)), np.zeros((4, 4)), np.zeros((1, 4, 5))):
+        with pytest.raises(ValueError):
+            ctx.set_multipoles(0, bad, 15.0, 100)
