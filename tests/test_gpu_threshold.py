@@ -39,9 +39,9 @@ def node_spacing(z, a, l):
 # cancels by ~1e28 at r = a (sqrt(8 z a) = 64), the tables fail their check
 # and every pair keeps its continued fractions; its energies stay at least
 # h / 2 from the thresholds (closer ones take the binary128 oracle minutes).
-CONFIGS = [(2.0, 15.0, (0, 3, 8, 5)), (1.0, 30.0, (0, 4, 10, 15)), (5.0, 5.0, (1, 2, 6, 12)),
+CASES = [(2.0, 15.0, (0, 3, 8, 5)), (1.0, 30.0, (0, 4, 10, 15)), (5.0, 5.0, (1, 2, 6, 12)),
            (12.0, 10.0, (0, 2, 4, 7)), (1.0, 5.0, (15, 0, 10, 2)), (26.0, 20.0, (2, 0, 4, 1))]
-REFUSED = len(CONFIGS) - 1
+REFUSED = len(CASES) - 1
 
 
 def _pw(z, a, ls, seed):
@@ -79,10 +79,10 @@ def _check_channel_functions(g, Es, pw, tag):
         assert np.abs(pw["a"] * (g[m, cl, 1] - cf["thp"][cl])).max(initial=0) < 1e-10, (tag, x)
 
 
-@pytest.mark.parametrize("ci", range(len(CONFIGS)))
+@pytest.mark.parametrize("ci", range(len(CASES)))
 def test_channel_functions_near_thresholds(rt, ci):
     torch, rmgb = rt
-    z, a, ls = CONFIGS[ci]
+    z, a, ls = CASES[ci]
     pw = _pw(z, a, ls, 900 + ci)
     Es = _energies(pw, close=ci != REFUSED)
     with rmgb.Context(channel_tables=1) as ctx:
@@ -96,7 +96,7 @@ def test_channel_functions_near_thresholds(rt, ci):
         g = out.cpu().numpy()
         w = w.cpu().numpy()
         assert not st.cpu().numpy().any()
-    _check_channel_functions(g, Es, pw, CONFIGS[ci])
+    _check_channel_functions(g, Es, pw, CASES[ci])
     # which pairs took the table: inside the zone unless the table was refused
     eps = Es[:, None] - pw["e_thr"][None, :]
     h = np.array([node_spacing(z, a, int(l)) for l in pw["l"]])
@@ -142,13 +142,13 @@ def test_k_omega_near_thresholds(rt, mode):
     assert not bad, bad[:10]
 
 
-@pytest.mark.parametrize("ci", range(len(CONFIGS) - 1))
+@pytest.mark.parametrize("ci", range(len(CASES) - 1))
 def test_open_tables_vs_oracle(rt, ci):
     """Open pairs beyond the near-threshold zone come from the channel's
     Chebyshev table (12 terms per k-segment of width 0.9 / a, up to 16 Ry):
     random energies up to 15 Ry above the thresholds against the oracle."""
     torch, rmgb = rt
-    z, a, ls = CONFIGS[ci]
+    z, a, ls = CASES[ci]
     pw = _pw(z, a, ls, 900 + ci)
     rng = np.random.default_rng(77 + ci)
     Es = np.sort(np.concatenate([rng.uniform(0.0, 2.0, 40), rng.uniform(2.0, 16.5, 40)]))
@@ -163,7 +163,7 @@ def test_open_tables_vs_oracle(rt, ci):
         g = out.cpu().numpy()
         w = w.cpu().numpy()
         assert not st.cpu().numpy().any()
-    _check_channel_functions(g, Es, pw, ("open table",) + CONFIGS[ci])
+    _check_channel_functions(g, Es, pw, ("open table",) + CASES[ci])
     eps = Es[:, None] - pw["e_thr"][None, :]
     h = np.array([node_spacing(z, a, int(l)) for l in pw["l"]])
     k0 = np.sqrt(THR_ZONE * h)[None, :]
@@ -173,7 +173,7 @@ def test_open_tables_vs_oracle(rt, ci):
     assert np.array_equal(w[..., 0] == 4, inside)
 
 
-@pytest.mark.parametrize("ci", range(len(CONFIGS) - 1))
+@pytest.mark.parametrize("ci", range(len(CASES) - 1))
 def test_closed_tables_vs_oracle(rt, ci):
     """Closed pairs beyond the near-threshold zone (direct mode) come from the
     channel's table of the direction (theta, a theta') in nu (cells of 0.25
@@ -183,7 +183,7 @@ def test_closed_tables_vs_oracle(rt, ci):
     threshold to the zone edge. All must match the oracle; deep closed pairs
     (smooth direction) must mostly come from the table."""
     torch, rmgb = rt
-    z, a, ls = CONFIGS[ci]
+    z, a, ls = CASES[ci]
     pw = _pw(z, a, ls, 900 + ci)
     pw["e_thr"] = np.array([0.0, 5.0, 10.0, 15.0])
     rng = np.random.default_rng(99 + ci)
@@ -200,7 +200,7 @@ def test_closed_tables_vs_oracle(rt, ci):
         g = out.cpu().numpy()
         w = w.cpu().numpy()
         assert not st.cpu().numpy().any()
-    _check_channel_functions(g, Es, pw, ("closed table",) + CONFIGS[ci])
+    _check_channel_functions(g, Es, pw, ("closed table",) + CASES[ci])
     eps = Es[:, None] - pw["e_thr"][None, :]
     h = np.array([node_spacing(z, a, int(l)) for l in pw["l"]])
     closed = (eps < 0) & (-eps >= THR_ZONE * h[None, :]) & (eps >= -16.0)
