@@ -1,7 +1,9 @@
 """Multi-rank path on CPU: two gloo ranks, each solving its share of the
 (partial wave, energy) pairs with the oracle, reproduce the single-process
-collision strengths -- for the interleaved energy shards (gather) and for the
-paper's twisted assignment (reduce)."""
+collision strengths -- for the interleaved energy shards (gather), for the
+paper's twisted assignment (reduce), and for energy shards with the
+outer-region propagation (every energy propagates on its own, so the same
+shards hold)."""
 import os
 import socket
 
@@ -11,7 +13,22 @@ import pytest
 torch = pytest.importorskip("torch")
 
 import oracle  # noqa: E402
+from oracle import propagate  # noqa: E402
 from paper_1909_07321_gb300 import partition, synth  # noqa: E402
+
+R1 = 22.0
+
+
+def _coupling(n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.normal(0.0, 0.3, (2, n, n))
+    return 0.5 * (A + A.transpose(0, 2, 1))
+
+
+def _solve(pw, E, p, prop):
+    if prop:
+        return propagate.solve_energies(pw, E, _coupling(4, 70 + p), R1)["omega"]
+    return oracle.solve_energies(pw, E)["omega"]
 
 
 def _pws():
@@ -38,11 +55,11 @@ def _worker(rank, world, port, mode, out_path):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     pws, E = _pws()
     n_tri = pws[0]["n_levels"] * (pws[0]["n_levels"] + 1) // 2
-    if mode == "gather":
+    if mode in ("gather", "gather_propagated"):
         idx = partition.energy_shard(E.size, rank, world)
         local = np.zeros((idx.size, n_tri))
         for p in partition.pw_order(len(pws), rank, world):
-            local += oracle.solve_energies(pws[p], E[idx])["omega"]
+            local += _solve(pws[p], E[idx], p, mode == "gather_propagated")
         full = partition.gather_omega(local, E.size, rank, world)
     else:
         part = np.zeros((E.size, n_tri))
@@ -55,7 +72,7 @@ def _worker(rank, world, port, mode, out_path):
     dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("mode", ["gather", "twisted"])
+@pytest.mark.parametrize("mode", ["gather", "twisted", "gather_propagated"])
 def test_two_ranks_reproduce_single_process(tmp_path, mode):
     import torch.multiprocessing as mp
     out = str(tmp_path / "omega.npy")
@@ -63,7 +80,7 @@ def test_two_ranks_reproduce_single_process(tmp_path, mode):
                        start_method="spawn")
     full = np.load(out)
     pws, E = _pws()
-    ref = sum(oracle.solve_energies(pw, E)["omega"] for pw in pws)
+    ref = sum(_solve(pw, E, p, mode == "gather_propagated") for p, pw in enumerate(pws))
     np.testing.assert_allclose(full, ref, rtol=1e-13, atol=1e-300)
 
 
