@@ -41,6 +41,10 @@ Readings (the paper names the controls only):
     has moved by more than qetest since the last interpolation within the
     segment; until then the last interpolation energy is reused (qetest <= 0
     re-interpolates at every energy).
+  * A partial wave may carry "prop" = (A, r1), the long-range coupling of
+    oracle/propagate.py: R is then propagated from a to r1 before the
+    matching, and the matching radius r1 takes the place of a everywhere
+    (channel functions, the kappa a cap of the eliminated set).
 """
 import numpy as np
 
@@ -51,6 +55,12 @@ SIN_MIN = 1e-3
 NODE_MIN_EPS = 2.5e-5      # x max(z^2, 1) Ry: closest a node may lie to a threshold
 
 
+def match_radius(pw):
+    """a, or r1 when the wave carries an outer-region propagation."""
+    prop = pw.get("prop")
+    return pw["a"] if prop is None else prop[1]
+
+
 def classes(E, pw, fnumin=0.0, margin=0.1, kappa_a_max=5.0, eps_thr=1e-10):
     """Channel classes at E (None if E lies on a threshold)."""
     e_thr = np.asarray(pw["e_thr"], dtype=np.float64)
@@ -58,7 +68,7 @@ def classes(E, pw, fnumin=0.0, margin=0.1, kappa_a_max=5.0, eps_thr=1e-10):
     eps = E - e_thr
     if np.any(np.abs(eps) < eps_thr):
         return None
-    z, a = pw["z"], pw["a"]
+    z, a = pw["z"], match_radius(pw)
     cls = np.full(e_thr.size, CL_DECAY, dtype=np.int32)
     cls[eps > 0] = CL_OPEN
     cl = eps < 0
@@ -145,12 +155,19 @@ def cayley(K):
 def k_unphysical(pw, x, cls_seg):
     """K_u at energy x with the segment's eliminated set (channel order of
     the open and eliminated channels), or None."""
-    cf = rm.channel_functions(x, pw["e_thr"], pw["l"], pw["z"], pw["a"])
+    am = match_radius(pw)
+    b = pw.get("b", 0.0)
+    cf = rm.channel_functions(x, pw["e_thr"], pw["l"], pw["z"], am)
     if cf["status"] != rm.RM_OK:
         return None
     R = rm.r_matrix(x, pw["E_k"], pw["W"], pw["a"])
-    _, Ku, _, _ = rm.match_mqdt(R, cf, pw["l"], pw["z"], pw["a"], pw.get("b", 0.0),
-                                Q=(cls_seg == CL_ELIM))
+    if pw.get("prop") is not None:
+        from . import propagate
+        R = propagate.propagate_r(R, pw["a"], am, x - np.asarray(pw["e_thr"], dtype=np.float64), pw["l"],
+                                  pw["z"], pw["prop"][0], b)
+        if R is None:
+            return None
+    _, Ku, _, _ = rm.match_mqdt(R, cf, pw["l"], pw["z"], am, b, Q=(cls_seg == CL_ELIM))
     return Ku
 
 

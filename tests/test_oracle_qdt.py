@@ -159,3 +159,31 @@ def test_qetest_reuses_the_last_interpolation_energy():
     np.testing.assert_array_equal(pl0["e_int"], E)
     with pytest.raises(ValueError):
         qdt.plan(pw, E, ieq=0)
+
+
+def test_every_energy_a_node_with_propagation():
+    """With the outer-region propagation (pw["prop"] = (A, r1)) every fine
+    energy a node still reduces the interpolation to the plain propagated
+    MQDT solve of oracle/propagate.py (the matching radius r1 in both)."""
+    from oracle import propagate
+    pw = _pw()
+    rng = np.random.default_rng(8)
+    A = rng.normal(0.0, 0.3, (2, 4, 4))
+    A = 0.5 * (A + A.transpose(0, 2, 1))
+    r1 = 13.0
+    pwp = dict(pw, prop=(A, r1))
+    E = synth.midpoint_grid(0.35, 1.75, 80)
+    res = qdt.solve_energies(pwp, E, ieq=-1, iqdt=2)
+    ref = propagate.solve_energies(pw, E, A, r1, mode=oracle.MODE_MQDT)
+    ok = _sin_ok(pwp, E) & (ref["status"] == 0)
+    assert ok.sum() > 60
+    n_elim = sum(int(np.sum(qdt.classes(float(x), pwp) == qdt.CL_ELIM)) for x in E[ok])
+    assert n_elim > 15
+    for m in np.nonzero(ok)[0]:
+        assert res["status"][m] == 0
+        np.testing.assert_allclose(res["K"][m], ref["K"][m], rtol=1e-12, atol=1e-12)
+        scale = max(1.0, np.abs(ref["omega"][m]).max())
+        np.testing.assert_allclose(res["omega"][m], ref["omega"][m], rtol=0, atol=1e-11 * scale)
+    # and the propagation changes the answer
+    plain = qdt.solve_energies(pw, E, ieq=-1, iqdt=2)
+    assert max(np.abs(res["omega"][m] - plain["omega"][m]).max() for m in np.nonzero(ok)[0]) > 1e-4
