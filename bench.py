@@ -450,6 +450,15 @@ def run_propagation(args, prec, sp, fp64_peak, stream):
     return out
 
 
+def _leg(fn, *a):
+    """Runs one auxiliary leg; a failure there is reported in its slot of the
+    JSON line instead of taking the headline measurement down with it."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -558,22 +567,22 @@ def run_ours(args, rank, world, local_rank):
 
     serving_line = None
     if rank == 0 and world == 1 and args.serving_requests > 0:
-        serving_line = run_serving(args, prec if prec != 0 else 2)
+        serving_line = _leg(run_serving, args, prec if prec != 0 else 2)
 
     if rank != 0:
         return
     peaks, peak_src = _peaks()
     wide = None
     if world == 1 and args.wide_energies > 0:
-        wide = run_wide(args, prec if prec != 0 else 2, stream, flush, peaks, peak_src)
+        wide = _leg(run_wide, args, prec if prec != 0 else 2, stream, flush, peaks, peak_src)
     qdt_line = None
     if world == 1 and args.qdt_ieq != 0:
-        qdt_line = run_qdt(args, prec, sp)
+        qdt_line = _leg(run_qdt, args, prec, sp)
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp64_peak = N_SM * FP64_FLOPS_PER_CLK_SM * sm_mhz * 1e6 / 1e12
     prop_line = None
     if world == 1 and args.prop_energies > 0:
-        prop_line = run_propagation(args, prec, sp, fp64_peak, stream)
+        prop_line = _leg(run_propagation, args, prec, sp, fp64_peak, stream)
     names = {rmgb.RM_PH_NEARPOLE: "nearpole", rmgb.RM_PH_CHANFN: "chanfn", rmgb.RM_PH_FORM: "form",
              rmgb.RM_PH_FIXUP: "fixup", rmgb.RM_PH_SOLVE: "solve", rmgb.RM_PH_SPLIT: "split"}
     total_phase_ms = sum(v[1] for v in phase.values())
