@@ -248,6 +248,27 @@ int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
 int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double *E, int ieq, double qetest,
                           int iqdt, int *n_open_out, int *status_out);
 
+/* Inspection of the host planning of rm_solve_energies_qdt (no device work;
+ * runs without a GPU): for n_E fine energies E (host, strictly ascending)
+ * with channel classes cls (host, [n_E][n_ch] signed char: 0 open, 1
+ * eliminated by MQDT, 2 other closed, 3 in every slot of an energy on a
+ * threshold), thresholds e_thr (host, [n_ch]), charge z and the sorted pole
+ * energies E_k (host, [n_poles]), cuts the segments and places the nodes as
+ * rm_solve_energies_qdt does (ieq, qetest; nodes dropped on a pole, within
+ * 2.5e-5 max(z^2, 1) Ry of a threshold, or where an eliminated channel has
+ * |sin pi nu| < 1e-3) and, taking every node's solve as successful, the
+ * interpolation of each fine energy. Outputs (host): seg [n_E] (segment, -1
+ * on a threshold), e_int [n_E] (interpolation energy, qetest), node_x and
+ * node_seg [node_cap] (valid nodes, segment by segment), *n_nodes, node_a,
+ * node_b [n_E] (K_u at the energy = (1 - t) node a + t node b; a = b with
+ * one node; -1 where the energy has none) and t [n_E]. Errors: RM_EINVAL
+ * (NULL or bad sizes, energies not ascending, ieq = 0, more nodes than
+ * node_cap). */
+int rm_qdt_plan_inspect(int n_ch, const double *e_thr, double z, int n_poles, const double *E_k,
+                        int n_E, const double *E, const signed char *cls, int ieq, double qetest,
+                        int node_cap, int *seg, double *e_int, int *n_nodes, double *node_x,
+                        int *node_seg, int *node_a, int *node_b, double *t);
+
 /* Copies the accumulated collision strengths to omega_out (host,
  * [n_E][n_levels*(n_levels+1)/2], upper triangle row-wise: (I, J), I <= J,
  * at I*n_levels - I*(I-1)/2 + (J - I)); entries of levels closed at E are 0.

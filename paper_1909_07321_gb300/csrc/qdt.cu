@@ -154,6 +154,51 @@ void qdt_weights(const QdtPlan &pl, const std::vector<int> &node_ok, int n_E, st
     }
 }
 
+}  // namespace rmgb
+
+// Inspection of the host planning (no device work): see rmgb.h.
+extern "C" int rm_qdt_plan_inspect(int n_ch, const double *e_thr, double z, int n_poles, const double *E_k, int n_E,
+                                   const double *E, const signed char *cls, int ieq, double qetest, int node_cap,
+                                   int *seg, double *e_int, int *n_nodes, double *node_x, int *node_seg,
+                                   int *node_a, int *node_b, double *t)
+{
+    using namespace rmgb;
+    if (n_ch <= 0 || n_E <= 0 || n_poles < 0 || node_cap < 0 || !e_thr || !E || !cls || (n_poles > 0 && !E_k) ||
+        !seg || !e_int || !n_nodes || (node_cap > 0 && (!node_x || !node_seg)) || !node_a || !node_b || !t)
+        return RM_EINVAL;
+    if (!std::isfinite(z) || z < 0.0) return RM_EINVAL;
+    QdtChannels ch{};
+    ch.n = n_ch;
+    ch.N = n_poles;
+    ch.e_thr = e_thr;
+    ch.l = nullptr;
+    ch.E_k = E_k;
+    ch.z = z;
+    QdtPlan pl;
+    if (qdt_plan(ch, E, n_E, cls, ieq, qetest, pl) != RM_SUCCESS) return RM_EINVAL;
+    const int nn = (int)pl.node_x.size();
+    if (nn > node_cap) return RM_EINVAL;
+    std::vector<int> ok(nn, 1);
+    std::vector<QdtFine> fine;
+    qdt_weights(pl, ok, n_E, fine);
+    for (int m = 0; m < n_E; ++m) {
+        seg[m] = pl.seg[m];
+        e_int[m] = pl.e_int[m];
+        const bool has = fine[m].flag == QDT_FLAG_OK;
+        node_a[m] = has ? fine[m].a : -1;
+        node_b[m] = has ? fine[m].b : -1;
+        t[m] = has ? fine[m].t : 0.0;
+    }
+    for (int k = 0; k < nn; ++k) {
+        node_x[k] = pl.node_x[k];
+        node_seg[k] = pl.node_seg[k];
+    }
+    *n_nodes = nn;
+    return RM_SUCCESS;
+}
+
+namespace rmgb {
+
 // ---- device ---------------------------------------------------------------------
 
 namespace {

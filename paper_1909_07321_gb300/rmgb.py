@@ -62,6 +62,8 @@ _SIGS = {
     "rm_collision_strengths": (_I, [_VP, _VP, _I]),
     "rm_collision_strengths_async": (_I, [_VP, _VP, _I]),
     "rm_solve_energies_qdt": (_I, [_VP, _I, _I, _VP, _I, _D, _I, _VP, _VP]),
+    "rm_qdt_plan_inspect": (_I, [_I, _VP, _D, _I, _VP, _I, _VP, _VP, _I, _D, _I, _VP, _VP, _VP, _VP, _VP,
+                                 _VP, _VP, _VP]),
     "rm_grid_shape": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rm_channel_functions": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "rm_form_r": (_I, [_VP, _I, _I, _VP, _VP]),
@@ -218,6 +220,37 @@ def rm_collision_strengths_async(ctx, omega_out, reset=False):
         raise ValueError("omega_out must be a host array of shape (%d, %d)" % (nE, ntri))
     return _check(ctx, lib().rm_collision_strengths_async(ctx, _ptr(omega_out, np.float64),
                                                           int(bool(reset))))
+
+
+def rm_qdt_plan_inspect(e_thr, z, E_k, E, cls, ieq, qetest=0.0):
+    """Host planning of the coarse-mesh interpolation (no GPU needed): cls is
+    [n_E][n_ch] int8 (0 open, 1 eliminated, 2 decaying, 3 on a threshold).
+    Returns dict seg, e_int, node_x, node_seg, node_a, node_b, t."""
+    e_thr = np.ascontiguousarray(e_thr, dtype=np.float64)
+    E_k = np.ascontiguousarray(E_k, dtype=np.float64)
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    cls = np.ascontiguousarray(cls, dtype=np.int8)
+    n_E, n = E.size, e_thr.size
+    if cls.shape != (n_E, n):
+        raise ValueError("cls must be [n_E][n_ch]")
+    cap = 4 * n_E + (abs(int(ieq)) if ieq > 0 else 0) + 8
+    seg = np.empty(n_E, dtype=np.int32)
+    e_int = np.empty(n_E)
+    nn = ctypes.c_int(0)
+    node_x = np.empty(cap)
+    node_seg = np.empty(cap, dtype=np.int32)
+    na = np.empty(n_E, dtype=np.int32)
+    nb = np.empty(n_E, dtype=np.int32)
+    t = np.empty(n_E)
+    rc = lib().rm_qdt_plan_inspect(n, _ptr(e_thr), float(z), E_k.size, _ptr(E_k) if E_k.size else None, n_E,
+                                   _ptr(E), cls.ctypes.data, int(ieq), float(qetest), cap, _ptr(seg),
+                                   _ptr(e_int), ctypes.byref(nn), _ptr(node_x), _ptr(node_seg), _ptr(na),
+                                   _ptr(nb), _ptr(t))
+    if rc:
+        raise RmError(rc, "rm_qdt_plan_inspect")
+    k = nn.value
+    return dict(seg=seg, e_int=e_int, node_x=node_x[:k].copy(), node_seg=node_seg[:k].copy(),
+                node_a=na, node_b=nb, t=t)
 
 
 def rm_channel_functions(ctx, pw, E, out, status=None):
