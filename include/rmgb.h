@@ -256,8 +256,10 @@ int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double *E, int ieq
  * energies E_k (host, [n_poles]), cuts the segments and places the nodes as
  * rm_solve_energies_qdt does (ieq, qetest; nodes dropped on a pole, within
  * 2.5e-5 max(z^2, 1) Ry of a threshold, or where an eliminated channel has
- * |sin pi nu| < 1e-3) and, taking every node's solve as successful, the
- * interpolation of each fine energy. Outputs (host): seg [n_E] (segment, -1
+ * |sin pi nu| < 1e-3) and the interpolation of each fine energy, taking the
+ * solve of node k as failed where node_ok[k] == 0 (node_ok: host, [node
+ * count], NULL: every node solved; the count is the *n_nodes of a call with
+ * NULL). Outputs (host): seg [n_E] (segment, -1
  * on a threshold), e_int [n_E] (interpolation energy, qetest), node_x and
  * node_seg [node_cap] (valid nodes, segment by segment), *n_nodes, node_a,
  * node_b [n_E] (K_u at the energy = (1 - t) node a + t node b; a = b with
@@ -266,8 +268,8 @@ int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double *E, int ieq
  * node_cap). */
 int rm_qdt_plan_inspect(int n_ch, const double *e_thr, double z, int n_poles, const double *E_k,
                         int n_E, const double *E, const signed char *cls, int ieq, double qetest,
-                        int node_cap, int *seg, double *e_int, int *n_nodes, double *node_x,
-                        int *node_seg, int *node_a, int *node_b, double *t);
+                        const int *node_ok, int node_cap, int *seg, double *e_int, int *n_nodes,
+                        double *node_x, int *node_seg, int *node_a, int *node_b, double *t);
 
 /* Copies the accumulated collision strengths to omega_out (host,
  * [n_E][n_levels*(n_levels+1)/2], upper triangle row-wise: (I, J), I <= J,

@@ -158,9 +158,9 @@ void qdt_weights(const QdtPlan &pl, const std::vector<int> &node_ok, int n_E, st
 
 // Inspection of the host planning (no device work): see rmgb.h.
 extern "C" int rm_qdt_plan_inspect(int n_ch, const double *e_thr, double z, int n_poles, const double *E_k, int n_E,
-                                   const double *E, const signed char *cls, int ieq, double qetest, int node_cap,
-                                   int *seg, double *e_int, int *n_nodes, double *node_x, int *node_seg,
-                                   int *node_a, int *node_b, double *t)
+                                   const double *E, const signed char *cls, int ieq, double qetest,
+                                   const int *node_ok, int node_cap, int *seg, double *e_int, int *n_nodes,
+                                   double *node_x, int *node_seg, int *node_a, int *node_b, double *t)
 {
     using namespace rmgb;
     if (n_ch <= 0 || n_E <= 0 || n_poles < 0 || node_cap < 0 || !e_thr || !E || !cls || (n_poles > 0 && !E_k) ||
@@ -179,6 +179,8 @@ extern "C" int rm_qdt_plan_inspect(int n_ch, const double *e_thr, double z, int 
     const int nn = (int)pl.node_x.size();
     if (nn > node_cap) return RM_EINVAL;
     std::vector<int> ok(nn, 1);
+    if (node_ok)
+        for (int k = 0; k < nn; ++k) ok[k] = node_ok[k] != 0;
     std::vector<QdtFine> fine;
     qdt_weights(pl, ok, n_E, fine);
     for (int m = 0; m < n_E; ++m) {

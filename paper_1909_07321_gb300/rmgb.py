@@ -62,8 +62,8 @@ _SIGS = {
     "rm_collision_strengths": (_I, [_VP, _VP, _I]),
     "rm_collision_strengths_async": (_I, [_VP, _VP, _I]),
     "rm_solve_energies_qdt": (_I, [_VP, _I, _I, _VP, _I, _D, _I, _VP, _VP]),
-    "rm_qdt_plan_inspect": (_I, [_I, _VP, _D, _I, _VP, _I, _VP, _VP, _I, _D, _I, _VP, _VP, _VP, _VP, _VP,
-                                 _VP, _VP, _VP]),
+    "rm_qdt_plan_inspect": (_I, [_I, _VP, _D, _I, _VP, _I, _VP, _VP, _I, _D, _VP, _I, _VP, _VP, _VP, _VP,
+                                 _VP, _VP, _VP, _VP]),
     "rm_grid_shape": (_I, [_VP, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "rm_channel_functions": (_I, [_VP, _I, _I, _VP, _VP, _VP]),
     "rm_form_r": (_I, [_VP, _I, _I, _VP, _VP]),
@@ -222,10 +222,11 @@ def rm_collision_strengths_async(ctx, omega_out, reset=False):
                                                           int(bool(reset))))
 
 
-def rm_qdt_plan_inspect(e_thr, z, E_k, E, cls, ieq, qetest=0.0):
+def rm_qdt_plan_inspect(e_thr, z, E_k, E, cls, ieq, qetest=0.0, node_ok=None):
     """Host planning of the coarse-mesh interpolation (no GPU needed): cls is
-    [n_E][n_ch] int8 (0 open, 1 eliminated, 2 decaying, 3 on a threshold).
-    Returns dict seg, e_int, node_x, node_seg, node_a, node_b, t."""
+    [n_E][n_ch] int8 (0 open, 1 eliminated, 2 decaying, 3 on a threshold);
+    node_ok (optional, one flag per valid node) marks node solves that
+    failed. Returns dict seg, e_int, node_x, node_seg, node_a, node_b, t."""
     e_thr = np.ascontiguousarray(e_thr, dtype=np.float64)
     E_k = np.ascontiguousarray(E_k, dtype=np.float64)
     E = np.ascontiguousarray(E, dtype=np.float64)
@@ -242,8 +243,11 @@ def rm_qdt_plan_inspect(e_thr, z, E_k, E, cls, ieq, qetest=0.0):
     na = np.empty(n_E, dtype=np.int32)
     nb = np.empty(n_E, dtype=np.int32)
     t = np.empty(n_E)
+    ok = None if node_ok is None else np.ascontiguousarray(node_ok, dtype=np.int32)
+    if ok is not None and ok.size < cap:
+        ok = np.concatenate([ok, np.ones(cap - ok.size, dtype=np.int32)])
     rc = lib().rm_qdt_plan_inspect(n, _ptr(e_thr), float(z), E_k.size, _ptr(E_k) if E_k.size else None, n_E,
-                                   _ptr(E), cls.ctypes.data, int(ieq), float(qetest), cap, _ptr(seg),
+                                   _ptr(E), cls.ctypes.data, int(ieq), float(qetest), _ptr(ok), cap, _ptr(seg),
                                    _ptr(e_int), ctypes.byref(nn), _ptr(node_x), _ptr(node_seg), _ptr(na),
                                    _ptr(nb), _ptr(t))
     if rc:

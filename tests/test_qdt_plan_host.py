@@ -74,3 +74,34 @@ def test_plan_rejects_bad_input():
         rmgb.rm_qdt_plan_inspect(pw["e_thr"], pw["z"], pw["E_k"], E, cls, 0)
     with pytest.raises(rmgb.RmError):
         rmgb.rm_qdt_plan_inspect(pw["e_thr"], pw["z"], pw["E_k"], E[::-1].copy(), cls[::-1].copy(), -3)
+
+
+def test_failed_nodes_are_left_out():
+    """Node solves that fail are skipped: the weights use the remaining nodes
+    of the segment (extrapolating beyond them), and a segment left without
+    nodes has none (its energies fail), as in the oracle, where a node whose
+    K_u cannot be formed is dropped."""
+    pw = _pw()
+    E = _grid(pw)
+    cls = _classes(pw, E)
+    first = rmgb.rm_qdt_plan_inspect(pw["e_thr"], pw["z"], pw["E_k"], E, cls, -9)
+    nn = first["node_x"].size
+    rng = np.random.default_rng(12)
+    ok = (rng.uniform(size=nn) > 0.35).astype(np.int32)
+    seg0 = first["node_seg"] == first["node_seg"][0]
+    ok[seg0] = 0                               # the first segment loses every node
+    lib = rmgb.rm_qdt_plan_inspect(pw["e_thr"], pw["z"], pw["E_k"], E, cls, -9, node_ok=ok)
+    assert np.array_equal(lib["node_x"], first["node_x"])
+    pl = qdt.plan(pw, E, -9, 0.0)
+    for s, (i0, i1, cls_seg) in enumerate(pl["segments"]):
+        idx = np.nonzero((lib["node_seg"] == s) & (ok != 0))[0]
+        xs = lib["node_x"][idx]
+        for m in range(i0, i1 + 1):
+            if xs.size == 0:
+                assert lib["node_a"][m] == -1
+            elif xs.size == 1:
+                assert lib["node_a"][m] == lib["node_b"][m] == idx[0]
+            else:
+                j, t = qdt.interpolation_weights(xs, pl["e_int"][m])
+                assert (lib["node_a"][m], lib["node_b"][m], lib["t"][m]) == (idx[j], idx[j + 1], t)
+    assert np.all(lib["node_a"][pl["segments"][0][0]:pl["segments"][0][1] + 1] == -1)
