@@ -432,3 +432,26 @@ def test_coulomb_open_random_scan(l, z, mag, a):
 @pytest.mark.parametrize("l,z,mag,a", _scan_points(202, 16))
 def test_whittaker_random_scan(l, z, mag, a):
     test_whittaker_vs_mpmath(l, z, -mag, a)
+
+
+def test_many_channel_invariants():
+    """At 64 channels (the benchmark's partial wave) the oracle's K stays
+    symmetric to rounding (every open channel's Wronskian normalisation and
+    the closed-channel treatment enter), and MQDT elimination reproduces the
+    direct K and Omega (an exact identity) where closed channels are present."""
+    from paper_1909_07321_gb300 import synth
+    pws, E = synth.workload_64ch(20000)
+    pw = pws[0]
+    for x in E[[5, 4000, 9000, 13000, 17000, 19990]]:
+        st, K, oi, _ = oracle.solve_energy(pw, float(x))
+        assert st == oracle.RM_OK
+        assert np.abs(K - K.T).max() <= 1e-13 * max(1.0, np.abs(K).max())
+    idx = [4000, 9000, 13000]
+    d = oracle.solve_energies(pw, E[idx])
+    m = oracle.solve_energies(pw, E[idx], mode=oracle.MODE_MQDT)
+    for k in range(len(idx)):
+        assert d["status"][k] == m["status"][k] == 0
+        assert d["n_open"][k] < pw["W"].shape[0]
+        np.testing.assert_allclose(m["K"][k], d["K"][k], rtol=0, atol=1e-12 * np.abs(d["K"][k]).max())
+        np.testing.assert_allclose(m["omega"][k], d["omega"][k], rtol=0,
+                                   atol=1e-12 * np.abs(d["omega"][k]).max())
