@@ -58,8 +58,9 @@ extern "C" {
 #define RM_ESINGULAR      3   /* matching system (or MQDT elimination) singular */
 #define RM_ECF_NOCONV     4   /* a Coulomb continued fraction did not converge */
 
-/* Precision of the R-matrix formation (step (a)). Channel functions, the
- * matching solve, T and Omega are always FP64. */
+/* Precision of the R-matrix formation (step (a)). Channel functions are
+ * always FP64; the matching solve and T follow rm_opts.solve_precision, and
+ * Omega is always accumulated in FP64. */
 #define RM_FP64           0   /* FP64 formation */
 #define RM_FP32           1   /* tensor cores: tf32 hi/lo split, 3 products, FP32
                                  accumulate; near-pole terms in FP64 */
@@ -360,8 +361,12 @@ int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms);
  * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream).
  * The library allocates nothing for it: its workspace is one static 32 MiB
  * device array per GPU, held from library load until process exit. The
- * first call on a device looks up that array's device address; make that
- * first call before any stream capture. Every call shares the array, so
+ * first call on a device looks up that array's device address and keeps it
+ * for the rest of the process; make that first call before any stream
+ * capture, and do not call this entry point on a device after a
+ * cudaDeviceReset of it (the kept address belongs to the old context). The
+ * call makes `device` current for its own work and restores the caller's
+ * current device before it returns. Every call shares the array, so
  * calls whose work overlaps on the GPU (different streams, threads or
  * processes sharing a context) race and must be serialised by the caller.
  * Limits: n_ch <= 96 (RM_EUNSUPPORTED beyond). errbuf (may be NULL) receives

@@ -36,6 +36,23 @@ int say(char *buf, size_t len, int code, const char *msg, long a = 0, long b = 0
 
 size_t round_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Puts the caller's current device back on every return path: the call
+// switches to `device` for its own work only.
+struct DeviceRestore {
+    int prev = -1;
+    DeviceRestore()
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+    }
+    ~DeviceRestore()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 extern "C" int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E,
@@ -61,12 +78,15 @@ extern "C" int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E,
         return say(errbuf, errlen, RM_EUNSUPPORTED,
                    "one energy needs %ld bytes of workspace, more than the %ld-byte static array",
                    (long)per_energy, (long)NOALLOC_SCRATCH_BYTES);
+    DeviceRestore restore;
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return say(errbuf, errlen, RM_ECUDA, "cudaSetDevice(%ld) failed", device);
     }
     // One-time set-up per device, with that device current: the device
-    // address of the static workspace.
+    // address of the static workspace. The address is kept for the life of
+    // the process, so it is stale after a cudaDeviceReset of that device
+    // (documented in the header).
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_setup_mu);

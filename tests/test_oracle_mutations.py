@@ -45,6 +45,19 @@ def _omega_double_count(row, T, open_idx, level, n_levels, g):
     return row
 
 
+def _omega_level_by_position(row, T, open_idx, level, n_levels, g):
+    # level of the open-channel position instead of the channel's own level
+    T2 = np.abs(T) ** 2
+    lv = np.asarray(level)[: len(open_idx)]
+    lv = np.sort(lv)
+    for p in range(lv.size):
+        for q in range(lv.size):
+            I, J = int(lv[p]), int(lv[q])
+            if I <= J:
+                row[orm.tri_index(I, J, n_levels)] += g * T2[p, q]
+    return row
+
+
 _orig_cf = orm.channel_functions
 
 
@@ -87,7 +100,10 @@ MUTATIONS = [
     ("r_matrix", _r_no_half_a, [(pins.test_r_matrix_bruteforce_and_symmetry,)]),
     ("r_matrix", _r_sign, [(pins.test_r_matrix_bruteforce_and_symmetry,)]),
     ("t_matrix", _t_no_inverse, [(pins.test_k_symmetric_and_s_unitary,)]),
-    ("omega_add", _omega_double_count, [(pins.test_omega_real_form_and_symmetry,)]),
+    ("omega_add", _omega_double_count, [(pins.test_omega_real_form_and_symmetry,),
+                                        (pins.test_omega_aggregation_from_unitarity, 3)]),
+    ("omega_add", _omega_level_by_position, [(pins.test_omega_aggregation_from_unitarity, 17),
+                                             (pins.test_omega_two_levels_by_hand,)]),
     ("channel_functions", _cf_bad_norm, [(pins.test_square_well_tan_delta, 6.0)]),
     ("channel_functions", _cf_flip_L, [(pins.test_mqdt_two_channel_vs_mpmath,)]),
     ("match_mqdt", _mqdt_flip_tan, [(pins.test_mqdt_equals_direct,)]),

@@ -393,6 +393,61 @@ def test_omega_real_form_and_symmetry():
         np.testing.assert_allclose(row, ref, atol=1e-13)
 
 
+def _level_matrix(row, n_levels):
+    """Symmetric level matrix from the row-wise upper triangle: Omega_IJ for
+    I <= J and Omega_JI otherwise."""
+    full = np.zeros((n_levels, n_levels))
+    for I in range(n_levels):
+        for J in range(I, n_levels):
+            full[I, J] = full[J, I] = row[oracle.tri_index(I, J, n_levels)]
+    return full
+
+
+@pytest.mark.parametrize("seed", [3, 17, 29])
+def test_omega_aggregation_from_unitarity(seed):
+    """With S unitary and K symmetric, sum_b |T_ab|^2 = -2 Re T_aa (optical
+    theorem), so for every target level I the row sum of the symmetric level
+    matrix is sum_J Omega_IJ = -2 g sum_{a in I} Re T_aa. This checks
+    omega_add's level indexing against an identity of the scattering
+    matrix, not against a restatement of the level sum. Channels of a level
+    are spread over the open-channel order, and one level has no open
+    channel (its row must vanish)."""
+    rng = np.random.default_rng(seed)
+    n_open, n_levels, g = 9, 5, 2.5
+    A = rng.normal(0.0, 1.3, (n_open, n_open))
+    K = 0.5 * (A + A.T)
+    T = oracle.t_matrix(K)
+    level_of_open = rng.permutation(np.array([0, 0, 1, 1, 1, 3, 3, 4, 4]))
+    level = np.concatenate([level_of_open, [2, 2]]).astype(np.int32)   # level 2: closed channels only
+    open_idx = np.arange(n_open)
+    row = oracle.omega_add(np.zeros(n_levels * (n_levels + 1) // 2), T, open_idx, level, n_levels, g)
+    full = _level_matrix(row, n_levels)
+    for I in range(n_levels):
+        ref = -2.0 * g * sum(T[a, a].real for a in range(n_open) if level_of_open[a] == I)
+        assert abs(full[I].sum() - ref) <= 1e-12 * max(1.0, abs(ref)), I
+    assert np.all(full[2] == 0.0)
+
+
+def test_omega_two_levels_by_hand():
+    """Two channels in two levels, K = [[p, q], [q, r]]: (1 - iK)^{-1} is the
+    adjugate over the determinant d = (1 - ip)(1 - ir) + q^2, so
+      T_00 = 2i (p (1 - ir) + i q^2) / d,  T_11 = 2i (r (1 - ip) + i q^2) / d,
+      T_01 = 2i q / d,
+    and Omega = g (|T_00|^2, |T_01|^2, |T_11|^2) in the row-wise upper triangle."""
+    p, q, r, g = 0.7, -0.4, 1.9, 1.5
+    d = (1 - 1j * p) * (1 - 1j * r) + q * q
+    T00 = 2j * (p * (1 - 1j * r) + 1j * q * q) / d
+    T11 = 2j * (r * (1 - 1j * p) + 1j * q * q) / d
+    T01 = 2j * q / d
+    K = np.array([[p, q], [q, r]])
+    row = oracle.omega_add(np.zeros(3), oracle.t_matrix(K), np.array([0, 1]), np.array([0, 1]), 2, g)
+    np.testing.assert_allclose(row, g * np.abs(np.array([T00, T01, T11])) ** 2, rtol=1e-14)
+    # the same two channels with their levels swapped: Omega_01 is unchanged,
+    # the elastic entries trade places
+    row2 = oracle.omega_add(np.zeros(3), oracle.t_matrix(K), np.array([0, 1]), np.array([1, 0]), 2, g)
+    np.testing.assert_allclose(row2, g * np.abs(np.array([T11, T01, T00])) ** 2, rtol=1e-14)
+
+
 def test_status_codes():
     pw = _mixed_pw()
     st, *_ = oracle.solve_energy(pw, float(pw["e_thr"][2]) + 1e-12)

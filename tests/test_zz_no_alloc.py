@@ -46,7 +46,11 @@ def _reference_K(torch, rmgb, pw, E):
     return K.cpu().numpy(), no.cpu().numpy(), st.cpu().numpy()
 
 
-def _noalloc_K(torch, fn, pw, E):
+def _noalloc_K(torch, fn, pw, E, free_bytes=None):
+    """K, n_open and statuses from rm_k_matrices_noalloc. With free_bytes (a
+    list), the device's free memory (cudaMemGetInfo) just before and just
+    after the call is appended to it; every buffer the call sees is made
+    before the first reading."""
     n, N = pw["W"].shape
     order = np.argsort(pw["E_k"], kind="stable")      # the call wants sorted poles
     dev = lambda x, t=torch.float64: torch.tensor(np.ascontiguousarray(x), dtype=t,  # noqa: E731
@@ -59,11 +63,16 @@ def _noalloc_K(torch, fn, pw, E):
     st = torch.full((E.size,), 7, dtype=torch.int32, device="cuda")   # must be cleared by the call
     err = ctypes.create_string_buffer(256)
     stream = torch.cuda.current_stream().cuda_stream or None
+    torch.cuda.synchronize()
+    if free_bytes is not None:
+        free_bytes.append(torch.cuda.mem_get_info()[0])
     rc = fn(0, n, N, E.size, Ek.data_ptr(), W.data_ptr(), thr.data_ptr(), l.data_ptr(),
             pw["z"], pw["a"], pw.get("b", 0.0), Ed.data_ptr(), 1e-10, K.data_ptr(),
             no.data_ptr(), st.data_ptr(), stream, err, 256)
     assert rc == 0, err.value
     torch.cuda.synchronize()
+    if free_bytes is not None:
+        free_bytes.append(torch.cuda.mem_get_info()[0])
     return K.cpu().numpy(), no.cpu().numpy(), st.cpu().numpy()
 
 
@@ -95,6 +104,23 @@ def test_noalloc_matches_solve_energies_twice(rt):
         second = _noalloc_K(torch, fn, pw, E)
         _assert_same_K(first, ref, n)
         _assert_same_K(second, ref, n)
+
+
+def test_noalloc_leaves_free_memory_unchanged(rt):
+    """The promise of the call's name: after a first (warm-up) call has loaded
+    the code, a second call over more energies than one workspace chunk holds
+    (the 64-channel workload: about 1700 energies per chunk) changes the
+    device's free memory by nothing, and leaves the caller's current device
+    as it was."""
+    torch, rmgb, fn = rt
+    pws, E = synth.workload_64ch(20000)
+    E = E[::8][:2500].copy()
+    _noalloc_K(torch, fn, pws[0], E)
+    dev_before = torch.cuda.current_device()
+    free = []
+    _noalloc_K(torch, fn, pws[0], E, free)
+    assert free[0] == free[1], "free device memory changed by %d bytes" % (free[0] - free[1])
+    assert torch.cuda.current_device() == dev_before
 
 
 def test_noalloc_rejects_oversize(rt):
