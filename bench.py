@@ -280,7 +280,7 @@ def _pe_tiles(n):
     return sum(min(n_ib, 2 * jb + 2) for jb in range(n_jb))
 
 
-def run_wide(args, prec, stream, flush, peaks, peak_src):
+def run_wide(args, prec, sp, stream, flush, peaks, peak_src):
     """The 1000-channel, 30000-pole workload (the per-energy tensor-core
     formation): a strided sample of its energy grid through the mixed path,
     and every 16th of those through the plain FP64 path, with the Omega error
@@ -298,8 +298,8 @@ def run_wide(args, prec, stream, flush, peaks, peak_src):
                         "30000 poles on [-5,200] Ry, w~N(0,0.02^2), a=20; %d of its 5000 energies on "
                         "0-10 Ry (evenly strided)" % E.size)}
     res = {}
-    for name, pr, Es in [("mixed", prec, E), ("fp64", 0, E[sub])]:
-        ctx = rmgb.Context(precision=pr, stream=stream.cuda_stream)
+    for name, pr, Es, spn in [("mixed", prec, E, sp), ("fp64", 0, E[sub], 0)]:
+        ctx = rmgb.Context(precision=pr, stream=stream.cuda_stream, solve_precision=spn)
         ctx.load_pw(0, pw)
         Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
@@ -574,7 +574,7 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_src = _peaks()
     wide = None
     if world == 1 and args.wide_energies > 0:
-        wide = _leg(run_wide, args, prec if prec != 0 else 2, stream, flush, peaks, peak_src)
+        wide = _leg(run_wide, args, prec if prec != 0 else 2, sp, stream, flush, peaks, peak_src)
     qdt_line = None
     if world == 1 and args.qdt_ieq != 0:
         qdt_line = _leg(run_qdt, args, prec, sp)

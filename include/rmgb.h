@@ -96,13 +96,16 @@ typedef struct rm_opts {
     int formulation;        /* mixed-precision formation (Eq. rmatrix on tensor cores):
                                RM_FORM_AUTO (default: pair operand while it is small,
                                per-energy GEMM above), RM_FORM_PAIRS, RM_FORM_ENERGY */
-    int solve_precision;    /* steps (c)-(d): RM_FP64 (default) or RM_FP32 (direct
-                               mode, shared-memory solver: the matching system is
-                               eliminated in FP32 and T = 2(1 - iK)^{-1} - 2 comes
-                               from an FP32 complex inversion of 1 - iK, whose error
-                               is that of a perturbation of 1 - iK of Frobenius norm
+    int solve_precision;    /* steps (c)-(d): RM_FP64 (default) or RM_FP32: the
+                               matching system is eliminated in FP32 (partial
+                               pivoting) and T = 2(1 - iK)^{-1} - 2 comes from an
+                               FP32 complex inversion of 1 - iK, whose error is that
+                               of a perturbation of 1 - iK of Frobenius norm
                                <= n_open 2^-24 ||1 - iK||_F; Omega is accumulated in
-                               FP64). Other cases run in FP64 whatever this asks */
+                               FP64. Shared-memory solver: direct mode only (MQDT
+                               runs in FP64). Global-memory solver: direct and MQDT
+                               mode (K_u in FP32, the quantum-defect elimination in
+                               FP64), up to about 3000 channels (above: FP64) */
     int channel_tables;     /* step (b): 1 builds the per-channel tables
                                (near-threshold interpolation, open- and closed-side
                                Chebyshev expansions; see rm_set_channels) and

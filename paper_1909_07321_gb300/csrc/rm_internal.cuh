@@ -214,10 +214,14 @@ cudaError_t launch_chanfn_export(const PwDev &pw, const double *E, int nE, const
 int solve_small_max_n();
 
 // Global-memory solver for any channel count (steps (c) and (d)).
+// f32 != 0: matching system, T step in FP32 (MQDT elimination, K and Omega
+// FP64), for channel counts where solve_large_f32_supported holds.
 size_t solve_large_bytes_per_energy(int n);
+bool solve_large_f32_supported(int n);
 cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
-                               double *omega, int n_tri, void *ws, int *launches, cudaStream_t s);
+                               double *omega, int n_tri, void *ws, int *launches, cudaStream_t s,
+                               int f32 = 0);
 
 // ---- MQDT coarse-mesh interpolation (qdt.cu) ------------------------------------
 enum QdtClass : signed char { QDT_OPEN = 0, QDT_ELIM = 1, QDT_DECAY = 2, QDT_THRESHOLD = 3 };

@@ -854,8 +854,9 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
         double *omb = omega ? omega + (size_t)e0 * ntri : nullptr;
         if (large) {
             int L = 0;
+            const int f32 = ctx->opts.solve_precision == RM_FP32 && !ku_out && solve_large_f32_supported(P.n);
             CK(launch_solve_large(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, ctx->wsL.p, &L, ctx->stream));
+                                  omb, ntri, ctx->wsL.p, &L, ctx->stream, f32));
             ctx->launches += L;
         } else {
             const int f32 = mode == RM_DIRECT && ctx->opts.solve_precision == RM_FP32 && !ku_out;

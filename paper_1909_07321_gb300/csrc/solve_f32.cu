@@ -241,20 +241,26 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
         // half-warp that holds row p. Columns <= c and the padding take the
         // update too: they are never read again (padding stays zero, as row
         // p's padding is zero); the pivot row's multiplier is zero.
+        // Tile columns at or left of c are never read again and tile columns
+        // past w are padding: both are skipped (the first per thread, the
+        // second uniformly).
         const int ip = p >> 4, src = (lane & 16) | (p & 15);
         float rb[TC];
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
             if (ip == i) {
 #pragma unroll
-                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(0xffffffffu, t[i][j], src);
+                for (int j = 0; j < TC; ++j)
+                    if (G16 * j < w) rb[j] = __shfl_sync(0xffffffffu, t[i][j], src);
             }
         }
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
+            if (G16 * i >= n) continue;
             const float f = colbuf[buf][ty + G16 * i];
 #pragma unroll
-            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f, rb[j], t[i][j]);
+            for (int j = 0; j < TC; ++j)
+                if (G16 * j < w && tx + G16 * j > c) t[i][j] = fmaf(-f, rb[j], t[i][j]);
         }
     }
     __syncthreads();
@@ -333,10 +339,13 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             vi[i] = vcol[buf][ty + G16 * i];
             uj[i] = ucol[buf][tx + G16 * i];
         }
+        // tiles of the padding (index >= n_o) are skipped uniformly
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
+            if (G16 * i >= no) continue;
 #pragma unroll
             for (int j = 0; j < TR; ++j) {
+                if (G16 * j >= no) continue;
                 float2 zz = z[i][j];
                 zz.x = fmaf(-vi[i].x, uj[j].x, fmaf(vi[i].y, uj[j].y, zz.x));
                 zz.y = fmaf(-vi[i].x, uj[j].y, fmaf(-vi[i].y, uj[j].x, zz.y));

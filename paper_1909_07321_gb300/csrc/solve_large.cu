@@ -15,12 +15,27 @@
 //   T             [1 + K^2 | K] -> lu -> X, Y = K X, |T|^2 = 4 (X^2 + Y^2)
 //   omega         thread per (energy, level pair I <= J), fixed summation order
 //
-// All FP64. Per-energy sizes differ (n_o, n_p vary with E); every kernel
-// reads them from the per-energy descriptors and idles outside them.
+// FP64 by default. With the FP32 matching option (rm_opts.solve_precision =
+// RM_FP32) the matching system is assembled and solved in FP32 and the T step
+// inverts 1 - iK in FP32 complex arithmetic (dense_global_f32.cuh: one CTA per
+// energy, blocked LU with partial pivoting; blocked sweep of the complex
+// symmetric 1 - iK), while the MQDT elimination, K and Omega stay FP64:
+//
+//   assemble_f32  [A | 0 | B] in FP32 (right-hand sides from a 4-aligned column)
+//   lu32          X = A^{-1} B for the P rows
+//   extract_f32   K_u (FP64) = X[P rows]; direct mode: K = K_u
+//   mqdt          as above (FP64)
+//   zbuild        Z = 1 - iK (FP32 complex)
+//   zsweep        Z -> -(1 - iK)^{-1};  T = 2 (1 - iK)^{-1} - 2
+//   t2z           |T_ab|^2 = 4 |Z_ab + delta_ab|^2 (symmetrised, FP64)
+//
+// Per-energy sizes differ (n_o, n_p vary with E); every kernel reads them from
+// the per-energy descriptors and idles outside them.
 #include <math.h>
 
 #include <algorithm>
 
+#include "dense_global_f32.cuh"
 #include "rm_internal.cuh"
 
 namespace rmgb {
@@ -31,10 +46,11 @@ constexpr int PNB = 32;     // LU panel width
 constexpr int GT = 64;      // GEMM / update tile
 constexpr int GK = 16;      // GEMM k-chunk
 
-// Per-energy layout of the workspace (doubles): [aug: n(2n+1)][ku: n^2][ks: n^2]
+// Per-energy layout of the workspace (doubles): [aug: n(2n+1)][ku: n^2][ks: n^2],
+// each slot rounded to 256 bytes (the FP32 kernels read it by float4)
 __host__ __device__ inline size_t slot_doubles(int n)
 {
-    return (size_t)n * (2 * n + 1) + 2 * (size_t)n * n;
+    return ((size_t)n * (2 * n + 1) + 2 * (size_t)n * n + 31) & ~(size_t)31;
 }
 
 struct EnergyDims {
@@ -577,7 +593,163 @@ __global__ void omega_kernel(PwDev pw, const double *__restrict__ E, int nE,
     }
 }
 
+// ---- FP32 path ---------------------------------------------------------------
+
+// [A | 0 | B] in FP32: A = diag(Ghat) - R diag(a Ghat' - b Ghat), B as in
+// assemble_kernel, right-hand sides from column rhs0(n), zero padding.
+__global__ void assemble_f32_kernel(PwDev pw, int nE, const ChanFn *__restrict__ cfa,
+                                    const double *__restrict__ Ra, const EnergyDims *__restrict__ dims,
+                                    const int *__restrict__ col_chan, double *ws)
+{
+    const int e = blockIdx.y;
+    const EnergyDims d = dims[e];
+    if (d.np < 0) return;
+    const int n = pw.n, rhs = f32d::rhs0(n), ld = f32d::aug_ld(n, d.np);
+    float *M = reinterpret_cast<float *>(slot_of(ws, n, e).aug);
+    const ChanFn *cf = cfa + (size_t)e * n;
+    const double *Rp = Ra + (size_t)e * tri_ld(n);
+    const int *cc = col_chan + (size_t)e * n;
+    const double a = pw.a, b = pw.b;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < (long long)n * ld;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / ld), c = (int)(q - (q / ld) * ld);
+        double v = 0.0;
+        if (c < n) {
+            const int j = cc[c];
+            const ChanFn cj = cf[j];
+            v = -Rp[r <= j ? tri_idx(r, j, n) : tri_idx(j, r, n)] * (a * cj.ghp - b * cj.gh);
+            if (r == j) v += cj.gh;
+        } else if (c >= rhs && c < rhs + d.np) {
+            const int o = cc[d.ncl + (c - rhs)];
+            const ChanFn co = cf[o];
+            v = Rp[r <= o ? tri_idx(r, o, n) : tri_idx(o, r, n)] * (a * co.sp - b * co.s);
+            if (r == o) v -= co.s;
+        }
+        M[(size_t)r * ld + c] = (float)v;
+    }
+}
+
+template <int PB>
+__global__ void __launch_bounds__(f32d::NTH, 1) lu32_kernel(int n, const EnergyDims *__restrict__ dims, double *ws,
+                                                            int *status)
+{
+    extern __shared__ float4 fsm4[];
+    const int e = blockIdx.x;
+    const EnergyDims d = dims[e];
+    if (d.np < 0) return;
+    float *M = reinterpret_cast<float *>(slot_of(ws, n, e).aug);
+    const int rhs = f32d::rhs0(n);
+    if (!f32d::lu32_factor_solve<PB>(M, f32d::aug_ld(n, d.np), n, rhs + d.np, rhs, d.ncl,
+                                     reinterpret_cast<float *>(fsm4)))
+        if (threadIdx.x == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
+}
+
+// K_u (FP64, np x np) = X[P rows]; without MQDT-eliminated channels also K
+// (symmetrised into ks, as written into K_out).
+__global__ void extract_f32_kernel(int n, int nE, const EnergyDims *dims, double *ws, double *K_out)
+{
+    const int e = blockIdx.y;
+    const EnergyDims d = dims[e];
+    if (d.np < 0) return;
+    const Slot s = slot_of(ws, n, e);
+    const float *M = reinterpret_cast<const float *>(s.aug);
+    const int ld = f32d::aug_ld(n, d.np), rhs = f32d::rhs0(n);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.np * d.np; q += gridDim.x * blockDim.x) {
+        const int p = q / d.np, r = q - (q / d.np) * d.np;
+        const double v = (double)M[(size_t)(d.ncl + p) * ld + rhs + r];
+        s.ku[(size_t)p * d.np + r] = v;
+        if (d.nq == 0) {
+            s.ks[(size_t)p * d.no + r] = 0.5 * (v + (double)M[(size_t)(d.ncl + r) * ld + rhs + p]);
+            if (K_out) K_out[(size_t)e * n * n + (size_t)p * n + r] = v;
+        }
+    }
+}
+
+// Z = 1 - iK (FP32 complex, row stride z_ld(no), zero padding) from K in ks.
+__global__ void zbuild_kernel(int n, int nE, const EnergyDims *dims, double *ws)
+{
+    const int e = blockIdx.y;
+    const EnergyDims d = dims[e];
+    if (d.np < 0) return;
+    const Slot s = slot_of(ws, n, e);
+    float2 *Z = reinterpret_cast<float2 *>(s.aug);
+    const int ldz = f32d::z_ld(d.no);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.no * ldz; q += gridDim.x * blockDim.x) {
+        const int p = q / ldz, r = q - (q / ldz) * ldz;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < d.no) v = make_float2(p == r ? 1.f : 0.f, (float)(-s.ks[(size_t)p * d.no + r]));
+        Z[q] = v;
+    }
+}
+
+template <int PB>
+__global__ void __launch_bounds__(f32d::NTH, 1) zsweep_kernel(int n, const EnergyDims *__restrict__ dims, double *ws,
+                                                              int *status)
+{
+    extern __shared__ float4 fsm4[];
+    const int e = blockIdx.x;
+    const EnergyDims d = dims[e];
+    if (d.np < 0) return;
+    float2 *Z = reinterpret_cast<float2 *>(slot_of(ws, n, e).aug);
+    if (!f32d::zsweep_invert<PB>(Z, f32d::z_ld(d.no), d.no, reinterpret_cast<float2 *>(fsm4)))
+        if (threadIdx.x == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
+}
+
+// |T_ab|^2 = 4 |W_ab - delta_ab|^2 with W = (1 - iK)^{-1} = -Z, symmetrised, into ks.
+__global__ void t2z_kernel(int n, int nE, const EnergyDims *dims, double *ws)
+{
+    const int e = blockIdx.y;
+    const EnergyDims d = dims[e];
+    if (d.np < 0) return;
+    const Slot s = slot_of(ws, n, e);
+    const float2 *Z = reinterpret_cast<const float2 *>(s.aug);
+    const int ldz = f32d::z_ld(d.no);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.no * d.no; q += gridDim.x * blockDim.x) {
+        const int p = q / d.no, r = q - (q / d.no) * d.no;
+        const float2 u = Z[(size_t)p * ldz + r], v = Z[(size_t)r * ldz + p];
+        const double ur = (double)u.x + (p == r ? 1.0 : 0.0), ui = u.y;
+        const double vr = (double)v.x + (p == r ? 1.0 : 0.0), vi = v.y;
+        s.ks[q] = 2.0 * (ur * ur + ui * ui + vr * vr + vi * vi);
+    }
+}
+
+int max_dyn_smem()
+{
+    static int v = -1;
+    if (v < 0) {
+        int dev = 0, x = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+            cudaGetLastError();
+            x = 48 * 1024;
+        }
+        v = x;
+    }
+    return v;
+}
+
+// Panel widths that fit shared memory for n channels (0: none fits).
+int lu_pb(int n)
+{
+    if (f32d::lu_smem<32>(n) <= (size_t)max_dyn_smem()) return 32;
+    if (f32d::lu_smem<16>(n) <= (size_t)max_dyn_smem()) return 16;
+    return 0;
+}
+int z_pb(int m)
+{
+    if (f32d::z_smem<16>(m) <= (size_t)max_dyn_smem()) return 16;
+    if (f32d::z_smem<8>(m) <= (size_t)max_dyn_smem()) return 8;
+    return 0;
+}
+
+template <class K> cudaError_t set_smem(K kern, size_t bytes)
+{
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 }  // namespace
+
+bool solve_large_f32_supported(int n) { return lu_pb(n) > 0 && z_pb(n) > 0; }
 
 size_t solve_large_bytes_per_energy(int n)
 {
@@ -590,8 +762,9 @@ size_t solve_large_bytes_per_energy(int n)
 cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const ChanFn *cf,
                                const double *R, int *status, double *K_out, int *n_open_out,
                                double *omega, int n_tri, void *ws_raw, int *launches,
-                               cudaStream_t st)
+                               cudaStream_t st, int f32)
 {
+    if (f32 && !solve_large_f32_supported(pw.n)) return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
     const int n = pw.n;
     char *p = static_cast<char *>(ws_raw);
@@ -623,17 +796,37 @@ cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const C
                                         n_open_out);
     LAUNCH_OK();
     const int xb = (int)std::min<long long>(64, ((long long)n * 2 * n + NTH - 1) / NTH);
-    assemble_kernel<<<dim3(xb, nE), NTH, 0, st>>>(pw, nE, cf, R, dims, col_chan, ws);
-    LAUNCH_OK();
-    jobs_match_kernel<<<eg, 128, 0, st>>>(n, nE, dims, ws, lu);
-    LAUNCH_OK();
-    lu_kernel<<<nE, NTH, 0, st>>>(lu, status);
-    LAUNCH_OK();
-    prune_kernel<<<eg, 128, 0, st>>>(nE, status, dims);
-    LAUNCH_OK();
     const int xb2 = (int)std::min<long long>(64, ((long long)n * n + NTH - 1) / NTH);
-    extract_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, ws, K_out);
-    LAUNCH_OK();
+    if (f32) {
+        assemble_f32_kernel<<<dim3(xb, nE), NTH, 0, st>>>(pw, nE, cf, R, dims, col_chan, ws);
+        LAUNCH_OK();
+        const int pb = lu_pb(n);
+        if (pb == 32) {
+            const size_t sm = f32d::lu_smem<32>(n);
+            if ((err = set_smem(lu32_kernel<32>, sm)) != cudaSuccess) return err;
+            lu32_kernel<32><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+        } else {
+            const size_t sm = f32d::lu_smem<16>(n);
+            if ((err = set_smem(lu32_kernel<16>, sm)) != cudaSuccess) return err;
+            lu32_kernel<16><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+        }
+        LAUNCH_OK();
+        prune_kernel<<<eg, 128, 0, st>>>(nE, status, dims);
+        LAUNCH_OK();
+        extract_f32_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, ws, K_out);
+        LAUNCH_OK();
+    } else {
+        assemble_kernel<<<dim3(xb, nE), NTH, 0, st>>>(pw, nE, cf, R, dims, col_chan, ws);
+        LAUNCH_OK();
+        jobs_match_kernel<<<eg, 128, 0, st>>>(n, nE, dims, ws, lu);
+        LAUNCH_OK();
+        lu_kernel<<<nE, NTH, 0, st>>>(lu, status);
+        LAUNCH_OK();
+        prune_kernel<<<eg, 128, 0, st>>>(nE, status, dims);
+        LAUNCH_OK();
+        extract_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, ws, K_out);
+        LAUNCH_OK();
+    }
     const int tiles = (n + GT - 1) / GT;
     // MQDT elimination (no-op for energies without eliminated channels)
     mqdt_build_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, cf, col_chan, qpos, opos, ws, lu, gj);
@@ -648,7 +841,29 @@ cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const C
     LAUNCH_OK();
     mqdt_copyback_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, ws);
     LAUNCH_OK();
-    if (omega) {
+    if (omega && f32) {
+        zbuild_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, ws);
+        LAUNCH_OK();
+        const int pb = z_pb(n);
+        if (pb == 16) {
+            const size_t sm = f32d::z_smem<16>(n);
+            if ((err = set_smem(zsweep_kernel<16>, sm)) != cudaSuccess) return err;
+            zsweep_kernel<16><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+        } else {
+            const size_t sm = f32d::z_smem<8>(n);
+            if ((err = set_smem(zsweep_kernel<8>, sm)) != cudaSuccess) return err;
+            zsweep_kernel<8><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+        }
+        LAUNCH_OK();
+        prune_kernel<<<eg, 128, 0, st>>>(nE, status, dims);
+        LAUNCH_OK();
+        t2z_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, ws);
+        LAUNCH_OK();
+        const int nl = pw.n_levels;
+        const int xb3 = (int)std::min<long long>(64, ((long long)nl * (nl + 1) / 2 + NTH - 1) / NTH);
+        omega_kernel<<<dim3(xb3, nE), NTH, 0, st>>>(pw, E, nE, dims, open_pos, ws, omega, n_tri);
+        LAUNCH_OK();
+    } else if (omega) {
         t_build_kernel<<<dim3(xb2, nE), NTH, 0, st>>>(n, nE, dims, ws, lu, gj);
         LAUNCH_OK();
         gemm_kernel<<<dim3(tiles, tiles, nE), NTH, 0, st>>>(gj);   // 1 + K^2
