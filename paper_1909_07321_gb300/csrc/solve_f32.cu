@@ -50,6 +50,51 @@ __device__ __forceinline__ T pick(const T (&v)[N], int k)
     return r;
 }
 
+// One step of the sweep on pivot k, after the pivot column has been
+// published: z_ij -= v_i u_j, then column k <- v, row k <- v^T and the pivot
+// <- -1/d (v = u / d, u = column k before the step; uniform tile indices).
+template <int TR>
+__device__ __forceinline__ void sweep_apply(float2 (&z)[TR][TR], int k, int tx, int ty, const float2 *vc,
+                                            const float2 *uc, float2 dinv)
+{
+    const int kk = k >> 4;
+    float2 vi[TR], uj[TR];
+#pragma unroll
+    for (int i = 0; i < TR; ++i) {
+        vi[i] = vc[ty + G16 * i];
+        uj[i] = uc[tx + G16 * i];
+    }
+#pragma unroll
+    for (int i = 0; i < TR; ++i) {
+#pragma unroll
+        for (int j = 0; j < TR; ++j) {
+            float2 zz = z[i][j];
+            zz.x = fmaf(-vi[i].x, uj[j].x, fmaf(vi[i].y, uj[j].y, zz.x));
+            zz.y = fmaf(-vi[i].x, uj[j].y, fmaf(-vi[i].y, uj[j].x, zz.y));
+            z[i][j] = zz;
+        }
+    }
+    if (tx == (k & 15)) {
+#pragma unroll
+        for (int j = 0; j < TR; ++j)
+            if (kk == j) {
+#pragma unroll
+                for (int i = 0; i < TR; ++i) z[i][j] = vi[i];
+            }
+    }
+    if (ty == (k & 15)) {
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+            if (kk == i) {
+#pragma unroll
+                for (int j = 0; j < TR; ++j) {
+                    const int c = tx + G16 * j;
+                    z[i][j] = (c == k) ? make_float2(-dinv.x, -dinv.y) : vc[c];
+                }
+            }
+    }
+}
+
 template <int TR, int TC>
 __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa, const double *__restrict__ Ra,
@@ -70,11 +115,13 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     __shared__ float rsv[MAXN], rss[MAXN];        // right-hand side k: a S' - b S, S
     __shared__ int kind_s[MAXN];
     __shared__ float colbuf[2][G16 * TR];         // multipliers a_rc / a_pc (0 for the pivot row)
-    __shared__ int pbuf[2];
-    __shared__ float pvbuf[2];
+    __shared__ float colbuf2[2][G16 * TR];        // second column of a pair
+    __shared__ int pbuf[2], pbuf2[2];
+    __shared__ float pvbuf[2], pvbuf2[2];
     __shared__ unsigned used_s[(G16 * TR + 31) / 32];
     __shared__ float2 vcol[2][G16 * TR];
-    __shared__ float2 dbuf[2], dinvbuf[2];
+    __shared__ float2 dbuf[2], dinvbuf[2], dbuf2[2], dinvbuf2[2];
+    __shared__ float2 vcol2[2][G16 * TR], ucol2[2][G16 * TR];
     __shared__ int rowpos[G16 * TR];
     __shared__ float pivval[MAXN];
     __shared__ float2 ucol[2][G16 * TR];
@@ -101,10 +148,12 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     // ---- channel order: closed first, then P (open), by warp prefix counts
     for (int i = tid; i < n; i += NT) kind_s[i] = cf[i].kind;
     for (int r = tid; r < G16 * TR; r += NT) {
-        ucol[0][r] = make_float2(0.0f, 0.0f);
-        ucol[1][r] = make_float2(0.0f, 0.0f);
-        vcol[0][r] = make_float2(0.0f, 0.0f);
-        vcol[1][r] = make_float2(0.0f, 0.0f);
+        for (int q = 0; q < 2; ++q) {
+            ucol[q][r] = make_float2(0.0f, 0.0f);
+            vcol[q][r] = make_float2(0.0f, 0.0f);
+            ucol2[q][r] = make_float2(0.0f, 0.0f);
+            vcol2[q][r] = make_float2(0.0f, 0.0f);
+        }
     }
     if (tid < (G16 * TR + 31) / 32) used_s[tid] = 0u;
     // R of this energy and the level tables, by coalesced loads
@@ -194,9 +243,118 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     }
 
     // ---- Gauss-Jordan elimination, implicit partial pivoting -----------------
+    // Columns are taken in pairs (c even, c + 1): their owner half-warps form
+    // one warp (lanes 0-15 column c, 16-31 column c + 1), which finds pivot
+    // p1 of column c, brings column c + 1 up to date with it by shuffles,
+    // finds its pivot p2, and publishes both multiplier columns; after one
+    // barrier every thread applies both eliminations in turn (the first
+    // leaves row p2 as a_p2j - m1_p2 a_p1j, the pivot row of the second).
     const unsigned hmask = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
-    for (int c = 0; c < n; ++c) {
-        const int buf = c & 1;
+    const unsigned full = 0xffffffffu;
+    int c_first_single = 0;
+    for (int c = 0; c + 1 < n; c += 2) {
+        const int buf = (c >> 1) & 1;
+        const int jc = c >> 4;
+        if ((tx >> 1) == ((c & 15) >> 1)) {
+            float v[TR];
+            unsigned key = 0u;
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                v[i] = pick<TC>(t[i], jc);
+                const int r = ty + G16 * i;
+                const bool used = (used_s[r >> 5] >> (r & 31)) & 1u;
+                const unsigned kv = (__float_as_uint(fabsf(v[i])) & ~0x7fu) | (unsigned)(127 - r);
+                if (r < n && !used && kv > key) key = kv;
+            }
+            key = __reduce_max_sync(hmask, key);
+            const unsigned keyA = __shfl_sync(full, key, 0);
+            const int p1 = keyA ? 127 - (int)(keyA & 0x7fu) : 0;
+            const float at_p1 = pick<TR>(v, p1 >> 4);
+            const float pv1 = __shfl_sync(full, at_p1, p1 & 15);
+            const float u1 = __shfl_sync(full, at_p1, 16 + (p1 & 15));   // a_{p1, c+1}
+            const float ipv1 = __frcp_rn(pv1);
+            float m1[TR], v2[TR];
+            unsigned key2 = 0u;
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                const int r = ty + G16 * i;
+                m1[i] = (r == p1) ? 0.0f : v[i] * ipv1;
+                const float mA = __shfl_xor_sync(full, m1[i], 16);
+                v2[i] = fmaf(-mA, u1, v[i]);
+                const bool used = ((used_s[r >> 5] >> (r & 31)) & 1u) || r == p1;
+                const unsigned kv = (__float_as_uint(fabsf(v2[i])) & ~0x7fu) | (unsigned)(127 - r);
+                if (r < n && !used && kv > key2) key2 = kv;
+            }
+            key2 = __reduce_max_sync(hmask, key2);
+            const unsigned keyB = __shfl_sync(full, key2, 16);
+            const int p2 = keyB ? 127 - (int)(keyB & 0x7fu) : 0;
+            const float pv2 = __shfl_sync(full, pick<TR>(v2, p2 >> 4), 16 + (p2 & 15));
+            const float ipv2 = __frcp_rn(pv2);
+            if ((tx & 1) == 0) {
+#pragma unroll
+                for (int i = 0; i < TR; ++i) colbuf[buf][ty + G16 * i] = m1[i];
+            } else {
+#pragma unroll
+                for (int i = 0; i < TR; ++i) {
+                    const int r = ty + G16 * i;
+                    colbuf2[buf][r] = (r == p2) ? 0.0f : v2[i] * ipv2;
+                }
+            }
+            if (lane == 0) {
+                pbuf[buf] = p1;
+                pvbuf[buf] = pv1;
+                pbuf2[buf] = p2;
+                pvbuf2[buf] = pv2;
+                used_s[p1 >> 5] |= 1u << (p1 & 31);
+                used_s[p2 >> 5] |= 1u << (p2 & 31);
+                rowpos[p1] = c;
+                rowpos[p2] = c + 1;
+                pivval[c] = pv1;
+                pivval[c + 1] = pv2;
+            }
+        }
+        __syncthreads();
+        const int p1 = pbuf[buf], p2 = pbuf2[buf];
+        const float pv1 = pvbuf[buf], pv2 = pvbuf2[buf];
+        if (!(fabsf(pv1) > 0.0f) || !isfinite(pv1) || !(fabsf(pv2) > 0.0f) || !isfinite(pv2)) {
+            if (tid == 0) status[e] = RM_ESINGULAR;
+            return;
+        }
+        // first elimination (row p1); it turns row p2 into its reduced form
+        // a_p2j - m1_p2 a_p1j, which the second elimination then uses
+        const int ip1 = p1 >> 4, src1 = (lane & 16) | (p1 & 15);
+        const int ip2 = p2 >> 4, src2 = (lane & 16) | (p2 & 15);
+        float rb[TC];
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            if (ip1 == i) {
+#pragma unroll
+                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(full, t[i][j], src1);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            const float f1 = colbuf[buf][ty + G16 * i];
+#pragma unroll
+            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f1, rb[j], t[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            if (ip2 == i) {
+#pragma unroll
+                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(full, t[i][j], src2);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+            const float f2 = colbuf2[buf][ty + G16 * i];
+#pragma unroll
+            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f2, rb[j], t[i][j]);
+        }
+        c_first_single = c + 2;
+    }
+    for (int c = c_first_single; c < n; ++c) {
+        const int buf = (c >> 1) & 1;
         if (tx == (c & 15)) {
             // the column's half-warp: pivot row by shuffles, then the multipliers
             const int jc = c >> 4;
@@ -241,26 +399,20 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
         // half-warp that holds row p. Columns <= c and the padding take the
         // update too: they are never read again (padding stays zero, as row
         // p's padding is zero); the pivot row's multiplier is zero.
-        // Tile columns at or left of c are never read again and tile columns
-        // past w are padding: both are skipped (the first per thread, the
-        // second uniformly).
         const int ip = p >> 4, src = (lane & 16) | (p & 15);
         float rb[TC];
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
             if (ip == i) {
 #pragma unroll
-                for (int j = 0; j < TC; ++j)
-                    if (G16 * j < w) rb[j] = __shfl_sync(0xffffffffu, t[i][j], src);
+                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(0xffffffffu, t[i][j], src);
             }
         }
 #pragma unroll
         for (int i = 0; i < TR; ++i) {
-            if (G16 * i >= n) continue;
             const float f = colbuf[buf][ty + G16 * i];
 #pragma unroll
-            for (int j = 0; j < TC; ++j)
-                if (G16 * j < w && tx + G16 * j > c) t[i][j] = fmaf(-f, rb[j], t[i][j]);
+            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f, rb[j], t[i][j]);
         }
     }
     __syncthreads();
@@ -301,8 +453,76 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             z[i][j] = v;
         }
     }
-    for (int k = 0; k < no; ++k) {
-        const int buf = k & 1;
+    // Pivots in pairs (k even, k + 1) as in the elimination: the owner warp
+    // finds d1 = z_kk and v1 = column k / d1 (lanes 0-15), brings column k + 1
+    // through the step on k (lanes 16-31: w_i = z_i,k+1 - v1_i z_k+1,k, and
+    // w_k = z_k+1,k / d1), takes d2 = w_k+1, and publishes both; every thread
+    // then applies both steps after one barrier.
+    int k_first_single = 0;
+    for (int k = 0; k + 1 < no; k += 2) {
+        const int buf = (k >> 1) & 1;
+        const int kk = k >> 4;
+        if ((tx >> 1) == ((k & 15) >> 1)) {
+            float2 u[TR];
+#pragma unroll
+            for (int i = 0; i < TR; ++i) u[i] = pick<TR>(z[i], kk);
+            const float2 ukk = pick<TR>(u, kk);
+            float2 d1, uk1;
+            d1.x = __shfl_sync(full, ukk.x, k & 15);
+            d1.y = __shfl_sync(full, ukk.y, k & 15);
+            uk1.x = __shfl_sync(full, ukk.x, (k + 1) & 15);   // z_{k+1,k}
+            uk1.y = __shfl_sync(full, ukk.y, (k + 1) & 15);
+            const float2 dinv1 = crcp_f(d1);
+            float2 w[TR];
+#pragma unroll
+            for (int i = 0; i < TR; ++i) {
+                const float2 v1 = cmul_f(u[i], dinv1);
+                float2 vA;
+                vA.x = __shfl_xor_sync(full, v1.x, 16);
+                vA.y = __shfl_xor_sync(full, v1.y, 16);
+                const int r = ty + G16 * i;
+                const float2 uv = cmul_f(vA, uk1);
+                w[i] = (r == k) ? cmul_f(uk1, dinv1) : make_float2(u[i].x - uv.x, u[i].y - uv.y);
+                if ((tx & 1) == 0 && r < no) {
+                    ucol[buf][r] = u[i];
+                    vcol[buf][r] = v1;
+                }
+            }
+            const float2 wk1 = pick<TR>(w, kk);
+            float2 d2;
+            d2.x = __shfl_sync(full, wk1.x, 16 + ((k + 1) & 15));
+            d2.y = __shfl_sync(full, wk1.y, 16 + ((k + 1) & 15));
+            const float2 dinv2 = crcp_f(d2);
+            if (tx & 1) {
+#pragma unroll
+                for (int i = 0; i < TR; ++i) {
+                    const int r = ty + G16 * i;
+                    if (r < no) {
+                        ucol2[buf][r] = w[i];
+                        vcol2[buf][r] = cmul_f(w[i], dinv2);
+                    }
+                }
+            }
+            if (lane == 0) {
+                dbuf[buf] = d1;
+                dinvbuf[buf] = dinv1;
+                dbuf2[buf] = d2;
+                dinvbuf2[buf] = dinv2;
+            }
+        }
+        __syncthreads();
+        const float2 d1 = dbuf[buf], d2 = dbuf2[buf];
+        if (!(fabsf(d1.x) + fabsf(d1.y) > 0.0f) || !isfinite(d1.x) || !isfinite(d1.y) ||
+            !(fabsf(d2.x) + fabsf(d2.y) > 0.0f) || !isfinite(d2.x) || !isfinite(d2.y)) {
+            if (tid == 0) status[e] = RM_ESINGULAR;
+            return;
+        }
+        sweep_apply<TR>(z, k, tx, ty, vcol[buf], ucol[buf], dinvbuf[buf]);
+        sweep_apply<TR>(z, k + 1, tx, ty, vcol2[buf], ucol2[buf], dinvbuf2[buf]);
+        k_first_single = k + 2;
+    }
+    for (int k = k_first_single; k < no; ++k) {
+        const int buf = (k >> 1) & 1;
         const int kk = k >> 4;
         if (tx == (k & 15)) {
             // column k's half-warp: u, the pivot d = u_k, and v = u / d
@@ -333,47 +553,7 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        float2 vi[TR], uj[TR];
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            vi[i] = vcol[buf][ty + G16 * i];
-            uj[i] = ucol[buf][tx + G16 * i];
-        }
-        // tiles of the padding (index >= n_o) are skipped uniformly
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            if (G16 * i >= no) continue;
-#pragma unroll
-            for (int j = 0; j < TR; ++j) {
-                if (G16 * j >= no) continue;
-                float2 zz = z[i][j];
-                zz.x = fmaf(-vi[i].x, uj[j].x, fmaf(vi[i].y, uj[j].y, zz.x));
-                zz.y = fmaf(-vi[i].x, uj[j].y, fmaf(-vi[i].y, uj[j].x, zz.y));
-                z[i][j] = zz;
-            }
-        }
-        // column k: u_i / d; row k: u_j / d (= v_j, the matrix being
-        // symmetric); the pivot: -1/d (uniform indices)
-        if (tx == (k & 15)) {
-#pragma unroll
-            for (int j = 0; j < TR; ++j)
-                if (kk == j) {
-#pragma unroll
-                    for (int i = 0; i < TR; ++i) z[i][j] = vi[i];
-                }
-        }
-        if (ty == (k & 15)) {
-            const float2 dinv = dinvbuf[buf];
-#pragma unroll
-            for (int i = 0; i < TR; ++i)
-                if (kk == i) {
-#pragma unroll
-                    for (int j = 0; j < TR; ++j) {
-                        const int c = tx + G16 * j;
-                        z[i][j] = (c == k) ? make_float2(-dinv.x, -dinv.y) : vcol[buf][c];
-                    }
-                }
-        }
+        sweep_apply<TR>(z, k, tx, ty, vcol[buf], ucol[buf], dinvbuf[buf]);
     }
     __syncthreads();   // every read of K in Pm is done
 #pragma unroll

@@ -695,7 +695,8 @@ __global__ void __launch_bounds__(f32d::NTH, 1) zsweep_kernel(int n, const Energ
         if (threadIdx.x == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
 }
 
-// |T_ab|^2 = 4 |W_ab - delta_ab|^2 with W = (1 - iK)^{-1} = -Z, symmetrised, into ks.
+// |T_ab|^2 = 4 |W_ab - delta_ab|^2 with W = (1 - iK)^{-1} = -Z (upper triangle
+// of Z, so |T|^2 is symmetric), into ks.
 __global__ void t2z_kernel(int n, int nE, const EnergyDims *dims, double *ws)
 {
     const int e = blockIdx.y;
@@ -706,10 +707,9 @@ __global__ void t2z_kernel(int n, int nE, const EnergyDims *dims, double *ws)
     const int ldz = f32d::z_ld(d.no);
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < d.no * d.no; q += gridDim.x * blockDim.x) {
         const int p = q / d.no, r = q - (q / d.no) * d.no;
-        const float2 u = Z[(size_t)p * ldz + r], v = Z[(size_t)r * ldz + p];
+        const float2 u = Z[(size_t)min(p, r) * ldz + max(p, r)];   // upper triangle
         const double ur = (double)u.x + (p == r ? 1.0 : 0.0), ui = u.y;
-        const double vr = (double)v.x + (p == r ? 1.0 : 0.0), vi = v.y;
-        s.ks[q] = 2.0 * (ur * ur + ui * ui + vr * vr + vi * vi);
+        s.ks[q] = 4.0 * (ur * ur + ui * ui);
     }
 }
 
