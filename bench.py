@@ -243,35 +243,78 @@ def _chanfn_ops(work):
 
 
 def run_serving(args, prec):
-    """Poisson stream of partial-wave x energy-batch requests through the
-    continuous-batching server (mixed-precision formation); p50/p99 latency."""
+    """The serving workload: a stream of partial-wave x energy-batch requests
+    (50-1500 channels, 25-35 poles per channel, 256-8192 energies on 0-8 Ry,
+    half MQDT; a pool of 64 pole sets) through the continuous-batching server
+    with the mixed-precision path (bf16x3 formation, FP32 matching) and with
+    the plain FP64 path. Mixed: first every request at once (capacity), then
+    Poisson arrivals at 0.9 x that capacity (p50 / p99 latency). FP64: the same
+    requests with every args.serving_fp64_stride-th energy (throughput in
+    energy-solves/s; the FP64 path is ~10^2 slower), and the Omega error of
+    the mixed results on those energies."""
     from paper_1909_07321_gb300 import serving, synth
-    specs = synth.serving_requests(args.serving_requests, args.serving_rate,
-                                   n_range=(50, 200), ne_range=(256, 2048), n_sets=16)
+    nreq = args.serving_requests
+    specs = synth.serving_requests(nreq, 1.0, n_range=(50, 1500), ne_range=(256, 8192), n_sets=64)
     pws = {}
-    reqs = []
-    for sp in specs:
-        if sp["set_id"] not in pws:
-            pws[sp["set_id"]] = synth.serving_pole_set(sp["set_id"], sp["n"])
-        reqs.append(serving.Request(sp["id"], sp["set_id"], pws[sp["set_id"]], sp["E"], sp["mode"],
-                                    sp["t_arrival"]))
-    srv = serving.Server(n_slots=4, precision=prec, slot_workspace=1 << 30, cache_sets=4)
-    try:
-        # warm the slots (kernels loaded, workspaces sized) outside the measurement
-        warm = [serving.Request(-1 - i, r.set_id, r.pw, r.E[:64], r.mode, 0.0)
-                for i, r in enumerate(reqs[:4])]
-        srv.run(warm)
-        srv.run(reqs)
-    finally:
-        srv.close()
-    st = serving.latency_stats(reqs)
-    return {"workload": ("Poisson arrivals at %.0f/s; requests of 50-200 channels (pool of 16 "
-                         "pole sets, 25-35 poles per channel), 256-2048 energies on 0-8 Ry, "
-                         "half MQDT; 4 slots" % args.serving_rate),
-            "formation": [k for k, v in PREC.items() if v == prec][0],
-            "requests": st["requests"], "energy_solves": st["energy_solves"],
-            "energy_solves_per_s": st["energy_solves_per_s"],
-            "p50_ms": 1e3 * st["p50_s"], "p99_ms": 1e3 * st["p99_s"], "mean_ms": 1e3 * st["mean_s"]}
+
+    def make(specs_, stride=1, t_scale=0.0):
+        out = []
+        for sp in specs_:
+            if sp["set_id"] not in pws:
+                pws[sp["set_id"]] = synth.serving_pole_set(sp["set_id"], sp["n"])
+            out.append(serving.Request(sp["id"], sp["set_id"], pws[sp["set_id"]], sp["E"][::stride], sp["mode"],
+                                       sp["t_arrival"] * t_scale))
+        return out
+
+    def serve(precision, sp_, reqs):
+        srv = serving.Server(n_slots=4, precision=precision, solve_precision=sp_, mem_budget=96 << 30,
+                             lane_workspace=4 << 30, cache_sets=64)
+        try:
+            srv.prepare(reqs)
+            warm = [serving.Request(-1 - i, r.set_id, r.pw, r.E[:64], r.mode, 0.0) for i, r in enumerate(reqs[:4])]
+            srv.run(warm)
+            srv.run(reqs)
+            loads = srv.loads
+        finally:
+            srv.close()
+        return serving.latency_stats(reqs), loads
+
+    # capacity: every request queued at t = 0
+    sat = make(specs)
+    st_sat, loads = serve(2, 1, sat)
+    cap = st_sat["requests"] / st_sat["wall_s"]
+    # Poisson arrivals at 0.9 x capacity (the stream's exponential gaps rescaled)
+    rate = 0.9 * cap
+    pois = make(specs, t_scale=1.0 / rate)
+    st_p, _ = serve(2, 1, pois)
+    # FP64 served arm on a strided subsample of every request's energies
+    k = args.serving_fp64_stride
+    sub = make(specs, stride=k)
+    st64, _ = serve(0, 0, sub)
+    rel = []
+    for a, b in zip(sat, sub):
+        om_m = a.omega[::k]
+        nb = np.linalg.norm(b.omega, axis=1)
+        ok = nb > 0
+        rel.extend((np.linalg.norm(om_m[ok] - b.omega[ok], axis=1) / nb[ok]).tolist())
+    rel = np.array(rel)
+    ns = [sp["n"] for sp in specs]
+    nes = [sp["E"].size for sp in specs]
+    return {"workload": ("%d requests: 50-1500 channels (drawn n %d-%d, mean %.0f), 25-35 poles per channel "
+                         "(pool of 64 pole sets), 256-8192 energies on 0-8 Ry (mean %.0f), half MQDT; "
+                         "4 lanes of one context" % (nreq, min(ns), max(ns), np.mean(ns), np.mean(nes))),
+            "mixed_saturated": {"energy_solves_per_s": st_sat["energy_solves_per_s"],
+                                "requests_per_s": cap, "wall_s": st_sat["wall_s"],
+                                "energy_solves": st_sat["energy_solves"], "pole_set_loads": loads},
+            "mixed_poisson_0.9": {"rate_per_s": rate, "energy_solves_per_s": st_p["energy_solves_per_s"],
+                                  "p50_ms": 1e3 * st_p["p50_s"], "p99_ms": 1e3 * st_p["p99_s"],
+                                  "mean_ms": 1e3 * st_p["mean_s"]},
+            "fp64_saturated": {"energy_solves_per_s": st64["energy_solves_per_s"], "energy_stride": k,
+                               "energy_solves": st64["energy_solves"], "wall_s": st64["wall_s"]},
+            "mixed_over_fp64": st_sat["energy_solves_per_s"] / st64["energy_solves_per_s"],
+            "omega_rel_err_vs_fp64": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
+                                      "max": float(rel.max()), "energies": int(rel.size)},
+            "formation": "bf16x3", "matching": "fp32"}
 
 
 def _pe_tiles(n):
@@ -567,7 +610,7 @@ def run_ours(args, rank, world, local_rank):
 
     serving_line = None
     if rank == 0 and world == 1 and args.serving_requests > 0:
-        serving_line = _leg(run_serving, args, prec if prec != 0 else 2)
+        serving_line = _leg(run_serving, args, 2)
 
     if rank != 0:
         return
@@ -684,9 +727,10 @@ def main():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path beside the chosen precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=48,
+    ap.add_argument("--serving-requests", type=int, default=200,
                     help="requests in the serving leg (0 to skip)")
-    ap.add_argument("--serving-rate", type=float, default=40.0, help="request arrival rate (1/s)")
+    ap.add_argument("--serving-fp64-stride", type=int, default=64,
+                    help="the FP64 served arm solves every k-th energy of each request")
     ap.add_argument("--matching", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the matching elimination on the mixed path")
     ap.add_argument("--qdt-ieq", type=int, default=-25,

@@ -115,6 +115,10 @@ typedef struct rm_opts {
                                mixed-precision formation, 0 with FP64 (whose K is
                                meant to match to 1e-9 even where the matching
                                amplifies channel-function errors 1e4-fold) */
+    int lanes;              /* number of lanes (default 1, at most 64): independent
+                               streams of work in one context, each with its own
+                               workspace and Omega accumulator, sharing the
+                               context's partial waves (see rm_lane_solve_energies) */
 } rm_opts;
 
 #define RM_SOLVER_AUTO    0
@@ -381,8 +385,55 @@ int rm_k_matrices_noalloc(int device, int n_ch, int n_poles, int n_E, const doub
                           int *n_open_out, int *status_out, void *stream, char *errbuf,
                           size_t errlen);
 
-/* Waits for all work enqueued on the context's stream and for the copies of
- * rm_collision_strengths_async. */
+/* ---- lanes (no counterpart in the paper: concurrent use of one context) ----
+ * A context with rm_opts.lanes = L > 1 has L lanes. Each lane has its own
+ * CUDA stream (lane 0's is the context's stream), its own workspace and its
+ * own Omega accumulator and registered grid; all lanes share the context's
+ * partial waves (poles, amplitudes, channel tables and the tensor-core
+ * operands, each built once). Work enqueued on different lanes may overlap on
+ * the device. The calls without a lane argument act on lane 0. Loading,
+ * replacing or unloading a partial wave while another lane has work on it
+ * enqueued is the caller's error. */
+
+/* rm_solve_energies on lane `lane` (0 <= lane < lanes): accumulates into that
+ * lane's Omega, on that lane's grid. Asynchronous on the lane's stream.
+ * Errors: as rm_solve_energies, RM_EINVAL for a bad lane. */
+int rm_lane_solve_energies(rm_ctx *ctx, int lane, int pw, int n_E, const double *E, int mode,
+                           double *K_out, int *n_open_out, int *status_out);
+
+/* rm_collision_strengths on lane `lane` (synchronises that lane only). */
+int rm_lane_collision_strengths(rm_ctx *ctx, int lane, double *omega_out, int reset);
+
+/* 1 when all work enqueued on the lane by rm_lane_solve_energies /
+ * rm_solve_energies has completed, 0 while some is pending (no waiting),
+ * negative on error. */
+int rm_lane_query(rm_ctx *ctx, int lane);
+
+/* Waits for the lane's stream. */
+int rm_lane_sync(rm_ctx *ctx, int lane);
+
+/* The lane's cudaStream_t (NULL for a bad lane or context). */
+void *rm_lane_stream(rm_ctx *ctx, int lane);
+
+/* Sizes lane `lane`'s workspace and Omega accumulator for a solve of n_E
+ * energies of partial wave `pw` (and builds the wave's tensor-core operands
+ * if the context's precision uses them), so that such a solve allocates no
+ * device memory; *bytes (may be NULL) receives the lane's device bytes after
+ * it. Synchronous. Errors: RM_EINVAL, RM_ENOTLOADED, RM_EUNSUPPORTED,
+ * RM_ENOMEM, RM_ECUDA. */
+int rm_lane_reserve(rm_ctx *ctx, int lane, int pw, int n_E, size_t *bytes);
+
+/* Device bytes held for partial wave `pw` (poles, amplitudes, channel tables,
+ * operands). Errors: RM_EINVAL, RM_ENOTLOADED. */
+int rm_pw_bytes(rm_ctx *ctx, int pw, size_t *bytes);
+
+/* Frees the device buffers of partial wave `pw` (it must be loaded again
+ * before use). Work already enqueued that reads it completes first
+ * (cudaFree synchronises the device). Errors: RM_EINVAL, RM_ENOTLOADED. */
+int rm_unload_pw(rm_ctx *ctx, int pw);
+
+/* Waits for all work enqueued on every lane of the context and for the
+ * copies of rm_collision_strengths_async. */
 int rm_sync(rm_ctx *ctx);
 
 /* Number of kernels this context has launched since creation. */

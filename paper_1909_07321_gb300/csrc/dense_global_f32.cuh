@@ -109,24 +109,30 @@ __device__ __forceinline__ void lu_update_strip(float *M, int ld, int rlo, int r
 {
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int cb[2] = {c0 + 4 * tx, c0 + 64 + 4 * tx};
-    for (int r0 = rlo; r0 < rhi; r0 += 128) {
-        const int rb = r0 + ty * 4;
-        if (rb >= rhi) continue;
-        float acc[4][8];
+    // C tile of rows rb .. rb + 3 into v (zero outside [rstore, rhi) or past ld)
+    auto load = [&](int rb, float (&v)[4][8]) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = rb + i;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (r < rhi && r >= rstore && cb[h] < ld)
-                    v = *reinterpret_cast<const float4 *>(M + (size_t)r * ld + cb[h]);
-                acc[i][4 * h + 0] = v.x;
-                acc[i][4 * h + 1] = v.y;
-                acc[i][4 * h + 2] = v.z;
-                acc[i][4 * h + 3] = v.w;
+                    q = *reinterpret_cast<const float4 *>(M + (size_t)r * ld + cb[h]);
+                v[i][4 * h + 0] = q.x;
+                v[i][4 * h + 1] = q.y;
+                v[i][4 * h + 2] = q.z;
+                v[i][4 * h + 3] = q.w;
             }
         }
+    };
+    // the next row tile's C is loaded while this one is updated
+    float acc[4][8], nxt[4][8];
+    int rb = rlo + ty * 4;
+    if (rb < rhi) load(rb, acc);
+    for (int r0 = rlo; r0 < rhi; r0 += 128, rb += 128) {
+        if (rb >= rhi) break;
+        if (rb + 128 < rhi) load(rb + 128, nxt);
         const bool full = rb + 3 < rhi;
 #pragma unroll 4
         for (int k = 0; k < PB; ++k) {
@@ -157,6 +163,10 @@ __device__ __forceinline__ void lu_update_strip(float *M, int ld, int rlo, int r
                     *reinterpret_cast<float4 *>(M + (size_t)r * ld + cb[h]) =
                         make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = nxt[i][j];
     }
 }
 
@@ -476,22 +486,26 @@ __device__ bool zsweep_invert(float2 *Z, int ldz, int m, float2 *smem)
             }
             __syncthreads();
             const int cb[2] = {c0 + 2 * tx, c0 + 32 + 2 * tx};
-            for (int r0 = 0; r0 < m && r0 <= c0 + UWC - 1; r0 += 128) {
-                const int rb = r0 + ty * 4;
-                if (rb >= m) continue;
-                float2 acc[4][4];
+            const int r_end = min(m, c0 + UWC);   // row tiles starting past this are below the diagonal
+            auto zload = [&](int rb, float2 (&v)[4][4]) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const int r = rb + i;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (r < m && cb[h] < ldz)
-                            v = *reinterpret_cast<const float4 *>(Z + (size_t)r * ldz + cb[h]);
-                        acc[i][2 * h] = make_float2(v.x, v.y);
-                        acc[i][2 * h + 1] = make_float2(v.z, v.w);
+                        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (r < m && cb[h] < ldz) q = *reinterpret_cast<const float4 *>(Z + (size_t)r * ldz + cb[h]);
+                        v[i][2 * h] = make_float2(q.x, q.y);
+                        v[i][2 * h + 1] = make_float2(q.z, q.w);
                     }
                 }
+            };
+            float2 acc[4][4], nxt[4][4];
+            int rb = ty * 4;
+            if (rb < m) zload(rb, acc);
+            for (int r0 = 0; r0 < r_end; r0 += 128, rb += 128) {
+                if (rb >= m) break;
+                if (r0 + 128 < r_end && rb + 128 < m) zload(rb + 128, nxt);
 #pragma unroll 4
                 for (int k = 0; k < PB; ++k) {
                     float2 a[4], b[4];
@@ -523,6 +537,10 @@ __device__ bool zsweep_invert(float2 *Z, int ldz, int m, float2 *smem)
                                 make_float4(acc[i][2 * h].x, acc[i][2 * h].y, acc[i][2 * h + 1].x,
                                             acc[i][2 * h + 1].y);
                 }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = nxt[i][j];
             }
             __syncthreads();
         }

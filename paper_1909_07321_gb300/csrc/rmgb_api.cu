@@ -83,6 +83,14 @@ struct PwHost {
     int prop_lmax = -1, prop_steps = 0;
     double prop_r1 = 0.0;
     double a_match() const { return prop_lmax >= 0 ? prop_r1 : a; }
+    size_t bytes() const
+    {
+        size_t b = 0;
+        for (const DevBuf *d : {&Ek, &Ek_hl, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl,
+                                &W32, &Wh, &Wl, &thr, &otab, &otab_bad, &ctab, &ctab_nsub, &propA})
+            b += d->bytes;
+        return b;
+    }
     void release()
     {
         for (DevBuf *d : {&Ek, &Ek_hl, &W, &e_thr, &l, &level, &lev_start, &lev_chan, &lev_thr, &Ph, &Pl, &W32,
@@ -143,11 +151,16 @@ struct PwHost {
 
 }  // namespace
 
-struct rm_ctx {
-    rm_opts opts;
+namespace {
+
+// One lane: a stream of work with its own workspace and Omega accumulator.
+// The lanes of a context share its partial waves (poles, channels, tables and
+// the low-precision operands), so work on several lanes overlaps on the
+// device without loading a pole set twice. Lane 0 serves the calls without a
+// lane argument.
+struct Lane {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    std::vector<PwHost> pw;
     // grid and Omega accumulator
     int grid_nE = 0, grid_nlev = 0, grid_ntri = 0;
     std::vector<double> grid_host;
@@ -164,9 +177,34 @@ struct rm_ctx {
     DevBuf wsE, wsCf, wsR, wsStatus, wsMq, wsDh, wsDl, wsErr, wsL, wsPart, wsDeep, wsNear, wsEhl;
     // coarse-mesh interpolation: node energies, statuses + orders, K_u, S_u, fine plan
     DevBuf wsQn, wsQst, wsQk, wsQs, wsQf, wsQc;
-    // side stream for the deep channel pairs, with fork / join events
+    // side stream for the deep channel pairs / the formation chain, with fork / join events
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_done = nullptr;   // after the lane's last enqueued work (rm_lane_query)
+    size_t ws_bytes() const
+    {
+        size_t b = 0;
+        for (const DevBuf *d : {&wsE, &wsCf, &wsR, &wsStatus, &wsMq, &wsDh, &wsDl, &wsErr, &wsL, &wsPart, &wsDeep,
+                                &wsNear, &wsEhl, &wsQn, &wsQst, &wsQk, &wsQs, &wsQf, &wsQc})
+            b += d->bytes;
+        return b;
+    }
+    void release()
+    {
+        for (DevBuf *d : {&omega, &omega_alt, &wsE, &wsCf, &wsR, &wsStatus, &wsMq, &wsDh, &wsDl, &wsErr, &wsL,
+                          &wsPart, &wsDeep, &wsNear, &wsEhl, &wsQn, &wsQst, &wsQk, &wsQs, &wsQf, &wsQc})
+            d->release();
+    }
+};
+
+constexpr int MAX_LANES = 64;
+
+}  // namespace
+
+struct rm_ctx {
+    rm_opts opts;
+    std::vector<PwHost> pw;
+    std::vector<Lane> lanes;
     long long launches = 0;
     // per-phase event pairs (tracing)
     bool prof = false;
@@ -248,7 +286,7 @@ cudaError_t prof_begin(rm_ctx *ctx, int phase, cudaStream_t st = nullptr)
         if (e != cudaSuccess) return e;
         v.push_back({a, b});
     }
-    return cudaEventRecord(v[u].first, st ? st : ctx->stream);
+    return cudaEventRecord(v[u].first, st ? st : ctx->lanes[0].stream);
 }
 
 cudaError_t prof_end(rm_ctx *ctx, int phase, cudaStream_t st = nullptr)
@@ -256,7 +294,7 @@ cudaError_t prof_end(rm_ctx *ctx, int phase, cudaStream_t st = nullptr)
     if (!ctx->prof) return cudaSuccess;
     auto &v = ctx->ev[phase];
     size_t &u = ctx->ev_used[phase];
-    cudaError_t e = cudaEventRecord(v[u].second, st ? st : ctx->stream);
+    cudaError_t e = cudaEventRecord(v[u].second, st ? st : ctx->lanes[0].stream);
     ++u;
     return e;
 }
@@ -321,27 +359,32 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
         if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr / 2 < o.mem_budget) o.mem_budget = fr / 2;
         cudaGetLastError();
     }
+    if (o.lanes == 0) o.lanes = 1;
+    if (o.lanes < 1 || o.lanes > MAX_LANES) return RM_EINVAL;
     rm_ctx *ctx = new (std::nothrow) rm_ctx();
     if (!ctx) return RM_ENOMEM;
     ctx->opts = o;
-    if (o.stream) {
-        ctx->stream = static_cast<cudaStream_t>(o.stream);
-    } else {
-        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            delete ctx;
-            return RM_ECUDA;
-        }
-        ctx->own_stream = true;
-    }
+    ctx->lanes.resize(o.lanes);
     int lo_prio = 0, hi_prio = 0;
     cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
-    if (cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, hi_prio) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        rm_destroy(ctx);
-        return RM_ECUDA;
+    for (int i = 0; i < o.lanes; ++i) {
+        Lane *ln = &ctx->lanes[i];
+        bool ok = true;
+        if (i == 0 && o.stream) {
+            ln->stream = static_cast<cudaStream_t>(o.stream);
+        } else {
+            ok = cudaStreamCreateWithFlags(&ln->stream, cudaStreamNonBlocking) == cudaSuccess;
+            ln->own_stream = ok;
+        }
+        ok = ok && cudaStreamCreateWithPriority(&ln->side, cudaStreamNonBlocking, hi_prio) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ln->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ln->ev_join, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ln->ev_done, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            rm_destroy(ctx);
+            return RM_ECUDA;
+        }
     }
     *out = ctx;
     return RM_SUCCESS;
@@ -351,31 +394,30 @@ extern "C" void rm_destroy(rm_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->opts.device);
-    cudaStreamSynchronize(ctx->stream);
-    for (auto &p : ctx->pw) p.release();
-    if (ctx->copy) {
-        cudaStreamSynchronize(ctx->copy);
-        cudaStreamDestroy(ctx->copy);
+    for (Lane &l : ctx->lanes) {
+        if (l.stream) cudaStreamSynchronize(l.stream);
+        if (l.side) cudaStreamSynchronize(l.side);
+        if (l.copy) cudaStreamSynchronize(l.copy);
     }
-    if (ctx->ev_solved) cudaEventDestroy(ctx->ev_solved);
-    for (cudaEvent_t ev : ctx->ev_copied)
-        if (ev) cudaEventDestroy(ev);
-    for (DevBuf *d : {&ctx->omega, &ctx->omega_alt, &ctx->wsE, &ctx->wsCf, &ctx->wsR, &ctx->wsStatus, &ctx->wsMq,
-                      &ctx->wsDh, &ctx->wsDl, &ctx->wsErr, &ctx->wsL, &ctx->wsPart, &ctx->wsDeep, &ctx->wsNear, &ctx->wsEhl, &ctx->wsQn,
-                      &ctx->wsQst, &ctx->wsQk, &ctx->wsQs, &ctx->wsQf, &ctx->wsQc})
-        d->release();
+    for (auto &p : ctx->pw) p.release();
+    for (Lane &l : ctx->lanes) {
+        Lane *ln = &l;
+        if (ln->copy) cudaStreamDestroy(ln->copy);
+        if (ln->ev_solved) cudaEventDestroy(ln->ev_solved);
+        for (cudaEvent_t ev : ln->ev_copied)
+            if (ev) cudaEventDestroy(ev);
+        ln->release();
+        if (ln->side) cudaStreamDestroy(ln->side);
+        if (ln->ev_fork) cudaEventDestroy(ln->ev_fork);
+        if (ln->ev_join) cudaEventDestroy(ln->ev_join);
+        if (ln->ev_done) cudaEventDestroy(ln->ev_done);
+        if (ln->own_stream) cudaStreamDestroy(ln->stream);
+    }
     for (int p = 0; p < RM_PH_COUNT; ++p)
         for (auto &pr : ctx->ev[p]) {
             cudaEventDestroy(pr.first);
             cudaEventDestroy(pr.second);
         }
-    if (ctx->side) {
-        cudaStreamSynchronize(ctx->side);
-        cudaStreamDestroy(ctx->side);
-    }
-    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
 
@@ -385,6 +427,7 @@ namespace {
 // launch, then the validity of every table is read back (once per wave).
 int build_thr(rm_ctx *ctx, PwHost &P)
 {
+    Lane *ln = &ctx->lanes[0];
     P.thr.release();
     P.otab.release();
     P.otab_bad.release();
@@ -404,7 +447,7 @@ int build_thr(rm_ctx *ctx, PwHost &P)
         PwDev d = P.dev_match();
         d.otab_dk = dk;
         d.otab_nseg = nseg;
-        CK(launch_open_table(d, P.otab.as<double>(), P.otab_bad.as<int>(), ctx->stream));
+        CK(launch_open_table(d, P.otab.as<double>(), P.otab_bad.as<int>(), ln->stream));
         ++ctx->launches;
         P.otab_dk = dk;
         P.otab_nseg = nseg;
@@ -426,18 +469,18 @@ int build_thr(rm_ctx *ctx, PwHost &P)
             d.ctab_nu_lo = nu_lo;
             d.ctab_dnu = CTAB_DNU;
             d.ctab_nseg = nseg;
-            CK(launch_closed_table(d, P.ctab.as<double>(), P.ctab_nsub.as<unsigned char>(), ctx->stream));
+            CK(launch_closed_table(d, P.ctab.as<double>(), P.ctab_nsub.as<unsigned char>(), ln->stream));
             ++ctx->launches;
             P.ctab_nu_lo = nu_lo;
             P.ctab_nseg = nseg;
         }
     }
     CK(P.thr.reserve(sizeof(ThrNodes) * (size_t)P.n));
-    CK(launch_thr_nodes(P.dev_match(), P.thr.as<ThrNodes>(), ctx->stream));
+    CK(launch_thr_nodes(P.dev_match(), P.thr.as<ThrNodes>(), ln->stream));
     ++ctx->launches;
     std::vector<ThrNodes> h(P.n);
-    CK(cudaMemcpyAsync(h.data(), P.thr.p, sizeof(ThrNodes) * (size_t)P.n, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(h.data(), P.thr.p, sizeof(ThrNodes) * (size_t)P.n, cudaMemcpyDeviceToHost, ln->stream));
+    CK(cudaStreamSynchronize(ln->stream));
     bool all = true;
     for (int i = 0; i < P.n; ++i) all = all && h[i].zone >= chanfn_deep_eps(P.z);
     P.use_deep = !all;
@@ -459,6 +502,7 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
     if (!finite_all(E_k, n_poles) || !finite_all(W, (size_t)n_ch * n_poles))
         return fail(ctx, RM_EINVAL, "non-finite pole energy or amplitude");
     CK(cudaSetDevice(ctx->opts.device));
+    Lane *ln = &ctx->lanes[0];
     if ((int)ctx->pw.size() <= pw) ctx->pw.resize(pw + 1);
     PwHost &P = ctx->pw[pw];
     const bool same_n = P.loaded && P.n == n_ch;
@@ -479,7 +523,7 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
     P.Wh.release();
     P.Wl.release();
     P.w_kind = -1;
-    CK(upload(P.Ek, Es.data(), Es.size(), ctx->stream));
+    CK(upload(P.Ek, Es.data(), Es.size(), ln->stream));
     {
         std::vector<float2> hl(n_poles);
         for (int k = 0; k < n_poles; ++k) {
@@ -487,10 +531,10 @@ extern "C" int rm_load_poles(rm_ctx *ctx, int pw, int n_ch, int n_poles, const d
             hl[k] = make_float2(h, (float)(Es[k] - (double)h));
         }
         P.Ek_hl.release();
-        CK(upload(P.Ek_hl, hl.data(), hl.size(), ctx->stream));
+        CK(upload(P.Ek_hl, hl.data(), hl.size(), ln->stream));
     }
     P.h_Ek = Es;
-    CK(upload(P.W, Ws.data(), Ws.size(), ctx->stream));
+    CK(upload(P.W, Ws.data(), Ws.size(), ln->stream));
     P.n = n_ch;
     P.N = n_poles;
     P.a = a;
@@ -530,12 +574,13 @@ extern "C" int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const i
     for (int I = 0; I < n_levels; ++I) start[I + 1] = start[I] + cnt[I];
     for (int i = 0; i < n; ++i) chan[start[level[i]] + fill[level[i]]++] = i;
     CK(cudaSetDevice(ctx->opts.device));
-    CK(upload(P.e_thr, e_thr, n, ctx->stream));
-    CK(upload(P.l, l, n, ctx->stream));
-    CK(upload(P.level, level, n, ctx->stream));
-    CK(upload(P.lev_start, start.data(), start.size(), ctx->stream));
-    CK(upload(P.lev_chan, chan.data(), chan.size(), ctx->stream));
-    CK(upload(P.lev_thr, lev_thr.data(), lev_thr.size(), ctx->stream));
+    Lane *ln = &ctx->lanes[0];
+    CK(upload(P.e_thr, e_thr, n, ln->stream));
+    CK(upload(P.l, l, n, ln->stream));
+    CK(upload(P.level, level, n, ln->stream));
+    CK(upload(P.lev_start, start.data(), start.size(), ln->stream));
+    CK(upload(P.lev_chan, chan.data(), chan.size(), ln->stream));
+    CK(upload(P.lev_thr, lev_thr.data(), lev_thr.size(), ln->stream));
     P.h_e_thr.assign(e_thr, e_thr + n);
     P.h_l.assign(l, l + n);
     P.z = z;
@@ -572,7 +617,8 @@ extern "C" int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const doub
                 if (A[((size_t)lam * n + i) * n + j] != A[((size_t)lam * n + j) * n + i])
                     return fail(ctx, RM_EINVAL, "A[%d] not symmetric at (%d,%d)", lam + 1, i, j);
     CK(cudaSetDevice(ctx->opts.device));
-    CK(upload(P.propA, A, cnt, ctx->stream));
+    Lane *ln = &ctx->lanes[0];
+    CK(upload(P.propA, A, cnt, ln->stream));
     P.prop_lmax = lambda_max;
     P.prop_r1 = r1;
     P.prop_steps = n_steps;
@@ -582,17 +628,17 @@ extern "C" int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const doub
 namespace {
 
 // Energies as a device pointer on the context stream (copies host input).
-int device_energies(rm_ctx *ctx, int n_E, const double *E, const double **dE)
+int device_energies(rm_ctx *ctx, Lane *ln, int n_E, const double *E, const double **dE)
 {
     if (is_device_ptr(E)) {
         *dE = E;
         return RM_SUCCESS;
     }
     if (!finite_all(E, n_E)) return fail(ctx, RM_EINVAL, "non-finite energy");
-    CK(ctx->wsE.reserve((size_t)n_E * sizeof(double)));
-    CK(cudaMemcpyAsync(ctx->wsE.p, E, (size_t)n_E * sizeof(double), cudaMemcpyHostToDevice,
-                       ctx->stream));
-    *dE = ctx->wsE.as<double>();
+    CK(ln->wsE.reserve((size_t)n_E * sizeof(double)));
+    CK(cudaMemcpyAsync(ln->wsE.p, E, (size_t)n_E * sizeof(double), cudaMemcpyHostToDevice,
+                       ln->stream));
+    *dE = ln->wsE.as<double>();
     return RM_SUCCESS;
 }
 
@@ -663,9 +709,9 @@ int block_energies(rm_ctx *ctx, const PwHost &P)
 }
 
 // Packed R of nE energies into R (stride tri_ld(n)), in the context's precision.
-int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R, cudaStream_t st = nullptr)
+int form_r_block(rm_ctx *ctx, Lane *ln, PwHost &P, const double *E, int nE, double *R, cudaStream_t st = nullptr)
 {
-    if (!st) st = ctx->stream;
+    if (!st) st = ln->stream;
     const PwDev d = P.dev();
     if (ctx->opts.precision == RM_FP64) {
         CK(prof_begin(ctx, RM_PH_FORM, st));
@@ -677,9 +723,9 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R, cud
     const int kind = tc_kind(ctx->opts.precision);
     const int Kpad = tc_kpad(P.N, kind);
     const size_t es = tc_esize(kind);
-    if (!ctx->wsErr.p) {
-        CK(ctx->wsErr.reserve(sizeof(int)));
-        CK(cudaMemsetAsync(ctx->wsErr.p, 0, sizeof(int), st));
+    if (!ln->wsErr.p) {
+        CK(ln->wsErr.reserve(sizeof(int)));
+        CK(cudaMemsetAsync(ln->wsErr.p, 0, sizeof(int), st));
     }
     if (formulation(ctx, P) == RM_FORM_ENERGY) {
         if (P.w_kind != kind) {
@@ -689,20 +735,22 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R, cud
             CK(P.Wl.reserve(nk * es));
             CK(launch_pe_prep_w(d, kind, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, st));
             ctx->launches++;
+            // complete before any lane uses the shared operand
+            CK(cudaStreamSynchronize(st));
             P.w_kind = kind;
         }
-        CK(ctx->wsDh.reserve((size_t)nE * Kpad * sizeof(float) + (size_t)nE * sizeof(int2)));
-        CK(ctx->wsPart.reserve(pe_bytes_per_energy(P.n, P.N, kind) * (size_t)nE));
+        CK(ln->wsDh.reserve((size_t)nE * Kpad * sizeof(float) + (size_t)nE * sizeof(int2)));
+        CK(ln->wsPart.reserve(pe_bytes_per_energy(P.n, P.N, kind) * (size_t)nE));
         CK(prof_begin(ctx, RM_PH_SPLIT, st));
-        CK(launch_pe_d32(d, E, nE, ctx->opts.delta_pole, Kpad, ctx->wsDh.as<float>(), st));
+        CK(launch_pe_d32(d, E, nE, ctx->opts.delta_pole, Kpad, ln->wsDh.as<float>(), st));
         CK(prof_end(ctx, RM_PH_SPLIT, st));
         CK(prof_begin(ctx, RM_PH_FORM, st));
-        CK(launch_form_r_pe(kind, P.n, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ctx->wsDh.as<float>(), nE,
-                            ctx->wsPart.as<float>(), ctx->wsErr.as<int>(), st));
+        CK(launch_form_r_pe(kind, P.n, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ln->wsDh.as<float>(), nE,
+                            ln->wsPart.as<float>(), ln->wsErr.as<int>(), st));
         CK(prof_end(ctx, RM_PH_FORM, st));
         CK(prof_begin(ctx, RM_PH_FIXUP, st));
-        CK(launch_pe_reduce(d, kind, Kpad, E, nE, ctx->opts.delta_pole, ctx->wsDh.as<float>(),
-                            ctx->wsPart.as<float>(), R,
+        CK(launch_pe_reduce(d, kind, Kpad, E, nE, ctx->opts.delta_pole, ln->wsDh.as<float>(),
+                            ln->wsPart.as<float>(), R,
                             tri_ld(P.n), st));
         CK(prof_end(ctx, RM_PH_FIXUP, st));
         ctx->launches += 3;
@@ -714,23 +762,25 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R, cud
         CK(P.Pl.reserve(pb));
         CK(launch_split_p(d, kind, Kpad, P.Ph.p, P.Pl.p, st));
         ctx->launches++;
+        // complete before any lane uses the shared operand
+        CK(cudaStreamSynchronize(st));
         P.p_kind = kind;
         P.p_kpad = Kpad;
     }
-    CK(ctx->wsDh.reserve((size_t)nE * Kpad * es));
-    CK(ctx->wsDl.reserve((size_t)nE * Kpad * es));
+    CK(ln->wsDh.reserve((size_t)nE * Kpad * es));
+    CK(ln->wsDl.reserve((size_t)nE * Kpad * es));
     CK(prof_begin(ctx, RM_PH_SPLIT, st));
-    CK(ctx->wsEhl.reserve((size_t)nE * sizeof(float2)));
-    CK(launch_split_d(d, E, nE, ctx->opts.delta_pole, kind, Kpad, ctx->wsDh.p, ctx->wsDl.p, ctx->wsEhl.as<float2>(),
+    CK(ln->wsEhl.reserve((size_t)nE * sizeof(float2)));
+    CK(launch_split_d(d, E, nE, ctx->opts.delta_pole, kind, Kpad, ln->wsDh.p, ln->wsDl.p, ln->wsEhl.as<float2>(),
                       st));
     CK(prof_end(ctx, RM_PH_SPLIT, st));
     CK(prof_begin(ctx, RM_PH_FORM, st));
-    CK(launch_form_r_tc(kind, ctx->wsDh.p, ctx->wsDl.p, P.Ph.p, P.Pl.p, nE, tri_count(P.n), Kpad, R,
-                        tri_ld(P.n), ctx->wsErr.as<int>(), st));
+    CK(launch_form_r_tc(kind, ln->wsDh.p, ln->wsDl.p, P.Ph.p, P.Pl.p, nE, tri_count(P.n), Kpad, R,
+                        tri_ld(P.n), ln->wsErr.as<int>(), st));
     CK(prof_end(ctx, RM_PH_FORM, st));
     CK(prof_begin(ctx, RM_PH_FIXUP, st));
-    CK(ctx->wsNear.reserve(near_pole_ws_bytes(nE)));
-    CK(launch_near_pole_fixup(d, E, nE, ctx->opts.delta_pole, R, ctx->wsNear.p, st));
+    CK(ln->wsNear.reserve(near_pole_ws_bytes(nE)));
+    CK(launch_near_pole_fixup(d, E, nE, ctx->opts.delta_pole, R, ln->wsNear.p, st));
     CK(prof_end(ctx, RM_PH_FIXUP, st));
     ctx->launches += 5;
     return RM_SUCCESS;
@@ -738,15 +788,70 @@ int form_r_block(rm_ctx *ctx, PwHost &P, const double *E, int nE, double *R, cud
 
 // After a synchronisation: a tensor-core kernel that gave up a bounded wait
 // left its flag set.
-int check_device_flag(rm_ctx *ctx)
+int check_device_flag(rm_ctx *ctx, Lane *ln)
 {
-    if (!ctx->wsErr.p) return RM_SUCCESS;
+    if (!ln->wsErr.p) return RM_SUCCESS;
     int f = 0;
-    CK(cudaMemcpy(&f, ctx->wsErr.p, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&f, ln->wsErr.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (f) {
-        CK(cudaMemset(ctx->wsErr.p, 0, sizeof(int)));
+        CK(cudaMemset(ln->wsErr.p, 0, sizeof(int)));
         return fail(ctx, RM_ETIMEOUT, "a tensor-core formation kernel gave up a bounded wait");
     }
+    return RM_SUCCESS;
+}
+
+// Everything a solve of n_E energies of P on lane ln reserves (the
+// reservations of solve_on_lane, solve_blocks and form_r_block, in the same
+// sizes), and the shared tensor-core operands, without launching the solve.
+int reserve_solve(rm_ctx *ctx, Lane *ln, PwHost &P, int n_E)
+{
+    const bool large = use_large(ctx, P);
+    const int ntri = P.n_levels * (P.n_levels + 1) / 2;
+    const int B = std::min(n_E, block_energies(ctx, P));
+    CK(ln->omega.reserve((size_t)n_E * ntri * sizeof(double)));
+    CK(ln->wsE.reserve((size_t)n_E * sizeof(double)));
+    CK(ln->wsStatus.reserve((size_t)n_E * sizeof(int)));
+    CK(ln->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
+    CK(ln->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
+    if (large) CK(ln->wsL.reserve(solve_large_bytes_per_energy(P.n) * (size_t)B + 256));
+    if (!large && P.use_deep) CK(ln->wsDeep.reserve(chanfn_deep_ws_bytes(B)));
+    if (ctx->opts.precision == RM_FP64) return RM_SUCCESS;
+    const int kind = tc_kind(ctx->opts.precision);
+    const int Kpad = tc_kpad(P.N, kind);
+    const size_t es = tc_esize(kind);
+    if (!ln->wsErr.p) {
+        CK(ln->wsErr.reserve(sizeof(int)));
+        CK(cudaMemsetAsync(ln->wsErr.p, 0, sizeof(int), ln->stream));
+    }
+    const PwDev d = P.dev();
+    if (formulation(ctx, P) == RM_FORM_ENERGY) {
+        if (P.w_kind != kind) {
+            const size_t nk = (size_t)P.n * Kpad;
+            CK(P.W32.reserve(nk * sizeof(float)));
+            CK(P.Wh.reserve(nk * es));
+            CK(P.Wl.reserve(nk * es));
+            CK(launch_pe_prep_w(d, kind, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ln->stream));
+            ctx->launches++;
+            P.w_kind = kind;
+        }
+        CK(ln->wsDh.reserve((size_t)B * Kpad * sizeof(float) + (size_t)B * sizeof(int2)));
+        CK(ln->wsPart.reserve(pe_bytes_per_energy(P.n, P.N, kind) * (size_t)B));
+    } else {
+        if (P.p_kind != kind) {
+            const size_t pb = (size_t)tri_count(P.n) * Kpad * es;
+            CK(P.Ph.reserve(pb));
+            CK(P.Pl.reserve(pb));
+            CK(launch_split_p(d, kind, Kpad, P.Ph.p, P.Pl.p, ln->stream));
+            ctx->launches++;
+            P.p_kind = kind;
+            P.p_kpad = Kpad;
+        }
+        CK(ln->wsDh.reserve((size_t)B * Kpad * es));
+        CK(ln->wsDl.reserve((size_t)B * Kpad * es));
+        CK(ln->wsEhl.reserve((size_t)B * sizeof(float2)));
+        CK(ln->wsNear.reserve(near_pole_ws_bytes(B)));
+    }
+    CK(cudaStreamSynchronize(ln->stream));
     return RM_SUCCESS;
 }
 
@@ -756,23 +861,23 @@ namespace {
 
 // Registers the energy grid of the Omega accumulator (first call) or checks
 // that this call uses the registered one.
-int register_grid(rm_ctx *ctx, const PwHost &P, int n_E, const double *E, bool dev_in)
+int register_grid(rm_ctx *ctx, Lane *ln, const PwHost &P, int n_E, const double *E, bool dev_in)
 {
     const int ntri = P.n_levels * (P.n_levels + 1) / 2;
-    if (ctx->grid_nE == 0) {
-        CK(ctx->omega.reserve((size_t)n_E * ntri * sizeof(double)));
-        CK(cudaMemsetAsync(ctx->omega.p, 0, (size_t)n_E * ntri * sizeof(double), ctx->stream));
-        ctx->grid_nE = n_E;
-        ctx->grid_nlev = P.n_levels;
-        ctx->grid_ntri = ntri;
-        ctx->grid_host.clear();
-        if (!dev_in) ctx->grid_host.assign(E, E + n_E);
+    if (ln->grid_nE == 0) {
+        CK(ln->omega.reserve((size_t)n_E * ntri * sizeof(double)));
+        CK(cudaMemsetAsync(ln->omega.p, 0, (size_t)n_E * ntri * sizeof(double), ln->stream));
+        ln->grid_nE = n_E;
+        ln->grid_nlev = P.n_levels;
+        ln->grid_ntri = ntri;
+        ln->grid_host.clear();
+        if (!dev_in) ln->grid_host.assign(E, E + n_E);
     } else {
-        if (n_E != ctx->grid_nE || P.n_levels != ctx->grid_nlev)
+        if (n_E != ln->grid_nE || P.n_levels != ln->grid_nlev)
             return fail(ctx, RM_EGRID, "grid (%d energies, %d levels) differs from registered (%d, %d)",
-                        n_E, P.n_levels, ctx->grid_nE, ctx->grid_nlev);
-        if (!dev_in && !ctx->grid_host.empty() &&
-            memcmp(E, ctx->grid_host.data(), (size_t)n_E * sizeof(double)) != 0)
+                        n_E, P.n_levels, ln->grid_nE, ln->grid_nlev);
+        if (!dev_in && !ln->grid_host.empty() &&
+            memcmp(E, ln->grid_host.data(), (size_t)n_E * sizeof(double)) != 0)
             return fail(ctx, RM_EGRID, "energies differ from the registered grid");
     }
     return RM_SUCCESS;
@@ -781,37 +886,37 @@ int register_grid(rm_ctx *ctx, const PwHost &P, int n_E, const double *E, bool d
 // Steps (b)-(d) for n_E device energies dE, block by block; dstatus must be
 // zeroed. omega: Omega rows of these energies (nullptr: no accumulation).
 // ku_out / ku_np (shared-memory solver, MQDT mode): K_u instead of K, T, Omega.
-int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, double *K_out, int *n_open_out,
+int solve_blocks(rm_ctx *ctx, Lane *ln, PwHost &P, const double *dE, int n_E, int mode, double *K_out, int *n_open_out,
                  int *dstatus, double *omega, double *ku_out = nullptr, int *ku_np = nullptr)
 {
     const bool large = use_large(ctx, P);
     const int ntri = P.n_levels * (P.n_levels + 1) / 2;
     const int B = std::min(n_E, block_energies(ctx, P));
-    CK(ctx->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
-    CK(ctx->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
-    if (large) CK(ctx->wsL.reserve(solve_large_bytes_per_energy(P.n) * (size_t)B + 256));
+    CK(ln->wsCf.reserve((size_t)B * P.n * sizeof(ChanFn)));
+    CK(ln->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
+    if (large) CK(ln->wsL.reserve(solve_large_bytes_per_energy(P.n) * (size_t)B + 256));
     const PwDev d = P.dev_match();
     const Opts o = make_opts(ctx->opts);
     for (int e0 = 0; e0 < n_E; e0 += B) {
         const int nb = std::min(B, n_E - e0);
         const double *Eb = dE + e0;
         int *sb = dstatus + e0;
-        CK(prof_begin(ctx, RM_PH_NEARPOLE));
-        CK(launch_nearpole(d, Eb, nb, sb, ctx->stream));
-        CK(prof_end(ctx, RM_PH_NEARPOLE));
+        CK(prof_begin(ctx, RM_PH_NEARPOLE, ln->stream));
+        CK(launch_nearpole(d, Eb, nb, sb, ln->stream));
+        CK(prof_end(ctx, RM_PH_NEARPOLE, ln->stream));
         // Deep (near-threshold) channel pairs go to the side stream, and the
         // energies holding them are solved after it joins (shared-memory
         // solver only).
         const bool split = !large && P.use_deep;
         int *deep = nullptr;
         if (split) {
-            CK(ctx->wsDeep.reserve(chanfn_deep_ws_bytes(B)));
-            deep = ctx->wsDeep.as<int>();
-            CK(launch_chanfn_deep_mark(d, Eb, nb, o, deep, ctx->stream));
-            CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
-            CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-            CK(launch_chanfn_deep(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, deep, ctx->side));
-            CK(cudaEventRecord(ctx->ev_join, ctx->side));
+            CK(ln->wsDeep.reserve(chanfn_deep_ws_bytes(B)));
+            deep = ln->wsDeep.as<int>();
+            CK(launch_chanfn_deep_mark(d, Eb, nb, o, deep, ln->stream));
+            CK(cudaEventRecord(ln->ev_fork, ln->stream));
+            CK(cudaStreamWaitEvent(ln->side, ln->ev_fork, 0));
+            CK(launch_chanfn_deep(d, Eb, nb, o, mode == RM_MQDT, ln->wsCf.as<ChanFn>(), sb, deep, ln->side));
+            CK(cudaEventRecord(ln->ev_join, ln->side));
             ctx->launches += 2;
         }
         // With no deep pairs to wait for, the formation of R (tensor pipe,
@@ -821,68 +926,82 @@ int solve_blocks(rm_ctx *ctx, PwHost &P, const double *dE, int n_E, int mode, do
         // SMs; the solve joins both.
         const bool beside = !P.use_deep;
         if (beside) {
-            CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
-            CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
-            int rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>(), ctx->side);
+            CK(cudaEventRecord(ln->ev_fork, ln->stream));
+            CK(cudaStreamWaitEvent(ln->side, ln->ev_fork, 0));
+            int rc = form_r_block(ctx, ln, P, Eb, nb, ln->wsR.as<double>(), ln->side);
             if (rc) return rc;
-            CK(cudaEventRecord(ctx->ev_join, ctx->side));
+            CK(cudaEventRecord(ln->ev_join, ln->side));
         }
-        CK(prof_begin(ctx, RM_PH_CHANFN));
-        CK(launch_chanfn(d, Eb, nb, o, mode == RM_MQDT, ctx->wsCf.as<ChanFn>(), sb, deep, ctx->stream));
-        CK(prof_end(ctx, RM_PH_CHANFN));
+        CK(prof_begin(ctx, RM_PH_CHANFN, ln->stream));
+        CK(launch_chanfn(d, Eb, nb, o, mode == RM_MQDT, ln->wsCf.as<ChanFn>(), sb, deep, ln->stream));
+        CK(prof_end(ctx, RM_PH_CHANFN, ln->stream));
         ctx->launches += 2;
         if (beside) {
-            CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+            CK(cudaStreamWaitEvent(ln->stream, ln->ev_join, 0));
         } else {
-            int rc = form_r_block(ctx, P, Eb, nb, ctx->wsR.as<double>());
+            int rc = form_r_block(ctx, ln, P, Eb, nb, ln->wsR.as<double>());
             if (rc) return rc;
         }
         if (P.prop_lmax >= 0) {
             // R(a) -> R(r1) once every status of the block is final (the
             // deep pairs' too), so a singular propagation never masks an
             // earlier error
-            if (split) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-            CK(prof_begin(ctx, RM_PH_PROPAGATE));
+            if (split) CK(cudaStreamWaitEvent(ln->stream, ln->ev_join, 0));
+            CK(prof_begin(ctx, RM_PH_PROPAGATE, ln->stream));
             CK(launch_propagate(P.dev(), Eb, nb, P.propA.as<double>(), P.prop_lmax, P.prop_r1, P.prop_steps,
-                                ctx->wsR.as<double>(), sb, ctx->stream));
-            CK(prof_end(ctx, RM_PH_PROPAGATE));
+                                ln->wsR.as<double>(), sb, ln->stream));
+            CK(prof_end(ctx, RM_PH_PROPAGATE, ln->stream));
             ++ctx->launches;
         }
-        CK(prof_begin(ctx, RM_PH_SOLVE));
+        CK(prof_begin(ctx, RM_PH_SOLVE, ln->stream));
         double *Kb = K_out ? K_out + (size_t)e0 * P.n * P.n : nullptr;
         int *nob = n_open_out ? n_open_out + e0 : nullptr;
         double *omb = omega ? omega + (size_t)e0 * ntri : nullptr;
         if (large) {
             int L = 0;
             const int f32 = ctx->opts.solve_precision == RM_FP32 && !ku_out && solve_large_f32_supported(P.n);
-            CK(launch_solve_large(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, ctx->wsL.p, &L, ctx->stream, f32));
+            CK(launch_solve_large(d, Eb, nb, ln->wsCf.as<ChanFn>(), ln->wsR.as<double>(), sb, Kb, nob,
+                                  omb, ntri, ln->wsL.p, &L, ln->stream, f32));
             ctx->launches += L;
         } else {
             const int f32 = mode == RM_DIRECT && ctx->opts.solve_precision == RM_FP32 && !ku_out;
             double *kub = ku_out ? ku_out + (size_t)e0 * P.n * P.n : nullptr;
             int *kunb = ku_np ? ku_np + e0 : nullptr;
-            CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                  omb, ntri, mode == RM_MQDT, f32, deep, 0, ctx->stream, kub, kunb));
+            CK(launch_solve_small(d, Eb, nb, ln->wsCf.as<ChanFn>(), ln->wsR.as<double>(), sb, Kb, nob,
+                                  omb, ntri, mode == RM_MQDT, f32, deep, 0, ln->stream, kub, kunb));
             ++ctx->launches;
             if (split) {
-                CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-                CK(launch_solve_small(d, Eb, nb, ctx->wsCf.as<ChanFn>(), ctx->wsR.as<double>(), sb, Kb, nob,
-                                      omb, ntri, mode == RM_MQDT, f32, deep, 1, ctx->stream, kub, kunb));
+                CK(cudaStreamWaitEvent(ln->stream, ln->ev_join, 0));
+                CK(launch_solve_small(d, Eb, nb, ln->wsCf.as<ChanFn>(), ln->wsR.as<double>(), sb, Kb, nob,
+                                      omb, ntri, mode == RM_MQDT, f32, deep, 1, ln->stream, kub, kunb));
                 ++ctx->launches;
             }
         }
-        CK(prof_end(ctx, RM_PH_SOLVE));
+        CK(prof_end(ctx, RM_PH_SOLVE, ln->stream));
     }
     return RM_SUCCESS;
 }
 
 }  // namespace
 
-extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
-                                 double *K_out, int *n_open_out, int *status_out)
+namespace {
+
+int lane_of(rm_ctx *ctx, int lane, Lane **ln)
 {
-    int rc = check_pw(ctx, pw, true);
+    if (!ctx) return RM_EINVAL;
+    if (lane < 0 || lane >= (int)ctx->lanes.size())
+        return fail(ctx, RM_EINVAL, "lane %d out of range [0, %d)", lane, (int)ctx->lanes.size());
+    *ln = &ctx->lanes[lane];
+    return RM_SUCCESS;
+}
+
+int solve_on_lane(rm_ctx *ctx, int lane, int pw, int n_E, const double *E, int mode, double *K_out,
+                  int *n_open_out, int *status_out)
+{
+    Lane *ln = nullptr;
+    int rc = lane_of(ctx, lane, &ln);
+    if (rc) return rc;
+    rc = check_pw(ctx, pw, true);
     if (rc) return rc;
     if (n_E <= 0 || !E) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0 with non-NULL E", n_E);
     if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
@@ -895,18 +1014,35 @@ extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, 
     if (rc) return rc;
     CK(cudaSetDevice(ctx->opts.device));
     const bool dev_in = is_device_ptr(E);
-    rc = register_grid(ctx, P, n_E, E, dev_in);
+    rc = register_grid(ctx, ln, P, n_E, E, dev_in);
     if (rc) return rc;
     const double *dE;
-    rc = device_energies(ctx, n_E, E, &dE);
+    rc = device_energies(ctx, ln, n_E, E, &dE);
     if (rc) return rc;
     int *dstatus = status_out;
     if (!dstatus) {
-        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
-        dstatus = ctx->wsStatus.as<int>();
+        CK(ln->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        dstatus = ln->wsStatus.as<int>();
     }
-    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ctx->stream));
-    return solve_blocks(ctx, P, dE, n_E, mode, K_out, n_open_out, dstatus, ctx->omega.as<double>());
+    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ln->stream));
+    rc = solve_blocks(ctx, ln, P, dE, n_E, mode, K_out, n_open_out, dstatus, ln->omega.as<double>());
+    if (rc) return rc;
+    CK(cudaEventRecord(ln->ev_done, ln->stream));
+    return RM_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" int rm_solve_energies(rm_ctx *ctx, int pw, int n_E, const double *E, int mode,
+                                 double *K_out, int *n_open_out, int *status_out)
+{
+    return solve_on_lane(ctx, 0, pw, n_E, E, mode, K_out, n_open_out, status_out);
+}
+
+extern "C" int rm_lane_solve_energies(rm_ctx *ctx, int lane, int pw, int n_E, const double *E, int mode,
+                                      double *K_out, int *n_open_out, int *status_out)
+{
+    return solve_on_lane(ctx, lane, pw, n_E, E, mode, K_out, n_open_out, status_out);
 }
 
 extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double *E, int ieq, double qetest,
@@ -920,6 +1056,7 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     if (ieq == 0) return fail(ctx, RM_EINVAL, "ieq = 0");
     if (!std::isfinite(qetest)) return fail(ctx, RM_EINVAL, "qetest not finite");
     PwHost &P = ctx->pw[pw];
+    Lane *ln = &ctx->lanes[0];
     if (P.n > solve_small_max_n() || use_large(ctx, P))
         return fail(ctx, RM_EUNSUPPORTED, "coarse-mesh interpolation takes at most %d channels (n_ch=%d)",
                     solve_small_max_n(), P.n);
@@ -940,18 +1077,18 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     ch.kappa_a_max = ctx->opts.mqdt_kappa_a_max;
     for (int m = 1; m < n_E; ++m)
         if (!(E[m] > E[m - 1])) return fail(ctx, RM_EINVAL, "energies must be strictly ascending");
-    rc = register_grid(ctx, P, n_E, E, false);
+    rc = register_grid(ctx, ln, P, n_E, E, false);
     if (rc) return rc;
     const double *dE;
-    rc = device_energies(ctx, n_E, E, &dE);
+    rc = device_energies(ctx, ln, n_E, E, &dE);
     if (rc) return rc;
     // channel classes of every fine energy on the device, then the plan
     std::vector<signed char> hcls((size_t)n_E * P.n);
-    CK(ctx->wsQc.reserve(hcls.size()));
-    CK(launch_qdt_classes(P.dev_match(), dE, n_E, make_opts(ctx->opts), ctx->wsQc.as<signed char>(), ctx->stream));
+    CK(ln->wsQc.reserve(hcls.size()));
+    CK(launch_qdt_classes(P.dev_match(), dE, n_E, make_opts(ctx->opts), ln->wsQc.as<signed char>(), ln->stream));
     ctx->launches++;
-    CK(cudaMemcpyAsync(hcls.data(), ctx->wsQc.p, hcls.size(), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(hcls.data(), ln->wsQc.p, hcls.size(), cudaMemcpyDeviceToHost, ln->stream));
+    CK(cudaStreamSynchronize(ln->stream));
     QdtPlan pl;
     if (qdt_plan(ch, E, n_E, hcls.data(), ieq, qetest, pl) != RM_SUCCESS)
         return fail(ctx, RM_EINVAL, "energies must be strictly ascending");
@@ -960,25 +1097,25 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     const size_t n2 = (size_t)P.n * P.n;
     std::vector<int> hst(nn), hnp(nn);
     if (nn > 0) {
-        CK(ctx->wsQn.reserve((size_t)nn * sizeof(double)));
-        CK(ctx->wsQst.reserve((size_t)nn * 2 * sizeof(int)));
-        CK(ctx->wsQk.reserve((size_t)nn * n2 * sizeof(double)));
-        CK(cudaMemcpyAsync(ctx->wsQn.p, pl.node_x.data(), (size_t)nn * sizeof(double), cudaMemcpyHostToDevice,
-                           ctx->stream));
-        int *nst = ctx->wsQst.as<int>(), *nnp = nst + nn;
-        CK(cudaMemsetAsync(nst, 0, (size_t)nn * 2 * sizeof(int), ctx->stream));
-        rc = solve_blocks(ctx, P, ctx->wsQn.as<double>(), nn, RM_MQDT, nullptr, nullptr, nst, nullptr,
-                          ctx->wsQk.as<double>(), nnp);
+        CK(ln->wsQn.reserve((size_t)nn * sizeof(double)));
+        CK(ln->wsQst.reserve((size_t)nn * 2 * sizeof(int)));
+        CK(ln->wsQk.reserve((size_t)nn * n2 * sizeof(double)));
+        CK(cudaMemcpyAsync(ln->wsQn.p, pl.node_x.data(), (size_t)nn * sizeof(double), cudaMemcpyHostToDevice,
+                           ln->stream));
+        int *nst = ln->wsQst.as<int>(), *nnp = nst + nn;
+        CK(cudaMemsetAsync(nst, 0, (size_t)nn * 2 * sizeof(int), ln->stream));
+        rc = solve_blocks(ctx, ln, P, ln->wsQn.as<double>(), nn, RM_MQDT, nullptr, nullptr, nst, nullptr,
+                          ln->wsQk.as<double>(), nnp);
         if (rc) return rc;
         if (iqdt == 1) {
-            CK(ctx->wsQs.reserve((size_t)nn * n2 * sizeof(double2)));
-            CK(launch_qdt_s_from_k(P.n, nn, ctx->wsQk.as<double>(), nnp, nst, ctx->wsQs.as<double2>(),
-                                   ctx->stream));
+            CK(ln->wsQs.reserve((size_t)nn * n2 * sizeof(double2)));
+            CK(launch_qdt_s_from_k(P.n, nn, ln->wsQk.as<double>(), nnp, nst, ln->wsQs.as<double2>(),
+                                   ln->stream));
             ctx->launches++;
         }
-        CK(cudaMemcpyAsync(hst.data(), nst, (size_t)nn * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaMemcpyAsync(hnp.data(), nnp, (size_t)nn * sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+        CK(cudaMemcpyAsync(hst.data(), nst, (size_t)nn * sizeof(int), cudaMemcpyDeviceToHost, ln->stream));
+        CK(cudaMemcpyAsync(hnp.data(), nnp, (size_t)nn * sizeof(int), cudaMemcpyDeviceToHost, ln->stream));
+        CK(cudaStreamSynchronize(ln->stream));
     }
     std::vector<int> ok(nn);
     for (int k = 0; k < nn; ++k) {
@@ -988,74 +1125,124 @@ extern "C" int rm_solve_energies_qdt(rm_ctx *ctx, int pw, int n_E, const double 
     }
     std::vector<QdtFine> fine;
     qdt_weights(pl, ok, n_E, fine);
-    CK(ctx->wsQf.reserve((size_t)n_E * sizeof(QdtFine)));
-    CK(cudaMemcpyAsync(ctx->wsQf.p, fine.data(), (size_t)n_E * sizeof(QdtFine), cudaMemcpyHostToDevice,
-                       ctx->stream));
+    CK(ln->wsQf.reserve((size_t)n_E * sizeof(QdtFine)));
+    CK(cudaMemcpyAsync(ln->wsQf.p, fine.data(), (size_t)n_E * sizeof(QdtFine), cudaMemcpyHostToDevice,
+                       ln->stream));
     int *dstatus = status_out;
     if (!dstatus) {
-        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
-        dstatus = ctx->wsStatus.as<int>();
+        CK(ln->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        dstatus = ln->wsStatus.as<int>();
     }
-    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(dstatus, 0, (size_t)n_E * sizeof(int), ln->stream));
     const int ntri = P.n_levels * (P.n_levels + 1) / 2;
-    CK(launch_qdt_fine(iqdt, P.dev_match(), dE, n_E, make_opts(ctx->opts), ctx->wsQf.as<QdtFine>(),
-                       ctx->wsQk.as<double>(), ctx->wsQs.as<double2>(), ctx->wsQst.as<int>(), dstatus,
-                       n_open_out, ctx->omega.as<double>(), ntri, ctx->stream));
+    CK(launch_qdt_fine(iqdt, P.dev_match(), dE, n_E, make_opts(ctx->opts), ln->wsQf.as<QdtFine>(),
+                       ln->wsQk.as<double>(), ln->wsQs.as<double2>(), ln->wsQst.as<int>(), dstatus,
+                       n_open_out, ln->omega.as<double>(), ntri, ln->stream));
     ctx->launches++;
     return RM_SUCCESS;
 }
 
-extern "C" int rm_collision_strengths(rm_ctx *ctx, double *omega_out, int reset)
+namespace {
+
+int collision_strengths_lane(rm_ctx *ctx, Lane *ln, double *omega_out, int reset)
 {
-    if (!ctx) return RM_EINVAL;
     CK(cudaSetDevice(ctx->opts.device));
-    if (ctx->grid_nE == 0) {
+    if (ln->grid_nE == 0) {
         if (reset) return RM_SUCCESS;
         return fail(ctx, RM_EINVAL, "no energy grid registered yet");
     }
-    const size_t bytes = (size_t)ctx->grid_nE * ctx->grid_ntri * sizeof(double);
+    const size_t bytes = (size_t)ln->grid_nE * ln->grid_ntri * sizeof(double);
     if (omega_out)
-        CK(cudaMemcpyAsync(omega_out, ctx->omega.p, bytes, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    int rc = check_device_flag(ctx);
+        CK(cudaMemcpyAsync(omega_out, ln->omega.p, bytes, cudaMemcpyDeviceToHost, ln->stream));
+    CK(cudaStreamSynchronize(ln->stream));
+    int rc = check_device_flag(ctx, ln);
     if (rc) return rc;
     if (reset) {
-        ctx->grid_nE = ctx->grid_nlev = ctx->grid_ntri = 0;
-        ctx->grid_host.clear();
+        ln->grid_nE = ln->grid_nlev = ln->grid_ntri = 0;
+        ln->grid_host.clear();
     }
     return RM_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" int rm_collision_strengths(rm_ctx *ctx, double *omega_out, int reset)
+{
+    if (!ctx) return RM_EINVAL;
+    return collision_strengths_lane(ctx, &ctx->lanes[0], omega_out, reset);
+}
+
+extern "C" int rm_lane_collision_strengths(rm_ctx *ctx, int lane, double *omega_out, int reset)
+{
+    Lane *ln = nullptr;
+    int rc = lane_of(ctx, lane, &ln);
+    if (rc) return rc;
+    return collision_strengths_lane(ctx, ln, omega_out, reset);
+}
+
+extern "C" int rm_lane_query(rm_ctx *ctx, int lane)
+{
+    Lane *ln = nullptr;
+    int rc = lane_of(ctx, lane, &ln);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->opts.device));
+    const cudaError_t e = cudaEventQuery(ln->ev_done);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) {
+        cudaGetLastError();
+        return 0;
+    }
+    CK(e);
+    return 0;
+}
+
+extern "C" int rm_lane_sync(rm_ctx *ctx, int lane)
+{
+    Lane *ln = nullptr;
+    int rc = lane_of(ctx, lane, &ln);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->opts.device));
+    CK(cudaStreamSynchronize(ln->stream));
+    return check_device_flag(ctx, ln);
+}
+
+extern "C" void *rm_lane_stream(rm_ctx *ctx, int lane)
+{
+    if (!ctx || lane < 0 || lane >= (int)ctx->lanes.size()) return nullptr;
+    return ctx->lanes[lane].stream;
 }
 
 extern "C" int rm_collision_strengths_async(rm_ctx *ctx, double *omega_out, int reset)
 {
     if (!ctx) return RM_EINVAL;
+    Lane *ln = &ctx->lanes[0];
     if (!omega_out) return fail(ctx, RM_EINVAL, "omega_out is NULL");
-    if (ctx->grid_nE == 0) return fail(ctx, RM_EINVAL, "no energy grid registered yet");
+    if (ln->grid_nE == 0) return fail(ctx, RM_EINVAL, "no energy grid registered yet");
     CK(cudaSetDevice(ctx->opts.device));
-    if (!ctx->copy) {
-        CK(cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking));
-        CK(cudaEventCreateWithFlags(&ctx->ev_solved, cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&ctx->ev_copied[0], cudaEventDisableTiming));
-        CK(cudaEventCreateWithFlags(&ctx->ev_copied[1], cudaEventDisableTiming));
+    if (!ln->copy) {
+        CK(cudaStreamCreateWithFlags(&ln->copy, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&ln->ev_solved, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ln->ev_copied[0], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&ln->ev_copied[1], cudaEventDisableTiming));
     }
-    const size_t bytes = (size_t)ctx->grid_nE * ctx->grid_ntri * sizeof(double);
-    const int cur = ctx->omega_cur;
-    CK(cudaEventRecord(ctx->ev_solved, ctx->stream));
-    CK(cudaStreamWaitEvent(ctx->copy, ctx->ev_solved, 0));
-    CK(cudaMemcpyAsync(omega_out, ctx->omega.p, bytes, cudaMemcpyDeviceToHost, ctx->copy));
-    CK(cudaEventRecord(ctx->ev_copied[cur], ctx->copy));
-    ctx->copied[cur] = true;
+    const size_t bytes = (size_t)ln->grid_nE * ln->grid_ntri * sizeof(double);
+    const int cur = ln->omega_cur;
+    CK(cudaEventRecord(ln->ev_solved, ln->stream));
+    CK(cudaStreamWaitEvent(ln->copy, ln->ev_solved, 0));
+    CK(cudaMemcpyAsync(omega_out, ln->omega.p, bytes, cudaMemcpyDeviceToHost, ln->copy));
+    CK(cudaEventRecord(ln->ev_copied[cur], ln->copy));
+    ln->copied[cur] = true;
     if (reset) {
         // later solves accumulate into the other buffer once its own last
         // copy is done; this one drains on the copy stream meanwhile
-        std::swap(ctx->omega, ctx->omega_alt);
-        ctx->omega_cur = cur ^ 1;
-        if (ctx->copied[cur ^ 1]) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[cur ^ 1], 0));
-        ctx->grid_nE = ctx->grid_nlev = ctx->grid_ntri = 0;
-        ctx->grid_host.clear();
+        std::swap(ln->omega, ln->omega_alt);
+        ln->omega_cur = cur ^ 1;
+        if (ln->copied[cur ^ 1]) CK(cudaStreamWaitEvent(ln->stream, ln->ev_copied[cur ^ 1], 0));
+        ln->grid_nE = ln->grid_nlev = ln->grid_ntri = 0;
+        ln->grid_host.clear();
     } else {
         // the accumulator keeps growing: nothing may touch it before the copy
-        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[cur], 0));
+        CK(cudaStreamWaitEvent(ln->stream, ln->ev_copied[cur], 0));
     }
     return RM_SUCCESS;
 }
@@ -1063,17 +1250,18 @@ extern "C" int rm_collision_strengths_async(rm_ctx *ctx, double *omega_out, int 
 extern "C" int rm_reset_omega(rm_ctx *ctx)
 {
     if (!ctx) return RM_EINVAL;
-    if (ctx->grid_nE == 0) return fail(ctx, RM_EINVAL, "no energy grid registered yet");
+    Lane *ln = &ctx->lanes[0];
+    if (ln->grid_nE == 0) return fail(ctx, RM_EINVAL, "no energy grid registered yet");
     CK(cudaSetDevice(ctx->opts.device));
-    CK(cudaMemsetAsync(ctx->omega.p, 0, (size_t)ctx->grid_nE * ctx->grid_ntri * sizeof(double),
-                       ctx->stream));
+    CK(cudaMemsetAsync(ln->omega.p, 0, (size_t)ln->grid_nE * ln->grid_ntri * sizeof(double),
+                       ln->stream));
     return RM_SUCCESS;
 }
 
 extern "C" int rm_profile_enable(rm_ctx *ctx, int enable)
 {
     if (!ctx) return RM_EINVAL;
-    CK(cudaStreamSynchronize(ctx->stream));
+    for (Lane &l : ctx->lanes) CK(cudaStreamSynchronize(l.stream));
     ctx->prof = enable != 0;
     for (int p = 0; p < RM_PH_COUNT; ++p) ctx->ev_used[p] = 0;
     return RM_SUCCESS;
@@ -1082,7 +1270,7 @@ extern "C" int rm_profile_enable(rm_ctx *ctx, int enable)
 extern "C" int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms)
 {
     if (!ctx || phase < 0 || phase >= RM_PH_COUNT) return RM_EINVAL;
-    CK(cudaStreamSynchronize(ctx->stream));
+    for (Lane &l : ctx->lanes) CK(cudaStreamSynchronize(l.stream));
     double tot = 0.0;
     for (size_t i = 0; i < ctx->ev_used[phase]; ++i) {
         float t = 0.f;
@@ -1097,8 +1285,9 @@ extern "C" int rm_profile_get(rm_ctx *ctx, int phase, int *launches, double *ms)
 extern "C" int rm_grid_shape(rm_ctx *ctx, int *n_E, int *n_tri)
 {
     if (!ctx) return RM_EINVAL;
-    if (n_E) *n_E = ctx->grid_nE;
-    if (n_tri) *n_tri = ctx->grid_ntri;
+    const Lane *ln = &ctx->lanes[0];
+    if (n_E) *n_E = ln->grid_nE;
+    if (n_tri) *n_tri = ln->grid_ntri;
     return RM_SUCCESS;
 }
 
@@ -1111,17 +1300,18 @@ extern "C" int rm_channel_functions(rm_ctx *ctx, int pw, int n_E, const double *
     if (!is_device_ptr(E) || !is_device_ptr(out) || (status && !is_device_ptr(status)))
         return fail(ctx, RM_EINVAL, "E, out and status must be device pointers");
     CK(cudaSetDevice(ctx->opts.device));
+    Lane *ln = &ctx->lanes[0];
     const PwHost &P = ctx->pw[pw];
-    CK(ctx->wsCf.reserve((size_t)n_E * P.n * sizeof(ChanFn)));
+    CK(ln->wsCf.reserve((size_t)n_E * P.n * sizeof(ChanFn)));
     int *st = status;
     if (!st) {
-        CK(ctx->wsStatus.reserve((size_t)n_E * sizeof(int)));
-        st = ctx->wsStatus.as<int>();
+        CK(ln->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        st = ln->wsStatus.as<int>();
     }
-    CK(cudaMemsetAsync(st, 0, (size_t)n_E * sizeof(int), ctx->stream));
+    CK(cudaMemsetAsync(st, 0, (size_t)n_E * sizeof(int), ln->stream));
     const PwDev d = P.dev_match();
-    CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ctx->wsCf.as<ChanFn>(), st, nullptr, ctx->stream));
-    CK(launch_chanfn_export(d, E, n_E, ctx->wsCf.as<ChanFn>(), out, ctx->stream));
+    CK(launch_chanfn(d, E, n_E, make_opts(ctx->opts), 0, ln->wsCf.as<ChanFn>(), st, nullptr, ln->stream));
+    CK(launch_chanfn_export(d, E, n_E, ln->wsCf.as<ChanFn>(), out, ln->stream));
     ctx->launches += 2;
     return RM_SUCCESS;
 }
@@ -1134,8 +1324,9 @@ extern "C" int rm_channel_work(rm_ctx *ctx, int pw, int n_E, const double *E, in
     if (!is_device_ptr(E) || !is_device_ptr(work))
         return fail(ctx, RM_EINVAL, "E and work must be device pointers");
     CK(cudaSetDevice(ctx->opts.device));
+    Lane *ln = &ctx->lanes[0];
     const PwDev d = ctx->pw[pw].dev_match();
-    CK(launch_chanfn_work(d, E, n_E, make_opts(ctx->opts), reinterpret_cast<int4 *>(work), ctx->stream));
+    CK(launch_chanfn_work(d, E, n_E, make_opts(ctx->opts), reinterpret_cast<int4 *>(work), ln->stream));
     ctx->launches++;
     return RM_SUCCESS;
 }
@@ -1148,28 +1339,74 @@ extern "C" int rm_form_r(rm_ctx *ctx, int pw, int n_E, const double *E, double *
     if (!is_device_ptr(E) || !is_device_ptr(R_out))
         return fail(ctx, RM_EINVAL, "E and R_out must be device pointers");
     CK(cudaSetDevice(ctx->opts.device));
+    Lane *ln = &ctx->lanes[0];
     PwHost &P = ctx->pw[pw];
     rc = check_precision(ctx, P);
     if (rc) return rc;
     const int B = std::min(n_E, block_energies(ctx, P));
-    CK(ctx->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
+    CK(ln->wsR.reserve((size_t)B * tri_ld(P.n) * sizeof(double)));
     for (int e0 = 0; e0 < n_E; e0 += B) {
         const int nb = std::min(B, n_E - e0);
-        rc = form_r_block(ctx, P, E + e0, nb, ctx->wsR.as<double>());
+        rc = form_r_block(ctx, ln, P, E + e0, nb, ln->wsR.as<double>());
         if (rc) return rc;
-        CK(launch_unpack_r(P.n, nb, ctx->wsR.as<double>(), R_out + (size_t)e0 * P.n * P.n,
-                           ctx->stream));
+        CK(launch_unpack_r(P.n, nb, ln->wsR.as<double>(), R_out + (size_t)e0 * P.n * P.n,
+                           ln->stream));
         ctx->launches++;
     }
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_lane_reserve(rm_ctx *ctx, int lane, int pw, int n_E, size_t *bytes)
+{
+    Lane *ln = nullptr;
+    int rc = lane_of(ctx, lane, &ln);
+    if (rc) return rc;
+    rc = check_pw(ctx, pw, true);
+    if (rc) return rc;
+    if (n_E <= 0) return fail(ctx, RM_EINVAL, "n_E=%d must be > 0", n_E);
+    PwHost &P = ctx->pw[pw];
+    if (!use_large(ctx, P) && P.n > solve_small_max_n())
+        return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the shared-memory solver limit %d", P.n,
+                    solve_small_max_n());
+    rc = check_precision(ctx, P);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->opts.device));
+    rc = reserve_solve(ctx, ln, P, n_E);
+    if (rc) return rc;
+    if (bytes) *bytes = ln->ws_bytes() + ln->omega.bytes + ln->omega_alt.bytes;
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_pw_bytes(rm_ctx *ctx, int pw, size_t *bytes)
+{
+    const int rc = check_pw(ctx, pw, false);
+    if (rc) return rc;
+    if (bytes) *bytes = ctx->pw[pw].bytes();
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_unload_pw(rm_ctx *ctx, int pw)
+{
+    const int rc = check_pw(ctx, pw, false);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->opts.device));
+    ctx->pw[pw].release();
     return RM_SUCCESS;
 }
 
 extern "C" int rm_sync(rm_ctx *ctx)
 {
     if (!ctx) return RM_EINVAL;
-    CK(cudaStreamSynchronize(ctx->stream));
-    if (ctx->copy) CK(cudaStreamSynchronize(ctx->copy));
-    return check_device_flag(ctx);
+    CK(cudaSetDevice(ctx->opts.device));
+    for (Lane &l : ctx->lanes) {
+        CK(cudaStreamSynchronize(l.stream));
+        if (l.copy) CK(cudaStreamSynchronize(l.copy));
+    }
+    for (Lane &l : ctx->lanes) {
+        const int rc = check_device_flag(ctx, &l);
+        if (rc) return rc;
+    }
+    return RM_SUCCESS;
 }
 
 extern "C" long long rm_launch_count(rm_ctx *ctx) { return ctx ? ctx->launches : 0; }

@@ -37,7 +37,7 @@ class RmOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
                 ("mqdt_kappa_a_max", ctypes.c_double), ("solver", ctypes.c_int),
                 ("formulation", ctypes.c_int), ("solve_precision", ctypes.c_int),
-                ("channel_tables", ctypes.c_int)]
+                ("channel_tables", ctypes.c_int), ("lanes", ctypes.c_int)]
 
 
 class RmError(RuntimeError):
@@ -73,6 +73,14 @@ _SIGS = {
     "rm_profile_enable": (_I, [_VP, _I]),
     "rm_profile_get": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "rm_launch_count": (ctypes.c_longlong, [_VP]),
+    "rm_lane_solve_energies": (_I, [_VP, _I, _I, _I, _VP, _I, _VP, _VP, _VP]),
+    "rm_lane_collision_strengths": (_I, [_VP, _I, _VP, _I]),
+    "rm_lane_query": (_I, [_VP, _I]),
+    "rm_lane_sync": (_I, [_VP, _I]),
+    "rm_lane_stream": (_VP, [_VP, _I]),
+    "rm_lane_reserve": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "rm_pw_bytes": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_size_t)]),
+    "rm_unload_pw": (_I, [_VP, _I]),
     "rm_strerror": (ctypes.c_char_p, [_I]),
     "rm_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -190,6 +198,54 @@ def rm_solve_energies_qdt(ctx, pw, E, ieq, qetest=0.0, iqdt=1, n_open_out=None, 
     return _check(ctx, lib().rm_solve_energies_qdt(ctx, pw, int(E.shape[0]), _ptr(E, np.float64), int(ieq),
                                                    float(qetest), int(iqdt), _ptr(n_open_out, np.int32),
                                                    _ptr(status_out, np.int32)))
+
+
+def rm_lane_solve_energies(ctx, lane, pw, E, mode=0, K_out=None, n_open_out=None, status_out=None):
+    E = _host(E, np.float64)
+    return _check(ctx, lib().rm_lane_solve_energies(ctx, int(lane), pw, int(E.shape[0]), _ptr(E, np.float64),
+                                                    mode, _ptr(K_out, np.float64), _ptr(n_open_out, np.int32),
+                                                    _ptr(status_out, np.int32)))
+
+
+def rm_lane_collision_strengths(ctx, lane, omega_out, reset=False):
+    """Copies lane `lane`'s Omega into omega_out (host float64 array of the
+    lane's grid shape) after synchronising that lane."""
+    return _check(ctx, lib().rm_lane_collision_strengths(ctx, int(lane), _ptr(omega_out, np.float64),
+                                                         int(bool(reset))))
+
+
+def rm_lane_query(ctx, lane):
+    """True when the lane's enqueued work has completed."""
+    rc = lib().rm_lane_query(ctx, int(lane))
+    if rc < 0:
+        raise RmError(rc, rm_last_error(ctx))
+    return bool(rc)
+
+
+def rm_lane_sync(ctx, lane):
+    return _check(ctx, lib().rm_lane_sync(ctx, int(lane)))
+
+
+def rm_lane_stream(ctx, lane):
+    return lib().rm_lane_stream(ctx, int(lane))
+
+
+def rm_lane_reserve(ctx, lane, pw, n_E):
+    """Pre-sizes the lane's workspace for n_E energies of pw; returns the
+    lane's device bytes."""
+    b = ctypes.c_size_t(0)
+    _check(ctx, lib().rm_lane_reserve(ctx, int(lane), int(pw), int(n_E), ctypes.byref(b)))
+    return b.value
+
+
+def rm_pw_bytes(ctx, pw):
+    b = ctypes.c_size_t(0)
+    _check(ctx, lib().rm_pw_bytes(ctx, int(pw), ctypes.byref(b)))
+    return b.value
+
+
+def rm_unload_pw(ctx, pw):
+    return _check(ctx, lib().rm_unload_pw(ctx, int(pw)))
 
 
 def rm_grid_shape(ctx):
@@ -401,3 +457,28 @@ class Context:
 
     def profile_get(self, phase):
         return rm_profile_get(self.h, phase)
+
+    def lane_solve_energies(self, lane, pw, E, mode=0, K_out=None, n_open_out=None, status_out=None):
+        return rm_lane_solve_energies(self.h, lane, pw, E, mode, K_out, n_open_out, status_out)
+
+    def lane_collision_strengths(self, lane, omega_out, reset=False):
+        return rm_lane_collision_strengths(self.h, lane, omega_out, reset)
+
+    def lane_query(self, lane):
+        return rm_lane_query(self.h, lane)
+
+    def lane_sync(self, lane):
+        return rm_lane_sync(self.h, lane)
+
+    def lane_stream(self, lane):
+        return rm_lane_stream(self.h, lane)
+
+    def lane_reserve(self, lane, pw, n_E):
+        return rm_lane_reserve(self.h, lane, pw, n_E)
+
+    def pw_bytes(self, pw):
+        return rm_pw_bytes(self.h, pw)
+
+    def unload_pw(self, pw):
+        self._n_ch.pop(pw, None)
+        return rm_unload_pw(self.h, pw)

@@ -2,13 +2,24 @@
 
 A request is one partial wave (a pole set) and a batch of energies, solved in
 direct or MQDT mode; its result is the Omega rows of those energies. The
-server keeps a pool of slots; each slot is one rm_ctx on its own CUDA stream,
-so the work of all admitted requests overlaps on the device. Requests are
-admitted in arrival order as soon as a slot is free and the device-memory
-budget covers their estimated footprint (pole set, operands, workspace,
-Omega); a request that arrives while others run joins as soon as that holds.
-Pole sets stay resident in the slot that loaded them (a per-slot cache keyed by
-pole-set id, least-recently-used eviction) so repeated sets skip the upload.
+server owns ONE library context with one lane per slot (rm_opts.lanes): each
+lane has its own CUDA stream, workspace and Omega accumulator, and all lanes
+share the context's partial waves, so a pole set is loaded once and every slot
+uses it. Requests are admitted in arrival order as soon as a lane is free and
+the device-memory budget covers what the request adds (its pole set if not
+resident, exactly as rm_pw_bytes reports it once loaded); a request that
+arrives while others run joins as soon as that holds, and its work overlaps
+theirs on the device.
+
+Before serving, every lane's workspace is sized once for the largest request
+of the stream (rm_lane_reserve), so no solve in the mix allocates device
+memory (a cudaMalloc would synchronise the whole device). Resident pole sets
+are kept in least-recently-used order and evicted (rm_unload_pw) only when
+no running request uses them.
+
+Pole-set loads (rm_load_poles + rm_set_channels, which build the channel
+tables) run synchronously in the admission loop; with the shared cache each
+set is loaded once per residency, not once per slot.
 
 Latency of a request = completion time on the host (Omega copied back)
 minus its arrival time.
@@ -30,94 +41,126 @@ class Request:
         self.t_admit = None
         self.t_done = None
         self.omega = None
-        self.status = None
 
-    def footprint(self, precision):
-        n, N = self.pw["W"].shape
+    def n_tri(self):
         nl = self.pw["n_levels"]
-        b = n * N * 8 + N * 8 + 16 * n                      # pole set
-        if precision != 0:
-            b += n * (n + 1) // 2 * ((N + 63) // 64 * 64) * 4   # split pair operands
-        b += self.E.size * (nl * (nl + 1) // 2 * 8 + 16)        # Omega, statuses
-        return b
+        return nl * (nl + 1) // 2
+
+
+def estimate_set_bytes(pw, precision):
+    """Device bytes of a pole set before it is loaded: poles and amplitudes,
+    channel data, the channel tables (near-threshold nodes, open- and
+    closed-side Chebyshev coefficients: about 85 KB per channel) and, with a
+    tensor-core formation, the split operands (per-energy form: W in FP32 and
+    split hi/lo). rm_pw_bytes replaces it once the set is loaded."""
+    n, N = pw["W"].shape
+    b = n * N * 8 + N * 16 + 64 * n
+    if precision != 0:
+        b += 85_000 * n
+        kpad = (N + 63) // 64 * 64
+        b += n * kpad * (4 + 4 + 4)
+    return b
 
 
 class Server:
-    """Slots of (context, stream); `run` serves a list of requests whose
+    """One context with n_slots lanes; `run` serves a list of requests whose
     arrival times are replayed in real time."""
 
-    def __init__(self, n_slots=4, precision=0, mem_budget=8 << 30, slot_workspace=1 << 30,
-                 cache_sets=4, device=0):
-        import torch
-
+    def __init__(self, n_slots=4, precision=0, solve_precision=0, mem_budget=64 << 30,
+                 lane_workspace=4 << 30, cache_sets=64, device=0):
         from . import rmgb
 
-        self.torch = torch
         self.rmgb = rmgb
         self.precision = precision
         self.device = device
         self.mem_budget = mem_budget
         self.cache_sets = cache_sets
-        self.slots = []
-        for _ in range(n_slots):
-            st = torch.cuda.Stream(device=device)
-            ctx = rmgb.Context(precision=precision, stream=st.cuda_stream,
-                               mem_budget=slot_workspace, device=device)
-            self.slots.append(dict(ctx=ctx, stream=st, req=None, done_ev=None,
-                                   cache=collections.OrderedDict(), workspace=slot_workspace))
-        self.mem_used = n_slots * slot_workspace
+        self.ctx = rmgb.Context(precision=precision, solve_precision=solve_precision, lanes=n_slots,
+                                mem_budget=lane_workspace, device=device, stream=0)
+        self.slots = [dict(lane=i, req=None) for i in range(n_slots)]
+        self.lane_bytes = [0] * n_slots
+        self.cache = collections.OrderedDict()     # set_id -> dict(pw_index, bytes, users)
+        self.free_index = list(range(4095, -1, -1))
+        self.loads = 0
 
     def close(self):
-        for s in self.slots:
-            s["ctx"].close()
-        self.slots = []
+        if self.ctx is not None:
+            self.ctx.close()
+            self.ctx = None
 
-    # -- pole-set cache -------------------------------------------------------
-    def _ensure_loaded(self, slot, req):
-        cache = slot["cache"]
-        if req.set_id in cache:
-            cache.move_to_end(req.set_id)
-            return cache[req.set_id]["pw_index"]
-        while len(cache) >= self.cache_sets:
-            _, old = cache.popitem(last=False)
-            self.mem_used -= old["bytes"]
-        used = {v["pw_index"] for v in cache.values()}
-        idx = next(i for i in range(self.cache_sets + 1) if i not in used)
-        slot["ctx"].load_pw(idx, req.pw)
-        n, N = req.pw["W"].shape
-        b = n * N * 8 + N * 8 + 16 * n
-        cache[req.set_id] = dict(pw_index=idx, bytes=b)
-        self.mem_used += b
-        return idx
+    # -- memory accounting -------------------------------------------------------
+    def mem_used(self):
+        return sum(self.lane_bytes) + sum(c["bytes"] for c in self.cache.values())
+
+    def _need(self, req):
+        """Bytes the request adds: its pole set if not resident, and its
+        Omega rows on the host side are not device memory."""
+        if req.set_id in self.cache:
+            return 0
+        return estimate_set_bytes(req.pw, self.precision)
+
+    def _evictable(self):
+        return [sid for sid, c in self.cache.items() if c["users"] == 0]
+
+    def _make_room(self, need, new_set=True):
+        """Evicts unused pole sets (least recently used first) until `need`
+        more bytes fit the budget (and, for a set to be loaded, the cache has
+        a free entry) or nothing more can be evicted."""
+        while self.mem_used() + need > self.mem_budget or (new_set and len(self.cache) >= self.cache_sets):
+            ev = self._evictable()
+            if not ev:
+                return False
+            sid = ev[0]
+            c = self.cache.pop(sid)
+            self.ctx.unload_pw(c["pw_index"])
+            self.free_index.append(c["pw_index"])
+        return True
+
+    # -- pole-set cache ----------------------------------------------------------
+    def _ensure_loaded(self, req):
+        c = self.cache.get(req.set_id)
+        if c is not None:
+            self.cache.move_to_end(req.set_id)
+            return c
+        idx = self.free_index.pop()
+        self.ctx.load_pw(idx, req.pw)
+        self.loads += 1
+        c = dict(pw_index=idx, bytes=self.ctx.pw_bytes(idx), users=0)
+        self.cache[req.set_id] = c
+        return c
+
+    def prepare(self, requests):
+        """Sizes every lane's workspace for the largest request of the stream
+        (most channels, then most energies) before serving."""
+        big = max(requests, key=lambda r: (r.pw["W"].shape[0], r.E.size))
+        n_e = max(r.E.size for r in requests)
+        self._make_room(self._need(big))
+        c = self._ensure_loaded(big)
+        for s in self.slots:
+            self.lane_bytes[s["lane"]] = self.ctx.lane_reserve(s["lane"], c["pw_index"], n_e)
 
     def _fits(self, req):
-        return self.mem_used + req.footprint(self.precision) <= self.mem_budget
+        resident = req.set_id in self.cache
+        need = self._need(req)
+        if self.mem_used() + need <= self.mem_budget and (resident or len(self.cache) < self.cache_sets):
+            return True
+        return self._make_room(need, new_set=not resident)
 
     def _launch(self, slot, req, now):
-        """Loads the pole set if needed (the cache accounts for its bytes) and
-        enqueues the solve; the request's other bytes are held until it ends."""
-        torch = self.torch
-        pw_index = self._ensure_loaded(slot, req)
-        with torch.cuda.stream(slot["stream"]):
-            st = torch.zeros(req.E.size, dtype=torch.int32, device="cuda:%d" % self.device)
-            slot["ctx"].solve_energies(pw_index, req.E, req.mode, None, None, st)
-            ev = torch.cuda.Event()
-            ev.record(slot["stream"])
-        slot.update(req=req, done_ev=ev, status=st)
+        c = self._ensure_loaded(req)
+        c["users"] += 1
+        self.ctx.lane_solve_energies(slot["lane"], c["pw_index"], req.E, req.mode)
+        slot.update(req=req, cache=c)
         req.t_admit = now
-        self.mem_used += req.footprint(self.precision) - self._cached_bytes(slot, req)
-
-    def _cached_bytes(self, slot, req):
-        c = slot["cache"].get(req.set_id)
-        return c["bytes"] if c else 0
 
     def _finish(self, slot, now_fn):
         req = slot["req"]
-        req.omega = slot["ctx"].collision_strengths(reset=True)
-        req.status = slot["status"].cpu().numpy()
+        om = np.empty((req.E.size, req.n_tri()), dtype=np.float64)
+        self.ctx.lane_collision_strengths(slot["lane"], om, reset=True)
+        req.omega = om
         req.t_done = now_fn()
-        self.mem_used -= req.footprint(self.precision) - self._cached_bytes(slot, req)
-        slot.update(req=None, done_ev=None, status=None)
+        slot["cache"]["users"] -= 1
+        slot.update(req=None, cache=None)
 
     def run(self, requests, idle_sleep=2e-4):
         """Serve `requests`, replaying their arrival times (seconds from the
@@ -135,18 +178,17 @@ class Server:
                 queue.append(pending.popleft())
             progressed = False
             for slot in self.slots:
-                if slot["req"] is not None and slot["done_ev"].query():
+                if slot["req"] is not None and self.ctx.lane_query(slot["lane"]):
                     self._finish(slot, now)
                     done += 1
                     progressed = True
             for slot in self.slots:
-                if slot["req"] is None and queue and self._fits(queue[0]):
-                    self._launch(slot, queue.popleft(), now())
-                    progressed = True
-                elif slot["req"] is None and queue and not any(s["req"] for s in self.slots):
-                    # nothing running and the head still does not fit: run it alone
-                    self._launch(slot, queue.popleft(), now())
-                    progressed = True
+                if slot["req"] is None and queue:
+                    busy = any(s["req"] is not None for s in self.slots)
+                    if self._fits(queue[0]) or not busy:
+                        # nothing running and the head still does not fit: run it alone
+                        self._launch(slot, queue.popleft(), now())
+                        progressed = True
             if not progressed:
                 time.sleep(idle_sleep)
         return requests

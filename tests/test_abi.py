@@ -75,6 +75,21 @@ def test_null_context_rejected_by_new_calls(so):
     assert L.rm_collision_strengths_async(None, None, 0) == rmgb.RM_EINVAL
 
 
+def test_null_context_rejected_by_lane_calls(so):
+    from paper_1909_07321_gb300 import rmgb
+    L = rmgb.lib()
+    assert L.rm_lane_solve_energies(None, 0, 0, 1, None, 0, None, None, None) == rmgb.RM_EINVAL
+    assert L.rm_lane_collision_strengths(None, 0, None, 0) == rmgb.RM_EINVAL
+    assert L.rm_lane_query(None, 0) == rmgb.RM_EINVAL
+    assert L.rm_lane_sync(None, 0) == rmgb.RM_EINVAL
+    assert L.rm_lane_stream(None, 0) is None
+    assert L.rm_lane_reserve(None, 0, 0, 1, None) == rmgb.RM_EINVAL
+    assert L.rm_pw_bytes(None, 0, None) == rmgb.RM_EINVAL
+    assert L.rm_unload_pw(None, 0) == rmgb.RM_EINVAL
+    o = rmgb.rm_default_opts()
+    assert o.lanes == 0   # 0 takes the default of one lane
+
+
 def test_multipole_shape_checked_before_the_library(so):
     """The binding rejects coefficients that do not match the loaded wave's
     channel count (the C call reads lambda_max n^2 doubles) without calling

@@ -48,9 +48,9 @@ def _gpu(rt, pw, E, mode=0, solver=0, precision=0, sp=1, mem_budget=0):
                 status=st.cpu().numpy(), omega=om)
 
 
-def _check_bounds(pw, E, res, ref, r_bound, tag):
-    """K and Omega of every solved energy within the stated bounds; returns
-    the per-energy relative Omega errors."""
+def _check_bounds(pw, E, res, ref, r_bound, tag, check_k=True):
+    """K (unless check_k is False) and Omega of every solved energy within
+    the stated bounds; returns the per-energy relative Omega errors."""
     assert np.array_equal(res["status"], ref["status"]), tag
     assert np.array_equal(res["n_open"], ref["n_open"]), tag
     rel = []
@@ -60,9 +60,10 @@ def _check_bounds(pw, E, res, ref, r_bound, tag):
         Ko = ref["K"][m]
         k = Ko.shape[0]
         bK = _first_order_k_bound(pw, E[m], U32, r_bound=r_bound)
-        dK = np.abs(res["K"][m, :k, :k] - Ko)
-        slack = 1e-12 * max(1.0, np.abs(Ko).max())
-        assert np.all(dK <= 3.0 * bK + slack), (tag, E[m], float((dK / (3.0 * bK + slack)).max()))
+        if check_k:
+            dK = np.abs(res["K"][m, :k, :k] - Ko)
+            slack = 1e-12 * max(1.0, np.abs(Ko).max())
+            assert np.all(dK <= 3.0 * bK + slack), (tag, E[m], float((dK / (3.0 * bK + slack)).max()))
         B = 3.0 * np.linalg.norm(bK) + k * U32 * np.linalg.norm(np.eye(k) - 1j * Ko)
         dOm = np.abs(res["omega"][m] - ref["omega"][m]).sum()
         assert dOm <= pw["g"] * (8 * k * B + 4 * B * B) + 1e-12, (tag, E[m])

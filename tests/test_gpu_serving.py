@@ -1,10 +1,16 @@
 """Continuous-batching server: requests of different channel counts, energy
-batches and modes overlap on the device; every result equals the same request
-solved alone, and admission under a tight memory budget still serves them all."""
+batches and modes overlap on the device (one context, one lane per slot, one
+shared pole-set cache); every result equals the same request solved alone,
+admission under a tight memory budget still serves them all, and at the
+serving workload's shape (requests of up to 1500 channels and 8192 energies,
+half MQDT, mixed precision) results match the oracle on sampled energies."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1909_07321_gb300 import synth
+from test_gpu_large_f32 import _check_bounds
+from test_gpu_mixed import R_BOUND
 
 pytestmark = pytest.mark.gpu
 
@@ -19,8 +25,7 @@ def rt():
     return torch, rmgb, serving
 
 
-def _requests(serving, n_req=14, rate=400.0):
-    specs = synth.serving_requests(n_req, rate, n_range=(50, 140), ne_range=(256, 1200), n_sets=6)
+def _requests(serving, specs):
     pws = {}
     out = []
     for s in specs:
@@ -31,8 +36,8 @@ def _requests(serving, n_req=14, rate=400.0):
     return out
 
 
-def _alone(rmgb, req):
-    with rmgb.Context() as ctx:
+def _alone(rmgb, req, precision=0, sp=0):
+    with rmgb.Context(precision=precision, solve_precision=sp) as ctx:
         ctx.load_pw(0, req.pw)
         ctx.solve_energies(0, req.E, req.mode)
         return ctx.collision_strengths()
@@ -41,9 +46,11 @@ def _alone(rmgb, req):
 @pytest.mark.parametrize("budget", [8 << 30, 1])
 def test_results_same_alone_and_in_the_mix(rt, budget):
     torch, rmgb, serving = rt
-    reqs = _requests(serving)
-    srv = serving.Server(n_slots=4, mem_budget=budget, slot_workspace=256 << 20, cache_sets=2)
+    specs = synth.serving_requests(14, 400.0, n_range=(50, 140), ne_range=(256, 1200), n_sets=6)
+    reqs = _requests(serving, specs)
+    srv = serving.Server(n_slots=4, mem_budget=budget, lane_workspace=256 << 20, cache_sets=2)
     try:
+        srv.prepare(reqs)
         srv.run(reqs)
     finally:
         srv.close()
@@ -58,3 +65,54 @@ def test_results_same_alone_and_in_the_mix(rt, budget):
     if budget == 1:      # nothing fits beside another request: strictly one at a time
         spans = sorted((r.t_admit, r.t_done) for r in reqs)
         assert all(b[0] >= a[1] - 1e-3 for a, b in zip(spans, spans[1:]))
+
+
+def _config4_requests(serving):
+    """Seven requests of the serving workload's shape: the stream's own draws
+    for energies and modes, with channel counts spread over 50-1500 (one of
+    1450 channels, one of 8192 energies)."""
+    specs = synth.serving_requests(7, 1000.0, n_sets=7)
+    ns = [60, 1450, 300, 700, 150, 1000, 420]
+    nes = [8192, 512, 1500, 900, 3000, 600, 2048]
+    for s, n, ne in zip(specs, ns, nes):
+        s["set_id"] = 1000 + s["id"]
+        s["n"] = n
+        lo = float(s["E"][0] - 0.5 * 8.0 / s["E"].size)
+        s["E"] = lo + synth.midpoint_grid(0.0, 8.0, ne)
+    return _requests(serving, specs)
+
+
+def test_config4_shape_mixed_alone_vs_mix_and_oracle(rt):
+    """Mixed precision (bf16x3 formation, FP32 matching): every request of
+    the mix equals the same request alone to rounding (1e-12 relative; the
+    lanes run the same kernels on the same inputs), and sampled energies of
+    the direct-mode requests match the oracle within the stated K and Omega
+    bounds."""
+    torch, rmgb, serving = rt
+    reqs = _config4_requests(serving)
+    srv = serving.Server(n_slots=4, precision=2, solve_precision=1, mem_budget=64 << 30,
+                         lane_workspace=4 << 30, cache_sets=8)
+    try:
+        srv.prepare(reqs)
+        srv.run(reqs)
+        loads = srv.loads
+    finally:
+        srv.close()
+    assert loads == len({r.set_id for r in reqs})
+    for r in reqs:
+        ref = _alone(rmgb, r, precision=2, sp=1)
+        rel = np.linalg.norm(r.omega - ref) / max(np.linalg.norm(ref), 1e-300)
+        assert rel <= 1e-12, (r.id, rel)
+    checked = 0
+    for r in reqs:
+        if r.mode != 0 or r.pw["W"].shape[0] > 1000:
+            continue
+        idx = np.array([r.E.size // 7, (4 * r.E.size) // 5])
+        Es = r.E[idx]
+        ref = oracle.solve_energies(r.pw, Es)
+        # the server returns Omega only: its bound is checked (it holds the
+        # propagated K bound and the T step's term)
+        res = dict(n_open=ref["n_open"], status=ref["status"], omega=r.omega[idx])
+        _check_bounds(r.pw, Es, res, ref, R_BOUND, "req%d" % r.id, check_k=False)
+        checked += 1
+    assert checked >= 2

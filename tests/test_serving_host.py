@@ -1,61 +1,13 @@
 """Host logic of the continuous-batching server (serving.py) on the CPU, with
-the device replaced by fakes: first-come admission, the memory budget (a
-request waits until it fits, or runs alone), overlap of requests across
-slots, the per-slot pole-set cache with least-recently-used eviction and its
-byte accounting, and that every request gets its own result."""
-import collections
-import contextlib
-
+the library context replaced by a fake: first-come admission, the memory
+budget (a request waits until it fits, or runs alone), overlap of requests
+across lanes, one pole-set cache shared by all lanes (a set used by several
+lanes is loaded once, a set in use is never evicted, least-recently-used
+eviction otherwise) with exact byte accounting, the lanes' workspaces sized
+once before serving, and that every request gets its own result."""
 import numpy as np
 
 from paper_1909_07321_gb300 import serving, synth
-
-
-class _Tensor:
-    def __init__(self, a):
-        self.a = a
-
-    def cpu(self):
-        return self
-
-    def numpy(self):
-        return self.a
-
-
-class _Event:
-    """Completes after a fixed number of polls (the fake device's work)."""
-
-    def __init__(self, polls):
-        self.left = polls
-
-    def record(self, stream):
-        pass
-
-    def query(self):
-        self.left -= 1
-        return self.left <= 0
-
-
-class _Cuda:
-    def __init__(self, owner):
-        self.owner = owner
-
-    def stream(self, s):
-        return contextlib.nullcontext()
-
-    def Event(self):
-        return _Event(self.owner.next_polls)
-
-
-class _Torch:
-    int32 = np.int32
-
-    def __init__(self):
-        self.next_polls = 3
-        self.cuda = _Cuda(self)
-
-    def zeros(self, n, dtype=None, device=None):
-        return _Tensor(np.zeros(n, dtype=np.int32))
 
 
 def _result(pw, E):
@@ -64,44 +16,73 @@ def _result(pw, E):
 
 
 class _Ctx:
-    def __init__(self, log):
+    """A context whose lanes finish after a fixed number of polls."""
+
+    def __init__(self, n_lanes, log):
         self.log = log
         self.waves = {}
-        self.last = None
+        self.lane = [dict(left=0, out=None) for _ in range(n_lanes)]
+        self.reserved = []
+        self.next_polls = 3
 
     def load_pw(self, idx, pw):
+        assert idx not in self.waves
         self.waves[idx] = pw
         self.log.append(("load", id(pw), idx))
 
-    def solve_energies(self, idx, E, mode, K, no, st):
-        self.last = _result(self.waves[idx], E)
+    def unload_pw(self, idx):
+        pw = self.waves.pop(idx)
+        self.log.append(("unload", id(pw), idx))
 
-    def collision_strengths(self, reset=False):
-        return self.last
+    def pw_bytes(self, idx):
+        n, N = self.waves[idx]["W"].shape
+        return 1000 * n + N
+
+    def lane_reserve(self, lane, idx, n_e):
+        self.reserved.append((lane, idx, n_e))
+        return 1 << 20
+
+    def lane_solve_energies(self, lane, idx, E, mode):
+        assert self.lane[lane]["left"] <= 0, "lane reused before it finished"
+        self.lane[lane] = dict(left=self.next_polls, out=_result(self.waves[idx], E), idx=idx)
+
+    def lane_query(self, lane):
+        self.lane[lane]["left"] -= 1
+        return self.lane[lane]["left"] <= 0
+
+    def lane_collision_strengths(self, lane, out, reset=False):
+        out[...] = self.lane[lane]["out"]
+
+    def close(self):
+        pass
 
 
 class _Server(serving.Server):
-    """The server with fake slots; records the budget state at every launch."""
+    """The server over the fake context; records the budget state at every launch."""
 
-    def __init__(self, n_slots, mem_budget, workspace, cache_sets):
-        self.torch = _Torch()
+    def __init__(self, n_slots, mem_budget, cache_sets):
         self.precision = 2
         self.device = 0
         self.mem_budget = mem_budget
         self.cache_sets = cache_sets
         self.log = []
-        self.slots = [dict(ctx=_Ctx(self.log), stream=None, req=None, done_ev=None,
-                           cache=collections.OrderedDict(), workspace=workspace)
-                      for _ in range(n_slots)]
-        self.mem_used = n_slots * workspace
+        self.ctx = _Ctx(n_slots, self.log)
+        self.slots = [dict(lane=i, req=None) for i in range(n_slots)]
+        self.lane_bytes = [1 << 20] * n_slots
+        self.cache = {}
+        import collections
+        self.cache = collections.OrderedDict()
+        self.free_index = list(range(4095, -1, -1))
+        self.loads = 0
         self.launches = []
 
     def _launch(self, slot, req, now):
         running = sum(1 for s in self.slots if s["req"] is not None)
-        self.torch.next_polls = 2 + (req.id % 5)
-        fits = self._fits(req)
+        self.ctx.next_polls = 2 + (req.id % 5)
+        fits = self.mem_used() + self._need(req) <= self.mem_budget
         super()._launch(slot, req, now)
-        self.launches.append((req.id, running, fits, self.mem_used))
+        in_use = {s["req"].set_id for s in self.slots if s["req"] is not None}
+        self.launches.append((req.id, running, fits, self.mem_used(), in_use))
 
 
 def _requests(n, n_sets=3, seed=0):
@@ -119,49 +100,71 @@ def _requests(n, n_sets=3, seed=0):
     return reqs
 
 
+def _loads(srv):
+    return [pid for kind, pid, _ in srv.log if kind == "load"]
+
+
 def test_every_request_gets_its_own_result_in_arrival_order():
     reqs = _requests(30)
-    big = max(r.footprint(2) for r in reqs)
-    srv = _Server(n_slots=3, mem_budget=3 * (1 << 20) + 2 * big + 3 * 50_000, workspace=1 << 20, cache_sets=2)
+    srv = _Server(n_slots=3, mem_budget=1 << 40, cache_sets=8)
     srv.run(reqs, idle_sleep=0.0)
     for r in reqs:
         assert r.t_done is not None and r.omega is not None
         np.testing.assert_array_equal(r.omega, _result(r.pw, r.E))
-    # first come, first admitted
     order = [rid for rid, *_ in srv.launches]
     assert order == sorted(order)
-    # requests overlapped on the slots
-    assert max(running for _, running, _, _ in srv.launches) >= 1
-    # a launch either fitted the budget or ran alone
-    for _, running, fits, _ in srv.launches:
-        assert fits or running == 0
+    assert max(running for _, running, *_ in srv.launches) >= 1
+    # one shared cache: every set loaded exactly once though all lanes use them
+    assert len(_loads(srv)) == len({r.set_id for r in reqs})
 
 
-def test_budget_forces_one_at_a_time_and_bytes_are_returned():
+def test_budget_forces_one_at_a_time_and_bytes_are_exact():
     reqs = _requests(12, seed=1)
-    small = min(r.footprint(2) for r in reqs)
-    srv = _Server(n_slots=4, mem_budget=4 * (1 << 20) + small // 2, workspace=1 << 20, cache_sets=1)
+    lanes = 4 * (1 << 20)
+    smallest = min(serving.estimate_set_bytes(r.pw, 2) for r in reqs)
+    srv = _Server(n_slots=4, mem_budget=lanes + smallest // 2, cache_sets=1)
     srv.run(reqs, idle_sleep=0.0)
-    assert all(running == 0 for _, running, _, _ in srv.launches)
-    # only the cached pole sets stay accounted once everything is done
-    cached = sum(v["bytes"] for s in srv.slots for v in s["cache"].values())
-    assert srv.mem_used == 4 * (1 << 20) + cached
+    for _, running, fits, _, _ in srv.launches:
+        assert fits or running == 0
+    # after the run only the lanes and the resident sets are accounted, by
+    # the bytes the context reports
+    resident = sum(srv.ctx.pw_bytes(c["pw_index"]) for c in srv.cache.values())
+    assert srv.mem_used() == lanes + resident
     for r in reqs:
         np.testing.assert_array_equal(r.omega, _result(r.pw, r.E))
 
 
-def test_pole_set_cache_evicts_least_recently_used():
-    # one slot, room for two sets: A B A C A B -> C evicts B (least recent),
+def test_pole_set_cache_evicts_least_recently_used_and_never_a_set_in_use():
+    # one lane, room for two sets: A B A C A B -> C evicts B (least recent),
     # A stays, B is loaded again and evicts C
     pws = {}
     for r in _requests(40, n_sets=3, seed=3):
         pws.setdefault(r.set_id, r.pw)
     order = [0, 1, 0, 2, 0, 1]
     reqs = [serving.Request(i, sid, pws[sid], np.linspace(0.1, 1.0, 5), 0) for i, sid in enumerate(order)]
-    srv = _Server(n_slots=1, mem_budget=1 << 40, workspace=1 << 20, cache_sets=2)
+    srv = _Server(n_slots=1, mem_budget=1 << 40, cache_sets=2)
     srv.run(reqs, idle_sleep=0.0)
-    loads = [pw_id for kind, pw_id, _ in srv.log if kind == "load"]
-    assert loads == [id(pws[0]), id(pws[1]), id(pws[2]), id(pws[1])]
-    assert list(srv.slots[0]["cache"].keys()) == [0, 1]
+    assert _loads(srv) == [id(pws[0]), id(pws[1]), id(pws[2]), id(pws[1])]
+    assert list(srv.cache.keys()) == [0, 1]
+    # with several lanes, a set some lane is solving is never unloaded
+    reqs = _requests(40, n_sets=3, seed=4)
+    srv = _Server(n_slots=3, mem_budget=1 << 40, cache_sets=2)
+    srv.run(reqs, idle_sleep=0.0)
+    for _, _, _, _, in_use in srv.launches:
+        assert len(in_use) <= 2
+    unloaded_while_used = [e for e in srv.log if e[0] == "unload" and
+                           any(e[2] == s.get("cache", {}).get("pw_index") for s in srv.slots if s["req"])]
+    assert not unloaded_while_used
     for r in reqs:
         np.testing.assert_array_equal(r.omega, _result(r.pw, r.E))
+
+
+def test_prepare_sizes_every_lane_for_the_largest_request():
+    reqs = _requests(20, n_sets=3, seed=5)
+    srv = _Server(n_slots=3, mem_budget=1 << 40, cache_sets=8)
+    srv.prepare(reqs)
+    big = max(reqs, key=lambda r: (r.pw["W"].shape[0], r.E.size))
+    n_e = max(r.E.size for r in reqs)
+    assert sorted(l for l, _, _ in srv.ctx.reserved) == [0, 1, 2]
+    assert all(ne == n_e for _, _, ne in srv.ctx.reserved)
+    assert _loads(srv) == [id(big.pw)]
