@@ -267,8 +267,8 @@ def run_serving(args, prec):
         return out
 
     def serve(precision, sp_, reqs):
-        srv = serving.Server(n_slots=4, precision=precision, solve_precision=sp_, mem_budget=96 << 30,
-                             lane_workspace=4 << 30, cache_sets=64)
+        srv = serving.Server(n_slots=4, precision=precision, solve_precision=sp_, mem_budget=120 << 30,
+                             lane_workspace=16 << 30, cache_sets=64)
         try:
             srv.prepare(reqs)
             warm = [serving.Request(-1 - i, r.set_id, r.pw, r.E[:64], r.mode, 0.0) for i, r in enumerate(reqs[:4])]
@@ -315,6 +315,111 @@ def run_serving(args, prec):
             "omega_rel_err_vs_fp64": {"median": float(np.median(rel)), "p99": float(np.quantile(rel, 0.99)),
                                       "max": float(rel.max()), "energies": int(rel.size)},
             "formation": "bf16x3", "matching": "fp32"}
+
+
+def run_batched(args):
+    """The batched workload: 40 partial waves of 20-400 channels (30 poles per
+    channel, z = 3) on 10000 energies over 0-5 Ry, mixed precision (bf16x3
+    formation chosen per wave by the autotuner, FP32 matching), solved by
+    rm_solve_batch over 4 lanes and replayed as one captured CUDA graph, against
+    the same waves one rm_solve_energies call after another on one lane; and
+    the FP64 batch on every 200th energy for the Omega error."""
+    import torch
+
+    from paper_1909_07321_gb300 import rmgb, synth
+    pws, E = synth.workload_batched()
+    ns = np.array([pw["W"].shape[0] for pw in pws])
+    Ed = torch.tensor(E, dtype=torch.float64, device="cuda")
+    ids = list(range(len(pws)))
+    out = {"workload": ("%d partial waves, %d-%d channels (sum %d), 30 poles per channel, z = 3, "
+                        "%d energies on 0-5 Ry, 100 levels" % (len(pws), ns.min(), ns.max(), ns.sum(), E.size))}
+    ctx = rmgb.Context(precision=2, solve_precision=1, lanes=4, autotune=1, mem_budget=8 << 30, stream=0)
+    try:
+        t0 = time.perf_counter()
+        for i, pw in enumerate(pws):
+            ctx.load_pw(i, pw)
+        load_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ctx.solve_batch(ids, Ed, 0, True)          # tunes, runs eagerly, captures
+        ctx.sync()
+        first_s = time.perf_counter() - t0
+        st = torch.cuda.Stream()
+        reps = 2
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ctx.reset_omega()
+        torch.cuda.synchronize()
+        lane0 = torch.cuda.ExternalStream(ctx.lane_stream(0))
+        ev[0].record(lane0)
+        for _ in range(reps):
+            ctx.solve_batch(ids, Ed, 0, True)      # graph replays
+        ev[1].record(lane0)
+        torch.cuda.synchronize()
+        t_batch = ev[0].elapsed_time(ev[1]) / reps / 1e3
+        om_batch = ctx.collision_strengths() / reps
+        info = [ctx.autotune_info(i) for i in ids]
+        del st
+    finally:
+        ctx.close()
+    choice = {}
+    for f, tn, stg, _ in info:
+        k = "pairs %dx%d/%d stages" % (128, tn, stg) if f == 1 else "per-energy"
+        choice[k] = choice.get(k, 0) + 1
+    # the same waves one call after another on one lane (same tuned choices)
+    ctx = rmgb.Context(precision=2, solve_precision=1, autotune=1, mem_budget=8 << 30, stream=0)
+    try:
+        for i, pw in enumerate(pws):
+            ctx.load_pw(i, pw)
+        for i in ids:
+            ctx.solve_energies(i, Ed[:2048])    # the batch's tuner bucket: the same choices
+        ctx.collision_strengths(reset=True)
+        lane0 = torch.cuda.ExternalStream(ctx.lane_stream(0))
+        torch.cuda.synchronize()
+        ev[0].record(lane0)
+        for i in ids:
+            ctx.solve_energies(i, Ed)
+        ev[1].record(lane0)
+        torch.cuda.synchronize()
+        t_seq = ev[0].elapsed_time(ev[1]) / 1e3
+        om_seq = ctx.collision_strengths()
+    finally:
+        ctx.close()
+    # FP64 batch on every 200th energy
+    sub = np.arange(0, E.size, 200)
+    ctx = rmgb.Context(precision=0, lanes=4, mem_budget=8 << 30, stream=0)
+    try:
+        for i, pw in enumerate(pws):
+            ctx.load_pw(i, pw)
+        Es = torch.tensor(E[sub], dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve_batch(ids, Es, 0, False)
+        om64 = ctx.collision_strengths()
+        t64 = time.perf_counter() - t0
+    finally:
+        ctx.close()
+    nrm = np.linalg.norm(om64, axis=1)
+    ok = nrm > 0
+    rel = np.linalg.norm(om_batch[sub][ok] - om64[ok], axis=1) / nrm[ok]
+    n_es = len(pws) * E.size
+    out.update({"batched_graph": {"energy_solves_per_s": n_es / t_batch, "s": t_batch,
+                                  "timing": "CUDA events on lane 0 around %d graph replays" % reps},
+                "one_call_per_wave": {"energy_solves_per_s": n_es / t_seq, "s": t_seq},
+                "speedup": t_seq / t_batch,
+                "omega_batch_vs_sequential_rel": _dist(np.linalg.norm(om_batch - om_seq, axis=1) /
+                                                       np.maximum(np.linalg.norm(om_seq, axis=1), 1e-300)),
+                "first_call_s": first_s, "load_s": load_s,
+                "autotune_choices": choice,
+                "fp64_batch": {"energy_solves_per_s": len(pws) * sub.size / t64, "energies": int(sub.size)},
+                "omega_rel_err_vs_fp64": _dist(rel),
+                "worst_energy_vs_fp64": {"E_ry": float(E[sub][ok][int(np.argmax(rel))]),
+                                         "omega_norm_over_median": float(nrm[ok][int(np.argmax(rel))] /
+                                                                         np.median(nrm[ok]))}})
+    return out
+
+
+def _dist(x):
+    x = np.asarray(x)
+    return {"median": float(np.median(x)), "p99": float(np.quantile(x, 0.99)), "max": float(x.max())}
 
 
 def _pe_tiles(n):
@@ -618,6 +723,9 @@ def run_ours(args, rank, world, local_rank):
     wide = None
     if world == 1 and args.wide_energies > 0:
         wide = _leg(run_wide, args, prec if prec != 0 else 2, sp, stream, flush, peaks, peak_src)
+    batched_line = None
+    if world == 1 and args.batched:
+        batched_line = _leg(run_batched, args)
     qdt_line = None
     if world == 1 and args.qdt_ieq != 0:
         qdt_line = _leg(run_qdt, args, prec, sp)
@@ -702,6 +810,7 @@ def run_ours(args, rank, world, local_rank):
             "phases_ms_per_step": {names[p]: phase[p][1] / args.steps for p in names},
             "phase_share": share,
             "fp64_path": fp64,
+            "batched_40pw": batched_line,
             "serving": serving_line,
             "wide_1000ch": wide,
             "mqdt_interpolation": qdt_line,
@@ -737,6 +846,7 @@ def main():
                     help="node spacing of the MQDT interpolation leg (0 to skip)")
     ap.add_argument("--wide-energies", type=int, default=256,
                     help="energies of the 1000-channel leg (0 to skip)")
+    ap.add_argument("--batched", type=int, default=1, help="run the batched 40-wave leg (0 to skip)")
     ap.add_argument("--prop-energies", type=int, default=1024,
                     help="energies of the multipole-propagation leg (0 to skip)")
     ap.add_argument("--energies", type=int, default=N_E,

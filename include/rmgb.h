@@ -85,8 +85,11 @@ typedef struct rm_opts {
     void *stream;           /* cudaStream_t to enqueue on (cudaStreamLegacy for
                                the legacy default stream); NULL = a non-blocking
                                stream the context creates and owns */
-    size_t mem_budget;      /* bytes of per-call device workspace (0 = 8 GiB, at most
-                               half the free device memory) */
+    size_t mem_budget;      /* bytes of per-call device workspace of each lane (0 =
+                               32 GiB, at most half the free device memory); it sets
+                               the energies per block, and a block of fewer energies
+                               than the GPU has SMs leaves the one-CTA-per-energy
+                               solvers part of the GPU */
     double mqdt_kappa_a_max;/* MQDT: closed channels with kappa a above this keep the
                                decaying condition (default 5; eliminating them costs
                                ~exp(2 kappa a) in precision) */
@@ -115,10 +118,24 @@ typedef struct rm_opts {
                                mixed-precision formation, 0 with FP64 (whose K is
                                meant to match to 1e-9 even where the matching
                                amplifies channel-function errors 1e4-fold) */
-    int lanes;              /* number of lanes (default 1, at most 64): independent
+    int lanes;              /* number of lanes (default 1, 0 = 1, at most 64): independent
                                streams of work in one context, each with its own
                                workspace and Omega accumulator, sharing the
                                context's partial waves (see rm_lane_solve_energies) */
+    int autotune;           /* 1: the mixed-precision formation of each partial wave
+                               (pair operand with tiles of 128 energies x 256 pairs
+                               and a 2-stage ring, 128 x 128 with 3 or 2 stages, or
+                               the per-energy GEMM) is chosen by timing every
+                               applicable candidate on the wave's first solve; the
+                               choice is kept per (operand type, channels, padded
+                               poles, energy-block size) for the whole process, so
+                               every context forms R of a wave shape the same way
+                               (rm_autotune_info reports it). 0 (default): fixed
+                               rules (pair operand up to 192 channels) */
+    int pair_tile;          /* pair-operand formation tile: 0 (default) the 128 x 256,
+                               2-stage tile or the autotuner's choice; 1, 2, 3 force
+                               128 x 256 with 2 stages, 128 x 128 with 3, 128 x 128
+                               with 2 */
 } rm_opts;
 
 #define RM_SOLVER_AUTO    0
@@ -431,6 +448,38 @@ int rm_pw_bytes(rm_ctx *ctx, int pw, size_t *bytes);
  * before use). Work already enqueued that reads it completes first
  * (cudaFree synchronises the device). Errors: RM_EINVAL, RM_ENOTLOADED. */
 int rm_unload_pw(rm_ctx *ctx, int pw);
+
+/* Batched solve of n_pw partial waves pws (host, [n_pw], distinct, all with
+ * the same n_levels) on one energy grid E (host or device, [n_E]) in `mode`,
+ * accumulating the sum over the waves of g |T|^2 into the context's Omega
+ * (lane 0's accumulator and grid, as rm_solve_energies). Partial waves are
+ * independent (Section "Computational details": the energy and partial-wave
+ * loops are the parallel ones), so the waves are spread over the context's
+ * lanes, largest first to the least-loaded lane (cost ~ n^2 (n_poles + 4 n):
+ * formation plus matching), each lane solving its waves one after another
+ * while the lanes overlap on the device; the other lanes' accumulators are
+ * then added into lane 0's in lane order, so the result is the same every
+ * call for a fixed lane count (it differs from one call per wave by the order
+ * of the additions only). With use_graph != 0 the whole launch sequence of
+ * the call (every lane, their fork and join) is also captured into a CUDA
+ * graph, and a later call with the same waves, energies, mode and
+ * accumulator replays it with one cudaGraphLaunch; a graph is dropped once
+ * any device buffer of the library has been freed or moved since it was
+ * captured. With rm_opts.autotune the formation of every wave is chosen
+ * before any capture. Lanes other than 0 have their accumulators overwritten.
+ * Per-energy statuses are not returned (an energy that fails in a wave adds
+ * nothing to Omega). Asynchronous on lane 0's stream. Errors: RM_EINVAL,
+ * RM_ENOTLOADED, RM_EGRID, RM_EUNSUPPORTED, RM_ENOMEM, RM_ECUDA. */
+int rm_solve_batch(rm_ctx *ctx, int n_pw, const int *pws, int n_E, const double *E, int mode, int use_graph);
+
+/* What the autotuner (rm_opts.autotune) chose for partial wave `pw`:
+ * formulation RM_FORM_PAIRS (tile of 128 energies x tile_n pairs, a ring of
+ * `stages`) or RM_FORM_ENERGY (tile_n = stages = 0), and ms4 (host, [4],
+ * nullable) the measured ms per energy of the candidates: pair 256 x 2, pair
+ * 128 x 3, pair 128 x 2, per-energy (-1 where not applicable or taken from
+ * an earlier choice for the same shape). Errors: RM_EINVAL (not tuned),
+ * RM_ENOTLOADED. */
+int rm_autotune_info(rm_ctx *ctx, int pw, int *formulation, int *tile_n, int *stages, double *ms4);
 
 /* Waits for all work enqueued on every lane of the context and for the
  * copies of rm_collision_strengths_async. */

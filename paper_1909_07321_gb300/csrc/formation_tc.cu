@@ -13,10 +13,10 @@
 // FP64 by the near-pole fix-up kernel.
 //
 // Kernel layout (one persistent CTA per SM, 192 threads):
-//   warp 0, one lane : TMA producer (D tile 128 x BK, P tile 256 x BK, hi and
-//                      lo, 128-byte swizzle) into a 2-stage ring,
-//   warp 1           : allocates 512 TMEM columns; one lane issues
-//                      tcgen05.mma (M = 128, N = 256) into one of two
+//   warp 0, one lane : TMA producer (D tile 128 x BK, P tile BN x BK, hi and
+//                      lo, 128-byte swizzle) into a ring of STAGES stages,
+//   warp 1           : allocates 2 BN TMEM columns; one lane issues
+//                      tcgen05.mma (M = 128, N = BN) into one of two
 //                      accumulators,
 //   warps 2..5       : epilogue; each reads its 32-lane quadrant of the
 //                      accumulator with tcgen05.ld, converts to FP64 and
@@ -33,21 +33,29 @@ namespace rmgb {
 namespace {
 
 constexpr int BM = 128;            // energies per tile (TMEM lanes)
-constexpr int BN = 256;            // pairs per tile (TMEM columns)
-constexpr int STAGES = 2;
 constexpr int NTHREADS = 192;
 constexpr int ROW_BYTES = TC_ROW_BYTES;
 constexpr int A_TILE = BM * ROW_BYTES;   // 16 KB
-constexpr int B_TILE = BN * ROW_BYTES;   // 32 KB
-constexpr int STAGE_BYTES = 2 * (A_TILE + B_TILE);   // hi + lo of both: 96 KB
-constexpr int TMEM_COLS = 512;     // two 256-column accumulators
-template <int KIND>
+
+// Tile variants (pairs per tile BN, ring depth STAGES): 256 x 2 stages (96
+// KB per stage), 128 x 3 and 128 x 2 (64 KB per stage); chosen per partial
+// wave by the context's autotuner, 256 x 2 otherwise.
+template <int BN> struct PairTile {
+    static constexpr int B_TILE = BN * ROW_BYTES;
+    static constexpr int STAGE_BYTES = 2 * (A_TILE + B_TILE);   // hi + lo of both operands
+    static constexpr int TMEM_COLS = 2 * BN;                    // two accumulators
+};
+
+template <int KIND, int BN, int STAGES>
 __global__ void __launch_bounds__(NTHREADS, 1)
     form_r_tc_kernel(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
                      const __grid_constant__ CUtensorMap tmPh, const __grid_constant__ CUtensorMap tmPl,
                      double *__restrict__ Rp, int ldR, int nE, int n_pairs, int n_kb, int n_ntiles,
                      int n_tiles, int *err_flag)
 {
+    constexpr int B_TILE = PairTile<BN>::B_TILE;
+    constexpr int STAGE_BYTES = PairTile<BN>::STAGE_BYTES;
+    constexpr int TMEM_COLS = PairTile<BN>::TMEM_COLS;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte alignment for the 128-byte swizzle atoms
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -381,36 +389,60 @@ cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delt
     return cudaGetLastError();
 }
 
-cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
-                             const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
-                             int *err_flag, cudaStream_t s)
+namespace {
+
+template <int KIND, int BN, int STAGES>
+cudaError_t launch_pair_variant(const void *D_hi, const void *D_lo, const void *P_hi, const void *P_lo, int nE,
+                                int n_pairs, int Kpad, double *Rp, int ldR, int *err_flag, cudaStream_t s)
 {
-    if (nE == 0) return cudaSuccess;
     CUtensorMap mDh, mDl, mPh, mPl;
-    if (!make_map(&mDh, D_hi, kind, Kpad, nE, BM) || !make_map(&mDl, D_lo, kind, Kpad, nE, BM) ||
-        !make_map(&mPh, P_hi, kind, Kpad, n_pairs, BN) || !make_map(&mPl, P_lo, kind, Kpad, n_pairs, BN))
+    if (!make_map(&mDh, D_hi, KIND, Kpad, nE, BM) || !make_map(&mDl, D_lo, KIND, Kpad, nE, BM) ||
+        !make_map(&mPh, P_hi, KIND, Kpad, n_pairs, BN) || !make_map(&mPl, P_lo, KIND, Kpad, n_pairs, BN))
         return cudaErrorInvalidValue;
-    const int bk = ROW_BYTES / ((kind == TC_BF16X3) ? 2 : 4);
+    const int bk = ROW_BYTES / ((KIND == TC_BF16X3) ? 2 : 4);
     const int n_kb = Kpad / bk;
     const int n_mt = (nE + BM - 1) / BM, n_nt = (n_pairs + BN - 1) / BN;
     const int n_tiles = n_mt * n_nt;
     const int grid = n_tiles < num_sms() ? n_tiles : num_sms();
-    const size_t smem = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-    cudaError_t e;
-    if (kind == TC_BF16X3) {
-        e = cudaFuncSetAttribute(form_r_tc_kernel<TC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        form_r_tc_kernel<TC_BF16X3><<<grid, NTHREADS, smem, s>>>(mDh, mDl, mPh, mPl, Rp, ldR, nE, n_pairs,
-                                                                 n_kb, n_nt, n_tiles, err_flag);
-    } else {
-        e = cudaFuncSetAttribute(form_r_tc_kernel<TC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        form_r_tc_kernel<TC_TF32X3><<<grid, NTHREADS, smem, s>>>(mDh, mDl, mPh, mPl, Rp, ldR, nE, n_pairs,
-                                                                 n_kb, n_nt, n_tiles, err_flag);
-    }
+    const size_t smem = (size_t)STAGES * PairTile<BN>::STAGE_BYTES + 1024 + 256;
+    cudaError_t e = cudaFuncSetAttribute(form_r_tc_kernel<KIND, BN, STAGES>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    form_r_tc_kernel<KIND, BN, STAGES><<<grid, NTHREADS, smem, s>>>(mDh, mDl, mPh, mPl, Rp, ldR, nE, n_pairs,
+                                                                    n_kb, n_nt, n_tiles, err_flag);
     return cudaGetLastError();
+}
+
+template <int KIND>
+cudaError_t launch_pair(int variant, const void *D_hi, const void *D_lo, const void *P_hi, const void *P_lo, int nE,
+                        int n_pairs, int Kpad, double *Rp, int ldR, int *err_flag, cudaStream_t s)
+{
+    switch (variant) {
+    case 1: return launch_pair_variant<KIND, 128, 3>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
+    case 2: return launch_pair_variant<KIND, 128, 2>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
+    default: return launch_pair_variant<KIND, 256, 2>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
+    }
+}
+
+}  // namespace
+
+int tc_pair_variants() { return 3; }
+
+void tc_pair_variant_shape(int variant, int *tile_n, int *stages)
+{
+    *tile_n = variant == 0 ? 256 : 128;
+    *stages = variant == 1 ? 3 : 2;
+}
+
+cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
+                             const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
+                             int *err_flag, cudaStream_t s, int variant)
+{
+    if (nE == 0) return cudaSuccess;
+    if (variant < 0 || variant >= tc_pair_variants()) return cudaErrorInvalidValue;
+    if (kind == TC_BF16X3)
+        return launch_pair<TC_BF16X3>(variant, D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
+    return launch_pair<TC_TF32X3>(variant, D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
 }
 
 size_t near_pole_ws_bytes(int nE) { return 16 + (size_t)nE * (sizeof(int) + sizeof(int2)); }

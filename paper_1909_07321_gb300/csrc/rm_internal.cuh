@@ -176,10 +176,14 @@ cudaError_t launch_split_p(const PwDev &pw, int kind, int Kpad, void *P_hi, void
 // pw.Ek_hl must be set; e_hl: nE float2 of scratch (E as hi + lo floats).
 cudaError_t launch_split_d(const PwDev &pw, const double *E, int nE, double delta, int kind, int Kpad,
                            void *D_hi, void *D_lo, float2 *e_hl, cudaStream_t s);
-// R_packed[e][p] = sum_k D[e][k] P[p][k] over the three hi/lo products.
+// R_packed[e][p] = sum_k D[e][k] P[p][k] over the three hi/lo products;
+// variant: tile of 128 energies x tile_n pairs with a ring of `stages`
+// (tc_pair_variant_shape), 0 <= variant < tc_pair_variants().
+int tc_pair_variants();
+void tc_pair_variant_shape(int variant, int *tile_n, int *stages);
 cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
                              const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
-                             int *err_flag, cudaStream_t s);
+                             int *err_flag, cudaStream_t s, int variant = 0);
 // R_packed[e][p] += (1/2a) w_ik w_jk / (E_k - E_e) over poles with |E_k - E_e| < delta (FP64),
 // the near/far decision taken exactly as launch_split_d takes it (pw.Ek_hl).
 // ws: near_pole_ws_bytes(nE) bytes of device scratch (list of the energies

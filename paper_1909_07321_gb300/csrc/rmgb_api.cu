@@ -7,12 +7,16 @@
 //   near-pole check -> channel functions -> R formation -> matching + T + Omega
 // on the context stream, with no host synchronisation.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -26,12 +30,20 @@ constexpr int MAX_PW = 4096;
 constexpr int MAX_L = 64;
 constexpr int MAX_BLOCK_E = 32768;
 
+// Bumped whenever any device buffer of the library is freed or moved: a
+// captured CUDA graph (rm_solve_batch) holds raw pointers and is replayed
+// only while the generation it was captured under is current.
+std::atomic<unsigned long long> g_buf_gen{1};
+
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            cudaFree(p);
+            g_buf_gen.fetch_add(1);
+        }
         p = nullptr;
         bytes = 0;
     }
@@ -63,6 +75,12 @@ struct PwHost {
     // per-energy formulation: W in FP32 and w split hi/lo (built on first use)
     DevBuf W32, Wh, Wl;
     int w_kind = -1;
+    // formation chosen by the autotuner (rm_opts.autotune): formulation and
+    // pair-kernel tile variant, and the measured ms per energy of every
+    // candidate (-1: not applicable)
+    bool tuned = false;
+    int tune_form = 0, tune_var = 0;
+    double tune_ms[4] = {-1.0, -1.0, -1.0, -1.0};
     std::vector<double> h_e_thr, h_Ek;   // host copies (thresholds, sorted poles)
     std::vector<int> h_l;
     // near-threshold interpolation tables (z > 0), built when the wave has
@@ -103,6 +121,7 @@ struct PwHost {
         loaded = channels = false;
         p_kind = -1;
         w_kind = -1;
+        tuned = false;
     }
     PwDev dev() const
     {
@@ -201,10 +220,30 @@ constexpr int MAX_LANES = 64;
 
 }  // namespace
 
+namespace {
+
+// One captured batch (rm_solve_batch): its arguments, the device pointers it
+// was captured with, the buffer generation, the executable graph and the
+// kernel launches it holds.
+struct BatchGraph {
+    std::vector<int> pws;
+    int n_E = 0, mode = 0, lanes = 0;
+    const double *E = nullptr;
+    const void *omega = nullptr;
+    unsigned long long gen = 0;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+};
+
+}  // namespace
+
 struct rm_ctx {
     rm_opts opts;
     std::vector<PwHost> pw;
     std::vector<Lane> lanes;
+    std::vector<BatchGraph> graphs;
+    DevBuf batchE;                 // host energies of rm_solve_batch, at a stable address
+    cudaEvent_t ev_batch = nullptr;
     long long launches = 0;
     // per-phase event pairs (tracing)
     bool prof = false;
@@ -331,6 +370,8 @@ extern "C" void rm_default_opts(rm_opts *o)
     o->formulation = RM_FORM_AUTO;
     o->solve_precision = RM_FP64;
     o->channel_tables = -1;
+    o->lanes = 1;
+    o->autotune = 0;
 }
 
 extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
@@ -355,11 +396,13 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
     }
     if (o.mem_budget == 0) {
         size_t fr = 0, tot = 0;
-        o.mem_budget = (size_t)8 << 30;
+        o.mem_budget = (size_t)32 << 30;
         if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && fr / 2 < o.mem_budget) o.mem_budget = fr / 2;
         cudaGetLastError();
     }
     if (o.lanes == 0) o.lanes = 1;
+    if (o.autotune != 0 && o.autotune != 1) return RM_EINVAL;
+    if (o.pair_tile < 0 || o.pair_tile > tc_pair_variants()) return RM_EINVAL;
     if (o.lanes < 1 || o.lanes > MAX_LANES) return RM_EINVAL;
     rm_ctx *ctx = new (std::nothrow) rm_ctx();
     if (!ctx) return RM_ENOMEM;
@@ -386,6 +429,11 @@ extern "C" int rm_create(rm_ctx **out, const rm_opts *opts)
             return RM_ECUDA;
         }
     }
+    if (cudaEventCreateWithFlags(&ctx->ev_batch, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        rm_destroy(ctx);
+        return RM_ECUDA;
+    }
     *out = ctx;
     return RM_SUCCESS;
 }
@@ -400,6 +448,10 @@ extern "C" void rm_destroy(rm_ctx *ctx)
         if (l.copy) cudaStreamSynchronize(l.copy);
     }
     for (auto &p : ctx->pw) p.release();
+    for (BatchGraph &g : ctx->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    ctx->batchE.release();
+    if (ctx->ev_batch) cudaEventDestroy(ctx->ev_batch);
     for (Lane &l : ctx->lanes) {
         Lane *ln = &l;
         if (ln->copy) cudaStreamDestroy(ln->copy);
@@ -663,6 +715,7 @@ int formulation(rm_ctx *ctx, const PwHost &P)
 {
     if (ctx->opts.precision == RM_FP64) return 0;
     if (ctx->opts.formulation != RM_FORM_AUTO) return ctx->opts.formulation;
+    if (P.tuned) return P.tune_form;
     const int kind = tc_kind(ctx->opts.precision);
     return (P.n <= AUTO_PAIRS_MAX_N && pair_operand_bytes(P, kind) <= MAX_P_BYTES) ? RM_FORM_PAIRS
                                                                                    : RM_FORM_ENERGY;
@@ -776,7 +829,8 @@ int form_r_block(rm_ctx *ctx, Lane *ln, PwHost &P, const double *E, int nE, doub
     CK(prof_end(ctx, RM_PH_SPLIT, st));
     CK(prof_begin(ctx, RM_PH_FORM, st));
     CK(launch_form_r_tc(kind, ln->wsDh.p, ln->wsDl.p, P.Ph.p, P.Pl.p, nE, tri_count(P.n), Kpad, R,
-                        tri_ld(P.n), ln->wsErr.as<int>(), st));
+                        tri_ld(P.n), ln->wsErr.as<int>(), st,
+                        ctx->opts.pair_tile > 0 ? ctx->opts.pair_tile - 1 : (P.tuned ? P.tune_var : 0)));
     CK(prof_end(ctx, RM_PH_FORM, st));
     CK(prof_begin(ctx, RM_PH_FIXUP, st));
     CK(ln->wsNear.reserve(near_pole_ws_bytes(nE)));
@@ -852,6 +906,90 @@ int reserve_solve(rm_ctx *ctx, Lane *ln, PwHost &P, int n_E)
         CK(ln->wsNear.reserve(near_pole_ws_bytes(B)));
     }
     CK(cudaStreamSynchronize(ln->stream));
+    return RM_SUCCESS;
+}
+
+// Process-wide autotuner choices: (operand type, channels, padded poles,
+// energy-block bucket) -> (formulation, pair tile variant).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+
+// Candidate index of a (formulation, variant): pair variants 0..2, per-energy 3.
+int tune_slot(int form, int var) { return form == RM_FORM_PAIRS ? var : 3; }
+
+// Chooses the formation of wave P by timing every applicable candidate on the
+// first min(n_E, 2048) energies dE (CUDA events on the lane's stream, one
+// warm-up and two timed formations each), or takes the process-wide choice
+// for its shape. Operands of the candidates not chosen are freed.
+int tune_wave(rm_ctx *ctx, Lane *ln, PwHost &P, const double *dE, int n_E)
+{
+    const int kind = tc_kind(ctx->opts.precision);
+    const int Kpad = tc_kpad(P.N, kind);
+    const int nb = std::min(n_E, 2048);
+    int bucket = 1;
+    while (bucket < nb) bucket <<= 1;
+    const auto key = std::make_tuple(kind, P.n, Kpad, bucket);
+    std::vector<std::pair<int, int>> cand;
+    if (pair_operand_bytes(P, kind) <= MAX_P_BYTES)
+        for (int v = 0; v < tc_pair_variants(); ++v) cand.push_back({RM_FORM_PAIRS, v});
+    if (P.n <= pe_max_n()) cand.push_back({RM_FORM_ENERGY, 0});
+    if (cand.empty()) return RM_SUCCESS;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            P.tuned = true;
+            P.tune_form = it->second.first;
+            P.tune_var = it->second.second;
+            return RM_SUCCESS;
+        }
+    }
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    CK(ln->wsR.reserve((size_t)nb * tri_ld(P.n) * sizeof(double)));
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    int best = -1;
+    double best_ms = 0.0;
+    int rc = RM_SUCCESS;
+    for (int c = 0; c < (int)cand.size() && rc == RM_SUCCESS; ++c) {
+        P.tuned = true;
+        P.tune_form = cand[c].first;
+        P.tune_var = cand[c].second;
+        rc = form_r_block(ctx, ln, P, dE, nb, ln->wsR.as<double>());
+        if (rc) break;
+        cudaEventRecord(a, ln->stream);
+        for (int r = 0; r < 2 && rc == RM_SUCCESS; ++r) rc = form_r_block(ctx, ln, P, dE, nb, ln->wsR.as<double>());
+        cudaEventRecord(b, ln->stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) rc = fail(ctx, RM_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        const double per = ms / (2.0 * nb);
+        P.tune_ms[tune_slot(cand[c].first, cand[c].second)] = per;
+        if (best < 0 || per < best_ms) {
+            best = c;
+            best_ms = per;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->prof = prof;
+    if (rc) return rc;
+    P.tune_form = cand[best].first;
+    P.tune_var = cand[best].second;
+    if (P.tune_form != RM_FORM_PAIRS) {
+        P.Ph.release();
+        P.Pl.release();
+        P.p_kind = -1;
+    } else {
+        P.W32.release();
+        P.Wh.release();
+        P.Wl.release();
+        P.w_kind = -1;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = {P.tune_form, P.tune_var};
     return RM_SUCCESS;
 }
 
@@ -1019,6 +1157,10 @@ int solve_on_lane(rm_ctx *ctx, int lane, int pw, int n_E, const double *E, int m
     const double *dE;
     rc = device_energies(ctx, ln, n_E, E, &dE);
     if (rc) return rc;
+    if (ctx->opts.autotune && ctx->opts.precision != RM_FP64 && ctx->opts.formulation == RM_FORM_AUTO && !P.tuned) {
+        rc = tune_wave(ctx, ln, P, dE, n_E);
+        if (rc) return rc;
+    }
     int *dstatus = status_out;
     if (!dstatus) {
         CK(ln->wsStatus.reserve((size_t)n_E * sizeof(int)));
@@ -1391,6 +1533,204 @@ extern "C" int rm_unload_pw(rm_ctx *ctx, int pw)
     if (rc) return rc;
     CK(cudaSetDevice(ctx->opts.device));
     ctx->pw[pw].release();
+    return RM_SUCCESS;
+}
+
+namespace {
+
+struct OmegaSrc {
+    const double *p[MAX_LANES];
+};
+
+// dst += src[0] + src[1] + ... (in lane order: the same rounding every call)
+__global__ void omega_sum_kernel(double *dst, OmegaSrc src, int n_src, size_t count)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+        double v = dst[i];
+        for (int l = 0; l < n_src; ++l) v += src.p[l][i];
+        dst[i] = v;
+    }
+}
+
+// The launch sequence of one batch: lanes 1.. fork from lane 0, zero their
+// accumulators, solve their waves in order, and join; lane 0 adds their
+// Omega to its own.
+int enqueue_batch(rm_ctx *ctx, const std::vector<std::vector<int>> &assign, const double *dE, int n_E, int mode,
+                  int ntri)
+{
+    Lane *l0 = &ctx->lanes[0];
+    const int L = (int)assign.size();
+    const size_t count = (size_t)n_E * ntri;
+    CK(cudaEventRecord(ctx->ev_batch, l0->stream));
+    for (int l = 1; l < L; ++l) {
+        Lane *ln = &ctx->lanes[l];
+        CK(cudaStreamWaitEvent(ln->stream, ctx->ev_batch, 0));
+        CK(cudaMemsetAsync(ln->omega.p, 0, count * sizeof(double), ln->stream));
+    }
+    for (int l = 0; l < L; ++l) {
+        Lane *ln = &ctx->lanes[l];
+        for (int w : assign[l]) {
+            CK(cudaMemsetAsync(ln->wsStatus.p, 0, (size_t)n_E * sizeof(int), ln->stream));
+            const int rc = solve_blocks(ctx, ln, ctx->pw[w], dE, n_E, mode, nullptr, nullptr, ln->wsStatus.as<int>(),
+                                        ln->omega.as<double>());
+            if (rc) return rc;
+        }
+    }
+    if (L > 1) {
+        OmegaSrc src = {};
+        for (int l = 1; l < L; ++l) {
+            Lane *ln = &ctx->lanes[l];
+            CK(cudaEventRecord(ln->ev_done, ln->stream));
+            CK(cudaStreamWaitEvent(l0->stream, ln->ev_done, 0));
+            src.p[l - 1] = ln->omega.as<double>();
+        }
+        const unsigned grid = (unsigned)std::min<size_t>((count + 255) / 256, 4096);
+        omega_sum_kernel<<<grid, 256, 0, l0->stream>>>(l0->omega.as<double>(), src, L - 1, count);
+        CK(cudaGetLastError());
+        ctx->launches++;
+    }
+    return RM_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" int rm_solve_batch(rm_ctx *ctx, int n_pw, const int *pws, int n_E, const double *E, int mode,
+                              int use_graph)
+{
+    if (!ctx) return RM_EINVAL;
+    if (n_pw <= 0 || !pws || n_E <= 0 || !E)
+        return fail(ctx, RM_EINVAL, "n_pw=%d, n_E=%d must be > 0 with non-NULL arrays", n_pw, n_E);
+    if (mode != RM_DIRECT && mode != RM_MQDT) return fail(ctx, RM_EINVAL, "mode %d", mode);
+    for (int i = 0; i < n_pw; ++i) {
+        int rc = check_pw(ctx, pws[i], true);
+        if (rc) return rc;
+        for (int j = 0; j < i; ++j)
+            if (pws[j] == pws[i]) return fail(ctx, RM_EINVAL, "partial wave %d listed twice", pws[i]);
+        PwHost &P = ctx->pw[pws[i]];
+        if (P.n_levels != ctx->pw[pws[0]].n_levels)
+            return fail(ctx, RM_EINVAL, "partial waves %d and %d have different level counts", pws[0], pws[i]);
+        if (!use_large(ctx, P) && P.n > solve_small_max_n())
+            return fail(ctx, RM_EUNSUPPORTED, "n_ch=%d above the shared-memory solver limit %d", P.n,
+                        solve_small_max_n());
+        rc = check_precision(ctx, P);
+        if (rc) return rc;
+    }
+    CK(cudaSetDevice(ctx->opts.device));
+    Lane *l0 = &ctx->lanes[0];
+    PwHost &P0 = ctx->pw[pws[0]];
+    const bool dev_in = is_device_ptr(E);
+    int rc = register_grid(ctx, l0, P0, n_E, E, dev_in);
+    if (rc) return rc;
+    const double *dE = E;
+    if (!dev_in) {
+        if (!finite_all(E, n_E)) return fail(ctx, RM_EINVAL, "non-finite energy");
+        CK(ctx->batchE.reserve((size_t)n_E * sizeof(double)));
+        CK(cudaMemcpyAsync(ctx->batchE.p, E, (size_t)n_E * sizeof(double), cudaMemcpyHostToDevice, l0->stream));
+        dE = ctx->batchE.as<double>();
+    }
+    const int ntri = P0.n_levels * (P0.n_levels + 1) / 2;
+    // the formation of every wave is chosen before anything is captured
+    if (ctx->opts.autotune && ctx->opts.precision != RM_FP64 && ctx->opts.formulation == RM_FORM_AUTO)
+        for (int i = 0; i < n_pw; ++i)
+            if (!ctx->pw[pws[i]].tuned) {
+                rc = tune_wave(ctx, l0, ctx->pw[pws[i]], dE, n_E);
+                if (rc) return rc;
+            }
+    // longest processing time first: each wave (cost ~ formation n^2 N plus
+    // matching n^3) goes to the lane with the least work so far
+    const int L = std::min((int)ctx->lanes.size(), n_pw);
+    std::vector<int> order(n_pw);
+    std::iota(order.begin(), order.end(), 0);
+    auto cost = [&](int i) {
+        const PwHost &P = ctx->pw[pws[i]];
+        return (double)P.n * P.n * ((double)P.N + 4.0 * P.n);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<std::vector<int>> assign(L);
+    std::vector<double> load(L, 0.0);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        assign[l].push_back(pws[i]);
+        load[l] += cost(i);
+    }
+    for (int l = 0; l < L; ++l) {
+        Lane *ln = &ctx->lanes[l];
+        for (int w : assign[l]) {
+            rc = reserve_solve(ctx, ln, ctx->pw[w], n_E);
+            if (rc) return rc;
+        }
+        CK(ln->wsStatus.reserve((size_t)n_E * sizeof(int)));
+        CK(ln->omega.reserve((size_t)n_E * ntri * sizeof(double)));
+    }
+    const bool graphs = use_graph && !ctx->prof && l0->stream != nullptr && l0->stream != cudaStreamLegacy &&
+                        l0->stream != cudaStreamPerThread;
+    const std::vector<int> key(pws, pws + n_pw);
+    if (graphs) {
+        const unsigned long long gen = g_buf_gen.load();
+        for (size_t g = 0; g < ctx->graphs.size(); ++g) {
+            BatchGraph &bg = ctx->graphs[g];
+            const bool same = bg.pws == key && bg.n_E == n_E && bg.mode == mode && bg.E == dE &&
+                              bg.omega == l0->omega.p && bg.lanes == L;
+            if (!same) continue;
+            if (bg.gen == gen) {
+                CK(cudaGraphLaunch(bg.exec, l0->stream));
+                ctx->launches += bg.launches;
+                CK(cudaEventRecord(l0->ev_done, l0->stream));
+                return RM_SUCCESS;
+            }
+            cudaGraphExecDestroy(bg.exec);   // captured under buffers since freed or moved
+            ctx->graphs.erase(ctx->graphs.begin() + g);
+            break;
+        }
+    }
+    const long long before = ctx->launches;
+    rc = enqueue_batch(ctx, assign, dE, n_E, mode, ntri);
+    if (rc) return rc;
+    CK(cudaEventRecord(l0->ev_done, l0->stream));
+    const long long nl = ctx->launches - before;
+    if (graphs) {
+        // the same sequence captured (not run) for later calls with these arguments
+        const unsigned long long gen = g_buf_gen.load();
+        CK(cudaStreamBeginCapture(l0->stream, cudaStreamCaptureModeRelaxed));
+        const int crc = enqueue_batch(ctx, assign, dE, n_E, mode, ntri);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(l0->stream, &g);
+        ctx->launches = before + nl;
+        if (crc == RM_SUCCESS && ce == cudaSuccess && g && g_buf_gen.load() == gen) {
+            cudaGraphExec_t ex = nullptr;
+            if (cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+                BatchGraph bg;
+                bg.pws = key;
+                bg.n_E = n_E;
+                bg.mode = mode;
+                bg.lanes = L;
+                bg.E = dE;
+                bg.omega = l0->omega.p;
+                bg.gen = gen;
+                bg.exec = ex;
+                bg.launches = nl;
+                ctx->graphs.push_back(bg);
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+    }
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_autotune_info(rm_ctx *ctx, int pw, int *formulation, int *tile_n, int *stages, double *ms4)
+{
+    const int rc = check_pw(ctx, pw, false);
+    if (rc) return rc;
+    const PwHost &P = ctx->pw[pw];
+    if (!P.tuned) return fail(ctx, RM_EINVAL, "partial wave %d has not been tuned", pw);
+    int tn = 0, st = 0;
+    if (P.tune_form == RM_FORM_PAIRS) tc_pair_variant_shape(P.tune_var, &tn, &st);
+    if (formulation) *formulation = P.tune_form;
+    if (tile_n) *tile_n = tn;
+    if (stages) *stages = st;
+    if (ms4)
+        for (int i = 0; i < 4; ++i) ms4[i] = P.tune_ms[i];
     return RM_SUCCESS;
 }
 

@@ -37,7 +37,8 @@ class RmOpts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("mem_budget", ctypes.c_size_t),
                 ("mqdt_kappa_a_max", ctypes.c_double), ("solver", ctypes.c_int),
                 ("formulation", ctypes.c_int), ("solve_precision", ctypes.c_int),
-                ("channel_tables", ctypes.c_int), ("lanes", ctypes.c_int)]
+                ("channel_tables", ctypes.c_int), ("lanes", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("pair_tile", ctypes.c_int)]
 
 
 class RmError(RuntimeError):
@@ -81,6 +82,8 @@ _SIGS = {
     "rm_lane_reserve": (_I, [_VP, _I, _I, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "rm_pw_bytes": (_I, [_VP, _I, ctypes.POINTER(ctypes.c_size_t)]),
     "rm_unload_pw": (_I, [_VP, _I]),
+    "rm_solve_batch": (_I, [_VP, _I, _VP, _I, _VP, _I, _I]),
+    "rm_autotune_info": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _VP]),
     "rm_strerror": (ctypes.c_char_p, [_I]),
     "rm_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -246,6 +249,24 @@ def rm_pw_bytes(ctx, pw):
 
 def rm_unload_pw(ctx, pw):
     return _check(ctx, lib().rm_unload_pw(ctx, int(pw)))
+
+
+def rm_solve_batch(ctx, pws, E, mode=0, use_graph=True):
+    """Solves the partial waves pws (sequence of indices) on the energies E,
+    spread over the context's lanes, accumulating into Omega."""
+    p = np.ascontiguousarray(pws, dtype=np.int32)
+    E = _host(E, np.float64)
+    return _check(ctx, lib().rm_solve_batch(ctx, int(p.size), _ptr(p, np.int32), int(E.shape[0]),
+                                            _ptr(E, np.float64), int(mode), int(bool(use_graph))))
+
+
+def rm_autotune_info(ctx, pw):
+    """(formulation, tile_n, stages, ms per energy of the 4 candidates)."""
+    f, t, st = _I(), _I(), _I()
+    ms = np.zeros(4)
+    _check(ctx, lib().rm_autotune_info(ctx, int(pw), ctypes.byref(f), ctypes.byref(t), ctypes.byref(st),
+                                       _ptr(ms, np.float64)))
+    return f.value, t.value, st.value, ms
 
 
 def rm_grid_shape(ctx):
@@ -478,6 +499,12 @@ class Context:
 
     def pw_bytes(self, pw):
         return rm_pw_bytes(self.h, pw)
+
+    def solve_batch(self, pws, E, mode=0, use_graph=True):
+        return rm_solve_batch(self.h, pws, E, mode, use_graph)
+
+    def autotune_info(self, pw):
+        return rm_autotune_info(self.h, pw)
 
     def unload_pw(self, pw):
         self._n_ch.pop(pw, None)

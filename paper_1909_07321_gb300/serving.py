@@ -66,8 +66,8 @@ class Server:
     """One context with n_slots lanes; `run` serves a list of requests whose
     arrival times are replayed in real time."""
 
-    def __init__(self, n_slots=4, precision=0, solve_precision=0, mem_budget=64 << 30,
-                 lane_workspace=4 << 30, cache_sets=64, device=0):
+    def __init__(self, n_slots=4, precision=0, solve_precision=0, mem_budget=96 << 30,
+                 lane_workspace=16 << 30, cache_sets=64, device=0):
         from . import rmgb
 
         self.rmgb = rmgb

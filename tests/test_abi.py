@@ -86,8 +86,10 @@ def test_null_context_rejected_by_lane_calls(so):
     assert L.rm_lane_reserve(None, 0, 0, 1, None) == rmgb.RM_EINVAL
     assert L.rm_pw_bytes(None, 0, None) == rmgb.RM_EINVAL
     assert L.rm_unload_pw(None, 0) == rmgb.RM_EINVAL
+    assert L.rm_solve_batch(None, 1, None, 1, None, 0, 1) == rmgb.RM_EINVAL
+    assert L.rm_autotune_info(None, 0, None, None, None, None) == rmgb.RM_EINVAL
     o = rmgb.rm_default_opts()
-    assert o.lanes == 0   # 0 takes the default of one lane
+    assert o.lanes == 1 and o.autotune == 0
 
 
 def test_multipole_shape_checked_before_the_library(so):

@@ -53,10 +53,10 @@ PRECS = [("bf16x3", 2), ("tf32x3", 1)]
 FORMS = [("pairs", 1), ("energy", 2)]
 
 
-def _gpu_r(rt, pw, Es, prec, form):
+def _gpu_r(rt, pw, Es, prec, form, pair_tile=0):
     torch, rmgb = rt
     n = pw["W"].shape[0]
-    with rmgb.Context(precision=prec, formulation=form) as ctx:
+    with rmgb.Context(precision=prec, formulation=form, pair_tile=pair_tile) as ctx:
         ctx.load_pw(0, pw)
         Ed = torch.tensor(Es, dtype=torch.float64, device="cuda")
         R = torch.zeros((Es.size, n, n), dtype=torch.float64, device="cuda")
@@ -85,6 +85,23 @@ def test_form_r_mixed_bound(rt, name, prec, fname, form):
         pw = pws[0]
         Es = _energies(pw, E, 80, 5)
         _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, prec, form), (name, fname))
+
+
+@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("name,prec", PRECS)
+def test_form_r_pair_tiles(rt, name, prec, tile):
+    """Every tile variant of the pair-operand kernel (128 x 256 with 2 stages,
+    128 x 128 with 3 and with 2) within the R bound: the 4-channel and
+    64-channel workloads, and 300 channels (45150 pairs: a ragged last tile
+    of every width) on 200 energies (a ragged energy tile)."""
+    for pws, E in [synth.workload_small(), synth.workload_64ch()]:
+        pw = pws[0]
+        Es = _energies(pw, E, 80, 9)
+        _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, prec, 1, tile), (name, tile))
+    pw = synth.random_pw(303, 300, 3000, z=2.0, a=20.0, e_max=3.0, sigma=0.05, pole_lo=-5.0,
+                         pole_hi=200.0, l_max=8)
+    Es = np.sort(np.random.default_rng(4).uniform(0.01, 4.0, 200))
+    _check_r_bound(pw, Es, _gpu_r(rt, pw, Es, prec, 1, tile), (name, tile, 300))
 
 
 @pytest.mark.parametrize("name,prec", PRECS)
