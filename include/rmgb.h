@@ -481,6 +481,19 @@ int rm_solve_batch(rm_ctx *ctx, int n_pw, const int *pws, int n_E, const double 
  * RM_ENOTLOADED. */
 int rm_autotune_info(rm_ctx *ctx, int pw, int *formulation, int *tile_n, int *stages, double *ms4);
 
+/* Self-test of the bounded device waits (no counterpart in the paper). Every
+ * wait of the tensor-core formation kernels on an mbarrier gives up after
+ * about 2 s, sets the context's error flag and lets the kernel exit, so that
+ * a fault of the pipeline reports RM_ETIMEOUT instead of hanging the GPU.
+ * With limit_ns > 0 (at most 10 s), each CTA of those kernels instead first
+ * waits, before it allocates tensor memory or issues any copy or MMA, on a
+ * barrier that nothing arrives at: the wait gives up after limit_ns, sets the
+ * flag and the CTA exits, so no R is formed and the next rm_sync or
+ * rm_collision_strengths returns RM_ETIMEOUT (the flag is then cleared).
+ * limit_ns = 0 (the default) restores normal operation; the context stays
+ * usable. Errors: RM_EINVAL. */
+int rm_set_wait_probe(rm_ctx *ctx, unsigned long long limit_ns);
+
 /* Waits for all work enqueued on every lane of the context and for the
  * copies of rm_collision_strengths_async. */
 int rm_sync(rm_ctx *ctx);

@@ -51,8 +51,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     form_r_tc_kernel(const __grid_constant__ CUtensorMap tmDh, const __grid_constant__ CUtensorMap tmDl,
                      const __grid_constant__ CUtensorMap tmPh, const __grid_constant__ CUtensorMap tmPl,
                      double *__restrict__ Rp, int ldR, int nE, int n_pairs, int n_kb, int n_ntiles,
-                     int n_tiles, int *err_flag)
+                     int n_tiles, int *err_flag, unsigned long long probe_ns)
 {
+    if (probe_ns) {
+        // bounded-wait self-test: nothing allocated or in flight yet
+        __shared__ uint64_t probe;
+        if (threadIdx.x == 0) wait_probe(&probe, probe_ns, err_flag);
+        __syncthreads();
+        return;
+    }
     constexpr int B_TILE = PairTile<BN>::B_TILE;
     constexpr int STAGE_BYTES = PairTile<BN>::STAGE_BYTES;
     constexpr int TMEM_COLS = PairTile<BN>::TMEM_COLS;
@@ -393,7 +400,8 @@ namespace {
 
 template <int KIND, int BN, int STAGES>
 cudaError_t launch_pair_variant(const void *D_hi, const void *D_lo, const void *P_hi, const void *P_lo, int nE,
-                                int n_pairs, int Kpad, double *Rp, int ldR, int *err_flag, cudaStream_t s)
+                                int n_pairs, int Kpad, double *Rp, int ldR, int *err_flag, cudaStream_t s,
+                                unsigned long long probe_ns)
 {
     CUtensorMap mDh, mDl, mPh, mPl;
     if (!make_map(&mDh, D_hi, KIND, Kpad, nE, BM) || !make_map(&mDl, D_lo, KIND, Kpad, nE, BM) ||
@@ -409,18 +417,25 @@ cudaError_t launch_pair_variant(const void *D_hi, const void *D_lo, const void *
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     form_r_tc_kernel<KIND, BN, STAGES><<<grid, NTHREADS, smem, s>>>(mDh, mDl, mPh, mPl, Rp, ldR, nE, n_pairs,
-                                                                    n_kb, n_nt, n_tiles, err_flag);
+                                                                    n_kb, n_nt, n_tiles, err_flag, probe_ns);
     return cudaGetLastError();
 }
 
 template <int KIND>
 cudaError_t launch_pair(int variant, const void *D_hi, const void *D_lo, const void *P_hi, const void *P_lo, int nE,
-                        int n_pairs, int Kpad, double *Rp, int ldR, int *err_flag, cudaStream_t s)
+                        int n_pairs, int Kpad, double *Rp, int ldR, int *err_flag, cudaStream_t s,
+                        unsigned long long probe_ns)
 {
     switch (variant) {
-    case 1: return launch_pair_variant<KIND, 128, 3>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
-    case 2: return launch_pair_variant<KIND, 128, 2>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
-    default: return launch_pair_variant<KIND, 256, 2>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
+    case 1:
+        return launch_pair_variant<KIND, 128, 3>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s,
+                                                 probe_ns);
+    case 2:
+        return launch_pair_variant<KIND, 128, 2>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s,
+                                                 probe_ns);
+    default:
+        return launch_pair_variant<KIND, 256, 2>(D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s,
+                                                 probe_ns);
     }
 }
 
@@ -436,13 +451,15 @@ void tc_pair_variant_shape(int variant, int *tile_n, int *stages)
 
 cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
                              const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
-                             int *err_flag, cudaStream_t s, int variant)
+                             int *err_flag, cudaStream_t s, int variant, unsigned long long probe_ns)
 {
     if (nE == 0) return cudaSuccess;
     if (variant < 0 || variant >= tc_pair_variants()) return cudaErrorInvalidValue;
     if (kind == TC_BF16X3)
-        return launch_pair<TC_BF16X3>(variant, D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
-    return launch_pair<TC_TF32X3>(variant, D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s);
+        return launch_pair<TC_BF16X3>(variant, D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s,
+                                      probe_ns);
+    return launch_pair<TC_TF32X3>(variant, D_hi, D_lo, P_hi, P_lo, nE, n_pairs, Kpad, Rp, ldR, err_flag, s,
+                                  probe_ns);
 }
 
 size_t near_pole_ws_bytes(int nE) { return 16 + (size_t)nE * (sizeof(int) + sizeof(int2)); }

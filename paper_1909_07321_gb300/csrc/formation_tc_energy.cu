@@ -143,8 +143,15 @@ template <int KIND>
 __global__ void __launch_bounds__(PE_THREADS, 1)
     form_r_pe_kernel(const __grid_constant__ CUtensorMap tmWh, const __grid_constant__ CUtensorMap tmWl,
                      const float *__restrict__ W32, const float *__restrict__ D32,
-                     float *__restrict__ part, const PeGeom g, int *err_flag)
+                     float *__restrict__ part, const PeGeom g, int *err_flag, unsigned long long probe_ns)
 {
+    if (probe_ns) {
+        // bounded-wait self-test: nothing allocated or in flight yet
+        __shared__ uint64_t probe;
+        if (threadIdx.x == 0) wait_probe(&probe, probe_ns, err_flag);
+        __syncthreads();
+        return;
+    }
     constexpr int BK = TC_ROW_BYTES / (KIND == TC_BF16X3 ? 2 : 4);   // K per chunk
     constexpr int EPC = Split16<KIND>::EPC;
     extern __shared__ uint8_t smem_raw[];
@@ -484,7 +491,8 @@ cudaError_t launch_pe_d32(const PwDev &pw, const double *E, int nE, double delta
 }
 
 cudaError_t launch_form_r_pe(int kind, int n, int Kpad, const float *W32, const void *Wh, const void *Wl,
-                             const float *D32, int nE, float *part, int *err_flag, cudaStream_t s)
+                             const float *D32, int nE, float *part, int *err_flag, cudaStream_t s,
+                             unsigned long long probe_ns)
 {
     if (nE == 0) return cudaSuccess;
     if (n > pe_max_n() || Kpad % 4 != 0) return cudaErrorInvalidValue;
@@ -499,13 +507,13 @@ cudaError_t launch_form_r_pe(int kind, int n, int Kpad, const float *W32, const 
                                  PE_SMEM);
         if (e != cudaSuccess) return e;
         form_r_pe_kernel<TC_BF16X3><<<(unsigned)grid, PE_THREADS, PE_SMEM, s>>>(mh, ml, W32, D32, part, g,
-                                                                                 err_flag);
+                                                                                 err_flag, probe_ns);
     } else {
         e = cudaFuncSetAttribute(form_r_pe_kernel<TC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  PE_SMEM);
         if (e != cudaSuccess) return e;
         form_r_pe_kernel<TC_TF32X3><<<(unsigned)grid, PE_THREADS, PE_SMEM, s>>>(mh, ml, W32, D32, part, g,
-                                                                                 err_flag);
+                                                                                 err_flag, probe_ns);
     }
     return cudaGetLastError();
 }

@@ -183,7 +183,7 @@ int tc_pair_variants();
 void tc_pair_variant_shape(int variant, int *tile_n, int *stages);
 cudaError_t launch_form_r_tc(int kind, const void *D_hi, const void *D_lo, const void *P_hi,
                              const void *P_lo, int nE, int n_pairs, int Kpad, double *Rp, int ldR,
-                             int *err_flag, cudaStream_t s, int variant = 0);
+                             int *err_flag, cudaStream_t s, int variant = 0, unsigned long long probe_ns = 0);
 // R_packed[e][p] += (1/2a) w_ik w_jk / (E_k - E_e) over poles with |E_k - E_e| < delta (FP64),
 // the near/far decision taken exactly as launch_split_d takes it (pw.Ek_hl).
 // ws: near_pole_ws_bytes(nE) bytes of device scratch (list of the energies
@@ -202,8 +202,11 @@ cudaError_t launch_pe_prep_w(const PwDev &pw, int kind, int Kpad, float *W32, vo
                              cudaStream_t s);
 cudaError_t launch_pe_d32(const PwDev &pw, const double *E, int nE, double delta, int Kpad, float *D32,
                           cudaStream_t s);
+// probe_ns != 0 (both tensor-core formations): the bounded-wait self-test
+// (rm_set_wait_probe) instead of the formation.
 cudaError_t launch_form_r_pe(int kind, int n, int Kpad, const float *W32, const void *Wh, const void *Wl,
-                             const float *D32, int nE, float *part, int *err_flag, cudaStream_t s);
+                             const float *D32, int nE, float *part, int *err_flag, cudaStream_t s,
+                             unsigned long long probe_ns = 0);
 // Sums the segments in FP64, adds the near-pole terms, scales by 1/2a -> packed R.
 cudaError_t launch_pe_reduce(const PwDev &pw, int kind, int Kpad, const double *E, int nE, double delta,
                              const float *D32, const float *part, double *Rp, int ldR, cudaStream_t s);

@@ -244,6 +244,7 @@ struct rm_ctx {
     std::vector<BatchGraph> graphs;
     DevBuf batchE;                 // host energies of rm_solve_batch, at a stable address
     cudaEvent_t ev_batch = nullptr;
+    unsigned long long wait_probe_ns = 0;   // rm_set_wait_probe
     long long launches = 0;
     // per-phase event pairs (tracing)
     bool prof = false;
@@ -799,7 +800,7 @@ int form_r_block(rm_ctx *ctx, Lane *ln, PwHost &P, const double *E, int nE, doub
         CK(prof_end(ctx, RM_PH_SPLIT, st));
         CK(prof_begin(ctx, RM_PH_FORM, st));
         CK(launch_form_r_pe(kind, P.n, Kpad, P.W32.as<float>(), P.Wh.p, P.Wl.p, ln->wsDh.as<float>(), nE,
-                            ln->wsPart.as<float>(), ln->wsErr.as<int>(), st));
+                            ln->wsPart.as<float>(), ln->wsErr.as<int>(), st, ctx->wait_probe_ns));
         CK(prof_end(ctx, RM_PH_FORM, st));
         CK(prof_begin(ctx, RM_PH_FIXUP, st));
         CK(launch_pe_reduce(d, kind, Kpad, E, nE, ctx->opts.delta_pole, ln->wsDh.as<float>(),
@@ -830,7 +831,8 @@ int form_r_block(rm_ctx *ctx, Lane *ln, PwHost &P, const double *E, int nE, doub
     CK(prof_begin(ctx, RM_PH_FORM, st));
     CK(launch_form_r_tc(kind, ln->wsDh.p, ln->wsDl.p, P.Ph.p, P.Pl.p, nE, tri_count(P.n), Kpad, R,
                         tri_ld(P.n), ln->wsErr.as<int>(), st,
-                        ctx->opts.pair_tile > 0 ? ctx->opts.pair_tile - 1 : (P.tuned ? P.tune_var : 0)));
+                        ctx->opts.pair_tile > 0 ? ctx->opts.pair_tile - 1 : (P.tuned ? P.tune_var : 0),
+                        ctx->wait_probe_ns));
     CK(prof_end(ctx, RM_PH_FORM, st));
     CK(prof_begin(ctx, RM_PH_FIXUP, st));
     CK(ln->wsNear.reserve(near_pole_ws_bytes(nE)));
@@ -1731,6 +1733,14 @@ extern "C" int rm_autotune_info(rm_ctx *ctx, int pw, int *formulation, int *tile
     if (stages) *stages = st;
     if (ms4)
         for (int i = 0; i < 4; ++i) ms4[i] = P.tune_ms[i];
+    return RM_SUCCESS;
+}
+
+extern "C" int rm_set_wait_probe(rm_ctx *ctx, unsigned long long limit_ns)
+{
+    if (!ctx) return RM_EINVAL;
+    if (limit_ns > 10000000000ull) return fail(ctx, RM_EINVAL, "probe limit %llu ns above 10 s", limit_ns);
+    ctx->wait_probe_ns = limit_ns;
     return RM_SUCCESS;
 }
 

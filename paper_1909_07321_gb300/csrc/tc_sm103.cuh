@@ -79,6 +79,25 @@ __device__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)
     }
 }
 
+// Self-test of the bounded waits (rm_set_wait_probe), called by one thread
+// of a CTA before the CTA allocates tensor memory or issues any copy or MMA:
+// waits on a freshly initialised barrier that nothing arrives at, gives up
+// after limit_ns and sets *err. Returns false when it gave up (always, as
+// nothing arrives).
+__device__ bool wait_probe(uint64_t *bar, unsigned long long limit_ns, int *err)
+{
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, 0)) return true;
+        if (globaltimer() - t0 > limit_ns) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
 // Spins for about `ns` nanoseconds (lets bulk copies in flight land before a
 // CTA that gave up a wait exits).
 __device__ __forceinline__ void spin_ns(unsigned long long ns)

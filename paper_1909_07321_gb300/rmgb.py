@@ -84,6 +84,7 @@ _SIGS = {
     "rm_unload_pw": (_I, [_VP, _I]),
     "rm_solve_batch": (_I, [_VP, _I, _VP, _I, _VP, _I, _I]),
     "rm_autotune_info": (_I, [_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _VP]),
+    "rm_set_wait_probe": (_I, [_VP, ctypes.c_ulonglong]),
     "rm_strerror": (ctypes.c_char_p, [_I]),
     "rm_last_error": (ctypes.c_char_p, [_VP]),
 }
@@ -505,6 +506,9 @@ class Context:
 
     def autotune_info(self, pw):
         return rm_autotune_info(self.h, pw)
+
+    def set_wait_probe(self, limit_ns):
+        return _check(self.h, lib().rm_set_wait_probe(self.h, int(limit_ns)))
 
     def unload_pw(self, pw):
         self._n_ch.pop(pw, None)
