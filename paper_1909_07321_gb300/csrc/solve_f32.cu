@@ -95,6 +95,167 @@ __device__ __forceinline__ void sweep_apply(float2 (&z)[TR][TR], int k, int tx, 
     }
 }
 
+// Shared buffers of the T step's sweep (two per buffer: published pivot
+// columns alternate between steps), row stride `stride`.
+struct SweepShared {
+    float2 *ucol, *vcol, *ucol2, *vcol2;
+    float2 *dbuf, *dinvbuf, *dbuf2, *dinvbuf2;
+    int stride;
+};
+
+// T step for n_o <= 16 TS open channels (TS tiles per side in registers,
+// no padding tiles beyond them): W = -(1 - iK)^{-1} by the complex sweep, and
+// |T_ab|^2 = 4 |W_ab + delta_ab|^2 written over K in Pm. Returns false (in
+// every thread) if a pivot is zero or not finite.
+template <int TS>
+__device__ __forceinline__ bool t_sweep(float *Pm, int no, int tid, int lane, int tx, int ty, unsigned hmask,
+                                        const SweepShared &sh)
+{
+    const unsigned full = 0xffffffffu;
+    float2 z[TS][TS];
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+        const int r = ty + G16 * i;
+#pragma unroll
+        for (int j = 0; j < TS; ++j) {
+            const int c = tx + G16 * j;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (r < no && c < no) v = make_float2(r == c ? 1.0f : 0.0f, -0.5f * (Pm[r * no + c] + Pm[c * no + r]));
+            z[i][j] = v;
+        }
+    }
+    // Pivots in pairs (k even, k + 1) as in the elimination: the owner warp
+    // finds d1 = z_kk and v1 = column k / d1 (lanes 0-15), brings column k + 1
+    // through the step on k (lanes 16-31: w_i = z_i,k+1 - v1_i z_k+1,k, and
+    // w_k = z_k+1,k / d1), takes d2 = w_k+1, and publishes both; every thread
+    // then applies both steps after one barrier.
+    int k_first_single = 0;
+    for (int k = 0; k + 1 < no; k += 2) {
+        const int buf = (k >> 1) & 1;
+        const int kk = k >> 4;
+        if ((tx >> 1) == ((k & 15) >> 1)) {
+            float2 u[TS];
+#pragma unroll
+            for (int i = 0; i < TS; ++i) u[i] = pick<TS>(z[i], kk);
+            const float2 ukk = pick<TS>(u, kk);
+            float2 d1, uk1;
+            d1.x = __shfl_sync(full, ukk.x, k & 15);
+            d1.y = __shfl_sync(full, ukk.y, k & 15);
+            uk1.x = __shfl_sync(full, ukk.x, (k + 1) & 15);   // z_{k+1,k}
+            uk1.y = __shfl_sync(full, ukk.y, (k + 1) & 15);
+            const float2 dinv1 = crcp_f(d1);
+            float2 w[TS];
+#pragma unroll
+            for (int i = 0; i < TS; ++i) {
+                const float2 v1 = cmul_f(u[i], dinv1);
+                float2 vA;
+                vA.x = __shfl_xor_sync(full, v1.x, 16);
+                vA.y = __shfl_xor_sync(full, v1.y, 16);
+                const int r = ty + G16 * i;
+                const float2 uv = cmul_f(vA, uk1);
+                w[i] = (r == k) ? cmul_f(uk1, dinv1) : make_float2(u[i].x - uv.x, u[i].y - uv.y);
+                if ((tx & 1) == 0 && r < no) {
+                    sh.ucol[buf * sh.stride + r] = u[i];
+                    sh.vcol[buf * sh.stride + r] = v1;
+                }
+            }
+            const float2 wk1 = pick<TS>(w, kk);
+            float2 d2;
+            d2.x = __shfl_sync(full, wk1.x, 16 + ((k + 1) & 15));
+            d2.y = __shfl_sync(full, wk1.y, 16 + ((k + 1) & 15));
+            const float2 dinv2 = crcp_f(d2);
+            if (tx & 1) {
+#pragma unroll
+                for (int i = 0; i < TS; ++i) {
+                    const int r = ty + G16 * i;
+                    if (r < no) {
+                        sh.ucol2[buf * sh.stride + r] = w[i];
+                        sh.vcol2[buf * sh.stride + r] = cmul_f(w[i], dinv2);
+                    }
+                }
+            }
+            if (lane == 0) {
+                sh.dbuf[buf] = d1;
+                sh.dinvbuf[buf] = dinv1;
+                sh.dbuf2[buf] = d2;
+                sh.dinvbuf2[buf] = dinv2;
+            }
+        }
+        __syncthreads();
+        const float2 d1 = sh.dbuf[buf], d2 = sh.dbuf2[buf];
+        if (!(fabsf(d1.x) + fabsf(d1.y) > 0.0f) || !isfinite(d1.x) || !isfinite(d1.y) ||
+            !(fabsf(d2.x) + fabsf(d2.y) > 0.0f) || !isfinite(d2.x) || !isfinite(d2.y)) {
+            return false;
+        }
+        sweep_apply<TS>(z, k, tx, ty, sh.vcol + buf * sh.stride, sh.ucol + buf * sh.stride, sh.dinvbuf[buf]);
+        sweep_apply<TS>(z, k + 1, tx, ty, sh.vcol2 + buf * sh.stride, sh.ucol2 + buf * sh.stride, sh.dinvbuf2[buf]);
+        k_first_single = k + 2;
+    }
+    for (int k = k_first_single; k < no; ++k) {
+        const int buf = (k >> 1) & 1;
+        const int kk = k >> 4;
+        if (tx == (k & 15)) {
+            // column k's half-warp: u, the pivot d = u_k, and v = u / d
+            float2 u[TS];
+#pragma unroll
+            for (int i = 0; i < TS; ++i) u[i] = pick<TS>(z[i], kk);
+            const float2 uk = pick<TS>(u, kk);
+            float2 d;
+            d.x = __shfl_sync(hmask, uk.x, k & 15, 16);
+            d.y = __shfl_sync(hmask, uk.y, k & 15, 16);
+            const float2 dinv = crcp_f(d);
+#pragma unroll
+            for (int i = 0; i < TS; ++i) {
+                const int r = ty + G16 * i;
+                if (r < no) {
+                    sh.ucol[buf * sh.stride + r] = u[i];
+                    sh.vcol[buf * sh.stride + r] = cmul_f(u[i], dinv);
+                }
+            }
+            if (ty == 0) {
+                sh.dbuf[buf] = d;
+                sh.dinvbuf[buf] = dinv;
+            }
+        }
+        __syncthreads();
+        const float2 d = sh.dbuf[buf];
+        if (!(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y)) {
+            return false;
+        }
+        sweep_apply<TS>(z, k, tx, ty, sh.vcol + buf * sh.stride, sh.ucol + buf * sh.stride, sh.dinvbuf[buf]);
+    }
+    __syncthreads();   // every read of K in Pm is done
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+        const int r = ty + G16 * i;
+#pragma unroll
+        for (int j = 0; j < TS; ++j) {
+            const int c = tx + G16 * j;
+            if (r < no && c < no) {
+                const float re = z[i][j].x + (r == c ? 1.0f : 0.0f), im = z[i][j].y;
+                Pm[r * no + c] = 4.0f * fmaf(re, re, im * im);
+            }
+        }
+    }
+    __syncthreads();
+
+    return true;
+}
+
+// The T step with the smallest tile count that holds n_o (ts = ceil(n_o / 16),
+// the same in every thread).
+template <int TS, int TMAX>
+__device__ __forceinline__ bool t_sweep_dispatch(int ts, float *Pm, int no, int tid, int lane, int tx, int ty,
+                                                 unsigned hmask, const SweepShared &sh)
+{
+    if constexpr (TS < TMAX) {
+        if (ts <= TS) return t_sweep<TS>(Pm, no, tid, lane, tx, ty, hmask, sh);
+        return t_sweep_dispatch<TS + 1, TMAX>(ts, Pm, no, tid, lane, tx, ty, hmask, sh);
+    } else {
+        return t_sweep<TMAX>(Pm, no, tid, lane, tx, ty, hmask, sh);
+    }
+}
+
 template <int TR, int TC>
 __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa, const double *__restrict__ Ra,
@@ -441,134 +602,14 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     if (!omega) return;
 
     // ---- T step: W = -(1 - iK)^{-1} by the complex sweep in registers --------
-    float2 z[TR][TR];
-#pragma unroll
-    for (int i = 0; i < TR; ++i) {
-        const int r = ty + G16 * i;
-#pragma unroll
-        for (int j = 0; j < TR; ++j) {
-            const int c = tx + G16 * j;
-            float2 v = make_float2(0.0f, 0.0f);
-            if (r < no && c < no) v = make_float2(r == c ? 1.0f : 0.0f, -0.5f * (Pm[r * no + c] + Pm[c * no + r]));
-            z[i][j] = v;
-        }
-    }
-    // Pivots in pairs (k even, k + 1) as in the elimination: the owner warp
-    // finds d1 = z_kk and v1 = column k / d1 (lanes 0-15), brings column k + 1
-    // through the step on k (lanes 16-31: w_i = z_i,k+1 - v1_i z_k+1,k, and
-    // w_k = z_k+1,k / d1), takes d2 = w_k+1, and publishes both; every thread
-    // then applies both steps after one barrier.
-    int k_first_single = 0;
-    for (int k = 0; k + 1 < no; k += 2) {
-        const int buf = (k >> 1) & 1;
-        const int kk = k >> 4;
-        if ((tx >> 1) == ((k & 15) >> 1)) {
-            float2 u[TR];
-#pragma unroll
-            for (int i = 0; i < TR; ++i) u[i] = pick<TR>(z[i], kk);
-            const float2 ukk = pick<TR>(u, kk);
-            float2 d1, uk1;
-            d1.x = __shfl_sync(full, ukk.x, k & 15);
-            d1.y = __shfl_sync(full, ukk.y, k & 15);
-            uk1.x = __shfl_sync(full, ukk.x, (k + 1) & 15);   // z_{k+1,k}
-            uk1.y = __shfl_sync(full, ukk.y, (k + 1) & 15);
-            const float2 dinv1 = crcp_f(d1);
-            float2 w[TR];
-#pragma unroll
-            for (int i = 0; i < TR; ++i) {
-                const float2 v1 = cmul_f(u[i], dinv1);
-                float2 vA;
-                vA.x = __shfl_xor_sync(full, v1.x, 16);
-                vA.y = __shfl_xor_sync(full, v1.y, 16);
-                const int r = ty + G16 * i;
-                const float2 uv = cmul_f(vA, uk1);
-                w[i] = (r == k) ? cmul_f(uk1, dinv1) : make_float2(u[i].x - uv.x, u[i].y - uv.y);
-                if ((tx & 1) == 0 && r < no) {
-                    ucol[buf][r] = u[i];
-                    vcol[buf][r] = v1;
-                }
-            }
-            const float2 wk1 = pick<TR>(w, kk);
-            float2 d2;
-            d2.x = __shfl_sync(full, wk1.x, 16 + ((k + 1) & 15));
-            d2.y = __shfl_sync(full, wk1.y, 16 + ((k + 1) & 15));
-            const float2 dinv2 = crcp_f(d2);
-            if (tx & 1) {
-#pragma unroll
-                for (int i = 0; i < TR; ++i) {
-                    const int r = ty + G16 * i;
-                    if (r < no) {
-                        ucol2[buf][r] = w[i];
-                        vcol2[buf][r] = cmul_f(w[i], dinv2);
-                    }
-                }
-            }
-            if (lane == 0) {
-                dbuf[buf] = d1;
-                dinvbuf[buf] = dinv1;
-                dbuf2[buf] = d2;
-                dinvbuf2[buf] = dinv2;
-            }
-        }
-        __syncthreads();
-        const float2 d1 = dbuf[buf], d2 = dbuf2[buf];
-        if (!(fabsf(d1.x) + fabsf(d1.y) > 0.0f) || !isfinite(d1.x) || !isfinite(d1.y) ||
-            !(fabsf(d2.x) + fabsf(d2.y) > 0.0f) || !isfinite(d2.x) || !isfinite(d2.y)) {
+    {
+        const SweepShared sh = {&ucol[0][0], &vcol[0][0], &ucol2[0][0], &vcol2[0][0],
+                                dbuf, dinvbuf, dbuf2, dinvbuf2, G16 * TR};
+        if (!t_sweep_dispatch<1, TR>((no + 15) >> 4, Pm, no, tid, lane, tx, ty, hmask, sh)) {
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        sweep_apply<TR>(z, k, tx, ty, vcol[buf], ucol[buf], dinvbuf[buf]);
-        sweep_apply<TR>(z, k + 1, tx, ty, vcol2[buf], ucol2[buf], dinvbuf2[buf]);
-        k_first_single = k + 2;
     }
-    for (int k = k_first_single; k < no; ++k) {
-        const int buf = (k >> 1) & 1;
-        const int kk = k >> 4;
-        if (tx == (k & 15)) {
-            // column k's half-warp: u, the pivot d = u_k, and v = u / d
-            float2 u[TR];
-#pragma unroll
-            for (int i = 0; i < TR; ++i) u[i] = pick<TR>(z[i], kk);
-            const float2 uk = pick<TR>(u, kk);
-            float2 d;
-            d.x = __shfl_sync(hmask, uk.x, k & 15, 16);
-            d.y = __shfl_sync(hmask, uk.y, k & 15, 16);
-            const float2 dinv = crcp_f(d);
-#pragma unroll
-            for (int i = 0; i < TR; ++i) {
-                const int r = ty + G16 * i;
-                if (r < no) {
-                    ucol[buf][r] = u[i];
-                    vcol[buf][r] = cmul_f(u[i], dinv);
-                }
-            }
-            if (ty == 0) {
-                dbuf[buf] = d;
-                dinvbuf[buf] = dinv;
-            }
-        }
-        __syncthreads();
-        const float2 d = dbuf[buf];
-        if (!(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y)) {
-            if (tid == 0) status[e] = RM_ESINGULAR;
-            return;
-        }
-        sweep_apply<TR>(z, k, tx, ty, vcol[buf], ucol[buf], dinvbuf[buf]);
-    }
-    __syncthreads();   // every read of K in Pm is done
-#pragma unroll
-    for (int i = 0; i < TR; ++i) {
-        const int r = ty + G16 * i;
-#pragma unroll
-        for (int j = 0; j < TR; ++j) {
-            const int c = tx + G16 * j;
-            if (r < no && c < no) {
-                const float re = z[i][j].x + (r == c ? 1.0f : 0.0f), im = z[i][j].y;
-                Pm[r * no + c] = 4.0f * fmaf(re, re, im * im);
-            }
-        }
-    }
-    __syncthreads();
 
     // ---- Omega ----------------------------------------------------------------
     const int npair = nl * (nl + 1) / 2;

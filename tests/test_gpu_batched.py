@@ -61,14 +61,44 @@ def _batch(rmgb, torch, pws, Es, prec, sp, lanes=4, calls=1, graph=True, autotun
     return outs, info
 
 
+def _cf_amplification(pws, x, seed=0):
+    """Largest factor over the waves by which a relative perturbation of 1e-13
+    of the oracle's channel functions at energy x moves K (relative,
+    Frobenius): the matching's amplification of channel-function errors."""
+    import oracle.rmatrix as orm
+    rng = np.random.default_rng(seed)
+    amp = 1.0
+    for pw in pws:
+        cf = orm.channel_functions(x, pw["e_thr"], pw["l"], pw["z"], pw["a"])
+        R = orm.r_matrix(x, pw["E_k"], pw["W"], pw["a"])
+        K0, _ = orm.match_direct(R, cf, pw["a"])
+        if K0 is None or K0.size == 0:
+            continue
+        cf2 = dict(cf)
+        for key in ("s", "sp", "c", "cp", "th", "thp"):
+            cf2[key] = cf[key] * (1.0 + 1e-13 * rng.standard_normal(cf[key].shape))
+        K1, _ = orm.match_direct(R, cf2, pw["a"])
+        amp = max(amp, np.linalg.norm(K1 - K0) / np.linalg.norm(K0) / 1e-13)
+    return amp
+
+
 def test_batched_fp64_equals_summed_oracle(rt, workload, oracle_sum):
+    """FP64 path: 1e-9 relative where the matching is well conditioned; at an
+    energy where it amplifies channel-function errors A-fold (2.5e5 at
+    2.5e-4 Ry above the 4 Ry threshold, eta = -190 in the channel just
+    opened) the bound is 1e-9 + 4 A 1e-11 (the channel functions' accuracy,
+    1e-11 of the amplitude, through K into |T|^2)."""
     torch, rmgb = rt
     pws, Es = workload
     (om,), _ = _batch(rmgb, torch, pws, Es, 0, 0)
     ref, _ = oracle_sum
     for m in range(Es.size):
         nrm = np.linalg.norm(ref[m])
-        assert np.linalg.norm(om[m] - ref[m]) <= 1e-9 * nrm, (m, np.linalg.norm(om[m] - ref[m]) / nrm)
+        rel = np.linalg.norm(om[m] - ref[m]) / nrm
+        if rel <= 1e-9:
+            continue
+        amp = _cf_amplification(pws, float(Es[m]))
+        assert amp > 1e3 and rel <= 1e-9 + 4.0 * amp * 1e-11, (m, rel, amp)
 
 
 def test_batched_mixed_within_summed_bounds_and_graph_replay(rt, workload, oracle_sum):
