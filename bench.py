@@ -363,9 +363,15 @@ def run_serving(args, prec):
                                        sp["t_arrival"] * t_scale))
         return out
 
-    def serve(precision, sp_, reqs):
+    def keep_rows(stride):
+        # host memory holds only the rows the FP64 comparison reads
+        def sink(req, om):
+            req.omega = om[::stride].copy() if stride else None
+        return sink
+
+    def serve(precision, sp_, reqs, keep):
         srv = serving.Server(n_slots=4, precision=precision, solve_precision=sp_, mem_budget=120 << 30,
-                             lane_workspace=16 << 30, cache_sets=64)
+                             lane_workspace=16 << 30, cache_sets=64, sink=keep_rows(keep))
         try:
             srv.prepare(reqs)
             warm = [serving.Request(-1 - i, r.set_id, r.pw, r.E[:64], r.mode, 0.0) for i, r in enumerate(reqs[:4])]
@@ -377,20 +383,20 @@ def run_serving(args, prec):
         return serving.latency_stats(reqs), loads
 
     # capacity: every request queued at t = 0
+    k = args.serving_fp64_stride
     sat = make(specs)
-    st_sat, loads = serve(2, 1, sat)
+    st_sat, loads = serve(2, 1, sat, k)
     cap = st_sat["requests"] / st_sat["wall_s"]
     # Poisson arrivals at 0.9 x capacity (the stream's exponential gaps rescaled)
     rate = 0.9 * cap
     pois = make(specs, t_scale=1.0 / rate)
-    st_p, _ = serve(2, 1, pois)
+    st_p, _ = serve(2, 1, pois, 0)
     # FP64 served arm on a strided subsample of every request's energies
-    k = args.serving_fp64_stride
     sub = make(specs, stride=k)
-    st64, _ = serve(0, 0, sub)
+    st64, _ = serve(0, 0, sub, 1)
     rel = []
     for a, b in zip(sat, sub):
-        om_m = a.omega[::k]
+        om_m = a.omega
         nb = np.linalg.norm(b.omega, axis=1)
         ok = nb > 0
         rel.extend((np.linalg.norm(om_m[ok] - b.omega[ok], axis=1) / nb[ok]).tolist())
@@ -698,6 +704,30 @@ def run_propagation(args, prec, sp, fp64_peak, stream):
                              "peak_source": "FP64 4 flop/clk/SM x 152 SMs at the sampled SM clock"},
                 "omega_rel_change_with_2x_steps": {"median": float(np.median(dn)), "max": float(dn.max())},
                 "timing": "CUDA events on the context stream around 2 solves after one warm-up"})
+    # 64 channels (the 512-thread kernel; lambda_max = 2) on the same energies
+    pw6, A6, r16, steps6, _ = synth.workload_multipole(args.prop_energies, n=64)
+    ctx = rmgb.Context(precision=prec, stream=stream.cuda_stream, solve_precision=sp)
+    ctx.load_pw(0, pw6)
+    ctx.set_multipoles(0, A6, r16, steps6)
+    with torch.cuda.stream(stream):
+        ctx.solve_energies(0, Ed)
+        ctx.reset_omega()
+        ctx.profile_enable(True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        ctx.solve_energies(0, Ed)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms6 = t0.elapsed_time(t1)
+        _, pms6 = ctx.profile_get(rmgb.RM_PH_PROPAGATE)
+    ctx.close()
+    f6 = E.size * steps6 * (4.0 * 64 ** 3 + (14.0 + 2.0 * A6.shape[0]) * 64 * 64)
+    a6 = f6 / (pms6 * 1e-3) / 1e12
+    out["64ch"] = {"energy_solves_per_s": E.size / (ms6 * 1e-3), "ms": ms6, "propagate_ms": pms6,
+                   "propagate_tflops": a6, "frac_of_fp64_peak": a6 / fp64_peak,
+                   "kernel": "propagate_kernel<512,8,64> (FP64 Numerov, one CTA per energy)"}
     return out
 
 

@@ -219,12 +219,16 @@ int rm_set_channels(rm_ctx *ctx, int pw, const double *e_thr, const int *l, doub
  * channel tables) are then taken at r1. The error is O(h^4), h = (r1 - a) /
  * n_steps; the coupling beyond r1 is not included. lambda_max = 0 switches
  * propagation off (A, r1, n_steps ignored). rm_load_poles clears it.
- * rm_form_r still returns R at a. At most 32 channels, 1 <= lambda_max <= 4.
+ * rm_form_r still returns R at a. At most 64 channels, 1 <= lambda_max <= 4,
+ * and above 16 channels the state (4 n_ch^2 doubles) and A (lambda_max n_ch^2
+ * doubles) must fit one CTA's shared memory (227 KB: lambda_max <= 3 at 64
+ * channels).
  * An energy whose r1 Psi' - b Psi (or a renormalisation) is singular gets
  * RM_ESINGULAR. Synchronous when the channels are set (their tables are
  * rebuilt for r1). Errors: RM_EINVAL (lambda_max out of range, A NULL,
  * non-finite or not symmetric, r1 < a, n_steps < 2), RM_EUNSUPPORTED
- * (n_ch > 32), RM_ENOTLOADED, RM_ENOMEM, RM_ECUDA. */
+ * (n_ch > 64, or the shared-memory limit above), RM_ENOTLOADED, RM_ENOMEM,
+ * RM_ECUDA. */
 int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const double *A, double r1, int n_steps);
 
 /* Solves n_E energies E (host or device, [n_E], Ry) of partial wave `pw` in

@@ -1,4 +1,5 @@
-// Dense linear algebra on one matrix per CTA in shared memory (256 threads),
+// Dense linear algebra on one matrix per CTA in shared memory (256 threads;
+// the elimination and back-substitution take the block size as NTH),
 // shared by the per-energy solvers: Gaussian elimination with partial
 // pivoting and back-substitution (FP64 or FP32), the symmetric sweep
 // inverse, the MQDT closed-channel elimination and the T-matrix / collision
@@ -27,7 +28,7 @@ struct ElimShared {
 // columns of the rows x w matrix M (row stride ld), whole block, in the
 // element type T (double, or float for the FP32 matching). Sets sh->bad on a
 // zero or non-finite pivot.
-template <typename T>
+template <typename T, int NTH = NT>
 __device__ void block_eliminate(T *M, int ld, int rows, int w, ElimShared *sh)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -54,7 +55,7 @@ __device__ void block_eliminate(T *M, int ld, int rows, int w, ElimShared *sh)
         __syncthreads();
         const int p = sh->piv;
         if (p != c) {
-            for (int q = c + tid; q < w; q += NT) {
+            for (int q = c + tid; q < w; q += NTH) {
                 const T t = M[c * ld + q];
                 M[c * ld + q] = M[p * ld + q];
                 M[p * ld + q] = t;
@@ -68,7 +69,7 @@ __device__ void block_eliminate(T *M, int ld, int rows, int w, ElimShared *sh)
         const T pinv = (T)sh->pivinv;
         const int nr = rows - c - 1;
         const T *prow = M + c * ld;
-        for (int q = tid; q < nr * G; q += NT) {
+        for (int q = tid; q < nr * G; q += NTH) {
             const int r = c + 1 + q / G, j = q - (q / G) * G;
             T *row = M + r * ld;
             const T f = row[c] * pinv;
@@ -81,10 +82,10 @@ __device__ void block_eliminate(T *M, int ld, int rows, int w, ElimShared *sh)
 // Back-substitution of the upper-triangular rows x rows system in M for the
 // n_rhs right-hand sides in columns rhs0.., over rows t = rows-1 .. row_lo,
 // in place; one thread per right-hand side.
-template <typename T>
+template <typename T, int NTH = NT>
 __device__ void block_backsub(T *M, int ld, int rows, int rhs0, int n_rhs, int row_lo)
 {
-    for (int qq = threadIdx.x; qq < n_rhs; qq += NT) {
+    for (int qq = threadIdx.x; qq < n_rhs; qq += NTH) {
         const int cq = rhs0 + qq;
         for (int t = rows - 1; t >= row_lo; --t) {
             T s = M[t * ld + cq];

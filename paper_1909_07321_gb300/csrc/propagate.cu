@@ -37,20 +37,24 @@
 namespace rmgb {
 namespace {
 
-// Elements of an n x n matrix one thread owns (q = tid + c NT, c < PROP_QN).
-constexpr int PROP_QN = (PROP_MAXN * PROP_MAXN + NT - 1) / NT;
+// One energy per CTA of NTP threads, n <= NMAX: a thread owns the elements
+// q = tid + c NTP, c < QN = NMAX^2 / NTP, of every n x n matrix (NTP = 256,
+// QN = 4 up to 32 channels; NTP = 512, QN = 8 up to 64 channels).
+// QN is the share of the several-energies kernel below (256 threads).
+constexpr int PROP_QN = 4;
 constexpr int PROP_START_SUB = 4;   // Runge-Kutta steps of h/4 to Psi_1
 
 // scale W(r) at the owned elements into Wd: sum_lambda A^lambda
 // r^-(lambda+1) plus the diagonal l(l+1)/r^2 - 2z/r - eps.
+template <int NTP, int QN>
 __device__ __forceinline__ void build_w(double *Wd, const double *As, const double *eps_s, const double *lt_s,
                                         int n, int lmax, double z, double r, double scale, int tid)
 {
     const int n2 = n * n;
     const double ir = 1.0 / r;
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c) {
-        const int q = tid + c * NT;
+    for (int c = 0; c < QN; ++c) {
+        const int q = tid + c * NTP;
         if (q < n2) {
             const int i = q / n, j = q - (q / n) * n;
             double u = 0.0, rp = ir * ir;
@@ -64,14 +68,15 @@ __device__ __forceinline__ void build_w(double *Wd, const double *As, const doub
     }
 }
 
-// (X S) at the owned elements, the PROP_QN dot products interleaved.
-__device__ __forceinline__ void mat_times(double (&kq)[PROP_QN], const double *X, const double *S, int n, int tid)
+// (X S) at the owned elements, the QN dot products interleaved.
+template <int NTP, int QN>
+__device__ __forceinline__ void mat_times(double (&kq)[QN], const double *X, const double *S, int n, int tid)
 {
     const int n2 = n * n;
-    int wi[PROP_QN], sj[PROP_QN];
+    int wi[QN], sj[QN];
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c) {
-        const int q = min(tid + c * NT, n2 - 1);
+    for (int c = 0; c < QN; ++c) {
+        const int q = min(tid + c * NTP, n2 - 1);
         wi[c] = (q / n) * n;
         sj[c] = q - wi[c];
         kq[c] = 0.0;
@@ -79,43 +84,44 @@ __device__ __forceinline__ void mat_times(double (&kq)[PROP_QN], const double *X
 #pragma unroll 2
     for (int k = 0; k < n; ++k) {
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) kq[c] = fma(X[wi[c] + k], S[k * n + sj[c]], kq[c]);
+        for (int c = 0; c < QN; ++c) kq[c] = fma(X[wi[c] + k], S[k * n + sj[c]], kq[c]);
     }
 }
 
 // nsub classical Runge-Kutta steps of hh from r_start on (psi, dps) in
 // registers. Scratch S0, S1 (stage inputs of Psi), W0, W1 (W at the step's
 // start and middle); on return S0 holds Psi. Starts and ends with a barrier.
-__device__ void rk4_steps(double (&psi)[PROP_QN], double (&dps)[PROP_QN], double *S0, double *S1, double *W0,
+template <int NTP, int QN>
+__device__ void rk4_steps(double (&psi)[QN], double (&dps)[QN], double *S0, double *S1, double *W0,
                           double *W1, const double *As, const double *eps_s, const double *lt_s, int n, int lmax,
                           double z, double r_start, double hh, int nsub, int tid)
 {
     const int n2 = n * n;
     const double h2 = 0.5 * hh, h3 = hh / 3.0, h6 = hh / 6.0;
-    double yp[PROP_QN], yq[PROP_QN], tq[PROP_QN], kq[PROP_QN];
+    double yp[QN], yq[QN], tq[QN], kq[QN];
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c)
-        if (tid + c * NT < n2) S0[tid + c * NT] = psi[c];
-    build_w(W0, As, eps_s, lt_s, n, lmax, z, r_start, 1.0, tid);
+    for (int c = 0; c < QN; ++c)
+        if (tid + c * NTP < n2) S0[tid + c * NTP] = psi[c];
+    build_w<NTP, QN>(W0, As, eps_s, lt_s, n, lmax, z, r_start, 1.0, tid);
     __syncthreads();
     for (int s = 0; s < nsub; ++s) {
         const double r0 = r_start + s * hh;
-        mat_times(kq, W0, S0, n, tid);                  // stage 1
+        mat_times<NTP, QN>(kq, W0, S0, n, tid);                  // stage 1
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
+        for (int c = 0; c < QN; ++c) {
+            const int q = tid + c * NTP;
             yp[c] = fma(h6, dps[c], psi[c]);
             yq[c] = fma(h6, kq[c], dps[c]);
             tq[c] = fma(h2, kq[c], dps[c]);
             if (q < n2) S1[q] = fma(h2, dps[c], psi[c]);
         }
-        build_w(W1, As, eps_s, lt_s, n, lmax, z, r0 + h2, 1.0, tid);
+        build_w<NTP, QN>(W1, As, eps_s, lt_s, n, lmax, z, r0 + h2, 1.0, tid);
         __syncthreads();
-        mat_times(kq, W1, S1, n, tid);                  // stage 2
+        mat_times<NTP, QN>(kq, W1, S1, n, tid);                  // stage 2
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
+        for (int c = 0; c < QN; ++c) {
+            const int q = tid + c * NTP;
             const double kp = tq[c];
             yp[c] = fma(h3, kp, yp[c]);
             yq[c] = fma(h3, kq[c], yq[c]);
@@ -123,22 +129,22 @@ __device__ void rk4_steps(double (&psi)[PROP_QN], double (&dps)[PROP_QN], double
             if (q < n2) S0[q] = fma(h2, kp, psi[c]);
         }
         __syncthreads();
-        mat_times(kq, W1, S0, n, tid);                  // stage 3
+        mat_times<NTP, QN>(kq, W1, S0, n, tid);                  // stage 3
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
+        for (int c = 0; c < QN; ++c) {
+            const int q = tid + c * NTP;
             const double kp = tq[c];
             yp[c] = fma(h3, kp, yp[c]);
             yq[c] = fma(h3, kq[c], yq[c]);
             tq[c] = fma(hh, kq[c], dps[c]);
             if (q < n2) S1[q] = fma(hh, kp, psi[c]);
         }
-        build_w(W0, As, eps_s, lt_s, n, lmax, z, r0 + hh, 1.0, tid);
+        build_w<NTP, QN>(W0, As, eps_s, lt_s, n, lmax, z, r0 + hh, 1.0, tid);
         __syncthreads();
-        mat_times(kq, W0, S1, n, tid);                  // stage 4
+        mat_times<NTP, QN>(kq, W0, S1, n, tid);                  // stage 4
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
+        for (int c = 0; c < QN; ++c) {
+            const int q = tid + c * NTP;
             psi[c] = fma(h6, tq[c], yp[c]);
             dps[c] = fma(h6, kq[c], yq[c]);
             if (q < n2) S0[q] = psi[c];
@@ -151,14 +157,15 @@ __device__ void rk4_steps(double (&psi)[PROP_QN], double (&dps)[PROP_QN], double
 // elements and leaves G^{-T} in its right half (M[j ld + n + k] =
 // (G^{-1})_kj). The caller has passed a barrier since M was last read.
 // False if G is singular.
-__device__ bool invert_owned(const double (&g)[PROP_QN], double *M, int n, ElimShared *esh, int tid)
+template <int NTP, int QN>
+__device__ bool invert_owned(const double (&g)[QN], double *M, int n, ElimShared *esh, int tid)
 {
     const int n2 = n * n, ld = 2 * n + 1;
-    for (int q = tid; q < n * ld; q += NT) M[q] = 0.0;
+    for (int q = tid; q < n * ld; q += NTP) M[q] = 0.0;
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c) {
-        const int q = tid + c * NT;
+    for (int c = 0; c < QN; ++c) {
+        const int q = tid + c * NTP;
         if (q < n2) {
             const int i = q / n, j = q - (q / n) * n;
             M[j * ld + i] = g[c];
@@ -167,24 +174,25 @@ __device__ bool invert_owned(const double (&g)[PROP_QN], double *M, int n, ElimS
     }
     if (tid == 0) esh->bad = 0;
     __syncthreads();
-    block_eliminate<double>(M, ld, n, 2 * n, esh);
+    block_eliminate<double, NTP>(M, ld, n, 2 * n, esh);
     if (esh->bad) return false;
-    block_backsub<double>(M, ld, n, n, n, 0);
+    block_backsub<double, NTP>(M, ld, n, n, n, 0);
     return true;
 }
 
 // x <- x G^{-1} at the owned elements, with G^{-T} in M (as invert_owned
 // leaves it) and SX (n^2 doubles, disjoint from M) as staging.
-__device__ void times_ginv(double (&x)[PROP_QN], const double *M, double *SX, int n, int tid)
+template <int NTP, int QN>
+__device__ void times_ginv(double (&x)[QN], const double *M, double *SX, int n, int tid)
 {
     const int n2 = n * n, ld = 2 * n + 1;
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c)
-        if (tid + c * NT < n2) SX[tid + c * NT] = x[c];
+    for (int c = 0; c < QN; ++c)
+        if (tid + c * NTP < n2) SX[tid + c * NTP] = x[c];
     __syncthreads();
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c) {
-        const int q = min(tid + c * NT, n2 - 1);
+    for (int c = 0; c < QN; ++c) {
+        const int q = min(tid + c * NTP, n2 - 1);
         const int i = q / n, j = q - (q / n) * n;
         double acc = 0.0;
         for (int k = 0; k < n; ++k) acc = fma(SX[i * n + k], M[j * ld + n + k], acc);
@@ -193,13 +201,14 @@ __device__ void times_ginv(double (&x)[PROP_QN], const double *M, double *SX, in
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double *__restrict__ E,
+template <int NTP, int QN, int NMAX>
+__global__ void __launch_bounds__(NTP, NTP == 256 ? 2 : 1) propagate_kernel(PwDev pw, const double *__restrict__ E,
                                                           const double *__restrict__ A, int lmax, double r1,
                                                           int steps, double *__restrict__ Rp,
                                                           int *__restrict__ status)
 {
     extern __shared__ double sm[];
-    __shared__ double eps_s[PROP_MAXN], lt_s[PROP_MAXN];
+    __shared__ double eps_s[NMAX], lt_s[NMAX];
     __shared__ ElimShared esh;
     const int e = blockIdx.x, tid = threadIdx.x;
     const int n = pw.n, n2 = n * n;
@@ -209,16 +218,16 @@ __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double
     double *SF = sm, *SG = sm + n2, *TA = sm + 2 * n2, *TB = sm + 3 * n2, *As = sm + 4 * n2;
     const double a = pw.a, b = pw.b, z = pw.z, x = E[e];
     double *Re = Rp + (size_t)e * tri_ld(n);
-    for (int q = tid; q < lmax * n2; q += NT) As[q] = A[q];
-    for (int i = tid; i < n; i += NT) {
+    for (int q = tid; q < lmax * n2; q += NTP) As[q] = A[q];
+    for (int i = tid; i < n; i += NTP) {
         eps_s[i] = x - pw.e_thr[i];
         lt_s[i] = (double)pw.l[i] * (pw.l[i] + 1);
     }
     const double h = (r1 - a) / steps, t12 = h * h / 12.0;
-    double psi[PROP_QN], dl[PROP_QN], tp[PROP_QN], tpp[PROP_QN], kq[PROP_QN];
+    double psi[QN], dl[QN], tp[QN], tpp[QN], kq[QN];
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c) {
-        const int q = tid + c * NT;
+    for (int c = 0; c < QN; ++c) {
+        const int q = tid + c * NTP;
         psi[c] = dl[c] = 0.0;
         if (q < n2) {
             const int i = q / n, j = q - (q / n) * n;
@@ -229,22 +238,22 @@ __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double
     }
     __syncthreads();
     // t_0 = T_0 Psi_0
-    build_w(TA, As, eps_s, lt_s, n, lmax, z, a, t12, tid);
+    build_w<NTP, QN>(TA, As, eps_s, lt_s, n, lmax, z, a, t12, tid);
     __syncthreads();
-    mat_times(tpp, TA, SF, n, tid);
+    mat_times<NTP, QN>(tpp, TA, SF, n, tid);
     // Psi_1 (dl: Psi'(a) in, then D_1 = Psi_1 - Psi_0), t_1 = T_1 Psi_1
     {
-        double p0[PROP_QN];
+        double p0[QN];
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) p0[c] = psi[c];
-        rk4_steps(psi, dl, SF, SG, TA, TB, As, eps_s, lt_s, n, lmax, z, a, h / PROP_START_SUB, PROP_START_SUB,
+        for (int c = 0; c < QN; ++c) p0[c] = psi[c];
+        rk4_steps<NTP, QN>(psi, dl, SF, SG, TA, TB, As, eps_s, lt_s, n, lmax, z, a, h / PROP_START_SUB, PROP_START_SUB,
                   tid);
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) dl[c] = psi[c] - p0[c];
+        for (int c = 0; c < QN; ++c) dl[c] = psi[c] - p0[c];
     }
-    build_w(TA, As, eps_s, lt_s, n, lmax, z, a + h, t12, tid);
+    build_w<NTP, QN>(TA, As, eps_s, lt_s, n, lmax, z, a + h, t12, tid);
     __syncthreads();
-    mat_times(tp, TA, SF, n, tid);
+    mat_times<NTP, QN>(tp, TA, SF, n, tid);
     // restart every `sector` steps, a sector being 1 / kappa_max long,
     // kappa_max^2 = max_i (l_i(l_i+1)/a^2 - eps_i)
     int sector = steps;
@@ -259,24 +268,24 @@ __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double
         double *Tk = (k & 1) ? TB : TA;
         // F and T_{k+1}
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
-            const int q = tid + c * NT;
+        for (int c = 0; c < QN; ++c) {
+            const int q = tid + c * NTP;
             if (q < n2) SF[q] = psi[c] + dl[c] + fma(10.0, tp[c], tpp[c]);
         }
-        build_w(Tk, As, eps_s, lt_s, n, lmax, z, a + (k + 1) * h, t12, tid);
+        build_w<NTP, QN>(Tk, As, eps_s, lt_s, n, lmax, z, a + (k + 1) * h, t12, tid);
         __syncthreads();
         // T F
-        mat_times(kq, Tk, SF, n, tid);
+        mat_times<NTP, QN>(kq, Tk, SF, n, tid);
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c)
-            if (tid + c * NT < n2) SG[tid + c * NT] = kq[c];
+        for (int c = 0; c < QN; ++c)
+            if (tid + c * NTP < n2) SG[tid + c * NTP] = kq[c];
         __syncthreads();
         // t_{k+1} = T F + T (T F); D, Psi; shift t
-        double g2[PROP_QN];
-        mat_times(g2, Tk, SG, n, tid);
+        double g2[QN];
+        mat_times<NTP, QN>(g2, Tk, SG, n, tid);
         const bool last = k == steps;
 #pragma unroll
-        for (int c = 0; c < PROP_QN; ++c) {
+        for (int c = 0; c < QN; ++c) {
             const double tn = kq[c] + g2[c];
             const double d = dl[c] + tn + fma(10.0, tp[c], tpp[c]);
             if (!last) {
@@ -293,37 +302,37 @@ __global__ void __launch_bounds__(NT, 2) propagate_kernel(PwDev pw, const double
         if (k % sector == 0 && k + 1 < steps) {
             // right-multiply the state by G^{-1}, G = r D / h - b Psi
             const double r = a + (k + 1) * h;
-            double g[PROP_QN];
+            double g[QN];
 #pragma unroll
-            for (int c = 0; c < PROP_QN; ++c) g[c] = fma(r / h, dl[c], -b * psi[c]);
+            for (int c = 0; c < QN; ++c) g[c] = fma(r / h, dl[c], -b * psi[c]);
             __syncthreads();
-            if (!invert_owned(g, sm, n, &esh, tid)) {
+            if (!invert_owned<NTP, QN>(g, sm, n, &esh, tid)) {
                 if (tid == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
                 return;
             }
             double *SX = sm + 3 * n2;
-            times_ginv(psi, sm, SX, n, tid);
-            times_ginv(dl, sm, SX, n, tid);
-            times_ginv(tp, sm, SX, n, tid);
-            times_ginv(tpp, sm, SX, n, tid);
+            times_ginv<NTP, QN>(psi, sm, SX, n, tid);
+            times_ginv<NTP, QN>(dl, sm, SX, n, tid);
+            times_ginv<NTP, QN>(tp, sm, SX, n, tid);
+            times_ginv<NTP, QN>(tpp, sm, SX, n, tid);
         }
     }
     // R(r1) = Psi_N (r1 Psi'_N - b Psi_N)^{-1}, written symmetrised
-    double g[PROP_QN];
+    double g[QN];
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c) g[c] = fma(r1, dl[c], -b * psi[c]);
+    for (int c = 0; c < QN; ++c) g[c] = fma(r1, dl[c], -b * psi[c]);
     __syncthreads();
-    if (!invert_owned(g, sm, n, &esh, tid)) {
+    if (!invert_owned<NTP, QN>(g, sm, n, &esh, tid)) {
         if (tid == 0) atomicCAS(status + e, RM_OK, RM_ESINGULAR);
         return;
     }
     double *SX = sm + 3 * n2;
-    times_ginv(psi, sm, SX, n, tid);
+    times_ginv<NTP, QN>(psi, sm, SX, n, tid);
 #pragma unroll
-    for (int c = 0; c < PROP_QN; ++c)
-        if (tid + c * NT < n2) SX[tid + c * NT] = psi[c];
+    for (int c = 0; c < QN; ++c)
+        if (tid + c * NTP < n2) SX[tid + c * NTP] = psi[c];
     __syncthreads();
-    for (int q = tid; q < tri_count(n); q += NT) {
+    for (int q = tid; q < tri_count(n); q += NTP) {
         int i, j;
         tri_pair(q, n, i, j);
         Re[tri_idx(i, j, n)] = 0.5 * (SX[i * n + j] + SX[j * n + i]);
@@ -672,6 +681,17 @@ __global__ void __launch_bounds__(NT, 2) propagate_small_kernel(PwDev pw, const 
 
 }  // namespace
 
+bool propagate_fits(int n, int lmax)
+{
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        optin = 227 * 1024;
+    }
+    return propagate_smem(n, lmax) <= (size_t)optin;
+}
+
 size_t propagate_smem(int n, int lmax)
 {
     const int gt = n <= PROP_SMALL_MAXN ? prop_groups(n) * n * n : n * n;
@@ -681,7 +701,8 @@ size_t propagate_smem(int n, int lmax)
 cudaError_t launch_propagate(const PwDev &pw, const double *E, int nE, const double *A, int lmax, double r1,
                              int steps, double *Rp, int *status, cudaStream_t s)
 {
-    if (pw.n > PROP_MAXN || lmax < 0 || lmax > PROP_MAX_LAMBDA || steps < 2) return cudaErrorInvalidValue;
+    if (pw.n > PROP_MAXN || lmax < 0 || lmax > PROP_MAX_LAMBDA || steps < 2 || !propagate_fits(pw.n, lmax))
+        return cudaErrorInvalidValue;
     if (nE == 0) return cudaSuccess;
     const size_t smem = propagate_smem(pw.n, lmax);
     if (pw.n <= PROP_SMALL_MAXN) {
@@ -692,9 +713,17 @@ cudaError_t launch_propagate(const PwDev &pw, const double *E, int nE, const dou
         propagate_small_kernel<<<(nE + G - 1) / G, NT, smem, s>>>(pw, E, nE, A, lmax, r1, steps, Rp, status);
         return cudaGetLastError();
     }
-    cudaError_t err = cudaFuncSetAttribute(propagate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (pw.n <= 32) {
+        cudaError_t err =
+            cudaFuncSetAttribute(propagate_kernel<256, 4, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        propagate_kernel<256, 4, 32><<<nE, 256, smem, s>>>(pw, E, A, lmax, r1, steps, Rp, status);
+        return cudaGetLastError();
+    }
+    cudaError_t err =
+        cudaFuncSetAttribute(propagate_kernel<512, 8, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    propagate_kernel<<<nE, NT, smem, s>>>(pw, E, A, lmax, r1, steps, Rp, status);
+    propagate_kernel<512, 8, 64><<<nE, 512, smem, s>>>(pw, E, A, lmax, r1, steps, Rp, status);
     return cudaGetLastError();
 }
 

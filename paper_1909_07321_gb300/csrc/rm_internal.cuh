@@ -105,9 +105,12 @@ struct Opts {
 // Outer-region propagation (see propagate.cu): R(a) in Rp (packed, stride
 // tri_ld(n)) replaced by R(r1) for every energy with status RM_OK; pw carries
 // the inner radius a; A = [lmax][n][n] coefficients on the device.
-constexpr int PROP_MAXN = 32;
+constexpr int PROP_MAXN = 64;
 constexpr int PROP_MAX_LAMBDA = 4;
 size_t propagate_smem(int n, int lmax);
+// The state and the coefficients fit one CTA's shared memory (above 32
+// channels at most (4 + lmax) n^2 doubles: lmax <= 3 at 64 channels).
+bool propagate_fits(int n, int lmax);
 cudaError_t launch_propagate(const PwDev &pw, const double *E, int nE, const double *A, int lmax, double r1,
                              int steps, double *Rp, int *status, cudaStream_t s);
 // FP32 matching and T step (direct mode, n <= solve_small_max_n()),

@@ -659,6 +659,9 @@ extern "C" int rm_set_multipoles(rm_ctx *ctx, int pw, int lambda_max, const doub
                                    PROP_MAXN, n);
     if (lambda_max < 0 || lambda_max > PROP_MAX_LAMBDA)
         return fail(ctx, RM_EINVAL, "lambda_max=%d out of [0,%d]", lambda_max, PROP_MAX_LAMBDA);
+    if (!propagate_fits(n, lambda_max))
+        return fail(ctx, RM_EUNSUPPORTED, "propagation of %d channels with lambda_max=%d needs more shared memory "
+                    "than one CTA has", n, lambda_max);
     if (!A) return fail(ctx, RM_EINVAL, "NULL multipole coefficients");
     if (!std::isfinite(r1) || !(r1 >= P.a)) return fail(ctx, RM_EINVAL, "r1=%g must be >= a=%g", r1, P.a);
     if (n_steps < 2) return fail(ctx, RM_EINVAL, "n_steps=%d must be >= 2", n_steps);

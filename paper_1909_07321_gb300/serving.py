@@ -22,7 +22,10 @@ tables) run synchronously in the admission loop; with the shared cache each
 set is loaded once per residency, not once per slot.
 
 Latency of a request = completion time on the host (Omega copied back)
-minus its arrival time.
+minus its arrival time. A completed request's Omega goes to the server's
+sink (a callable taking the request and its Omega rows) if one is given,
+else to request.omega: a long stream's results (up to 8192 energies x 70k
+level pairs each) need not all stay in host memory.
 """
 import collections
 import time
@@ -67,10 +70,11 @@ class Server:
     arrival times are replayed in real time."""
 
     def __init__(self, n_slots=4, precision=0, solve_precision=0, mem_budget=96 << 30,
-                 lane_workspace=16 << 30, cache_sets=64, device=0):
+                 lane_workspace=16 << 30, cache_sets=64, device=0, sink=None):
         from . import rmgb
 
         self.rmgb = rmgb
+        self.sink = sink
         self.precision = precision
         self.device = device
         self.mem_budget = mem_budget
@@ -157,8 +161,11 @@ class Server:
         req = slot["req"]
         om = np.empty((req.E.size, req.n_tri()), dtype=np.float64)
         self.ctx.lane_collision_strengths(slot["lane"], om, reset=True)
-        req.omega = om
         req.t_done = now_fn()
+        if self.sink is not None:
+            self.sink(req, om)
+        else:
+            req.omega = om
         slot["cache"]["users"] -= 1
         slot.update(req=None, cache=None)
 

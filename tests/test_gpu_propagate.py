@@ -107,6 +107,39 @@ def test_propagated_lambda_max_4_and_b(rt):
     _compare(E, K, no, st, om, ref)
 
 
+@pytest.mark.parametrize("n,lmax,mode", [(20, 2, 0), (48, 2, 0), (48, 2, 1), (64, 3, 0), (64, 3, 1)])
+def test_propagated_above_16_channels(rt, n, lmax, mode):
+    """The one-energy-per-CTA kernels: 20 channels (the 256-thread kernel,
+    ragged against its 32-channel tiles), 48 and 64 channels (the 512-thread
+    kernel; 64 with lambda_max = 3, the most that fits one CTA), direct and
+    MQDT modes, against the oracle at 1e-9."""
+    pw = _pw(n=n, seed=900 + n, z=2.0)
+    A = _coupling(n, lmax, 40 + n, scale=0.2)
+    E = _energies(pw, m=16, seed=n)
+    K, no, st, om = _gpu_solve(rt, pw, E, A, mode)
+    ref = pr.solve_energies(pw, E, A, R1, mode=oracle.MODE_MQDT if mode else oracle.MODE_DIRECT)
+    assert (ref["status"] == 0).sum() >= E.size - 2
+    _compare(E, K, no, st, om, ref)
+
+
+def test_propagated_64_channels_mixed(rt):
+    """64 channels, bf16x3 formation and the FP32 solve on propagated R:
+    Omega within 1e-4 of the oracle in the median and 1e-2 at most (relative
+    to the energy's largest entry). The FP32 elimination's backward error
+    grows as n 2^-24 (4e-6 at 64 channels, before the matching's
+    conditioning), 16x that of the 4-channel case's 1e-5."""
+    pw = _pw(n=64, seed=964, z=2.0)
+    A = _coupling(64, 3, 104, scale=0.2)
+    E = _energies(pw, m=16, seed=64)
+    K, no, st, om = _gpu_solve(rt, pw, E, A, 0, precision=2, solve_precision=1)
+    ref = pr.solve_energies(pw, E, A, R1)
+    assert np.array_equal(st, ref["status"])
+    errs = [np.abs(om[m] - ref["omega"][m]).max() / np.abs(ref["omega"][m]).max()
+            for m in range(E.size) if not st[m] and np.abs(ref["omega"][m]).max()]
+    assert len(errs) >= 8
+    assert np.median(errs) < 1e-4 and max(errs) < 1e-2, errs
+
+
 def test_coupling_matters_and_off_switch(rt):
     """The coupling changes Omega; lambda_max = 0 (A None) restores the
     unpropagated results bit for bit; reloading the poles clears it."""
@@ -188,10 +221,16 @@ def test_set_multipoles_rejects_bad_arguments(rt):
         with pytest.raises(rmgb.RmError) as ei:
             ctx.set_multipoles(1, A, R1, STEPS)
         assert ei.value.code == rmgb.RM_ENOTLOADED
-        big = synth.random_pw(3, 33, 100, z=1.0, a=A_)
+        big = synth.random_pw(3, 65, 130, z=1.0, a=A_)
         ctx.load_pw(2, big)
         with pytest.raises(rmgb.RmError) as ei:
-            ctx.set_multipoles(2, np.zeros((1, 33, 33)), R1, STEPS)
+            ctx.set_multipoles(2, np.zeros((1, 65, 65)), R1, STEPS)
+        assert ei.value.code == rmgb.RM_EUNSUPPORTED
+        # 64 channels: lambda_max = 3 fits one CTA's shared memory, 4 does not
+        ctx.load_pw(3, synth.random_pw(4, 64, 128, z=1.0, a=A_))
+        ctx.set_multipoles(3, np.zeros((3, 64, 64)), R1, STEPS)
+        with pytest.raises(rmgb.RmError) as ei:
+            ctx.set_multipoles(3, np.zeros((4, 64, 64)), R1, STEPS)
         assert ei.value.code == rmgb.RM_EUNSUPPORTED
 
 

@@ -60,8 +60,9 @@ class _Ctx:
 class _Server(serving.Server):
     """The server over the fake context; records the budget state at every launch."""
 
-    def __init__(self, n_slots, mem_budget, cache_sets):
+    def __init__(self, n_slots, mem_budget, cache_sets, sink=None):
         self.precision = 2
+        self.sink = sink
         self.device = 0
         self.mem_budget = mem_budget
         self.cache_sets = cache_sets
@@ -168,3 +169,19 @@ def test_prepare_sizes_every_lane_for_the_largest_request():
     assert sorted(l for l, _, _ in srv.ctx.reserved) == [0, 1, 2]
     assert all(ne == n_e for _, _, ne in srv.ctx.reserved)
     assert _loads(srv) == [id(big.pw)]
+
+
+def test_sink_receives_each_result_once_and_nothing_is_kept():
+    reqs = _requests(16, seed=6)
+    got = {}
+
+    def sink(req, om):
+        assert req.id not in got and req.t_done is not None
+        got[req.id] = om[::3].copy()
+
+    srv = _Server(n_slots=3, mem_budget=1 << 40, cache_sets=8, sink=sink)
+    srv.run(reqs, idle_sleep=0.0)
+    assert sorted(got) == [r.id for r in reqs]
+    for r in reqs:
+        assert r.omega is None
+        np.testing.assert_array_equal(got[r.id], _result(r.pw, r.E)[::3])
