@@ -7,6 +7,8 @@
 // barrier.
 #pragma once
 
+#include "rcp.cuh"
+
 #include <math.h>
 
 #include "rm_internal.cuh"
@@ -148,12 +150,17 @@ __device__ void spd_sweep_inverse(double *A, int ld, int m, double *v, ElimShare
     __syncthreads();
 }
 
-// Complex FP32 reciprocal (scaled against overflow) and product.
+// Complex FP32 reciprocal 1/d = conj(d) / |d|^2 and product. d is first
+// scaled by a power of two (exact) so that its larger component lies in
+// [1, 2) and |d|^2 can neither overflow nor underflow; the scale is applied
+// again to the result. A zero, infinite or NaN d gives a non-finite result.
 __device__ __forceinline__ float2 crcp_f(float2 d)
 {
-    const float s = fmaxf(fabsf(d.x), fabsf(d.y));
-    const float xr = d.x / s, xi = d.y / s;
-    const float t = __frcp_rn(s * fmaf(xr, xr, xi * xi));
+    const float m = fmaxf(fabsf(d.x), fabsf(d.y));
+    const int ex = min((__float_as_int(m) >> 23) & 0xff, 253);   // biased exponent of m
+    const float sc = __int_as_float((254 - ex) << 23);            // 2^(127 - ex)
+    const float xr = d.x * sc, xi = d.y * sc;
+    const float t = rcp_nr_f(fmaf(xr, xr, xi * xi)) * sc;   // |d'|^2 in [1, 8)
     return make_float2(xr * t, -xi * t);
 }
 

@@ -19,4 +19,18 @@ __device__ __forceinline__ double rcp_nr(double x)
     return fma(r, e, r);
 }
 
+// 1/x in FP32 for the pivots of the FP32 matching solve: rcp.approx.ftz.f32
+// refined by one Newton-Raphson step r <- r + r (1 - x r) (fused), which
+// squares the approximation's relative error, leaving the result within one
+// ulp of 1/x for normal, finite x. Subnormal x is flushed to zero (the
+// result is then infinite); callers treat |x| below the smallest normal
+// number as a zero pivot.
+__device__ __forceinline__ float rcp_nr_f(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    const float e = fmaf(-x, r, 1.0f);
+    return fmaf(r, e, r);
+}
+
 }  // namespace rmgb

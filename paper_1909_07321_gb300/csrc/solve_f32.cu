@@ -9,23 +9,42 @@
 // and columns tx + 16 j of the n x (n + n_o) augmented matrix, so the 16
 // owners of a column form one half-warp. Gauss-Jordan elimination with
 // partial pivoting, the pivot rows left in place (implicit pivoting): for
-// column c its half-warp finds the pivot row p among the rows not yet used
-// (largest magnitude to 2^-17, lowest index among those) by one max-reduction
-// and publishes the multipliers and p; after one barrier every thread takes the pivot row's values
-// for its columns by a shuffle from the lane of its own half-warp that holds
-// row p, and every other row r (used or not) takes a_rj -= (a_rc / a_pc) a_pj
-// for j > c. After n columns the unknowns are x_c = a_{p(c), rhs} / a_{p(c), c},
-// with no back-substitution.
+// column c the pivot row p is the largest magnitude among the rows not yet
+// used (to 2^-17, lowest index among those), every other row r (used or not)
+// takes a_rj -= m_r a_pj, m_r = a_rc (1 / a_pc), for j > c (the reciprocal
+// by rcp.approx and one Newton-Raphson step, within one ulp; a pivot below
+// the smallest normal number counts as zero). After n columns the unknowns
+// are x_c = a_{p(c), rhs} / a_{p(c), c}, with no back-substitution.
+//
+// The columns are eliminated in blocks of KB. The block's columns are copied
+// to shared memory and one warp (lane l holds rows l + 32 s) runs the KB
+// steps on them alone: pivot by one warp max-reduction, multipliers, and the
+// step's update of the block's later columns. It publishes the KB pivot rows
+// and multiplier columns; after one barrier every thread applies the KB
+// steps to its columns past the block in the same order (the pivot row's
+// values for a thread's columns come from the thread of its half-warp that
+// holds that row, through shared memory). Every element therefore takes the
+// same operations, in the same order, as in the column-by-column
+// elimination, with two barriers per KB columns instead of one per column;
+// columns left of the block and the padding beyond n + n_o are not touched.
 //
 // (d) T = 2iK(1 - iK)^{-1} = 2(1 - iK)^{-1} - 2 (Section "Glossary of
 // terms"): 1 - iK (complex, K symmetrised) in registers in the same 16 x 16
 // layout, inverted in place by the sweep operator (Gauss-Jordan without
 // pivoting: its Hermitian part is the identity, so every pivot has a
-// positive real part); the matrix is symmetric, so each step publishes one
-// column and needs one barrier. The sweep leaves W = -(1 - iK)^{-1}, and
-// |T_ab|^2 = 4 |W_ab + delta_ab|^2. For target levels I <= J one thread owns
-// Omega_IJ(E) and adds g sum_{a in I, b in J} |T_ab|^2 in FP64, in a fixed
-// order (deterministic, no atomics).
+// positive real part). One sweep step on pivot k with u = column k and
+// d = u_k, v = u / d: z_ij -= v_i u_j, then column k <- v, row k <- v^T and
+// z_kk <- -1/d. The pivots are taken in blocks the same way: one warp sweeps
+// the block's columns through its KB steps and publishes each step's u and v;
+// every thread then applies z_ij -= v_i u_j for the KB steps and takes the
+// block's rows and columns from the swept block (the matrix is symmetric).
+// The sweep leaves W = -(1 - iK)^{-1}, and |T_ab|^2 = 4 |W_ab + delta_ab|^2.
+// For target levels I <= J one thread owns Omega_IJ(E) and adds
+// g sum_{a in I, b in J} |T_ab|^2, the level pair's sum in FP32 (as the
+// values; relative error <= |I||J| 2^-24) and the addition to Omega in FP64
+// by one atomic add, the only addition to that entry in the launch: launches
+// on a stream are ordered, so the sum over partial waves is deterministic,
+// and the add needs no read of Omega by the kernel.
 #include <math.h>
 
 #include "dense_smem.cuh"
@@ -36,6 +55,8 @@ namespace {
 
 constexpr int G16 = 16;                          // thread grid 16 x 16
 constexpr int MAXN = SOLVE_SMALL_MAXN;
+constexpr int KBG = 8;                           // columns per elimination block
+constexpr float kMinNormal = 1.17549435e-38f;    // smallest normal FP32 number: smaller pivots count as zero
 
 // Element k of a register array for an index k that is the same in every
 // thread of the warp: a uniform branch per case keeps the array in
@@ -50,68 +71,139 @@ __device__ __forceinline__ T pick(const T (&v)[N], int k)
     return r;
 }
 
-// One step of the sweep on pivot k, after the pivot column has been
-// published: z_ij -= v_i u_j, then column k <- v, row k <- v^T and the pivot
-// <- -1/d (v = u / d, u = column k before the step; uniform tile indices).
-template <int TR>
-__device__ __forceinline__ void sweep_apply(float2 (&z)[TR][TR], int k, int tx, int ty, const float2 *vc,
-                                            const float2 *uc, float2 dinv)
+// Element [s][q] of a 2-D register array, s uniform, q a compile-time index.
+template <int S, int Q, typename T>
+__device__ __forceinline__ T pick_s(const T (&v)[S][Q], int s, int q)
 {
-    const int kk = k >> 4;
-    float2 vi[TR], uj[TR];
+    T r = v[0][q];
 #pragma unroll
-    for (int i = 0; i < TR; ++i) {
-        vi[i] = vc[ty + G16 * i];
-        uj[i] = uc[tx + G16 * i];
+    for (int k = 1; k < S; ++k)
+        if (s == k) r = v[k][q];
+    return r;
+}
+
+__device__ __forceinline__ float2 shfl2(float2 v, int src)
+{
+    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Loads TR consecutive floats (f, 16-byte aligned) by vector loads.
+template <int TR>
+__device__ __forceinline__ void load_row(float (&f)[TR], const float *src)
+{
+#pragma unroll
+    for (int i = 0; i < TR; i += 4) {
+        if (i + 4 <= TR) {
+            const float4 v = *reinterpret_cast<const float4 *>(src + i);
+            f[i] = v.x, f[i + 1] = v.y, f[i + 2] = v.z, f[i + 3] = v.w;
+        } else {
+            const float2 v = *reinterpret_cast<const float2 *>(src + i);
+            f[i] = v.x, f[i + 1] = v.y;
+        }
     }
+}
+
+// Whether the elimination steps skip the tiles left of the block and the
+// padding tiles (uniform branches) or update every tile.
+constexpr bool kSkipTiles = true;
+
+// One elimination step on this thread's tiles: the thread of the half-warp
+// that holds pivot row p writes its values for the half-warp's columns to rb,
+// then t_ij -= f_i rb_j (f: the step's multipliers for this thread's rows).
+template <int TR, int TC, int TRP>
+__device__ __forceinline__ void gj_step(float (&t)[TR][TC], int p, const float *fq, float *rb, int ty, int jlo,
+                                        int jhi)
+{
+    if (ty == (p & 15)) {
+        const int ip = p >> 4;
 #pragma unroll
-    for (int i = 0; i < TR; ++i) {
+        for (int i = 0; i < TR; ++i)
+            if (ip == i) {
 #pragma unroll
-        for (int j = 0; j < TR; ++j) {
+                for (int j = 0; j < TC; j += 4)
+                    *reinterpret_cast<float4 *>(rb + j) = make_float4(t[i][j], t[i][j + 1], t[i][j + 2], t[i][j + 3]);
+            }
+    }
+    __syncwarp();
+    float f[TR], u[TC];
+    load_row<TR>(f, fq);
+    load_row<TC>(u, rb);
+#pragma unroll
+    for (int j = 0; j < TC; ++j) {
+        if (!kSkipTiles || (j >= jlo && j < jhi)) {
+#pragma unroll
+            for (int i = 0; i < TR; ++i) t[i][j] = fmaf(-f[i], u[j], t[i][j]);
+        }
+    }
+}
+
+// Shared-memory layout of the blocked elimination and sweep for TR row tiles
+// (sizes in floats; both phases use the same buffer one after the other).
+template <int TR, int TC>
+struct BlkLayout {
+    static constexpr int ROWS = G16 * TR;
+    static constexpr int TRP = (TR + 3) & ~3;     // per-thread row values, padded for vector loads
+    // elimination: block columns [KBG][ROWS], multipliers [KBG][16][TRP],
+    // pivot-row values [2][16][TC]
+    static constexpr int GJ = KBG * ROWS + KBG * G16 * TRP + 2 * G16 * TC;
+    // sweep (float2): block columns and swept block [KBT][ROWS] each, u and v
+    // [KBT][16][VST] each (VST = TRP + 2: rows of consecutive ty start in
+    // different banks), KBT <= 8
+    static constexpr int VST = TRP + 2;
+    static constexpr int SW = 2 * (2 * 8 * ROWS + 2 * 8 * G16 * VST);
+    static constexpr int FLOATS = GJ > SW ? GJ : SW;
+};
+
+// Loads TS consecutive complex values (16-byte aligned) by vector loads.
+template <int TS>
+__device__ __forceinline__ void load_cvec(float2 (&v)[TS], const float2 *src)
+{
+#pragma unroll
+    for (int i = 0; i < TS; i += 2) {
+        if (i + 2 <= TS) {
+            const float4 w = *reinterpret_cast<const float4 *>(src + i);
+            v[i] = make_float2(w.x, w.y), v[i + 1] = make_float2(w.z, w.w);
+        } else {
+            v[i] = src[i];
+        }
+    }
+}
+
+// One sweep step on this thread's tiles: z_ij -= v_i u_j (v for its rows,
+// u for its columns).
+template <int TS>
+__device__ __forceinline__ void sweep_step(float2 (&z)[TS][TS], const float2 *vq, const float2 *uq)
+{
+    float2 vi[TS], uj[TS];
+    load_cvec<TS>(vi, vq);
+    load_cvec<TS>(uj, uq);
+#pragma unroll
+    for (int i = 0; i < TS; ++i) {
+#pragma unroll
+        for (int j = 0; j < TS; ++j) {
             float2 zz = z[i][j];
             zz.x = fmaf(-vi[i].x, uj[j].x, fmaf(vi[i].y, uj[j].y, zz.x));
             zz.y = fmaf(-vi[i].x, uj[j].y, fmaf(-vi[i].y, uj[j].x, zz.y));
             z[i][j] = zz;
         }
     }
-    if (tx == (k & 15)) {
-#pragma unroll
-        for (int j = 0; j < TR; ++j)
-            if (kk == j) {
-#pragma unroll
-                for (int i = 0; i < TR; ++i) z[i][j] = vi[i];
-            }
-    }
-    if (ty == (k & 15)) {
-#pragma unroll
-        for (int i = 0; i < TR; ++i)
-            if (kk == i) {
-#pragma unroll
-                for (int j = 0; j < TR; ++j) {
-                    const int c = tx + G16 * j;
-                    z[i][j] = (c == k) ? make_float2(-dinv.x, -dinv.y) : vc[c];
-                }
-            }
-    }
 }
 
-// Shared buffers of the T step's sweep (two per buffer: published pivot
-// columns alternate between steps), row stride `stride`.
-struct SweepShared {
-    float2 *ucol, *vcol, *ucol2, *vcol2;
-    float2 *dbuf, *dinvbuf, *dbuf2, *dinvbuf2;
-    int stride;
-};
-
-// T step for n_o <= 16 TS open channels (TS tiles per side in registers,
-// no padding tiles beyond them): W = -(1 - iK)^{-1} by the complex sweep, and
+// T step for n_o <= 16 TS open channels (TS tiles per side in registers),
+// pivots in blocks of KBT: W = -(1 - iK)^{-1} by the complex sweep, and
 // |T_ab|^2 = 4 |W_ab + delta_ab|^2 written over K in Pm. Returns false (in
 // every thread) if a pivot is zero or not finite.
-template <int TS>
-__device__ __forceinline__ bool t_sweep(float *Pm, int no, int tid, int lane, int tx, int ty, unsigned hmask,
-                                        const SweepShared &sh)
+template <int TS, int TR, int TC, int KBT>
+__device__ __forceinline__ bool t_sweep(float *Pm, int no, int lane, int warp, int tx, int ty, float *xs,
+                                        float2 *dk)
 {
-    const unsigned full = 0xffffffffu;
+    using L = BlkLayout<TR, TC>;
+    constexpr int ROWS = L::ROWS, VST = L::VST;
+    constexpr int RWT = (G16 * TS + 31) / 32;     // rows per lane of the sweeping warp
+    float2 *zp = reinterpret_cast<float2 *>(xs);  // [KBT][ROWS] the block's columns
+    float2 *zf = zp + 8 * ROWS;                   // [KBT][ROWS] the swept block
+    float2 *Vb = zf + 8 * ROWS;                   // [KBT][16][VST] v by (ty, i)
+    float2 *Ub = Vb + 8 * G16 * VST;              // [KBT][16][VST] u by (tx, j)
     float2 z[TS][TS];
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
@@ -124,107 +216,108 @@ __device__ __forceinline__ bool t_sweep(float *Pm, int no, int tid, int lane, in
             z[i][j] = v;
         }
     }
-    // Pivots in pairs (k even, k + 1) as in the elimination: the owner warp
-    // finds d1 = z_kk and v1 = column k / d1 (lanes 0-15), brings column k + 1
-    // through the step on k (lanes 16-31: w_i = z_i,k+1 - v1_i z_k+1,k, and
-    // w_k = z_k+1,k / d1), takes d2 = w_k+1, and publishes both; every thread
-    // then applies both steps after one barrier.
-    int k_first_single = 0;
-    for (int k = 0; k + 1 < no; k += 2) {
-        const int buf = (k >> 1) & 1;
-        const int kk = k >> 4;
-        if ((tx >> 1) == ((k & 15) >> 1)) {
-            float2 u[TS];
+    for (int k0 = 0; k0 < no; k0 += KBT) {
+        const int kb = min(KBT, no - k0);
+        const int jb = k0 >> 4, tx0 = k0 & 15;
+        if (tx >= tx0 && tx < tx0 + kb) {
+            float2 *col = zp + (tx - tx0) * ROWS;
 #pragma unroll
-            for (int i = 0; i < TS; ++i) u[i] = pick<TS>(z[i], kk);
-            const float2 ukk = pick<TS>(u, kk);
-            float2 d1, uk1;
-            d1.x = __shfl_sync(full, ukk.x, k & 15);
-            d1.y = __shfl_sync(full, ukk.y, k & 15);
-            uk1.x = __shfl_sync(full, ukk.x, (k + 1) & 15);   // z_{k+1,k}
-            uk1.y = __shfl_sync(full, ukk.y, (k + 1) & 15);
-            const float2 dinv1 = crcp_f(d1);
-            float2 w[TS];
+            for (int i = 0; i < TS; ++i) col[ty + G16 * i] = pick<TS>(z[i], jb);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            float2 a[RWT][KBT];
 #pragma unroll
-            for (int i = 0; i < TS; ++i) {
-                const float2 v1 = cmul_f(u[i], dinv1);
-                float2 vA;
-                vA.x = __shfl_xor_sync(full, v1.x, 16);
-                vA.y = __shfl_xor_sync(full, v1.y, 16);
-                const int r = ty + G16 * i;
-                const float2 uv = cmul_f(vA, uk1);
-                w[i] = (r == k) ? cmul_f(uk1, dinv1) : make_float2(u[i].x - uv.x, u[i].y - uv.y);
-                if ((tx & 1) == 0 && r < no) {
-                    sh.ucol[buf * sh.stride + r] = u[i];
-                    sh.vcol[buf * sh.stride + r] = v1;
-                }
+            for (int s = 0; s < RWT; ++s) {
+                const int r = lane + 32 * s;
+#pragma unroll
+                for (int q = 0; q < KBT; ++q)
+                    a[s][q] = (q < kb && r < G16 * TS) ? zp[q * ROWS + r] : make_float2(0.0f, 0.0f);
             }
-            const float2 wk1 = pick<TS>(w, kk);
-            float2 d2;
-            d2.x = __shfl_sync(full, wk1.x, 16 + ((k + 1) & 15));
-            d2.y = __shfl_sync(full, wk1.y, 16 + ((k + 1) & 15));
-            const float2 dinv2 = crcp_f(d2);
-            if (tx & 1) {
 #pragma unroll
-                for (int i = 0; i < TS; ++i) {
-                    const int r = ty + G16 * i;
-                    if (r < no) {
-                        sh.ucol2[buf * sh.stride + r] = w[i];
-                        sh.vcol2[buf * sh.stride + r] = cmul_f(w[i], dinv2);
+            for (int q = 0; q < KBT; ++q) {
+                if (q < kb) {
+                    const int kq = k0 + q;
+                    const float2 d = shfl2(pick_s(a, kq >> 5, q), kq & 31);
+                    const float2 dinv = crcp_f(d);
+                    float2 v[RWT];
+#pragma unroll
+                    for (int s = 0; s < RWT; ++s) {
+                        const int r = lane + 32 * s;
+                        v[s] = cmul_f(a[s][q], dinv);
+                        if (r < G16 * TS) {
+                            const int idx = (q * G16 + (r & 15)) * VST + (r >> 4);
+                            Ub[idx] = a[s][q];
+                            Vb[idx] = v[s];
+                        }
                     }
+#pragma unroll
+                    for (int q2 = 0; q2 < KBT; ++q2) {
+                        if (q2 != q && q2 < kb) {
+                            const int k2 = k0 + q2;
+                            const float2 u2 = shfl2(pick_s(a, k2 >> 5, q), k2 & 31);   // z_{k2, kq}
+                            const float2 vk2 = cmul_f(u2, dinv);
+#pragma unroll
+                            for (int s = 0; s < RWT; ++s) {
+                                const int r = lane + 32 * s;
+                                float2 zz = a[s][q2];
+                                zz.x = fmaf(-v[s].x, u2.x, fmaf(v[s].y, u2.y, zz.x));
+                                zz.y = fmaf(-v[s].x, u2.y, fmaf(-v[s].y, u2.x, zz.y));
+                                a[s][q2] = (r == kq) ? vk2 : zz;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int s = 0; s < RWT; ++s) {
+                        const int r = lane + 32 * s;
+                        a[s][q] = (r == kq) ? make_float2(-dinv.x, -dinv.y) : v[s];
+                    }
+                    if (lane == 0) dk[q] = d;
                 }
             }
-            if (lane == 0) {
-                sh.dbuf[buf] = d1;
-                sh.dinvbuf[buf] = dinv1;
-                sh.dbuf2[buf] = d2;
-                sh.dinvbuf2[buf] = dinv2;
+#pragma unroll
+            for (int s = 0; s < RWT; ++s) {
+                const int r = lane + 32 * s;
+#pragma unroll
+                for (int q = 0; q < KBT; ++q)
+                    if (q < kb && r < G16 * TS) zf[q * ROWS + r] = a[s][q];
             }
         }
         __syncthreads();
-        const float2 d1 = sh.dbuf[buf], d2 = sh.dbuf2[buf];
-        if (!(fabsf(d1.x) + fabsf(d1.y) > 0.0f) || !isfinite(d1.x) || !isfinite(d1.y) ||
-            !(fabsf(d2.x) + fabsf(d2.y) > 0.0f) || !isfinite(d2.x) || !isfinite(d2.y)) {
-            return false;
+        bool bad = false;
+        for (int q = 0; q < kb; ++q) {
+            const float2 d = dk[q];
+            bad |= !(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y);
         }
-        sweep_apply<TS>(z, k, tx, ty, sh.vcol + buf * sh.stride, sh.ucol + buf * sh.stride, sh.dinvbuf[buf]);
-        sweep_apply<TS>(z, k + 1, tx, ty, sh.vcol2 + buf * sh.stride, sh.ucol2 + buf * sh.stride, sh.dinvbuf2[buf]);
-        k_first_single = k + 2;
-    }
-    for (int k = k_first_single; k < no; ++k) {
-        const int buf = (k >> 1) & 1;
-        const int kk = k >> 4;
-        if (tx == (k & 15)) {
-            // column k's half-warp: u, the pivot d = u_k, and v = u / d
-            float2 u[TS];
+        if (bad) return false;
+        if (kb == KBT) {
 #pragma unroll
-            for (int i = 0; i < TS; ++i) u[i] = pick<TS>(z[i], kk);
-            const float2 uk = pick<TS>(u, kk);
-            float2 d;
-            d.x = __shfl_sync(hmask, uk.x, k & 15, 16);
-            d.y = __shfl_sync(hmask, uk.y, k & 15, 16);
-            const float2 dinv = crcp_f(d);
+            for (int q = 0; q < KBT; ++q) sweep_step<TS>(z, Vb + (q * G16 + ty) * VST, Ub + (q * G16 + tx) * VST);
+        } else {
+            for (int q = 0; q < kb; ++q) sweep_step<TS>(z, Vb + (q * G16 + ty) * VST, Ub + (q * G16 + tx) * VST);
+        }
+        // the block's rows, then its columns, from the swept block (so that an
+        // entry in both keeps the swept column's value)
+        if (ty >= tx0 && ty < tx0 + kb) {
+            const float2 *col = zf + (ty - tx0) * ROWS;
 #pragma unroll
-            for (int i = 0; i < TS; ++i) {
-                const int r = ty + G16 * i;
-                if (r < no) {
-                    sh.ucol[buf * sh.stride + r] = u[i];
-                    sh.vcol[buf * sh.stride + r] = cmul_f(u[i], dinv);
+            for (int i = 0; i < TS; ++i)
+                if (i == jb) {
+#pragma unroll
+                    for (int j = 0; j < TS; ++j) z[i][j] = col[tx + G16 * j];
                 }
-            }
-            if (ty == 0) {
-                sh.dbuf[buf] = d;
-                sh.dinvbuf[buf] = dinv;
-            }
         }
-        __syncthreads();
-        const float2 d = sh.dbuf[buf];
-        if (!(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y)) {
-            return false;
+        if (tx >= tx0 && tx < tx0 + kb) {
+            const float2 *col = zf + (tx - tx0) * ROWS;
+#pragma unroll
+            for (int j = 0; j < TS; ++j)
+                if (j == jb) {
+#pragma unroll
+                    for (int i = 0; i < TS; ++i) z[i][j] = col[ty + G16 * i];
+                }
         }
-        sweep_apply<TS>(z, k, tx, ty, sh.vcol + buf * sh.stride, sh.ucol + buf * sh.stride, sh.dinvbuf[buf]);
     }
-    __syncthreads();   // every read of K in Pm is done
+    __syncthreads();   // every read of K in Pm and of the buffers is done
 #pragma unroll
     for (int i = 0; i < TS; ++i) {
         const int r = ty + G16 * i;
@@ -242,27 +335,37 @@ __device__ __forceinline__ bool t_sweep(float *Pm, int no, int tid, int lane, in
     return true;
 }
 
+// Pivots per sweep block for TS tiles (the sweeping warp holds TS x TS
+// complex tile values and its block of columns at the same time).
+template <int TS>
+struct SweepBlock {
+    static constexpr int value = TS <= 2 ? 8 : 4;
+};
+
 // The T step with the smallest tile count that holds n_o (ts = ceil(n_o / 16),
 // the same in every thread).
-template <int TS, int TMAX>
-__device__ __forceinline__ bool t_sweep_dispatch(int ts, float *Pm, int no, int tid, int lane, int tx, int ty,
-                                                 unsigned hmask, const SweepShared &sh)
+template <int TS, int TR, int TC>
+__device__ __forceinline__ bool t_sweep_dispatch(int ts, float *Pm, int no, int lane, int warp, int tx, int ty,
+                                                 float *xs, float2 *dk)
 {
-    if constexpr (TS < TMAX) {
-        if (ts <= TS) return t_sweep<TS>(Pm, no, tid, lane, tx, ty, hmask, sh);
-        return t_sweep_dispatch<TS + 1, TMAX>(ts, Pm, no, tid, lane, tx, ty, hmask, sh);
+    if constexpr (TS < TR) {
+        if (ts <= TS) return t_sweep<TS, TR, TC, SweepBlock<TS>::value>(Pm, no, lane, warp, tx, ty, xs, dk);
+        return t_sweep_dispatch<TS + 1, TR, TC>(ts, Pm, no, lane, warp, tx, ty, xs, dk);
     } else {
-        return t_sweep<TMAX>(Pm, no, tid, lane, tx, ty, hmask, sh);
+        return t_sweep<TR, TR, TC, SweepBlock<TR>::value>(Pm, no, lane, warp, tx, ty, xs, dk);
     }
 }
 
 template <int TR, int TC>
-__global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
+__global__ void __launch_bounds__(NT, TR >= 6 ? 2 : (TR >= 4 ? 3 : 4)) solve_f32_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa, const double *__restrict__ Ra,
     int *__restrict__ status, double *__restrict__ K_out, int *__restrict__ n_open_out,
     double *__restrict__ omega, int n_tri, const int *__restrict__ deep_ws, int deep_cap, int pass)
 {
     static_assert(TC == 2 * TR && G16 * TR <= MAXN, "tile shape");
+    using L = BlkLayout<TR, TC>;
+    constexpr int ROWS = L::ROWS, TRP = L::TRP;
+    constexpr int RWG = (ROWS + 31) / 32;         // rows per lane of the factoring warp
     if (deep_ws) {
         const bool deferred = deep_ws[0] <= deep_cap && deep_ws[1 + deep_cap + blockIdx.x] != 0;
         if (pass == 0 ? deferred : !deferred) return;
@@ -270,22 +373,18 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     extern __shared__ float fsm[];                // [packed R of this energy][K, later |T|^2 (n_o x n_o)]
     float *Rs = fsm;
     float *Pm = fsm + tri_ld(pw.n);
+    __shared__ __align__(16) float xs[L::FLOATS]; // the elimination's, then the sweep's block buffers
     __shared__ int col_chan[MAXN];                // unknown column -> channel
     __shared__ int open_pos[MAXN];                // channel -> position in P (-1: closed)
-    __shared__ float colv[MAXN], dgv[MAXN];       // unknown column: a Ghat' - b Ghat, Ghat
-    __shared__ float rsv[MAXN], rss[MAXN];        // right-hand side k: a S' - b S, S
+    __shared__ float cv_s[MAXN], dg_s[MAXN];      // channel: a Ghat' - b Ghat, Ghat (its unknown's column)
+    __shared__ float sv_s[MAXN], ss_s[MAXN];      // channel: a S' - b S, S (its right-hand side)
     __shared__ int kind_s[MAXN];
-    __shared__ float colbuf[2][G16 * TR];         // multipliers a_rc / a_pc (0 for the pivot row)
-    __shared__ float colbuf2[2][G16 * TR];        // second column of a pair
-    __shared__ int pbuf[2], pbuf2[2];
-    __shared__ float pvbuf[2], pvbuf2[2];
-    __shared__ unsigned used_s[(G16 * TR + 31) / 32];
-    __shared__ float2 vcol[2][G16 * TR];
-    __shared__ float2 dbuf[2], dinvbuf[2], dbuf2[2], dinvbuf2[2];
-    __shared__ float2 vcol2[2][G16 * TR], ucol2[2][G16 * TR];
-    __shared__ int rowpos[G16 * TR];
+    __shared__ bool open_s[MAXN];                 // channel open at this energy
+    __shared__ __align__(16) int pbk[KBG];        // the block's pivot rows
+    __shared__ float pvk[KBG];                    // and pivots
+    __shared__ float2 dk[8];                      // the sweep block's pivots
+    __shared__ int rowpos[ROWS];
     __shared__ float pivval[MAXN];
-    __shared__ float2 ucol[2][G16 * TR];
     __shared__ double lev_thr_s[MAXN];
     __shared__ int lev_start_s[MAXN + 1], lev_chan_s[MAXN];
     __shared__ int s_no, s_np;
@@ -297,7 +396,23 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     const double x = E[e];
     const ChanFn *cf = cfa + (size_t)e * n;
     const double *Rp = Ra + (size_t)e * tri_ld(n);
-    if (status[e] != RM_OK) {
+    const int st_e = status[e];
+    const double a = pw.a, b = pw.b;
+    const int nl = pw.n_levels;
+    const int npair = nl * (nl + 1) / 2;
+    double *om = omega ? omega + (size_t)e * n_tri : nullptr;
+    // this energy's channel data (as the matrix entries need them), R and the
+    // level tables into shared memory, every load issued before the first barrier
+    for (int i = tid; i < n; i += NT) {
+        const ChanFn c = cf[i];
+        kind_s[i] = c.kind;
+        cv_s[i] = (float)(a * c.ghp - b * c.gh);
+        dg_s[i] = (float)c.gh;
+        sv_s[i] = (float)(a * c.sp - b * c.s);
+        ss_s[i] = (float)c.s;
+        open_s[i] = x - pw.e_thr[i] > 0.0;
+    }
+    if (st_e != RM_OK) {
         if (tid == 0 && n_open_out) {
             int no = 0;
             for (int i = 0; i < n; ++i) no += (x - pw.e_thr[i] > 0.0);
@@ -305,21 +420,7 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
         }
         return;
     }
-
-    // ---- channel order: closed first, then P (open), by warp prefix counts
-    for (int i = tid; i < n; i += NT) kind_s[i] = cf[i].kind;
-    for (int r = tid; r < G16 * TR; r += NT) {
-        for (int q = 0; q < 2; ++q) {
-            ucol[q][r] = make_float2(0.0f, 0.0f);
-            vcol[q][r] = make_float2(0.0f, 0.0f);
-            ucol2[q][r] = make_float2(0.0f, 0.0f);
-            vcol2[q][r] = make_float2(0.0f, 0.0f);
-        }
-    }
-    if (tid < (G16 * TR + 31) / 32) used_s[tid] = 0u;
-    // R of this energy and the level tables, by coalesced loads
     for (int q = tid; q < tri_ld(n); q += NT) Rs[q] = (float)Rp[q];
-    const int nl = pw.n_levels;
     const bool lev_sm = nl <= MAXN;    // more levels than that (some without channels): read them in place
     if (lev_sm) {
         for (int q = tid; q < nl; q += NT) lev_thr_s[q] = pw.lev_thr[q];
@@ -329,6 +430,8 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     __syncthreads();
     const double *lthr = lev_sm ? lev_thr_s : pw.lev_thr;
     const int *lstart = lev_sm ? lev_start_s : pw.lev_start;
+
+    // ---- channel order: closed first, then P (open), by warp prefix counts
     if (warp == 0) {
         int ncl_run = 0, np_run = 0, no_run = 0;
         for (int base = 0; base < n; base += 32) {
@@ -338,7 +441,7 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             const bool pch = in && !closed;
             const unsigned bc = __ballot_sync(0xffffffffu, closed);
             const unsigned bp = __ballot_sync(0xffffffffu, pch);
-            const unsigned bo = __ballot_sync(0xffffffffu, in && x - pw.e_thr[i] > 0.0);
+            const unsigned bo = __ballot_sync(0xffffffffu, in && open_s[i]);
             const unsigned lt = (1u << lane) - 1u;
             if (closed) {
                 col_chan[ncl_run + __popc(bc & lt)] = i;
@@ -365,17 +468,6 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     for (int i = tid; i < n; i += NT)
         if (open_pos[i] >= 0) col_chan[ncl + open_pos[i]] = i;
     __syncthreads();
-    const double a = pw.a, b = pw.b;
-    for (int c = tid; c < n; c += NT) {
-        const ChanFn cj = cf[col_chan[c]];
-        colv[c] = (float)(a * cj.ghp - b * cj.gh);
-        dgv[c] = (float)cj.gh;
-        if (c >= ncl) {
-            rsv[c - ncl] = (float)(a * cj.sp - b * cj.s);
-            rss[c - ncl] = (float)cj.s;
-        }
-    }
-    __syncthreads();
 
     // ---- assemble the tile of [A | B] (FP32, as it is eliminated) -----------
     const int w = n + np;
@@ -390,190 +482,128 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             if (r < n && c < w) {
                 if (c < n) {
                     const int ch = col_chan[c];
-                    v = -Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)] * colv[c];
-                    if (r == ch) v += dgv[c];
+                    v = -Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)] * cv_s[ch];
+                    if (r == ch) v += dg_s[ch];
                 } else {
-                    const int k = c - n;
-                    const int ch = col_chan[ncl + k];
-                    v = Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)] * rsv[k];
-                    if (r == ch) v -= rss[k];
+                    const int ch = col_chan[ncl + c - n];
+                    v = Rs[r <= ch ? tri_idx(r, ch, n) : tri_idx(ch, r, n)] * sv_s[ch];
+                    if (r == ch) v -= ss_s[ch];
                 }
             }
             t[i][j] = v;
         }
     }
 
-    // ---- Gauss-Jordan elimination, implicit partial pivoting -----------------
-    // Columns are taken in pairs (c even, c + 1): their owner half-warps form
-    // one warp (lanes 0-15 column c, 16-31 column c + 1), which finds pivot
-    // p1 of column c, brings column c + 1 up to date with it by shuffles,
-    // finds its pivot p2, and publishes both multiplier columns; after one
-    // barrier every thread applies both eliminations in turn (the first
-    // leaves row p2 as a_p2j - m1_p2 a_p1j, the pivot row of the second).
-    const unsigned hmask = (lane & 16) ? 0xffff0000u : 0x0000ffffu;
+    // ---- Gauss-Jordan elimination in blocks of KBG columns --------------------
+    float *pan = xs;                              // [KBG][ROWS] the block's columns
+    float *mb = xs + KBG * ROWS;                  // [KBG][16][TRP] multipliers, by (ty, i)
+    float *rowb = mb + KBG * G16 * TRP;           // [2][16][TC] pivot-row values, by column class
     const unsigned full = 0xffffffffu;
-    int c_first_single = 0;
-    for (int c = 0; c + 1 < n; c += 2) {
-        const int buf = (c >> 1) & 1;
-        const int jc = c >> 4;
-        if ((tx >> 1) == ((c & 15) >> 1)) {
-            float v[TR];
-            unsigned key = 0u;
+    const int jhi = (w + G16 - 1) >> 4;           // tiles holding a column < n + n_o
+    // factoring warp: row lane + 32 s takes part in the pivot search while
+    // umask[s] is all ones (rows < n not yet used); rtag[s] = 127 - row
+    unsigned umask[RWG], rtag[RWG];
 #pragma unroll
-            for (int i = 0; i < TR; ++i) {
-                v[i] = pick<TC>(t[i], jc);
-                const int r = ty + G16 * i;
-                const bool used = (used_s[r >> 5] >> (r & 31)) & 1u;
-                const unsigned kv = (__float_as_uint(fabsf(v[i])) & ~0x7fu) | (unsigned)(127 - r);
-                if (r < n && !used && kv > key) key = kv;
+    for (int s = 0; s < RWG; ++s) {
+        umask[s] = lane + 32 * s < n ? ~0u : 0u;
+        rtag[s] = (unsigned)(127 - (lane + 32 * s));
+    }
+    for (int c0 = 0; c0 < n; c0 += KBG) {
+        const int kb = min(KBG, n - c0);
+        const int jb = c0 >> 4, tx0 = c0 & 15;
+        if (tx >= tx0 && tx < tx0 + kb) {
+            float *col = pan + (tx - tx0) * ROWS;
+#pragma unroll
+            for (int i = 0; i < TR; ++i) col[ty + G16 * i] = pick<TC>(t[i], jb);
+        }
+        __syncthreads();
+        if (warp == 0) {
+            float a[RWG][KBG];
+            int myp = 0;
+            float mypv = 0.0f;
+#pragma unroll
+            for (int s = 0; s < RWG; ++s) {
+                const int r = lane + 32 * s;
+#pragma unroll
+                for (int q = 0; q < KBG; ++q) a[s][q] = (q < kb && r < ROWS) ? pan[q * ROWS + r] : 0.0f;
             }
-            key = __reduce_max_sync(hmask, key);
-            const unsigned keyA = __shfl_sync(full, key, 0);
-            const int p1 = keyA ? 127 - (int)(keyA & 0x7fu) : 0;
-            const float at_p1 = pick<TR>(v, p1 >> 4);
-            const float pv1 = __shfl_sync(full, at_p1, p1 & 15);
-            const float u1 = __shfl_sync(full, at_p1, 16 + (p1 & 15));   // a_{p1, c+1}
-            const float ipv1 = __frcp_rn(pv1);
-            float m1[TR], v2[TR];
-            unsigned key2 = 0u;
 #pragma unroll
-            for (int i = 0; i < TR; ++i) {
-                const int r = ty + G16 * i;
-                m1[i] = (r == p1) ? 0.0f : v[i] * ipv1;
-                const float mA = __shfl_xor_sync(full, m1[i], 16);
-                v2[i] = fmaf(-mA, u1, v[i]);
-                const bool used = ((used_s[r >> 5] >> (r & 31)) & 1u) || r == p1;
-                const unsigned kv = (__float_as_uint(fabsf(v2[i])) & ~0x7fu) | (unsigned)(127 - r);
-                if (r < n && !used && kv > key2) key2 = kv;
-            }
-            key2 = __reduce_max_sync(hmask, key2);
-            const unsigned keyB = __shfl_sync(full, key2, 16);
-            const int p2 = keyB ? 127 - (int)(keyB & 0x7fu) : 0;
-            const float pv2 = __shfl_sync(full, pick<TR>(v2, p2 >> 4), 16 + (p2 & 15));
-            const float ipv2 = __frcp_rn(pv2);
-            if ((tx & 1) == 0) {
+            for (int q = 0; q < KBG; ++q) {
+                if (q < kb) {
+                    // pivot: one max-reduction over keys |v| (low 7 mantissa bits
+                    // replaced by 127 - r, so rows within 2^-17 of the largest
+                    // magnitude tie and the lowest one wins); unused rows only
+                    unsigned key = 0u;
 #pragma unroll
-                for (int i = 0; i < TR; ++i) colbuf[buf][ty + G16 * i] = m1[i];
-            } else {
+                    for (int s = 0; s < RWG; ++s)
+                        key = max(key, ((__float_as_uint(a[s][q]) & 0x7fffff80u) | rtag[s]) & umask[s]);
+                    key = __reduce_max_sync(full, key);
+                    const int p = key ? 127 - (int)(key & 0x7fu) : 0;
+                    const int ps = p >> 5, pl = p & 31;
+                    const float pv = __shfl_sync(full, pick_s(a, ps, q), pl);
+                    const float ipv = rcp_nr_f(pv);
+                    float m[RWG];
 #pragma unroll
-                for (int i = 0; i < TR; ++i) {
-                    const int r = ty + G16 * i;
-                    colbuf2[buf][r] = (r == p2) ? 0.0f : v2[i] * ipv2;
+                    for (int s = 0; s < RWG; ++s) {
+                        const int r = lane + 32 * s;
+                        m[s] = (r == p) ? 0.0f : a[s][q] * ipv;
+                        if (r < ROWS) mb[(q * G16 + (r & 15)) * TRP + (r >> 4)] = m[s];
+                    }
+#pragma unroll
+                    for (int q2 = q + 1; q2 < KBG; ++q2) {
+                        if (q2 < kb) {
+                            const float u = __shfl_sync(full, pick_s(a, ps, q2), pl);
+#pragma unroll
+                            for (int s = 0; s < RWG; ++s) a[s][q2] = fmaf(-m[s], u, a[s][q2]);
+                        }
+                    }
+                    if (lane == pl) {
+#pragma unroll
+                        for (int s = 0; s < RWG; ++s)
+                            if (ps == s) umask[s] = 0u;
+                    }
+                    if (lane == q) {
+                        myp = p;
+                        mypv = pv;
+                    }
                 }
             }
-            if (lane == 0) {
-                pbuf[buf] = p1;
-                pvbuf[buf] = pv1;
-                pbuf2[buf] = p2;
-                pvbuf2[buf] = pv2;
-                used_s[p1 >> 5] |= 1u << (p1 & 31);
-                used_s[p2 >> 5] |= 1u << (p2 & 31);
-                rowpos[p1] = c;
-                rowpos[p2] = c + 1;
-                pivval[c] = pv1;
-                pivval[c + 1] = pv2;
+            if (lane < kb) {   // lane q records step q
+                pbk[lane] = myp;
+                pvk[lane] = mypv;
+                rowpos[myp] = c0 + lane;
+                pivval[c0 + lane] = mypv;
             }
         }
         __syncthreads();
-        const int p1 = pbuf[buf], p2 = pbuf2[buf];
-        const float pv1 = pvbuf[buf], pv2 = pvbuf2[buf];
-        if (!(fabsf(pv1) > 0.0f) || !isfinite(pv1) || !(fabsf(pv2) > 0.0f) || !isfinite(pv2)) {
+        bool bad = false;
+        for (int q = 0; q < kb; ++q) {
+            const float pv = pvk[q];
+            bad |= !(fabsf(pv) >= kMinNormal) || !isfinite(pv);
+        }
+        if (bad) {   // the same in every thread
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
-        // first elimination (row p1); it turns row p2 into its reduced form
-        // a_p2j - m1_p2 a_p1j, which the second elimination then uses
-        const int ip1 = p1 >> 4, src1 = (lane & 16) | (p1 & 15);
-        const int ip2 = p2 >> 4, src2 = (lane & 16) | (p2 & 15);
-        float rb[TC];
+        // the block's steps on this thread's columns past the block (tiles
+        // jlo..jhi-1; columns of tile jlo left of the block's end take the
+        // update too, and are never read again)
+        const int jlo = (c0 + kb) >> 4;
+        if (kb == KBG) {
+            int pk[KBG];
 #pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            if (ip1 == i) {
-#pragma unroll
-                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(full, t[i][j], src1);
+            for (int q = 0; q < KBG; q += 4) {
+                const int4 v4 = *reinterpret_cast<const int4 *>(pbk + q);
+                pk[q] = v4.x, pk[q + 1] = v4.y, pk[q + 2] = v4.z, pk[q + 3] = v4.w;
             }
-        }
 #pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            const float f1 = colbuf[buf][ty + G16 * i];
-#pragma unroll
-            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f1, rb[j], t[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            if (ip2 == i) {
-#pragma unroll
-                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(full, t[i][j], src2);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            const float f2 = colbuf2[buf][ty + G16 * i];
-#pragma unroll
-            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f2, rb[j], t[i][j]);
-        }
-        c_first_single = c + 2;
-    }
-    for (int c = c_first_single; c < n; ++c) {
-        const int buf = (c >> 1) & 1;
-        if (tx == (c & 15)) {
-            // the column's half-warp: pivot row by shuffles, then the multipliers
-            const int jc = c >> 4;
-            float v[TR];
-            // pivot: one max-reduction over keys |v| (low 7 mantissa bits
-            // replaced by 127 - r, so rows within 2^-17 of the largest
-            // magnitude tie and the lowest one wins); unused rows only
-            unsigned key = 0u;
-#pragma unroll
-            for (int i = 0; i < TR; ++i) {
-                v[i] = pick<TC>(t[i], jc);
-                const int r = ty + G16 * i;
-                const bool used = (used_s[r >> 5] >> (r & 31)) & 1u;
-                const unsigned kv = (__float_as_uint(fabsf(v[i])) & ~0x7fu) | (unsigned)(127 - r);
-                if (r < n && !used && kv > key) key = kv;
-            }
-            key = __reduce_max_sync(hmask, key);
-            const int p = key ? 127 - (int)(key & 0x7fu) : 0;
-            const float pv = __shfl_sync(hmask, pick<TR>(v, p >> 4), p & 15, 16);
-            const float ipv = __frcp_rn(pv);
-#pragma unroll
-            for (int i = 0; i < TR; ++i) {
-                const int r = ty + G16 * i;
-                colbuf[buf][r] = (r == p) ? 0.0f : v[i] * ipv;
-            }
-            if (ty == 0) {
-                pbuf[buf] = p;
-                pvbuf[buf] = pv;
-                used_s[p >> 5] |= 1u << (p & 31);
-                rowpos[p] = c;
-                pivval[c] = pv;
-            }
-        }
-        __syncthreads();
-        const int p = pbuf[buf];
-        const float pv = pvbuf[buf];
-        if (!(fabsf(pv) > 0.0f) || !isfinite(pv)) {   // the same in every thread
-            if (tid == 0) status[e] = RM_ESINGULAR;
-            return;
-        }
-        // row p's values for this thread's columns, from the lane of this
-        // half-warp that holds row p. Columns <= c and the padding take the
-        // update too: they are never read again (padding stays zero, as row
-        // p's padding is zero); the pivot row's multiplier is zero.
-        const int ip = p >> 4, src = (lane & 16) | (p & 15);
-        float rb[TC];
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            if (ip == i) {
-#pragma unroll
-                for (int j = 0; j < TC; ++j) rb[j] = __shfl_sync(0xffffffffu, t[i][j], src);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < TR; ++i) {
-            const float f = colbuf[buf][ty + G16 * i];
-#pragma unroll
-            for (int j = 0; j < TC; ++j) t[i][j] = fmaf(-f, rb[j], t[i][j]);
+            for (int q = 0; q < KBG; ++q)
+                gj_step<TR, TC, TRP>(t, pk[q], mb + (q * G16 + ty) * TRP, rowb + ((q & 1) * G16 + tx) * TC, ty,
+                                     jlo, jhi);
+        } else {
+            for (int q = 0; q < kb; ++q)
+                gj_step<TR, TC, TRP>(t, pbk[q], mb + (q * G16 + ty) * TRP, rowb + ((q & 1) * G16 + tx) * TC, ty,
+                                     jlo, jhi);
         }
     }
     __syncthreads();
@@ -602,30 +632,23 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     if (!omega) return;
 
     // ---- T step: W = -(1 - iK)^{-1} by the complex sweep in registers --------
-    {
-        const SweepShared sh = {&ucol[0][0], &vcol[0][0], &ucol2[0][0], &vcol2[0][0],
-                                dbuf, dinvbuf, dbuf2, dinvbuf2, G16 * TR};
-        if (!t_sweep_dispatch<1, TR>((no + 15) >> 4, Pm, no, tid, lane, tx, ty, hmask, sh)) {
-            if (tid == 0) status[e] = RM_ESINGULAR;
-            return;
-        }
+    if (!t_sweep_dispatch<1, TR, TC>((no + 15) >> 4, Pm, no, lane, warp, tx, ty, xs, dk)) {
+        if (tid == 0) status[e] = RM_ESINGULAR;
+        return;
     }
 
     // ---- Omega ----------------------------------------------------------------
-    const int npair = nl * (nl + 1) / 2;
     const double g = pw.g;
-    double *om = omega + (size_t)e * n_tri;
     for (int q = tid; q < npair; q += NT) {
         int I, J;
         tri_pair(q, nl, I, J);
         if (!(x - lthr[I] > 0.0) || !(x - lthr[J] > 0.0)) continue;
-        double s = 0.0;
+        float s = 0.0f;   // the level pair's |I||J| values of |T|^2, FP32 like them
         for (int ia = lstart[I]; ia < lstart[I + 1]; ++ia) {
             const int pa = open_pos[lev_chan_s[ia]];
-            for (int ib = lstart[J]; ib < lstart[J + 1]; ++ib)
-                s += (double)Pm[pa * no + open_pos[lev_chan_s[ib]]];
+            for (int ib = lstart[J]; ib < lstart[J + 1]; ++ib) s += Pm[pa * no + open_pos[lev_chan_s[ib]]];
         }
-        om[q] += g * s;
+        atomicAdd(om + q, g * (double)s);   // the only addition to om[q] in this launch
     }
 }
 
