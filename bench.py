@@ -344,8 +344,9 @@ def run_serving(args, prec):
     (50-1500 channels, 25-35 poles per channel, 256-8192 energies on 0-8 Ry,
     half MQDT; a pool of 64 pole sets) through the continuous-batching server
     with the mixed-precision path (bf16x3 formation, FP32 matching) and with
-    the plain FP64 path. Mixed: first every request at once (capacity), then
-    Poisson arrivals at 0.9 x that capacity (p50 / p99 latency). FP64: the same
+    the plain FP64 path. Mixed: first every request at once (capacity), the
+    same requests back to back on one lane, then Poisson arrivals at 0.9 x the
+    capacity (p50 / p99 latency). FP64: the same
     requests with every args.serving_fp64_stride-th energy (throughput in
     energy-solves/s; the FP64 path is ~10^2 slower), and the Omega error of
     the mixed results on those energies."""
@@ -369,8 +370,8 @@ def run_serving(args, prec):
             req.omega = om[::stride].copy() if stride else None
         return sink
 
-    def serve(precision, sp_, reqs, keep):
-        srv = serving.Server(n_slots=4, precision=precision, solve_precision=sp_, mem_budget=120 << 30,
+    def serve(precision, sp_, reqs, keep, n_slots=4):
+        srv = serving.Server(n_slots=n_slots, precision=precision, solve_precision=sp_, mem_budget=120 << 30,
                              lane_workspace=16 << 30, cache_sets=64, sink=keep_rows(keep))
         try:
             srv.prepare(reqs)
@@ -387,6 +388,8 @@ def run_serving(args, prec):
     sat = make(specs)
     st_sat, loads = serve(2, 1, sat, k)
     cap = st_sat["requests"] / st_sat["wall_s"]
+    # the same requests back to back: one lane of one context
+    st_one, _ = serve(2, 1, make(specs), 0, n_slots=1)
     # Poisson arrivals at 0.9 x capacity (the stream's exponential gaps rescaled)
     rate = 0.9 * cap
     pois = make(specs, t_scale=1.0 / rate)
@@ -409,6 +412,8 @@ def run_serving(args, prec):
             "mixed_saturated": {"energy_solves_per_s": st_sat["energy_solves_per_s"],
                                 "requests_per_s": cap, "wall_s": st_sat["wall_s"],
                                 "energy_solves": st_sat["energy_solves"], "pole_set_loads": loads},
+            "mixed_one_lane": {"energy_solves_per_s": st_one["energy_solves_per_s"], "wall_s": st_one["wall_s"],
+                               "saturated_over_one_lane": st_sat["energy_solves_per_s"] / st_one["energy_solves_per_s"]},
             "mixed_poisson_0.9": {"rate_per_s": rate, "energy_solves_per_s": st_p["energy_solves_per_s"],
                                   "p50_ms": 1e3 * st_p["p50_s"], "p99_ms": 1e3 * st_p["p99_s"],
                                   "mean_ms": 1e3 * st_p["mean_s"]},

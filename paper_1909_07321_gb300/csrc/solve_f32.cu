@@ -16,17 +16,20 @@
 // the smallest normal number counts as zero). After n columns the unknowns
 // are x_c = a_{p(c), rhs} / a_{p(c), c}, with no back-substitution.
 //
-// The columns are eliminated in blocks of KB. The block's columns are copied
-// to shared memory and one warp (lane l holds rows l + 32 s) runs the KB
-// steps on them alone: pivot by one warp max-reduction, multipliers, and the
-// step's update of the block's later columns. It publishes the KB pivot rows
-// and multiplier columns; after one barrier every thread applies the KB
-// steps to its columns past the block in the same order (the pivot row's
+// The columns are eliminated in blocks of KBG. The block's columns are
+// copied to shared memory and one warp (lane l holds rows l + 32 s) runs the
+// KBG steps on them alone: pivot by one warp max-reduction, multipliers, and
+// the step's update of the block's later columns. It publishes the KBG pivot
+// rows and multiplier columns; after one barrier every thread applies the
+// KBG steps to its columns past the block in the same order (the pivot row's
 // values for a thread's columns come from the thread of its half-warp that
 // holds that row, through shared memory). Every element therefore takes the
 // same operations, in the same order, as in the column-by-column
-// elimination, with two barriers per KB columns instead of one per column;
+// elimination, with two barriers per KBG columns instead of one per column;
 // columns left of the block and the padding beyond n + n_o are not touched.
+// The serial part of every block is one warp's, so the throughput comes from
+// the energies resident on an SM: block sizes and tiles are chosen to keep a
+// thread within 64 registers, four CTAs per SM, up to 64 channels.
 //
 // (d) T = 2iK(1 - iK)^{-1} = 2(1 - iK)^{-1} - 2 (Section "Glossary of
 // terms"): 1 - iK (complex, K symmetrised) in registers in the same 16 x 16
@@ -55,7 +58,7 @@ namespace {
 
 constexpr int G16 = 16;                          // thread grid 16 x 16
 constexpr int MAXN = SOLVE_SMALL_MAXN;
-constexpr int KBG = 8;                           // columns per elimination block
+constexpr int KBG = 4;                           // columns per elimination block
 constexpr float kMinNormal = 1.17549435e-38f;    // smallest normal FP32 number: smaller pivots count as zero
 
 // Element k of a register array for an index k that is the same in every
@@ -336,10 +339,11 @@ __device__ __forceinline__ bool t_sweep(float *Pm, int no, int lane, int warp, i
 }
 
 // Pivots per sweep block for TS tiles (the sweeping warp holds TS x TS
-// complex tile values and its block of columns at the same time).
+// complex tile values and its block of columns at the same time, within the
+// 64 registers a thread has at four CTAs per SM).
 template <int TS>
 struct SweepBlock {
-    static constexpr int value = TS <= 2 ? 8 : 4;
+    static constexpr int value = TS <= 2 ? 4 : 2;
 };
 
 // The T step with the smallest tile count that holds n_o (ts = ceil(n_o / 16),
@@ -357,7 +361,7 @@ __device__ __forceinline__ bool t_sweep_dispatch(int ts, float *Pm, int no, int 
 }
 
 template <int TR, int TC>
-__global__ void __launch_bounds__(NT, TR >= 6 ? 2 : (TR >= 4 ? 3 : 4)) solve_f32_kernel(
+__global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     PwDev pw, const double *__restrict__ E, const ChanFn *__restrict__ cfa, const double *__restrict__ Ra,
     int *__restrict__ status, double *__restrict__ K_out, int *__restrict__ n_open_out,
     double *__restrict__ omega, int n_tri, const int *__restrict__ deep_ws, int deep_cap, int pass)
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : (TR >= 4 ? 3 : 4)) solve_f32
     __shared__ float2 dk[8];                      // the sweep block's pivots
     __shared__ int rowpos[ROWS];
     __shared__ float pivval[MAXN];
-    __shared__ double lev_thr_s[MAXN];
+    __shared__ bool lev_open_s[MAXN];             // level open at this energy
     __shared__ int lev_start_s[MAXN + 1], lev_chan_s[MAXN];
     __shared__ int s_no, s_np;
 
@@ -420,15 +424,32 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : (TR >= 4 ? 3 : 4)) solve_f32
         }
         return;
     }
-    for (int q = tid; q < tri_ld(n); q += NT) Rs[q] = (float)Rp[q];
+    {
+        // R in batches of RB loads in flight per thread (each conversion waits
+        // for its load)
+        constexpr int RB = 8;
+        const int m = tri_ld(n);
+        for (int q0 = tid; q0 < m; q0 += RB * NT) {
+            double v[RB];
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const int q = q0 + k * NT;
+                v[k] = q < m ? Rp[q] : 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < RB; ++k) {
+                const int q = q0 + k * NT;
+                if (q < m) Rs[q] = (float)v[k];
+            }
+        }
+    }
     const bool lev_sm = nl <= MAXN;    // more levels than that (some without channels): read them in place
     if (lev_sm) {
-        for (int q = tid; q < nl; q += NT) lev_thr_s[q] = pw.lev_thr[q];
+        for (int q = tid; q < nl; q += NT) lev_open_s[q] = x - pw.lev_thr[q] > 0.0;
         for (int q = tid; q <= nl; q += NT) lev_start_s[q] = pw.lev_start[q];
     }
     for (int q = tid; q < n; q += NT) lev_chan_s[q] = pw.lev_chan[q];
     __syncthreads();
-    const double *lthr = lev_sm ? lev_thr_s : pw.lev_thr;
     const int *lstart = lev_sm ? lev_start_s : pw.lev_start;
 
     // ---- channel order: closed first, then P (open), by warp prefix counts
@@ -642,7 +663,8 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : (TR >= 4 ? 3 : 4)) solve_f32
     for (int q = tid; q < npair; q += NT) {
         int I, J;
         tri_pair(q, nl, I, J);
-        if (!(x - lthr[I] > 0.0) || !(x - lthr[J] > 0.0)) continue;
+        if (lev_sm ? !(lev_open_s[I] && lev_open_s[J]) : !(x - pw.lev_thr[I] > 0.0 && x - pw.lev_thr[J] > 0.0))
+            continue;
         float s = 0.0f;   // the level pair's |I||J| values of |T|^2, FP32 like them
         for (int ia = lstart[I]; ia < lstart[I + 1]; ++ia) {
             const int pa = open_pos[lev_chan_s[ia]];
