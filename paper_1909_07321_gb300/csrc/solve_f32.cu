@@ -140,6 +140,52 @@ __device__ __forceinline__ void gj_step(float (&t)[TR][TC], int p, const float *
     }
 }
 
+// The same step on tiles J0..TC-1 (J0 fixed at compile time: no per-tile
+// conditions; padding tiles past n + n_o hold zeros in every row, the pivot
+// row's too, and stay zero). Only the quads of rb from J0's on are written.
+template <int TR, int TC, int TRP, int J0>
+__device__ __forceinline__ void gj_step_from(float (&t)[TR][TC], int p, const float *fq, float *rb, int ty)
+{
+    constexpr int JQ = J0 & ~3;
+    if (ty == (p & 15)) {
+        const int ip = p >> 4;
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+            if (ip == i) {
+#pragma unroll
+                for (int j = JQ; j < TC; j += 4)
+                    *reinterpret_cast<float4 *>(rb + j) = make_float4(t[i][j], t[i][j + 1], t[i][j + 2], t[i][j + 3]);
+            }
+    }
+    __syncwarp();
+    float f[TR], u[TC];
+    load_row<TR>(f, fq);
+#pragma unroll
+    for (int j = JQ; j < TC; j += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(rb + j);
+        u[j] = v.x, u[j + 1] = v.y, u[j + 2] = v.z, u[j + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = J0; j < TC; ++j) {
+#pragma unroll
+        for (int i = 0; i < TR; ++i) t[i][j] = fmaf(-f[i], u[j], t[i][j]);
+    }
+}
+
+// A full block's KBG steps on tiles j0..TC-1, the first live tile dispatched
+// to a compile-time J0 (one branch per block instead of one per tile and step).
+template <int TR, int TC, int TRP, int KB, int J0 = 0>
+__device__ __forceinline__ void gj_block_from(int j0, float (&t)[TR][TC], const int (&pk)[KB], const float *mbt,
+                                              float *rbt, int ty)
+{
+    if constexpr (J0 + 1 < TC) {
+        if (j0 > J0) return gj_block_from<TR, TC, TRP, KB, J0 + 1>(j0, t, pk, mbt, rbt, ty);
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q)
+        gj_step_from<TR, TC, TRP, J0>(t, pk[q], mbt + q * G16 * TRP, rbt + (q & 1) * G16 * TC, ty);
+}
+
 // Shared-memory layout of the blocked elimination and sweep for TR row tiles
 // (sizes in floats; both phases use the same buffer one after the other).
 template <int TR, int TC>
@@ -617,10 +663,7 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
                 const int4 v4 = *reinterpret_cast<const int4 *>(pbk + q);
                 pk[q] = v4.x, pk[q + 1] = v4.y, pk[q + 2] = v4.z, pk[q + 3] = v4.w;
             }
-#pragma unroll
-            for (int q = 0; q < KBG; ++q)
-                gj_step<TR, TC, TRP>(t, pk[q], mb + (q * G16 + ty) * TRP, rowb + ((q & 1) * G16 + tx) * TC, ty,
-                                     jlo, jhi);
+            gj_block_from<TR, TC, TRP, KBG>(jlo, t, pk, mb + ty * TRP, rowb + tx * TC, ty);
         } else {
             for (int q = 0; q < kb; ++q)
                 gj_step<TR, TC, TRP>(t, pbk[q], mb + (q * G16 + ty) * TRP, rowb + ((q & 1) * G16 + tx) * TC, ty,
