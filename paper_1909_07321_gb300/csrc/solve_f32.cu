@@ -244,7 +244,7 @@ __device__ __forceinline__ void sweep_step(float2 (&z)[TS][TS], const float2 *vq
 // every thread) if a pivot is zero or not finite.
 template <int TS, int TR, int TC, int KBT>
 __device__ __forceinline__ bool t_sweep(float *Pm, int no, int lane, int warp, int tx, int ty, float *xs,
-                                        float2 *dk)
+                                        int *s_bad)
 {
     using L = BlkLayout<TR, TC>;
     constexpr int ROWS = L::ROWS, VST = L::VST;
@@ -276,6 +276,7 @@ __device__ __forceinline__ bool t_sweep(float *Pm, int no, int lane, int warp, i
         __syncthreads();
         if (warp == 0) {
             float2 a[RWT][KBT];
+            bool bad = false;   // a zero or non-finite pivot in this block (the same in every lane)
 #pragma unroll
             for (int s = 0; s < RWT; ++s) {
                 const int r = lane + 32 * s;
@@ -288,6 +289,7 @@ __device__ __forceinline__ bool t_sweep(float *Pm, int no, int lane, int warp, i
                 if (q < kb) {
                     const int kq = k0 + q;
                     const float2 d = shfl2(pick_s(a, kq >> 5, q), kq & 31);
+                    bad |= !(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y);
                     const float2 dinv = crcp_f(d);
                     float2 v[RWT];
 #pragma unroll
@@ -321,7 +323,6 @@ __device__ __forceinline__ bool t_sweep(float *Pm, int no, int lane, int warp, i
                         const int r = lane + 32 * s;
                         a[s][q] = (r == kq) ? make_float2(-dinv.x, -dinv.y) : v[s];
                     }
-                    if (lane == 0) dk[q] = d;
                 }
             }
 #pragma unroll
@@ -331,14 +332,10 @@ __device__ __forceinline__ bool t_sweep(float *Pm, int no, int lane, int warp, i
                 for (int q = 0; q < KBT; ++q)
                     if (q < kb && r < G16 * TS) zf[q * ROWS + r] = a[s][q];
             }
+            if (lane == 0) *s_bad = bad;
         }
         __syncthreads();
-        bool bad = false;
-        for (int q = 0; q < kb; ++q) {
-            const float2 d = dk[q];
-            bad |= !(fabsf(d.x) + fabsf(d.y) > 0.0f) || !isfinite(d.x) || !isfinite(d.y);
-        }
-        if (bad) return false;
+        if (*s_bad) return false;   // the same in every thread
         if (kb == KBT) {
 #pragma unroll
             for (int q = 0; q < KBT; ++q) sweep_step<TS>(z, Vb + (q * G16 + ty) * VST, Ub + (q * G16 + tx) * VST);
@@ -396,13 +393,13 @@ struct SweepBlock {
 // the same in every thread).
 template <int TS, int TR, int TC>
 __device__ __forceinline__ bool t_sweep_dispatch(int ts, float *Pm, int no, int lane, int warp, int tx, int ty,
-                                                 float *xs, float2 *dk)
+                                                 float *xs, int *s_bad)
 {
     if constexpr (TS < TR) {
-        if (ts <= TS) return t_sweep<TS, TR, TC, SweepBlock<TS>::value>(Pm, no, lane, warp, tx, ty, xs, dk);
-        return t_sweep_dispatch<TS + 1, TR, TC>(ts, Pm, no, lane, warp, tx, ty, xs, dk);
+        if (ts <= TS) return t_sweep<TS, TR, TC, SweepBlock<TS>::value>(Pm, no, lane, warp, tx, ty, xs, s_bad);
+        return t_sweep_dispatch<TS + 1, TR, TC>(ts, Pm, no, lane, warp, tx, ty, xs, s_bad);
     } else {
-        return t_sweep<TR, TR, TC, SweepBlock<TR>::value>(Pm, no, lane, warp, tx, ty, xs, dk);
+        return t_sweep<TR, TR, TC, SweepBlock<TR>::value>(Pm, no, lane, warp, tx, ty, xs, s_bad);
     }
 }
 
@@ -431,13 +428,13 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     __shared__ int kind_s[MAXN];
     __shared__ bool open_s[MAXN];                 // channel open at this energy
     __shared__ __align__(16) int pbk[KBG];        // the block's pivot rows
-    __shared__ float pvk[KBG];                    // and pivots
-    __shared__ float2 dk[8];                      // the sweep block's pivots
+    __shared__ int s_bad;                         // the block has a zero or non-finite pivot
     __shared__ int rowpos[ROWS];
     __shared__ float pivval[MAXN];
     __shared__ bool lev_open_s[MAXN];             // level open at this energy
     __shared__ int lev_start_s[MAXN + 1], lev_chan_s[MAXN];
-    __shared__ int s_no, s_np;
+    __shared__ int olev[MAXN];                    // the levels open at this energy, ascending
+    __shared__ int s_no, s_np, s_nlo;
 
     const int e = blockIdx.x;
     const int n = pw.n;
@@ -523,6 +520,17 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             s_np = np_run;
             s_no = no_run;
             if (n_open_out) n_open_out[e] = no_run;
+        }
+        if (lev_sm) {
+            int nlo_run = 0;
+            for (int base = 0; base < nl; base += 32) {
+                const int q = base + lane;
+                const bool op = q < nl && lev_open_s[q];
+                const unsigned bo = __ballot_sync(0xffffffffu, op);
+                if (op) olev[nlo_run + __popc(bo & ((1u << lane) - 1u))] = q;
+                nlo_run += __popc(bo);
+            }
+            if (lane == 0) s_nlo = nlo_run;
         }
     }
     __syncthreads();
@@ -637,18 +645,15 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
             }
             if (lane < kb) {   // lane q records step q
                 pbk[lane] = myp;
-                pvk[lane] = mypv;
                 rowpos[myp] = c0 + lane;
                 pivval[c0 + lane] = mypv;
             }
+            const unsigned badq =
+                __ballot_sync(full, lane < kb && (!(fabsf(mypv) >= kMinNormal) || !isfinite(mypv)));
+            if (lane == 0) s_bad = badq != 0u;
         }
         __syncthreads();
-        bool bad = false;
-        for (int q = 0; q < kb; ++q) {
-            const float pv = pvk[q];
-            bad |= !(fabsf(pv) >= kMinNormal) || !isfinite(pv);
-        }
-        if (bad) {   // the same in every thread
+        if (s_bad) {   // the same in every thread
             if (tid == 0) status[e] = RM_ESINGULAR;
             return;
         }
@@ -696,24 +701,40 @@ __global__ void __launch_bounds__(NT, TR >= 6 ? 2 : 4) solve_f32_kernel(
     if (!omega) return;
 
     // ---- T step: W = -(1 - iK)^{-1} by the complex sweep in registers --------
-    if (!t_sweep_dispatch<1, TR, TC>((no + 15) >> 4, Pm, no, lane, warp, tx, ty, xs, dk)) {
+    if (!t_sweep_dispatch<1, TR, TC>((no + 15) >> 4, Pm, no, lane, warp, tx, ty, xs, &s_bad)) {
         if (tid == 0) status[e] = RM_ESINGULAR;
         return;
     }
 
     // ---- Omega ----------------------------------------------------------------
     const double g = pw.g;
-    for (int q = tid; q < npair; q += NT) {
-        int I, J;
-        tri_pair(q, nl, I, J);
-        if (lev_sm ? !(lev_open_s[I] && lev_open_s[J]) : !(x - pw.lev_thr[I] > 0.0 && x - pw.lev_thr[J] > 0.0))
-            continue;
-        float s = 0.0f;   // the level pair's |I||J| values of |T|^2, FP32 like them
+    // the level pair's |I||J| values of |T|^2, summed in FP32 like them
+    auto pair_sum = [&](int I, int J) {
+        float s = 0.0f;
         for (int ia = lstart[I]; ia < lstart[I + 1]; ++ia) {
             const int pa = open_pos[lev_chan_s[ia]];
             for (int ib = lstart[J]; ib < lstart[J + 1]; ++ib) s += Pm[pa * no + open_pos[lev_chan_s[ib]]];
         }
-        atomicAdd(om + q, g * (double)s);   // the only addition to om[q] in this launch
+        return s;
+    };
+    if (lev_sm) {
+        // open level pairs I <= J only: warp w takes the rows of the open-level
+        // triangle w, w + 8, ..., its lanes the row's pairs
+        const int nlo = s_nlo;
+        for (int ip = warp; ip < nlo; ip += NT / 32) {
+            const int I = olev[ip];
+            for (int jp = ip + lane; jp < nlo; jp += 32) {
+                const int J = olev[jp];
+                atomicAdd(om + tri_idx(I, J, nl), g * (double)pair_sum(I, J));   // the only addition in this launch
+            }
+        }
+    } else {
+        for (int q = tid; q < npair; q += NT) {
+            int I, J;
+            tri_pair(q, nl, I, J);
+            if (!(x - pw.lev_thr[I] > 0.0 && x - pw.lev_thr[J] > 0.0)) continue;
+            atomicAdd(om + q, g * (double)pair_sum(I, J));   // the only addition to om[q] in this launch
+        }
     }
 }
 
