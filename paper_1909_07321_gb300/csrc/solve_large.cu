@@ -104,6 +104,47 @@ __global__ void classify_kernel(PwDev pw, const double *__restrict__ E, int nE,
     dims[e] = d;
 }
 
+// ---- CTA order of the per-energy FP32 kernels ------------------------------
+
+// order[0 .. nE) = the energies by decreasing n_p (the matching system's
+// right-hand sides; the LU's cost grows with n_p, the T step's with n_o^3 and
+// n_o <= n_p), skipped energies last: the longest CTAs start first, so the
+// short ones fill the SMs at the end of the launch (longest-processing-time
+// order). One CTA; a counting sort over the n + 2 keys in shared memory
+// (dynamic, (n + 2) ints). The order among equal keys is arbitrary: every CTA
+// computes its own energy, so the results do not depend on it.
+__global__ void order_kernel(int n, int nE, const EnergyDims *__restrict__ dims, int *order)
+{
+    extern __shared__ int hist[];
+    const int nb = n + 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto bin = [&](int e) {
+        const int np = dims[e].np;
+        return np < 0 ? n + 1 : n - min(np, n);
+    };
+    for (int b = tid; b < nb; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int e = tid; e < nE; e += blockDim.x) atomicAdd(&hist[bin(e)], 1);
+    __syncthreads();
+    if (warp == 0) {   // exclusive prefix sum, 32 bins at a time
+        int run = 0;
+        for (int base = 0; base < nb; base += 32) {
+            const int b = base + lane;
+            const int v = b < nb ? hist[b] : 0;
+            int incl = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
+            if (b < nb) hist[b] = run + incl - v;
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < nE; e += blockDim.x) order[atomicAdd(&hist[bin(e)], 1)] = e;
+}
+
 // ---- assemble [A | B] -----------------------------------------------------
 
 __global__ void assemble_kernel(PwDev pw, int nE, const ChanFn *__restrict__ cfa,
@@ -631,10 +672,10 @@ __global__ void assemble_f32_kernel(PwDev pw, int nE, const ChanFn *__restrict__
 
 template <int PB>
 __global__ void __launch_bounds__(f32d::NTH, 1) lu32_kernel(int n, const EnergyDims *__restrict__ dims, double *ws,
-                                                            int *status)
+                                                            int *status, const int *__restrict__ order)
 {
     extern __shared__ float4 fsm4[];
-    const int e = blockIdx.x;
+    const int e = order[blockIdx.x];
     const EnergyDims d = dims[e];
     if (d.np < 0) return;
     float *M = reinterpret_cast<float *>(slot_of(ws, n, e).aug);
@@ -684,10 +725,10 @@ __global__ void zbuild_kernel(int n, int nE, const EnergyDims *dims, double *ws)
 
 template <int PB>
 __global__ void __launch_bounds__(f32d::NTH, 1) zsweep_kernel(int n, const EnergyDims *__restrict__ dims, double *ws,
-                                                              int *status)
+                                                              int *status, const int *__restrict__ order)
 {
     extern __shared__ float4 fsm4[];
-    const int e = blockIdx.x;
+    const int e = order[blockIdx.x];
     const EnergyDims d = dims[e];
     if (d.np < 0) return;
     float2 *Z = reinterpret_cast<float2 *>(slot_of(ws, n, e).aug);
@@ -754,7 +795,7 @@ bool solve_large_f32_supported(int n) { return lu_pb(n) > 0 && z_pb(n) > 0; }
 size_t solve_large_bytes_per_energy(int n)
 {
     return slot_doubles(n) * sizeof(double) + sizeof(EnergyDims) + 4 * (size_t)n * sizeof(int) +
-           sizeof(LuJob) + sizeof(GemmJob) + 64;
+           sizeof(LuJob) + sizeof(GemmJob) + sizeof(int) + 64;
 }
 
 // Runs steps (c) and (d) for a block of nE energies. ws must hold
@@ -782,6 +823,9 @@ cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const C
     p += sizeof(LuJob) * nE;
     p = reinterpret_cast<char *>(((uintptr_t)p + 15) & ~(uintptr_t)15);
     GemmJob *gj = reinterpret_cast<GemmJob *>(p);
+    p += sizeof(GemmJob) * nE;
+    p = reinterpret_cast<char *>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    int *order = reinterpret_cast<int *>(p);
 
     const int eg = (nE + 127) / 128;
     int L = 0;
@@ -798,17 +842,19 @@ cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const C
     const int xb = (int)std::min<long long>(64, ((long long)n * 2 * n + NTH - 1) / NTH);
     const int xb2 = (int)std::min<long long>(64, ((long long)n * n + NTH - 1) / NTH);
     if (f32) {
+        order_kernel<<<1, 1024, (size_t)(n + 2) * sizeof(int), st>>>(n, nE, dims, order);
+        LAUNCH_OK();
         assemble_f32_kernel<<<dim3(xb, nE), NTH, 0, st>>>(pw, nE, cf, R, dims, col_chan, ws);
         LAUNCH_OK();
         const int pb = lu_pb(n);
         if (pb == 32) {
             const size_t sm = f32d::lu_smem<32>(n);
             if ((err = set_smem(lu32_kernel<32>, sm)) != cudaSuccess) return err;
-            lu32_kernel<32><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+            lu32_kernel<32><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status, order);
         } else {
             const size_t sm = f32d::lu_smem<16>(n);
             if ((err = set_smem(lu32_kernel<16>, sm)) != cudaSuccess) return err;
-            lu32_kernel<16><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+            lu32_kernel<16><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status, order);
         }
         LAUNCH_OK();
         prune_kernel<<<eg, 128, 0, st>>>(nE, status, dims);
@@ -848,11 +894,11 @@ cudaError_t launch_solve_large(const PwDev &pw, const double *E, int nE, const C
         if (pb == 16) {
             const size_t sm = f32d::z_smem<16>(n);
             if ((err = set_smem(zsweep_kernel<16>, sm)) != cudaSuccess) return err;
-            zsweep_kernel<16><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+            zsweep_kernel<16><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status, order);
         } else {
             const size_t sm = f32d::z_smem<8>(n);
             if ((err = set_smem(zsweep_kernel<8>, sm)) != cudaSuccess) return err;
-            zsweep_kernel<8><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status);
+            zsweep_kernel<8><<<nE, f32d::NTH, sm, st>>>(n, dims, ws, status, order);
         }
         LAUNCH_OK();
         prune_kernel<<<eg, 128, 0, st>>>(nE, status, dims);
