@@ -913,16 +913,16 @@ def run_ours(args, rank, world, local_rank):
         fp32_peak = N_SM * 256.0 * sm_mhz * 1e6 / 1e12
         ach = fl32 / t_solve / 1e12
         # DRAM bytes per launch from one ncu capture of this kernel on 2000
-        # energies of the same workload (58.19 MB read, 2.30 MB written),
-        # scaled to the launch's energies
-        traffic = (58.19e6 + 2.30e6) * (E.size / 2000.0) if n == 64 else None
+        # energies of the same workload (58.20 MB read, 6 KB written: Omega
+        # stays in L2 at that size), scaled to the launch's energies
+        traffic = (58.20e6 + 0.006e6) * (E.size / 2000.0) if n == 64 else None
         solve_roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                       "frac": ach / fp32_peak, "traffic": traffic,
                       "kernel": "solve_f32_kernel (FP32 Gauss-Jordan, FP32 complex T sweep, register tiles)",
                       "peak_source": "FP32 128 FMA/clk/SM x 152 SMs at the sampled SM clock",
                       "note": "one CTA per energy, four per SM; pivots in blocks factored by one warp "
                               "(n/4 + n_o/2 barrier pairs); ncu: barrier stalls (the block's serial pivot "
-                              "chain) dominate, FMA pipe 23% busy, issue 58% (bound by the pivot chain's "
+                              "chain) dominate, FMA pipe 22% busy, issue 52% (bound by the pivot chain's "
                               "latency and the energies resident per SM, not by a pipe)"}
     else:
         ach = fl64 / t_solve / 1e12
