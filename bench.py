@@ -82,20 +82,26 @@ def oracle_throughput(pool, n_cores, per_core):
 # clocks
 
 class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 20 ms, each sample stamped
+    with the host clock, so that stop() can keep the samples taken inside a
+    timed window (window(t0, t1)); the window's neighbours are used only when
+    the window is shorter than the sampling interval."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 20
 
     def __init__(self, gpu_id):
         self.gpu_id = gpu_id
         self.proc = None
         self.lines = []
+        self.win = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -104,7 +110,16 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout=3.0):
+        """Waits until nvidia-smi has printed its first sample."""
+        t0 = time.perf_counter()
+        while self.proc is not None and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def window(self, t0, t1):
+        self.win = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -115,9 +130,20 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.t.join(timeout=2)
+        lines = self.lines
+        in_window = None
+        if self.win is not None:
+            t0, t1 = self.win
+            inside = [x for x in lines if t0 <= x[0] <= t1]
+            in_window = len(inside)
+            if not inside:   # window shorter than the interval: the samples next to it
+                before = [x for x in lines if x[0] < t0][-1:]
+                after = [x for x in lines if x[0] > t1][:1]
+                inside = before + after
+            lines = inside
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             p = [x.strip() for x in ln.split(",")]
             if len(p) < 8:
                 continue
@@ -131,7 +157,8 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "samples_in_timed_region": in_window,
+                "interval_ms": self.INTERVAL_MS}
 
 
 # --------------------------------------------------------------------------
@@ -794,8 +821,10 @@ def run_ours(args, rank, world, local_rank):
         props = torch.cuda.get_device_properties(dev)
         clk = ClockSampler("GPU-%s" % props.uuid if getattr(props, "uuid", None) else local_rank)
         clk.start()
-        time.sleep(0.3)
+        clk.wait_first()
+        tw0 = time.perf_counter()
         t_step, phase, launches = _time_steps(ctx, Ed, stream, flush, args.steps, rmgb, torch)
+        clk.window(tw0, time.perf_counter())
         clocks = clk.stop()
         t_step = max_over_ranks(t_step)
         value = world * E.size / (t_step * 1e-3)
