@@ -201,7 +201,7 @@ def test_mixed_k_and_omega_bounds(rt, name, prec, form, sp):
     assert np.median(eK) <= K_MED, np.median(eK)
 
 
-@pytest.mark.parametrize("wl", ["small", "64ch", "80ch", "30ch"])
+@pytest.mark.parametrize("wl", ["small", "64ch", "80ch", "30ch", "96ch", "97ch"])
 def test_fp32_solve_alone_within_bound(rt, wl):
     """FP64 formation with the FP32 solve (matching elimination and complex
     T step) against the oracle: K within the elimination's propagated
@@ -218,8 +218,10 @@ def test_fp32_solve_alone_within_bound(rt, wl):
         pw = pws[0]
         Es = _energies(pw, E, 120, 8)
     else:
-        # 80 (30) channels: the 6 x 12 (2 x 4) register tiles
-        nch = 80 if wl == "80ch" else 30
+        # 80 (30) channels: the 6 x 12 (2 x 4) register tiles; 96 channels
+        # fill the 6 x 12 tiles (the shared-memory solver's largest size),
+        # 97 take the global-memory FP32 solver under the automatic choice
+        nch = int(wl[:-2])
         pw = synth.random_pw(4800 + nch, nch, 30 * nch, z=2.0, a=15.0, e_max=2.0, sigma=0.05,
                              pole_lo=-2.0, pole_hi=60.0, l_max=8)
         Es = synth.midpoint_grid(0.01, 2.5, 4000)[::31]
