@@ -21,6 +21,8 @@
 // energy, blocked LU with partial pivoting; blocked sweep of the complex
 // symmetric 1 - iK), while the MQDT elimination, K and Omega stay FP64:
 //
+//   order         the energies by decreasing n_p: the LU's and the sweep's
+//                 CTAs take them in that order (longest first)
 //   assemble_f32  [A | 0 | B] in FP32 (right-hand sides from a 4-aligned column)
 //   lu32          X = A^{-1} B for the P rows
 //   extract_f32   K_u (FP64) = X[P rows]; direct mode: K = K_u
