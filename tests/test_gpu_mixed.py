@@ -274,3 +274,39 @@ def test_mixed_matches_fp64_path_statuses_and_layout(rt, form):
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     d = np.linalg.norm(outs[0][2] - outs[1][2], axis=1) / np.maximum(np.linalg.norm(outs[0][2], axis=1), 1e-300)
     assert d.max() < OM_MAX
+
+
+@pytest.mark.parametrize("solver", ["auto", "large"])
+def test_neutral_target_mixed_within_bound(rt, solver):
+    """Neutral target (z = 0: Riccati-Bessel open channels, modified spherical
+    Bessel closed ones) through the mixed path, bf16x3 formation and the FP32
+    solve of either solver: K within the first-order propagation of the R
+    bound plus the FP32 elimination's backward error, Omega within the bound
+    with the T step's term."""
+    torch, rmgb = rt
+    sv = rmgb.RM_SOLVER_AUTO if solver == "auto" else rmgb.RM_SOLVER_LARGE
+    pw = synth.random_pw(90, 6, 120, z=0.0, a=12.0, e_max=1.2, l_max=4)
+    E = synth.midpoint_grid(0.01, 1.6, 300)
+    n = pw["W"].shape[0]
+    with rmgb.Context(precision=rmgb.RM_BF16X3, solver=sv, solve_precision=rmgb.RM_FP32) as ctx:
+        ctx.load_pw(0, pw)
+        K = torch.zeros((E.size, n * n), dtype=torch.float64, device="cuda")
+        no = torch.zeros(E.size, dtype=torch.int32, device="cuda")
+        st = torch.zeros(E.size, dtype=torch.int32, device="cuda")
+        ctx.solve_energies(0, torch.tensor(E, device="cuda"), 0, K, no, st)
+        om = ctx.collision_strengths()
+    K = K.cpu().numpy().reshape(E.size, n, n)
+    st = st.cpu().numpy()
+    ref = oracle.solve_energies(pw, E)
+    assert np.array_equal(st, ref["status"])
+    assert np.array_equal(no.cpu().numpy(), ref["n_open"])
+    assert (st == 0).all()
+    for m in range(E.size):
+        Ko = ref["K"][m]
+        k = Ko.shape[0]
+        bK = _first_order_k_bound(pw, E[m], U32)
+        dK = np.abs(K[m, :k, :k] - Ko)
+        assert np.all(dK <= 3.0 * bK + 1e-12 * max(1.0, np.abs(Ko).max())), E[m]
+        B = 3.0 * np.linalg.norm(bK) + k * U32 * np.linalg.norm(np.eye(k) - 1j * Ko)
+        dOm = np.abs(om[m] - ref["omega"][m]).sum()
+        assert dOm <= pw["g"] * (8 * k * B + 4 * B * B) + 1e-12, E[m]
