@@ -120,3 +120,38 @@ def test_qdt_rejects_bad_input(rt):
             ctx.solve_energies_qdt(0, np.array([0.4, 0.5]), 0)
         with pytest.raises(rmgb.RmError):
             ctx.solve_energies_qdt(0, np.array([0.4, 0.5]), -2, 0.0, 3)
+
+
+@pytest.mark.parametrize("iqdt", [1, 2])
+def test_qdt_on_propagated_wave_matches_oracle(rt, iqdt):
+    """The coarse-mesh interpolation on a wave that carries the outer-region
+    propagation (rm_set_multipoles: R carried from a to r1 by Numerov, the
+    matching and the kappa r cap of the eliminated set at r1) against
+    oracle/qdt.py on the same wave (R propagated by DOP853): with a = 10,
+    r1 = 13 and 4000 steps Numerov's O(h^4) error is ~1e-13 of R, so Omega
+    agrees to the FP64 tolerance, statuses and open counts exactly."""
+    torch, rmgb = rt
+    pw = _pw4()
+    rng = np.random.default_rng(4713)
+    A = rng.normal(0.0, 0.3, (2, 4, 4))
+    A = 0.5 * (A + A.transpose(0, 2, 1))
+    r1, steps = 13.0, 4000
+    E = synth.midpoint_grid(0.3, 2.4, 160)
+    E = E[np.abs(E[:, None] - pw["e_thr"][None, :]).min(axis=1) > 5e-3]
+    with rmgb.Context() as ctx:
+        ctx.load_pw(0, pw)
+        ctx.set_multipoles(0, A, r1, steps)
+        st = torch.zeros(E.size, dtype=torch.int32, device="cuda")
+        no = torch.zeros(E.size, dtype=torch.int32, device="cuda")
+        ctx.solve_energies_qdt(0, E, -6, 0.0, iqdt, no, st)
+        om = ctx.collision_strengths()
+        st, no = st.cpu().numpy(), no.cpu().numpy()
+    pwp = dict(pw)
+    pwp["prop"] = (A, r1)
+    ref = qdt.solve_energies(pwp, E, ieq=-6, qetest=0.0, iqdt=iqdt)
+    assert np.array_equal(st, ref["status"]), np.nonzero(st != ref["status"])[0][:10]
+    assert np.array_equal(no, ref["n_open"])
+    n_elim = sum(int(np.sum(c == qdt.CL_ELIM)) for _, _, c in ref["plan"]["segments"])
+    assert n_elim > 0 and (st == 0).sum() > 100
+    bad = [m for m in range(E.size) if st[m] == 0 and not _close(om[m], ref["omega"][m], TOL)]
+    assert not bad, bad[:10]
