@@ -510,3 +510,109 @@ def test_many_channel_invariants():
         np.testing.assert_allclose(m["K"][k], d["K"][k], rtol=0, atol=1e-12 * np.abs(d["K"][k]).max())
         np.testing.assert_allclose(m["omega"][k], d["omega"][k], rtol=0,
                                    atol=1e-12 * np.abs(d["omega"][k]).max())
+
+
+def _grouped_wave(seed=2027):
+    """8 channels in two groups, the even and the odd channels (thresholds
+    interleaved), each group coupled only to its own 30 poles."""
+    rng = np.random.default_rng(seed)
+    n, N = 8, 60
+    e_thr = np.linspace(0.0, 1.4, n)
+    l = rng.integers(0, 5, n).astype(np.int32)
+    E_k = np.sort(rng.uniform(-1.0, 30.0, N))
+    pole_group = rng.permutation(np.arange(N) % 2)
+    W = rng.normal(0.0, 0.1, (n, N))
+    W[(np.arange(n)[:, None] % 2) != pole_group[None, :]] = 0.0
+    pw = dict(E_k=E_k, W=W, a=15.0, b=0.0, e_thr=e_thr, l=l, z=2.0,
+              level=np.arange(n, dtype=np.int32), n_levels=n, g=1.0)
+    return pw, pole_group
+
+
+def _energies_off_thresholds(e_thr, lo, hi, m):
+    E = synth.midpoint_grid(lo, hi, m)
+    return E[np.abs(E[:, None] - np.asarray(e_thr)[None, :]).min(axis=1) > 1e-3]
+
+
+@pytest.mark.parametrize("mode", [oracle.MODE_DIRECT, oracle.MODE_MQDT])
+def test_decoupled_channel_groups(mode):
+    """Channels that share no poles with another group do not couple to it:
+    R is block-diagonal, so K (over the open channels) is block-diagonal and
+    each block, and each group's collision strengths, equal those of the
+    group solved alone as its own partial wave (its channels and poles). The
+    groups interleave in channel order, so an open-position, channel-order or
+    level-pair index mixed up anywhere breaks the equality."""
+    pw, pole_group = _grouped_wave()
+    E = _energies_off_thresholds(pw["e_thr"], 0.05, 1.9, 40)
+    full = oracle.solve_energies(pw, E, mode=mode)
+    n = pw["W"].shape[0]
+    subs = []
+    for gidx in (0, 1):
+        ch = np.arange(n)[np.arange(n) % 2 == gidx]
+        pk = np.nonzero(pole_group == gidx)[0]
+        sub = dict(pw, E_k=pw["E_k"][pk], W=pw["W"][np.ix_(ch, pk)], e_thr=pw["e_thr"][ch], l=pw["l"][ch],
+                   level=np.arange(ch.size, dtype=np.int32), n_levels=ch.size)
+        subs.append((ch, oracle.solve_energies(sub, E, mode=mode)))
+    checked = 0
+    for m in range(E.size):
+        if full["status"][m]:
+            continue
+        K = full["K"][m]
+        oi = np.nonzero(E[m] > pw["e_thr"])[0]
+        assert K.shape == (oi.size, oi.size)
+        pos = {c: i for i, c in enumerate(oi)}
+        for ch, res in subs:
+            assert res["status"][m] == 0
+            oc = [pos[c] for c in ch if c in pos]
+            other = [pos[c] for c in oi if c not in ch]
+            if oc:
+                np.testing.assert_allclose(K[np.ix_(oc, oc)], res["K"][m], rtol=0,
+                                           atol=1e-12 * max(1.0, np.abs(res["K"][m]).max()))
+            if oc and other:
+                assert np.all(K[np.ix_(oc, other)] == 0.0)
+            for I, cI in enumerate(ch):
+                for J, cJ in enumerate(ch):
+                    if I <= J:
+                        a = full["omega"][m][oracle.tri_index(cI, cJ, n)]
+                        b = res["omega"][m][oracle.tri_index(I, J, ch.size)]
+                        assert abs(a - b) <= 1e-12 * max(1.0, abs(b)), (m, cI, cJ)
+        ev, od = np.arange(0, n, 2), np.arange(1, n, 2)
+        for cI in ev:
+            for cJ in od:
+                assert full["omega"][m][oracle.tri_index(min(cI, cJ), max(cI, cJ), n)] == 0.0
+        checked += 1
+    assert checked > 30
+
+
+def test_channel_relabelling():
+    """Relabelling the channels (thresholds, l, levels and the rows of W
+    permuted together) permutes K over the open channels the same way and
+    moves each collision strength to the relabelled level pair: nothing in
+    the method depends on the order the channels are listed in."""
+    pw = synth.random_pw(2029, 7, 140, z=1.0, a=18.0, e_max=1.5, sigma=0.1, l_max=4)
+    rng = np.random.default_rng(2030)
+    perm = rng.permutation(7)           # new channel i is old channel perm[i]
+    inv = np.argsort(perm)
+    pp = dict(pw, e_thr=pw["e_thr"][perm], l=pw["l"][perm], W=pw["W"][perm],
+              level=inv[pw["level"]][perm].astype(np.int32))
+    E = _energies_off_thresholds(pw["e_thr"], 0.05, 1.8, 30)
+    a = oracle.solve_energies(pw, E)
+    b = oracle.solve_energies(pp, E)
+    assert np.array_equal(a["status"], b["status"]) and np.array_equal(a["n_open"], b["n_open"])
+    nl = pw["n_levels"]
+    checked = 0
+    for m in range(E.size):
+        if a["status"][m]:
+            continue
+        oi_a = np.nonzero(E[m] > pw["e_thr"])[0]          # old labels, ascending
+        oi_b = np.nonzero(E[m] > pp["e_thr"])[0]          # new labels, ascending
+        sel = [int(np.nonzero(oi_a == perm[c])[0][0]) for c in oi_b]
+        np.testing.assert_allclose(b["K"][m], a["K"][m][np.ix_(sel, sel)], rtol=0,
+                                   atol=1e-12 * max(1.0, np.abs(a["K"][m]).max()))
+        for I in range(nl):
+            for J in range(I, nl):
+                nI, nJ = sorted((int(inv[I]), int(inv[J])))
+                x = a["omega"][m][oracle.tri_index(I, J, nl)]
+                y = b["omega"][m][oracle.tri_index(nI, nJ, nl)]
+                assert abs(x - y) <= 1e-12 * max(1.0, abs(x)), (m, I, J)
+        checked += 1
+    assert checked > 20
