@@ -41,6 +41,11 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
                         and b each fail one); round trip a -> r1 -> a; an
                         independent RK4 converges to it at fourth order;
                         sector lengths do not change K
+  many-channel          tests/test_oracle_pins.py: interleaved channel groups
+  structure             that share no poles give a block-diagonal K whose
+                        blocks and collision strengths equal each group
+                        solved alone (direct and MQDT); relabelling the
+                        channels permutes K and the level pairs of Omega
   cross-threshold K, Omega beyond these checks: parity unpinned (the paper
                         prints no K or Omega values for any system).
 """
